@@ -1,0 +1,79 @@
+"""Pins for the oracle's Algorithm 3 (lagged-diffusivity fixed point around MLSQR)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _dense(apply, shape):
+    n = int(np.prod(shape))
+    return np.stack([np.asarray(apply(np.eye(n)[i].reshape(shape))).ravel() for i in range(n)], 1)
+
+
+def _fd(n):
+    return np.eye(n, k=1) - np.eye(n)
+
+
+def test_tikhonov_full_solve_is_direct_normal_equation_solve():
+    """r = t^2/2 gives kappa = 1 and the linear problem (1.7)-(1.8): with an exact M^{-1}
+    and enough inner iterations every outer step returns (A^T A + tau D^T D)^{-1} A^T g."""
+    shape = (8, 10)
+    rng = np.random.default_rng(21)
+    op = O.Operator("blur", shape, sigma=(1.0, 1.4), radius=(3, 4))
+    g = op.A(rng.uniform(0, 1, shape)) + 0.01 * rng.standard_normal(shape)
+    tau = 0.05
+    out = O.solve(op, g, "tikhonov", 1.0, tau, n_outer=2, n_inner=200, levels=1)
+    Dx = np.kron(np.eye(8), _fd(10))
+    Dy = np.kron(_fd(8), np.eye(10))
+    A = _dense(op.A, shape)
+    fd = np.linalg.solve(A.T @ A + tau * (Dx.T @ Dx + Dy.T @ Dy), A.T @ g.ravel())
+    assert np.linalg.norm(out["f"].ravel() - fd) <= 1e-9 * np.linalg.norm(fd)
+    assert out["R_hist"][0] == 0.0
+    assert out["R_hist"][-1] == pytest.approx(0.5 * ((Dx @ fd) ** 2 + (Dy @ fd) ** 2).sum(), rel=1e-8)
+    assert out["resid_hist"][-1] == pytest.approx(np.linalg.norm(g.ravel() - A @ fd), rel=1e-8)
+
+
+def test_outer_steps_restart_and_record():
+    shape = (16, 16)
+    rng = np.random.default_rng(22)
+    op = O.Operator("blur", shape, sigma=(1.5, 1.5), radius=(4, 4))
+    f0 = np.zeros(shape)
+    f0[4:12, 3:9] = 1.0
+    g = op.A(f0) + 0.01 * rng.standard_normal(shape)
+    out = O.solve(op, g, "tv", 0.05, 0.0, n_outer=4, n_inner=6, levels=3)
+    assert out["status"] == 0
+    # f^0 = 0: R(0) = N T for smoothed TV
+    assert out["R_hist"][0] == pytest.approx(256 * 0.05)
+    # the inner solve restarts from f = 0 (Sec. 4.3): each step's first residual estimate
+    # is below ||g|| and the run of one outer step reproduces the first row
+    one = O.solve(op, g, "tv", 0.05, 0.0, n_outer=1, n_inner=6, levels=3)
+    assert np.array_equal(one["rbar_hist"][0], out["rbar_hist"][0])
+    for k in range(4):
+        assert out["rbar_hist"][k][0] < np.linalg.norm(g)
+        # tau = 0: ||rbar_i|| is the true residual, non-increasing within a step
+        assert np.all(np.diff(out["rbar_hist"][k]) <= 1e-12)
+    # tau = 0: the last estimate of each step equals ||g - A f^k||
+    assert out["rbar_hist"][-1][-1] == pytest.approx(out["resid_hist"][-1], rel=1e-8)
+
+
+def test_lagged_diffusivity_fixed_point():
+    """With an exact M^{-1}, tau > 0 and converged inner solves, Algorithm 3 is lagged
+    diffusivity (Sec. 4.1): f^k approaches a solution of (4.1), (A^T A + tau M_f) f = A^T g."""
+    shape = (12, 12)
+    rng = np.random.default_rng(23)
+    op = O.Operator("blur", shape, sigma=(1.2, 1.2), radius=(3, 3))
+    f0 = np.zeros(shape)
+    f0[3:9, 4:10] = 1.0
+    g = op.A(f0) + 0.01 * rng.standard_normal(shape)
+    tau, T = 2e-3, 0.1
+    A = _dense(op.A, shape)
+
+    def grad_residual(f):
+        kappa, _ = O.diffusivity(f, "tv", T, kfloor=1e-4)
+        return np.linalg.norm(A.T @ (A @ f.ravel() - g.ravel()) + tau * O.apply_M(kappa, f).ravel())
+
+    res = [grad_residual(O.solve(op, g, "tv", T, tau, n_outer=k, n_inner=300, levels=1)["f"])
+           for k in (1, 4, 30)]
+    scale = np.linalg.norm(A.T @ g.ravel())
+    assert res[2] < res[1] < res[0]
+    assert res[2] < 1e-6 * scale
