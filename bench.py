@@ -1,0 +1,372 @@
+"""Benchmark: solves/s of the priorconditioned lagged-diffusivity solver on one workload.
+
+One step = one batch of B complete solves (Algorithm 3: n_outer lagged-diffusivity steps,
+each with n_inner MLSQR iterations and a fresh V-cycle priorconditioner) of the 1024x1024
+FP32 deblurring workload (Gaussian blur sigma 4 truncated at radius 12, 1% noise,
+Perona-Malik log regulariser T = 5e-2, tau = 1e-3, 15 x 50 iterations, 6-level V-cycle with
+2 red-black sweeps per side), inputs resident in device memory.  Multi-GPU runs are replicas
+(independent instances per rank, no collective on the data path; weak scaling).
+
+JSON line keys beyond the base contract: p50_ms/p99_ms (per-step latency), roofline of the
+dominant kernel class (eager profiling pass with CUDA events on the launch stream),
+cpu_baseline (the FP64 CPU oracle on a bounded sample, extrapolated), e2e (host buffers, copies
+inside the timed region), clocks (nvidia-smi sampled during the timed region), accuracy (the
+first MLSQR residual estimates against the oracle's).
+
+--impl reference times the FP64 CPU oracle itself on the same workload and metric.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 126 * 1024 * 1024
+METRIC = "solves/s and p50/p99 ms at <=1e-4 rel err vs FP64 oracle; HBM GB/s vs peak"
+
+# Algorithmic bytes per instance and per launch of each kernel class, in units of
+# (vector element size x N): the minimum reads and writes each pass forces.
+#   fwd:     v~ in, u_prev in, u out                         3
+#   adj:     u in, p~ in, p~ out                             3
+#   gs_fine: x of the other colour in (1/2), kappa in (1), b of this colour in (1/2),
+#            x of this colour out (1/2)                      2.5
+ALG_UNITS = {"fwd": 3.0, "adj": 3.0, "gs_fine": 2.5}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--workload", default="deblur1024_fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1308_6634_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kclass, workload):
+    """DRAM bytes per launch of a kernel class from profiles/traffic.txt, when that capture
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    with open(p) as fh:
+        for ln in fh:
+            parts = ln.split()
+            if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kclass and parts[1] == workload \
+                    and parts[3] == cur:
+                return float(parts[2])
+    return None
+
+
+def make_inputs(W, S, seeds, torch, dev):
+    """Device g for each seed: A f_true through the library's own forward map, plus noise."""
+    from paper_1308_6634_gb300 import synth
+    gs = []
+    for seed in seeds:
+        f, mask, z = W.inputs(seed)
+        Af = S.apply_A(torch.as_tensor(f, dtype=S.dtype, device=dev))
+        sig = W.noise * float(torch.linalg.vector_norm(Af.double())) / np.sqrt(Af.numel())
+        g = (Af.double() + sig * torch.as_tensor(z, device=dev)).to(S.dtype).contiguous()
+        gs.append(g)
+    return gs
+
+
+def cpu_baseline(W, budget_s=20.0):
+    """The FP64 CPU oracle on a bounded sample: one outer step with i1 and i2 inner
+    iterations; the difference gives the cost of one iteration, the rest the per-outer-step
+    cost (diffusivity, hierarchy, coarse factorisation, initialisation); both extrapolated
+    to the full n_outer x n_inner solve."""
+    import oracle as O
+    from paper_1308_6634_gb300 import synth
+    f, mask, z = W.inputs(0)
+    op = O.Operator(W.kind, W.shape, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
+                    n_bins=W.n_bins)
+    g = synth.add_noise(op.A(f), W.noise, z)
+    i1, i2 = 2, 6
+    t0 = time.perf_counter()
+    r1 = O.solve(op, g, W.reg, W.T, W.tau, 1, i1, W.levels, W.nu, W.cycles)
+    t1 = time.perf_counter()
+    r2 = O.solve(op, g, W.reg, W.T, W.tau, 1, i2, W.levels, W.nu, W.cycles)
+    t2 = time.perf_counter()
+    per_iter = max((t2 - t1) - (t1 - t0), 1e-9) / (i2 - i1)
+    per_outer = max((t1 - t0) - i1 * per_iter, 0.0)
+    t_solve = W.n_outer * (per_outer + W.n_inner * per_iter)
+    return dict(value=1.0 / t_solve, t_solve=t_solve, per_iter=per_iter, per_outer=per_outer,
+                sample_s=t2 - t0, rbar=r2["rbar_hist"][0], sample=f"oracle: 1 outer step x {i1} and x {i2} inner "
+                f"iterations on seed 0 ({t2 - t0:.1f} s), extrapolated to {W.n_outer} x {W.n_inner}")
+
+
+def run_reference(args, W):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    vals = []
+    t0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        info = cpu_baseline(W)
+        vals.append(info["t_solve"])
+    wall = time.perf_counter() - t0
+    t_solve = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": 1.0 / t_solve, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W.name, "shape": list(W.shape), "n_outer": W.n_outer, "n_inner": W.n_inner,
+                   "batch": 1, "parallelism": "replicas"},
+        "cpu_baseline": {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": info["sample"]},
+        "e2e": {"value": 1.0 / t_solve, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    from paper_1308_6634_gb300 import synth
+    W = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, W)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1308_6634_gb300 import plsqr
+    B = args.batch
+    S = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles, max_batch=B)
+    S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, n_angles=W.n_angles, n_bins=W.n_bins)
+    seeds = [rank * B + b for b in range(B)]
+    gs = make_inputs(W, S, seeds, torch, dev)
+    fs = [torch.empty(W.shape, dtype=S.dtype, device=dev) for _ in range(B)]
+    regs, Ts, taus = [W.reg] * B, [W.T] * B, [W.tau] * B
+
+    def step(stats=False):
+        if B == 1:
+            return S.solve(gs[0], W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=fs[0], stats=stats)
+        return S.solve_batch(gs, regs, Ts, taus, W.n_outer, W.n_inner, f_outs=fs, stats=stats)
+
+    esz = 4 if W.precision == "fp32" else 8
+    working_set = B * W.shape[0] * W.shape[1] * (W.shape[2] if len(W.shape) > 2 else 1) * esz * 10
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if working_set < L2_BYTES else None
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    _, info = step(stats=True)
+    launches_per_step = S.last_launches()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            starts[k].record()
+            step()
+            ends[k].record()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    per_step = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    total_ms = float(per_step.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer API: H2D of g, solve, D2H of f inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin_g = [torch.empty(g.shape, dtype=g.dtype, pin_memory=True) for g in gs]
+        for pg, g in zip(pin_g, gs):
+            pg.copy_(g)
+        pin_f = [torch.empty(W.shape, dtype=S.dtype, pin_memory=True) for _ in range(B)]
+        e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(e_steps):
+            if B == 1:
+                S.solve_host(pin_g[0].numpy(), W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=pin_f[0].numpy())
+            else:
+                dg = [pg.to(dev, non_blocking=True) for pg in pin_g]
+                S.solve_batch(dg, regs, Ts, taus, W.n_outer, W.n_inner, f_outs=fs, stats=False)
+                for pf, f in zip(pin_f, fs):
+                    pf.copy_(f, non_blocking=True)
+                torch.cuda.synchronize()
+        t1.record()
+        torch.cuda.synchronize()
+        e_ms = t0.elapsed_time(t1)
+        e2e = {"value": world * B * e_steps / (e_ms / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(B * gs[0].numel() * esz), "d2h_bytes_per_step": int(B * W_N(W) * esz)}
+
+    # roofline of the dominant kernel class: eager profiling pass, CUDA events on the launch stream
+    roofline = None
+    if not args.no_profile:
+        S.profile(True)
+        step()
+        torch.cuda.synchronize()
+        prof = S.profile_read()
+        S.profile(False)
+        cand = {k: v for k, v in prof.items() if k in ALG_UNITS and v[1] > 0}
+        top = max(prof.items(), key=lambda kv: kv[1][0])[0]
+        dom = max(cand.items(), key=lambda kv: kv[1][0])[0] if cand else None
+        peak, src = measured_peaks()
+        if dom is not None:
+            ms, cnt = prof[dom]
+            bytes_per_launch = ALG_UNITS[dom] * esz * W_N(W) * B
+            achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
+            total_prof = sum(v[0] for v in prof.values())
+            roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                        "traffic": ncu_traffic(dom, W.name), "alg_bytes_per_launch": bytes_per_launch,
+                        "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
+                        "share_of_eager_device_time": ms / total_prof, "largest_class": top,
+                        "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(W)
+        cpu = {"value": cb["value"], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+        ref = cb["rbar"]
+        got = info[0]["rbar_hist"][0][: len(ref)] if isinstance(info, list) else info["rbar_hist"][0][: len(ref)]
+        acc = {"rbar_first_iters_rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+               "iters_compared": int(len(ref)),
+               "note": "long-horizon parity is tested against the oracle's rounding envelope (tests/)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if W.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": W.name, "shape": list(W.shape), "n_outer": W.n_outer, "n_inner": W.n_inner,
+                       "reg": W.reg, "T": W.T, "tau": W.tau, "levels": W.levels, "sweeps": W.nu,
+                       "batch": B, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps" if flush is not None else "working set larger than L2"},
+            "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
+            "gpu_launches": int(launches_per_step * args.steps),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "accuracy": acc,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def W_N(W):
+    return int(np.prod(W.shape))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

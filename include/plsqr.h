@@ -1,0 +1,192 @@
+/*
+ * plsqr.h -- C ABI of libplsqr, a GB300 (sm_103a) implementation of the inner solve of
+ * Arridge, Betcke & Harhanen's priorconditioned lagged-diffusivity method (arXiv 1308.6634):
+ * the factorization-free priorconditioned LSQR iteration MLSQR (Algorithm 2) run inside each
+ * step of the lagged-diffusivity fixed point (Algorithm 3) for
+ *
+ *      min_f  1/2 ||g - A f||^2 + tau R(f),     R(f) = sum_i r(|grad f|_i)       (eq. 1.6)
+ *
+ * with r one of (1.3)-(1.5).  The priorconditioner is a fixed symmetric geometric-multigrid
+ * V-cycle P approximating M_f^{-1}, M_f = sum_d D_d^T diag(kappa) D_d (eq. 1.13, Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are dense, C order, x fastest: an image is [ny][nx], a volume [nz][ny][nx], a
+ *    sinogram [n_angles][n_bins].  Element type is double for a PLSQR_FP64 handle and float
+ *    for a PLSQR_FP32 handle; scalars of the Krylov recurrences are always double.
+ *  - "device" pointers point to memory on the handle's device (cudaMalloc, or a PyTorch
+ *    tensor's storage); "host" pointers to ordinary or pinned host memory.  The caller owns
+ *    all of them; the library never frees or keeps a caller pointer after a call returns,
+ *    except the operator mask, which set_operator copies.
+ *  - All device work is enqueued on the stream given to plsqr_create (NULL = legacy default
+ *    stream).  Entry points that return host results (histories, R) synchronise that stream.
+ *  - Every call returns a plsqr_status and never aborts; on error plsqr_last_error(h)
+ *    returns a message.  Handles are not thread safe: use one per host thread.
+ *  - Numerical breakdown (a Golub-Kahan norm that is zero, tiny or not finite) stops that
+ *    inner solve with the last complete iterate kept; the solve continues with the next
+ *    outer step and finally returns PLSQR_E_BREAKDOWN.
+ */
+#ifndef PLSQR_H
+#define PLSQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plsqr_ctx* plsqr_handle;
+
+typedef enum {
+    PLSQR_OK = 0,
+    PLSQR_E_INVALID = 1,   /* bad argument or size */
+    PLSQR_E_NOMEM = 2,     /* device allocation failed */
+    PLSQR_E_CUDA = 3,      /* a CUDA call failed */
+    PLSQR_E_BREAKDOWN = 4, /* Golub-Kahan breakdown in some inner solve */
+    PLSQR_E_TIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    PLSQR_E_STATE = 6      /* call out of order (e.g. solve before set_operator) */
+} plsqr_status;
+
+/* r(t) of eqs. (1.3)-(1.5); kappa(t) = r'(t)/t is the diffusivity of (1.13). */
+typedef enum {
+    PLSQR_R_TIKHONOV = 0, /* r = t^2/2                          kappa = 1               (1.3) */
+    PLSQR_R_TV = 1,       /* r = T sqrt(1+(t/T)^2)              kappa = 1/sqrt(T^2+t^2) (1.4) */
+    PLSQR_R_PM_LOG = 2,   /* r = T^2/2 log(1+(t/T)^2)           kappa = 1/(1+(t/T)^2)   (1.5) */
+    PLSQR_R_PM_EXP = 3    /* r = T^2/2 (1-exp(-t^2/T^2))        kappa = exp(-t^2/T^2)   (1.5) */
+} plsqr_reg;
+
+typedef enum {
+    PLSQR_OP_BLUR = 0,      /* separable Gaussian blur B, zero boundary; A = A^T = B          */
+    PLSQR_OP_BLUR_MASK = 1, /* inpainting: A = D B, A^T = B D, D = diag(mask)                 */
+    PLSQR_OP_JOSEPH = 2,    /* 2D parallel-beam Joseph projector, gather-form exact adjoint  */
+    PLSQR_OP_IDENTITY = 3   /* A = I (denoising)                                             */
+} plsqr_op_kind;
+
+typedef enum { PLSQR_FP64 = 0, PLSQR_FP32 = 1 } plsqr_precision;
+
+/* Problem size and priorconditioner shape. */
+typedef struct {
+    int32_t ndim;        /* 2 or 3 */
+    int32_t precision;   /* plsqr_precision of the bulk vectors and stencils */
+    int64_t n[3];        /* nx, ny, nz (nz ignored for ndim 2); each n[d] divisible by
+                            2^(mg_levels-1) (cell-centred coarsening, Sec. 4.2) */
+    int32_t mg_levels;   /* V-cycle levels including the finest (>= 1; 1 = exact M^{-1}) */
+    int32_t mg_sweeps;   /* nu: red-black Gauss-Seidel sweeps before and after the coarse
+                            correction (mirrored order keeps P symmetric, Sec. 4.2) */
+    int32_t mg_cycles;   /* V-cycles per application of P (x <- x + V(b - M x)) */
+    int32_t max_batch;   /* instances per batched solve (>= 1) */
+    double kappa_floor;  /* kappa >= kappa_floor * kappa(0); 0 disables the floor */
+} plsqr_config;
+
+/* Forward map A (Sec. 1: matrix-free A, given by its action on a vector). */
+typedef struct {
+    int32_t kind;          /* plsqr_op_kind */
+    int32_t n_angles;      /* Joseph: angles a*pi/n_angles, a = 0..n_angles-1 */
+    int32_t n_bins;        /* Joseph: detector bins at (k-(n_bins-1)/2)*bin_spacing */
+    int32_t reserved;
+    double sigma[3];       /* blur: Gaussian widths along x, y, z in cells */
+    int32_t radius[3];     /* blur: truncation radii (taps -R..R), normalised to unit sum */
+    int32_t reserved2;
+    double bin_spacing;    /* Joseph: detector spacing in pixel units (> 0) */
+    const uint8_t* mask;   /* BLUR_MASK: device pointer to N bytes, nonzero = observed;
+                              shared by every instance of a batch; copied by set_operator */
+} plsqr_operator;
+
+/* Optional per-solve outputs (host arrays, caller owned; NULL members are skipped). */
+typedef struct {
+    double* rbar_hist;     /* [n_outer][n_inner]: ||rbar_i||, the LSQR estimate of the
+                              residual norm of the damped problem (Sec. 3.4) */
+    double* R_hist;        /* [n_outer + 1]: R(f^0) .. R(f^n_outer) (Algorithm 3 step 5) */
+    double* resid_hist;    /* [n_outer]: ||g - A f^k|| (Morozov quantity, Sec. 3.4 S4) */
+    int32_t status;        /* plsqr_status of this instance */
+    int32_t reserved;
+} plsqr_stats;
+
+/* Create a handle for problems of one size on the current CUDA device.  Allocates the whole
+ * workspace for cfg->max_batch instances.  stream: a cudaStream_t (NULL = default stream).
+ * Errors: PLSQR_E_INVALID (sizes, levels), PLSQR_E_NOMEM, PLSQR_E_CUDA. */
+int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out);
+
+/* Set the forward map A (Sec. 1).  Precomputes blur taps / Joseph angle tables and copies
+ * the mask.  Joseph needs ndim 2 and nx == ny.  Errors: PLSQR_E_INVALID, PLSQR_E_NOMEM. */
+int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op);
+
+/* Algorithm 3: f^0 = 0; for k = 1..n_outer: kappa from f^{k-1} (eq. 1.13, kappa floored),
+ * build the V-cycle P ~ M_{f^{k-1}}^{-1}, run n_inner MLSQR iterations (Algorithm 2) from
+ * f = 0 on (eq. 4.3) with damping sqrt(tau) (eq. 2.3), giving f^k.
+ * g: device, m values (m = N, or n_angles*n_bins for Joseph); f_out: device, N values.
+ * stats may be NULL (then the call does not synchronise).  T > 0, tau >= 0. */
+int plsqr_solve(plsqr_handle h, const void* g, int32_t reg, double T, double tau,
+                int32_t n_outer, int32_t n_inner, void* f_out, plsqr_stats* stats);
+
+/* plsqr_solve with host buffers: copies g host->device, solves, copies f device->host and
+ * synchronises.  Pinned host memory makes the copies asynchronous with respect to the host. */
+int plsqr_solve_host(plsqr_handle h, const void* g_host, int32_t reg, double T, double tau,
+                     int32_t n_outer, int32_t n_inner, void* f_host_out, plsqr_stats* stats);
+
+/* Batched Algorithm 3: `count` (<= max_batch) independent instances of the handle's size
+ * and operator, solved together (every kernel launch covers all instances).  g[b], f_out[b]
+ * are device pointers; reg/T/tau are per instance; stats is NULL or an array of `count`. */
+int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const int32_t* reg,
+                      const double* T, const double* tau, int32_t n_outer, int32_t n_inner,
+                      void* const* f_out, plsqr_stats* stats);
+
+void plsqr_destroy(plsqr_handle h);
+const char* plsqr_last_error(plsqr_handle h);
+/* Device bytes a handle with this config would allocate (for admission by memory). */
+int64_t plsqr_workspace_bytes(const plsqr_config* cfg, const plsqr_operator* op);
+
+/* ---- single steps of the path (for parity tests and custom loops) ---------------------- */
+
+/* y = A x (x: device N values, y: device m values).  Sec. 1 (forward map). */
+int plsqr_apply_A(plsqr_handle h, const void* x, void* y);
+/* x = A^T y.  Gather form for Joseph (no atomics), B D for the masked blur. */
+int plsqr_apply_At(plsqr_handle h, const void* y, void* x);
+/* kappa_i = max(r'(t_i)/t_i, kappa_floor*kappa(0)) with t_i = |(D f)_i|, forward
+ * differences and a ghost 0 past the high end of each axis (eqs. 1.12-1.13); *R_out =
+ * sum_i r(t_i) (discrete eq. 1.2), computed on the device in double.  Synchronises. */
+int plsqr_diffusivity(plsqr_handle h, const void* f, int32_t reg, double T, void* kappa_out,
+                      double* R_out);
+/* Build the priorconditioner hierarchy from kappa (device, N values): Galerkin coarse
+ * conductances and the exact inverse of the coarsest operator (Sec. 4.2). */
+int plsqr_prec_setup(plsqr_handle h, const void* kappa);
+/* x = P b with the hierarchy of the last plsqr_prec_setup (b, x: device, N values). */
+int plsqr_prec_apply(plsqr_handle h, const void* b, void* x);
+/* y = M_f x with the kappa of the last plsqr_prec_setup (eq. 1.13). */
+int plsqr_apply_M(plsqr_handle h, const void* x, void* y);
+/* One MLSQR inner solve (Algorithm 2) from f = 0 with the current hierarchy:
+ * n_inner iterations, damping sqrt(tau).  rbar_hist: host, n_inner values, or NULL.
+ * Returns PLSQR_E_BREAKDOWN if it stopped early; *iters_done (may be NULL) counts the
+ * completed iterations.  Synchronises. */
+int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void* f_out,
+                double* rbar_hist, int32_t* iters_done);
+
+/* ---- instrumentation --------------------------------------------------------------------- */
+
+/* Kernel classes reported by plsqr_profile_read. */
+typedef enum {
+    PLSQR_KC_FWD = 0,      /* A with the forward Golub-Kahan epilogue and the beta norm    */
+    PLSQR_KC_ADJ = 1,      /* A^T with the p~ update                                        */
+    PLSQR_KC_OP_PLAIN = 2, /* A or A^T without epilogue                                     */
+    PLSQR_KC_GS_FINE = 3,  /* red-black Gauss-Seidel half sweeps on the finest level         */
+    PLSQR_KC_MG_OTHER = 4, /* coarser sweeps, residual + restriction, prolongation           */
+    PLSQR_KC_COARSE = 5,   /* dense solve on the coarsest level                             */
+    PLSQR_KC_GK = 6,       /* norms, dot product + rotations, solution update               */
+    PLSQR_KC_SETUP = 7,    /* diffusivity, coarsening, band assembly, Cholesky, inverse      */
+    PLSQR_KC_COUNT = 8
+} plsqr_kclass;
+
+/* enable != 0: later calls launch eagerly (no CUDA graph) and bracket every kernel (or
+ * kernel group of one operator application) with CUDA events, accumulating device time per
+ * class.  Resets the accumulators.  Synchronises.  Not part of any numerical result. */
+int plsqr_profile(plsqr_handle h, int32_t enable);
+/* Accumulated device milliseconds and timed launches per class (arrays of n entries). */
+int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
+/* Number of kernel launches the last solve executed (graph replays included), or -1. */
+int64_t plsqr_last_launches(plsqr_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLSQR_H */

@@ -1,0 +1,131 @@
+// common.cuh -- shared device types and helpers of libplsqr (sm_103a).
+//
+// Every kernel covers a batch of B independent instances of one grid size: bulk arrays
+// are [B][N] (T = float or double), and each instance has its own double-precision Krylov
+// state (GkState).  Norms and dot products are reduced deterministically: each block
+// writes one double partial, the last block of the instance (atomic ticket) sums the
+// partials in a fixed order and runs the scalar recurrence on one thread.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace plsqr {
+
+// Status codes mirrored from plsqr.h (device side).
+constexpr int ST_OK = 0;
+constexpr int ST_BREAKDOWN = 4;
+
+// Regulariser ids (plsqr_reg).
+constexpr int REG_TIKHONOV = 0, REG_TV = 1, REG_PM_LOG = 2, REG_PM_EXP = 3;
+
+// Per-instance scalar state of one MLSQR solve (Algorithm 2) and of the outer loop.
+// alpha/beta hold alpha_i, beta_i of the current iteration; beta_new holds beta_{i+1}
+// between the forward step and the rotation.  The c_* fields are the scale factors the
+// bulk kernels apply to the raw (unnormalised) vectors; they are computed once by the
+// thread that finalises a reduction so that no bulk thread divides in double:
+//   c_fwd_a = 1/alpha_i, c_fwd_p = alpha_i/beta_i          (step 10)
+//   c_adj_a = 1/beta_{i+1}, c_adj_p = beta_{i+1}/alpha_i    (step 11)
+//   c_upd_v = 1/alpha_{i+1}, cf = phi_i/rho_i, cw = theta_{i+1}/rho_i  (steps 15, 19-20)
+struct GkState {
+    double alpha, beta, beta_new, beta1;
+    double phibar, rhobar, res2;
+    double cf, cw;
+    double c_fwd_a, c_fwd_p, c_adj_a, c_adj_p, c_upd_v;
+    double tau, sqrt_tau, T;
+    double R;            // R(f) from the last diffusivity pass
+    int32_t reg;
+    int32_t status;      // ST_OK or ST_BREAKDOWN for the current inner solve
+    int32_t status_any;  // sticky over the whole solve
+    int32_t iter;        // completed inner iterations of the current inner solve
+    int32_t outer;       // current outer step (0-based), history row
+    int32_t pad_;
+};
+
+// Per-instance solve parameters written by the host before a solve.
+struct SolveParams {
+    double T, tau;
+    int32_t reg, pad_;
+};
+
+// Histories on the device: [B][n_outer][n_inner], [B][n_outer+1], [B][n_outer].
+struct Hist {
+    double* rbar;
+    double* R;
+    double* resid;
+    int32_t n_outer, n_inner;
+};
+
+// Scratch of the two-level reductions: partials[B][max_blocks], counters[B].
+struct Red {
+    double* partials;
+    unsigned* counters;
+    int32_t max_blocks;
+};
+
+// Grid extents of one level (nz = 1 for 2D).
+struct Dims {
+    int32_t nx, ny, nz, ndim;
+    int64_t N;  // nx*ny*nz
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  Fixed reduction tree.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = (lane < NT / 32) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Two-level deterministic reduction.  Every block of instance `inst` calls this with its
+// thread's contribution; returns true in thread 0 of the last block of the instance, with
+// the instance total in *total.  nblk = blocks of this instance in this launch (<= rd.max_blocks).
+// Threads must use a 1D thread index 0..NT-1 (threadIdx.x).
+template <int NT>
+__device__ __forceinline__ bool reduce_last(double v, const Red& rd, int inst, int blk, int nblk,
+                                            double* total) {
+    __shared__ double sh[NT / 32];
+    __shared__ bool is_last;
+    double bs = block_sum<NT>(v, sh);
+    if (threadIdx.x == 0) {
+        rd.partials[(int64_t)inst * rd.max_blocks + blk] = bs;
+        __threadfence();
+        unsigned prev = atomicAdd(&rd.counters[inst], 1u);
+        is_last = (prev == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += NT) s += __ldcg(&rd.partials[(int64_t)inst * rd.max_blocks + i]);
+    double tot = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) {
+        rd.counters[inst] = 0u;
+        *total = tot;
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool good_pos(double x, double ref) {
+    return isfinite(x) && x > 1e-30 * ref;
+}
+
+}  // namespace plsqr

@@ -1,0 +1,299 @@
+// k_lsqr.cu -- Golub-Kahan scalar recurrences and vector updates of MLSQR (Algorithm 2).
+//
+// The norms beta = ||u|| and alpha = sqrt(v~ . p~) are reduced in double (per-thread partial
+// in the bulk type over a handful of elements, double across threads and blocks, fixed
+// order).  The last block of an instance runs the orthogonal transformation (Algorithm 1
+// steps 10-16) on one thread in double, including the Paige-Saunders damping rotation
+// that eliminates sqrt(tau) I (eq. 3.6), and records ||rbar_i||.
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "kernels.cuh"
+
+namespace plsqr {
+
+
+Profiler*& current_profiler() {
+    static thread_local Profiler* p = nullptr;
+    return p;
+}
+
+void Profiler::begin(int cls, cudaStream_t s) {
+    if (!enabled || open) return;
+    if (n_recs == cap) {
+        const int nc = cap ? 2 * cap : 1024;
+        Rec* nr = new Rec[nc];
+        for (int i = 0; i < n_recs; ++i) nr[i] = recs[i];
+        for (int i = n_recs; i < nc; ++i) {
+            cudaEventCreate(&nr[i].a);
+            cudaEventCreate(&nr[i].b);
+        }
+        delete[] recs;
+        recs = nr;
+        cap = nc;
+    }
+    recs[n_recs].cls = cls;
+    cudaEventRecord(recs[n_recs].a, s);
+    open = true;
+}
+
+void Profiler::finish(cudaStream_t s) {
+    if (!enabled || !open) return;
+    cudaEventRecord(recs[n_recs].b, s);
+    ++n_recs;
+    open = false;
+}
+
+void Profiler::collect() {
+    for (int i = 0; i < n_recs; ++i) {
+        float t = 0.f;
+        cudaEventSynchronize(recs[i].b);
+        if (cudaEventElapsedTime(&t, recs[i].a, recs[i].b) == cudaSuccess) {
+            ms[recs[i].cls] += t;
+            count[recs[i].cls] += 1;
+        }
+    }
+    n_recs = 0;
+}
+
+void Profiler::release() {
+    for (int i = 0; i < cap; ++i) {
+        cudaEventDestroy(recs[i].a);
+        cudaEventDestroy(recs[i].b);
+    }
+    delete[] recs;
+    recs = nullptr;
+    cap = n_recs = 0;
+}
+
+void kbegin(int cls, cudaStream_t s) {
+    if (Profiler* p = current_profiler()) p->begin(cls, s);
+}
+
+void klaunched(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (Profiler* p = current_profiler()) p->launches += 1;
+}
+
+void kfinish(cudaStream_t s) {
+    if (Profiler* p = current_profiler()) p->finish(s);
+}
+
+int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 1024)); }
+
+__global__ void k_set_params(GkState* st, const SolveParams* prm, int B, int reset_outer) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    GkState& s = st[b];
+    s.reg = prm[b].reg;
+    s.T = prm[b].T;
+    s.tau = prm[b].tau;
+    s.sqrt_tau = sqrt(prm[b].tau);
+    if (reset_outer) {
+        s.outer = 0;
+        s.status_any = ST_OK;
+        s.status = ST_OK;
+    }
+}
+
+void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s) {
+    kbegin(KC_GK, s);
+    k_set_params<<<(B + 63) / 64, 64, 0, s>>>(st, prm, B, reset_outer ? 1 : 0);
+    klaunched("k_set_params");
+    kfinish(s);
+}
+
+// beta_1 = ||g||, u_1 = g/beta_1 (kept raw), phibar_1 = beta_1 (Algorithm 2 steps 2, 7).
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_norm(const T* __restrict__ g, int64_t m, GkState* st, Red red) {
+    const int inst = blockIdx.y;
+    const T* gi = g + (int64_t)inst * m;
+    T part = (T)0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256)
+        part = fma(gi[i], gi[i], part);
+    double tot;
+    if (reduce_last<256>((double)part, red, inst, blockIdx.x, gridDim.x, &tot)) {
+        GkState& s = st[inst];
+        const double b1 = sqrt(tot);
+        s.beta1 = b1;
+        s.beta = b1;
+        s.beta_new = b1;
+        s.phibar = b1;
+        s.res2 = 0.0;
+        s.iter = 0;
+        s.cf = 0.0;
+        s.cw = 0.0;
+        if (!(isfinite(b1) && b1 > 0.0)) {
+            s.status = ST_BREAKDOWN;
+            s.status_any = ST_BREAKDOWN;
+        } else {
+            s.status = ST_OK;
+            s.c_adj_a = 1.0 / b1;
+        }
+    }
+}
+
+template <typename T>
+void gk_init_norm(const T* g, int64_t m, int B, GkState* st, Red red, cudaStream_t s) {
+    kbegin(KC_GK, s);
+    int nblk = std::min(red_blocks(m), red.max_blocks);
+    k_init_norm<T><<<dim3(nblk, B), 256, 0, s>>>(g, m, st, red);
+    klaunched("k_init_norm");
+    kfinish(s);
+}
+
+// alpha_{i+1} = sqrt(v~ . p~) (steps 5 / 13), then the rotations and the update coefficients.
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(256) k_dot_rotate(const T* __restrict__ v, const T* __restrict__ p, int64_t N,
+                                                    GkState* st, Hist hist, Red red) {
+    const int inst = blockIdx.y;
+    if (st[inst].status != ST_OK) return;
+    const T* vi = v + (int64_t)inst * N;
+    const T* pi = p + (int64_t)inst * N;
+    T part = (T)0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
+        part = fma(vi[i], pi[i], part);
+    double tot;
+    if (!reduce_last<256>((double)part, red, inst, blockIdx.x, gridDim.x, &tot)) return;
+    GkState& s = st[inst];
+    const double an = sqrt(tot);
+    if (!good_pos(an, s.beta1)) {
+        s.status = ST_BREAKDOWN;
+        s.status_any = ST_BREAKDOWN;
+        return;
+    }
+    if (INIT) {  // step 7: rhobar_1 = alpha_1, w~_1 = v~_1
+        s.alpha = an;
+        s.rhobar = an;
+        s.c_upd_v = 1.0 / an;
+        s.c_fwd_a = 1.0 / an;
+        s.c_fwd_p = an / s.beta;
+        return;
+    }
+    // damping rotation: eliminate sqrt(tau) below rhobar (Paige-Saunders, eq. 3.6)
+    double rhohat = s.rhobar, psi = 0.0;
+    if (s.tau > 0.0) {
+        rhohat = sqrt(s.rhobar * s.rhobar + s.tau);
+        const double c1 = s.rhobar / rhohat, s1 = s.sqrt_tau / rhohat;
+        psi = s1 * s.phibar;
+        s.phibar = c1 * s.phibar;
+    }
+    // Algorithm 1 steps 10-16
+    const double beta = s.beta_new;
+    const double rho = sqrt(rhohat * rhohat + beta * beta);
+    const double c = rhohat / rho, sn = beta / rho;
+    const double theta = sn * an;
+    s.rhobar = -c * an;
+    const double phi = c * s.phibar;
+    s.phibar = sn * s.phibar;
+    s.res2 += psi * psi;
+    s.cf = phi / rho;
+    s.cw = theta / rho;
+    s.iter += 1;
+    if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
+        hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] =
+            sqrt(s.phibar * s.phibar + s.res2);
+    s.alpha = an;
+    s.beta = beta;
+    s.c_upd_v = 1.0 / an;
+    s.c_fwd_a = 1.0 / an;
+    s.c_fwd_p = an / beta;
+}
+
+template <typename T>
+void gk_dot_rotate(const T* v, const T* p, int64_t N, int B, bool init, GkState* st, Hist hist, Red red,
+                   cudaStream_t s) {
+    kbegin(KC_GK, s);
+    int nblk = std::min(red_blocks(N), red.max_blocks);
+    if (init) k_dot_rotate<T, true><<<dim3(nblk, B), 256, 0, s>>>(v, p, N, st, hist, red);
+    else k_dot_rotate<T, false><<<dim3(nblk, B), 256, 0, s>>>(v, p, N, st, hist, red);
+    klaunched("k_dot_rotate");
+    kfinish(s);
+}
+
+// Steps 19-20: f += (phi/rho) w~, w~ = v~ - (theta/rho) w~ with v~ = v_raw/alpha.
+// INIT: f = 0, w~_1 = v~_1 (step 7).
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(256) k_update(T* __restrict__ f, T* __restrict__ w, const T* __restrict__ v,
+                                                int64_t N, const GkState* st) {
+    const int inst = blockIdx.y;
+    const GkState& s = st[inst];
+    if (!INIT && s.status != ST_OK) return;
+    const T cv = (T)s.c_upd_v, cf = (T)s.cf, cw = (T)s.cw;
+    const int64_t off = (int64_t)inst * N;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+        if (INIT) {
+            f[off + i] = (T)0;
+            w[off + i] = v[off + i] * cv;
+        } else {
+            const T wi = w[off + i];
+            f[off + i] = fma(cf, wi, f[off + i]);
+            w[off + i] = v[off + i] * cv - cw * wi;
+        }
+    }
+}
+
+template <typename T>
+void gk_update(T* f, T* w, const T* v, int64_t N, int B, bool init, const GkState* st, cudaStream_t s) {
+    kbegin(KC_GK, s);
+    int nblk = (int)std::min<int64_t>((N + 1023) / 1024, 2048);
+    if (init) k_update<T, true><<<dim3(nblk, B), 256, 0, s>>>(f, w, v, N, st);
+    else k_update<T, false><<<dim3(nblk, B), 256, 0, s>>>(f, w, v, N, st);
+    klaunched("k_update");
+    kfinish(s);
+}
+
+// ||g - A f^k|| for the outer history; advances the outer step counter.
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ g, const T* __restrict__ Af, int64_t m,
+                                                    GkState* st, Hist hist, Red red) {
+    const int inst = blockIdx.y;
+    const T* gi = g + (int64_t)inst * m;
+    const T* ai = Af + (int64_t)inst * m;
+    T part = (T)0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256) {
+        const T r = gi[i] - ai[i];
+        part = fma(r, r, part);
+    }
+    double tot;
+    if (reduce_last<256>((double)part, red, inst, blockIdx.x, gridDim.x, &tot)) {
+        GkState& s = st[inst];
+        if (hist.resid && s.outer < hist.n_outer) hist.resid[(int64_t)inst * hist.n_outer + s.outer] = sqrt(tot);
+        s.outer += 1;
+    }
+}
+
+template <typename T>
+void resid_norm(const T* g, const T* Af, int64_t m, int B, GkState* st, Hist hist, Red red, cudaStream_t s) {
+    kbegin(KC_GK, s);
+    int nblk = std::min(red_blocks(m), red.max_blocks);
+    k_resid_norm<T><<<dim3(nblk, B), 256, 0, s>>>(g, Af, m, st, hist, red);
+    klaunched("k_resid_norm");
+    kfinish(s);
+}
+
+__global__ void k_fill_nan(double* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) p[i] = nan("");
+}
+
+void fill_nan(double* p, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    kbegin(KC_GK, s);
+    k_fill_nan<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(p, n);
+    klaunched("k_fill_nan");
+    kfinish(s);
+}
+
+#define PLSQR_INST_LSQR(T)                                                                                   \
+    template void gk_init_norm<T>(const T*, int64_t, int, GkState*, Red, cudaStream_t);                       \
+    template void gk_dot_rotate<T>(const T*, const T*, int64_t, int, bool, GkState*, Hist, Red, cudaStream_t); \
+    template void gk_update<T>(T*, T*, const T*, int64_t, int, bool, const GkState*, cudaStream_t);           \
+    template void resid_norm<T>(const T*, const T*, int64_t, int, GkState*, Hist, Red, cudaStream_t);
+
+PLSQR_INST_LSQR(float)
+PLSQR_INST_LSQR(double)
+
+}  // namespace plsqr

@@ -1,0 +1,484 @@
+// k_mg.cu -- diffusivity and the geometric-multigrid priorconditioner (Sec. 4.2).
+//
+// M_f = sum_d D_d^T diag(kappa) D_d (eq. 1.13) on the tensor grid: forward differences,
+// ghost value 0 beyond the high end of each axis.  In conductance form the edge from cell i
+// to i+e_d carries c_d(i) (= kappa_i on the finest level), and
+//     (M x)_i = sum_d c_d(i) (x_i - x_{i+e_d}) + c_d(i-e_d) (x_i - x_{i-e_d}).
+// P approximates M^{-1} by V-cycles from a zero initial guess: red-black Gauss-Seidel
+// (red = even index sum; nu sweeps red->black before, black->red after), restriction
+// R = P^T (sum of the 2^d children), piecewise-constant prolongation, Galerkin coarse
+// conductances (sum of the fine conductances crossing a coarse face), and an exact solve
+// on the coarsest level through its explicit inverse (banded Cholesky factor in double,
+// inverse columns by two triangular solves, stored symmetric).  Mirrored smoothing, R = P^T
+// and the exact coarse solve keep P a fixed SPD operator.
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "kernels.cuh"
+
+namespace plsqr {
+
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---- diffusivity (Algorithm 3 step 3) ----------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T kappa_of(int reg, T Tp, T t) {
+    const T q = t / Tp;
+    switch (reg) {
+        case REG_TIKHONOV: return (T)1;
+        case REG_TV: return (T)1 / sqrt(Tp * Tp + t * t);
+        case REG_PM_LOG: return (T)1 / ((T)1 + q * q);
+        default: return exp(-q * q);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T r_of(int reg, T Tp, T t) {
+    const T q = t / Tp;
+    switch (reg) {
+        case REG_TIKHONOV: return (T)0.5 * t * t;
+        case REG_TV: return Tp * sqrt((T)1 + q * q);
+        case REG_PM_LOG: return (T)0.5 * Tp * Tp * log1p(q * q);
+        default: return (T)-0.5 * Tp * Tp * expm1(-q * q);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T* __restrict__ kappa, Dims d,
+                                                     GkState* st, Hist hist, double kfloor, Red red) {
+    const int inst = blockIdx.y;
+    const int reg = st[inst].reg;
+    const T Tp = (T)st[inst].T;
+    const T kmin = (T)kfloor * kappa_of<T>(reg, Tp, (T)0);
+    const T* fi = f + (int64_t)inst * d.N;
+    T* ki = kappa + (int64_t)inst * d.N;
+    double part = 0.0;
+    const int64_t plane = (int64_t)d.nx * d.ny;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * 256) {
+        const int x = (int)(i % d.nx);
+        const int y = (int)((i / d.nx) % d.ny);
+        const int z = (int)(i / plane);
+        const T c = fi[i];
+        T gx = (x + 1 < d.nx ? fi[i + 1] : (T)0) - c;
+        T t2 = gx * gx;
+        T gy = (y + 1 < d.ny ? fi[i + d.nx] : (T)0) - c;
+        t2 += gy * gy;
+        if (d.ndim == 3) {
+            T gz = (z + 1 < d.nz ? fi[i + plane] : (T)0) - c;
+            t2 += gz * gz;
+        }
+        const T t = sqrt(t2);
+        const T k = kappa_of<T>(reg, Tp, t);
+        ki[i] = k > kmin ? k : kmin;
+        part += (double)r_of<T>(reg, Tp, t);
+    }
+    double tot;
+    if (reduce_last<256>(part, red, inst, blockIdx.x, gridDim.x, &tot)) {
+        GkState& s = st[inst];
+        s.R = tot;
+        if (hist.R) hist.R[(int64_t)inst * (hist.n_outer + 1) + s.outer] = tot;
+    }
+}
+
+template <typename T>
+void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, double kfloor, Red red,
+                 cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    int nblk = std::min(red_blocks(d.N), red.max_blocks);
+    k_diffusivity<T><<<dim3(nblk, B), 256, 0, s>>>(f, kappa, d, st, hist, kfloor, red);
+    klaunched("k_diffusivity");
+    kfinish(s);
+}
+
+// ---- level stencil -------------------------------------------------------------------------
+
+// Conductance c_d(i) of the edge i -> i+e_d: kappa_i on the finest level, else cond[d][i].
+template <typename T, bool KAPPA>
+__device__ __forceinline__ T cond_at(const T* __restrict__ c, int dd, int64_t N, int64_t i) {
+    return KAPPA ? c[i] : c[(int64_t)dd * N + i];
+}
+
+// diag = sum_d c_d(i) + c_d(i-e_d);  off = sum_d c_d(i) x_{i+e_d} + c_d(i-e_d) x_{i-e_d}
+template <typename T, bool KAPPA, bool WITH_X>
+__device__ __forceinline__ void stencil(const T* __restrict__ c, const T* x, const Dims& d, int64_t i, int cx,
+                                        int cy, int cz, T& diag, T& off) {
+    diag = (T)0;
+    off = (T)0;
+    const int co[3] = {cx, cy, cz};
+    const int n[3] = {d.nx, d.ny, d.nz};
+    const int64_t strd[3] = {1, (int64_t)d.nx, (int64_t)d.nx * d.ny};
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        if (dd >= d.ndim) break;
+        const T chi = cond_at<T, KAPPA>(c, dd, d.N, i);
+        if (co[dd] > 0) {
+            const T clo = cond_at<T, KAPPA>(c, dd, d.N, i - strd[dd]);
+            diag += chi + clo;
+            if (WITH_X) {
+                if (co[dd] + 1 < n[dd]) off += chi * x[i + strd[dd]];
+                off += clo * x[i - strd[dd]];
+            }
+        } else {
+            diag += chi;
+            if (WITH_X && co[dd] + 1 < n[dd]) off += chi * x[i + strd[dd]];
+        }
+    }
+}
+
+// One red-black Gauss-Seidel half sweep: cells of `colour` get x = (b + off)/diag.
+// zero_init: x is implicitly 0 (first half sweep of a level); the other colour is written 0.
+template <typename T, bool KAPPA, bool ZERO>
+__global__ void __launch_bounds__(256) k_gs_half(const T* __restrict__ cond, const T* __restrict__ b, T* x, Dims d,
+                                                 int colour) {
+    const int inst = blockIdx.y;
+    const int hx = d.nx >> 1;
+    const int64_t Nh = d.N >> 1;
+    const int64_t h = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (h >= Nh) return;
+    const int64_t rest = h / hx;
+    const int y = (int)(rest % d.ny), z = (int)(rest / d.ny);
+    const int par = (y + z + colour) & 1;
+    const int xx = 2 * (int)(h - rest * hx) + par;
+    const int64_t i = xx + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
+    const T* bi = b + (int64_t)inst * d.N;
+    T* xi = x + (int64_t)inst * d.N;
+    T diag, off;
+    stencil<T, KAPPA, !ZERO>(c, xi, d, i, xx, y, z, diag, off);
+    xi[i] = (bi[i] + off) / diag;
+    if (ZERO) xi[i + (par ? -1 : 1)] = (T)0;
+}
+
+template <typename T>
+void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colour, bool zero_init, int B,
+                cudaStream_t s) {
+    kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
+    dim3 grid((unsigned)((d.N / 2 + 255) / 256), B);
+    if (is_kappa) {
+        if (zero_init) k_gs_half<T, true, true><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+        else k_gs_half<T, true, false><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+    } else {
+        if (zero_init) k_gs_half<T, false, true><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+        else k_gs_half<T, false, false><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+    }
+    klaunched("k_gs_half");
+    kfinish(s);
+}
+
+// Coarse right-hand side: bc_I = sum over the 2^d children i of (b_i - (M x)_i).
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ cond, const T* __restrict__ b,
+                                                        const T* __restrict__ x, T* __restrict__ bc, Dims df,
+                                                        Dims dc) {
+    const int inst = blockIdx.y;
+    const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (I >= dc.N) return;
+    const int X = (int)(I % dc.nx), Y = (int)((I / dc.nx) % dc.ny), Z = (int)(I / ((int64_t)dc.nx * dc.ny));
+    const T* c = cond + (KAPPA ? (int64_t)inst * df.N : (int64_t)inst * df.ndim * df.N);
+    const T* bi = b + (int64_t)inst * df.N;
+    const T* xi = x + (int64_t)inst * df.N;
+    T sum = (T)0;
+    const int zc = df.ndim == 3 ? 2 : 1;
+    for (int oz = 0; oz < zc; ++oz)
+        for (int oy = 0; oy < 2; ++oy)
+            for (int ox = 0; ox < 2; ++ox) {
+                const int fx = 2 * X + ox, fy = 2 * Y + oy, fz = df.ndim == 3 ? 2 * Z + oz : 0;
+                const int64_t i = fx + (int64_t)df.nx * (fy + (int64_t)df.ny * fz);
+                T diag, off;
+                stencil<T, KAPPA, true>(c, xi, df, i, fx, fy, fz, diag, off);
+                sum += bi[i] - (diag * xi[i] - off);
+            }
+    bc[(int64_t)inst * dc.N + I] = sum;
+}
+
+template <typename T>
+void mg_resid_restrict(const T* cond, bool is_kappa, const T* b, const T* x, T* bc, Dims df, Dims dc, int B,
+                       cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    dim3 grid((unsigned)((dc.N + 255) / 256), B);
+    if (is_kappa) k_resid_restrict<T, true><<<grid, 256, 0, s>>>(cond, b, x, bc, df, dc);
+    else k_resid_restrict<T, false><<<grid, 256, 0, s>>>(cond, b, x, bc, df, dc);
+    klaunched("k_resid_restrict");
+    kfinish(s);
+}
+
+// x_i += xc_parent(i)
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ xc, T* __restrict__ x, Dims df, Dims dc) {
+    const int inst = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= df.N) return;
+    const int fx = (int)(i % df.nx), fy = (int)((i / df.nx) % df.ny), fz = (int)(i / ((int64_t)df.nx * df.ny));
+    const int64_t I = (fx >> 1) + (int64_t)dc.nx * ((fy >> 1) + (int64_t)dc.ny * (fz >> 1));
+    x[(int64_t)inst * df.N + i] += xc[(int64_t)inst * dc.N + I];
+}
+
+template <typename T>
+void mg_prolong_add(const T* xc, T* x, Dims df, Dims dc, int B, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    k_prolong_add<T><<<dim3((unsigned)((df.N + 255) / 256), B), 256, 0, s>>>(xc, x, df, dc);
+    klaunched("k_prolong_add");
+    kfinish(s);
+}
+
+// y = M x, or y = b - M x when b is given.
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_apply_level(const T* __restrict__ cond, const T* __restrict__ x,
+                                                     const T* __restrict__ b, T* __restrict__ y, Dims d) {
+    const int inst = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= d.N) return;
+    const int cx = (int)(i % d.nx), cy = (int)((i / d.nx) % d.ny), cz = (int)(i / ((int64_t)d.nx * d.ny));
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
+    const T* xi = x + (int64_t)inst * d.N;
+    T diag, off;
+    stencil<T, KAPPA, true>(c, xi, d, i, cx, cy, cz, diag, off);
+    const T mx = diag * xi[i] - off;
+    y[(int64_t)inst * d.N + i] = b ? b[(int64_t)inst * d.N + i] - mx : mx;
+}
+
+template <typename T>
+void mg_apply_level(const T* cond, bool is_kappa, const T* x, const T* b, T* y, Dims d, int B, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    dim3 grid((unsigned)((d.N + 255) / 256), B);
+    if (is_kappa) k_apply_level<T, true><<<grid, 256, 0, s>>>(cond, x, b, y, d);
+    else k_apply_level<T, false><<<grid, 256, 0, s>>>(cond, x, b, y, d);
+    klaunched("k_apply_level");
+    kfinish(s);
+}
+
+template <typename T>
+__global__ void k_axpy(T* y, const T* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) y[i] += x[i];
+}
+
+template <typename T>
+void mg_axpy(T* y, const T* x, int64_t n, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    int nblk = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_axpy<T><<<nblk, 256, 0, s>>>(y, x, n);
+    klaunched("k_axpy");
+    kfinish(s);
+}
+
+// Galerkin coarsening: c_{l+1,d}(I) = sum of c_{l,d}(i) over the fine cells i of coarse
+// cell I with i_d = 2 I_d + 1 (their edge i -> i+e_d crosses the high face of I).
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_coarsen(const T* __restrict__ cf, T* __restrict__ cc, Dims df, Dims dc) {
+    const int inst = blockIdx.y;
+    const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (I >= dc.N) return;
+    const int X = (int)(I % dc.nx), Y = (int)((I / dc.nx) % dc.ny), Z = (int)(I / ((int64_t)dc.nx * dc.ny));
+    const T* c = cf + (KAPPA ? (int64_t)inst * df.N : (int64_t)inst * df.ndim * df.N);
+    T* o = cc + (int64_t)inst * dc.ndim * dc.N;
+    for (int dd = 0; dd < df.ndim; ++dd) {
+        const int zlo = df.ndim == 3 ? (dd == 2 ? 2 * Z + 1 : 2 * Z) : 0;
+        const int zhi = df.ndim == 3 ? 2 * Z + 1 : 0;
+        const int ylo = dd == 1 ? 2 * Y + 1 : 2 * Y, yhi = 2 * Y + 1;
+        const int xlo = dd == 0 ? 2 * X + 1 : 2 * X, xhi = 2 * X + 1;
+        T s = (T)0;
+        for (int fz = zlo; fz <= zhi; ++fz)
+            for (int fy = ylo; fy <= yhi; ++fy)
+                for (int fx = xlo; fx <= xhi; ++fx)
+                    s += cond_at<T, KAPPA>(c, dd, df.N, fx + (int64_t)df.nx * (fy + (int64_t)df.ny * fz));
+        o[(int64_t)dd * dc.N + I] = s;
+    }
+}
+
+template <typename T>
+void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    dim3 grid((unsigned)((dc.N + 255) / 256), B);
+    if (fine_is_kappa) k_coarsen<T, true><<<grid, 256, 0, s>>>(cf, cc, df, dc);
+    else k_coarsen<T, false><<<grid, 256, 0, s>>>(cf, cc, df, dc);
+    klaunched("k_coarsen");
+    kfinish(s);
+}
+
+// ---- exact coarse solve ----------------------------------------------------------------------
+
+// Lower band of the coarsest operator in double: band[i][k] = M(i, i-k), k = 0..bw.
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_coarse_assemble(const T* __restrict__ cond, double* __restrict__ band,
+                                                         Dims d, int bw) {
+    const int inst = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= d.N) return;
+    const int W = bw + 1;
+    double* row = band + ((int64_t)inst * d.N + i) * W;
+    for (int k = 0; k < W; ++k) row[k] = 0.0;
+    const int cx = (int)(i % d.nx), cy = (int)((i / d.nx) % d.ny), cz = (int)(i / ((int64_t)d.nx * d.ny));
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
+    T diag, off;
+    stencil<T, KAPPA, false>(c, (const T*)nullptr, d, i, cx, cy, cz, diag, off);
+    row[0] = (double)diag;
+    const int co[3] = {cx, cy, cz};
+    const int64_t strd[3] = {1, (int64_t)d.nx, (int64_t)d.nx * d.ny};
+    for (int dd = 0; dd < d.ndim; ++dd)
+        if (co[dd] > 0) row[strd[dd]] = -(double)cond_at<T, KAPPA>(c, dd, d.N, i - strd[dd]);
+}
+
+template <typename T>
+void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw, int B, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    dim3 grid((unsigned)((d.N + 255) / 256), B);
+    if (is_kappa) k_coarse_assemble<T, true><<<grid, 256, 0, s>>>(cond, band, d, bw);
+    else k_coarse_assemble<T, false><<<grid, 256, 0, s>>>(cond, band, d, bw);
+    klaunched("k_coarse_assemble");
+    kfinish(s);
+}
+
+// In-place banded Cholesky M = L L^T, one block of 1024 threads per instance.  Column j's
+// trailing update uses the unscaled column and the pivot a_j (L(i,k) -= L(i,j) L(k,j)/a_j),
+// and the column is scaled by 1/sqrt(a_j) during the next column's update, which touches
+// disjoint entries: one barrier per column.
+__global__ void __launch_bounds__(1024) k_chol_band(double* band_all, int nc, int bw) {
+    double* band = band_all + (int64_t)blockIdx.x * nc * (bw + 1);
+    const int W = bw + 1;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double a_prev = 1.0;
+    for (int j = 0; j <= nc; ++j) {
+        if (j > 0) {  // scale column j-1
+            const double r = sqrt(a_prev);
+            for (int t = threadIdx.x; t < W; t += 1024) {
+                const int i = j - 1 + t;
+                if (i >= nc) break;
+                if (t == 0) band[(int64_t)i * W] = r;
+                else band[(int64_t)i * W + t] /= r;
+            }
+        }
+        if (j == nc) break;
+        const double a = band[(int64_t)j * W];
+        const double inv_a = 1.0 / a;
+        for (int ii = ty; ii < bw; ii += 32) {
+            const int i = j + 1 + ii;
+            if (i >= nc) break;
+            const double lij = band[(int64_t)i * W + (i - j)];
+            if (lij == 0.0) continue;
+            const double f = lij * inv_a;
+            for (int kk = tx; kk <= ii; kk += 32) {
+                const int k = j + 1 + kk;
+                const double lkj = band[(int64_t)k * W + (k - j)];
+                band[(int64_t)i * W + (i - k)] -= f * lkj;
+            }
+        }
+        a_prev = a;
+        __syncthreads();
+    }
+}
+
+void coarse_cholesky(double* band, int nc, int bw, int B, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    k_chol_band<<<B, 1024, 0, s>>>(band, nc, bw);
+    klaunched("k_chol_band");
+    kfinish(s);
+}
+
+// Inverse of the coarsest operator from its band factor: one warp per column j solves
+// L y = e_j (rows j..nc-1), then L^T x = y (rows nc-1..j); X(i,j) = X(j,i) = x_i, i >= j.
+__global__ void k_band_inverse(const double* __restrict__ band_all, double* __restrict__ X_all, int nc, int bw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int inst = blockIdx.y;
+    const int j = blockIdx.x * wpb + warp;
+    if (j >= nc) return;
+    const double* band = band_all + (int64_t)inst * nc * (bw + 1);
+    double* X = X_all + (int64_t)inst * nc * nc;
+    double* y = reinterpret_cast<double*>(smraw) + (int64_t)warp * nc;
+    const int W = bw + 1;
+    for (int i = j; i < nc; ++i) {
+        double s = 0.0;
+        const int kmin = max(j, i - bw);
+        for (int k = i - 1 - lane; k >= kmin; k -= 32) s += band[(int64_t)i * W + (i - k)] * y[k];
+        s = warp_sum(s);
+        const double yi = ((i == j ? 1.0 : 0.0) - s) / band[(int64_t)i * W];
+        if (lane == 0) y[i] = yi;
+        __syncwarp();
+    }
+    for (int i = nc - 1; i >= j; --i) {
+        double s = 0.0;
+        const int kmax = min(i + bw, nc - 1);
+        for (int k = i + 1 + lane; k <= kmax; k += 32) s += band[(int64_t)k * W + (k - i)] * y[k];
+        s = warp_sum(s);
+        const double xi = (y[i] - s) / band[(int64_t)i * W];
+        __syncwarp();
+        if (lane == 0) y[i] = xi;
+        __syncwarp();
+    }
+    for (int i = j + lane; i < nc; i += 32) {
+        const double v = y[i];
+        X[(int64_t)i * nc + j] = v;
+        X[(int64_t)j * nc + i] = v;
+    }
+}
+
+void coarse_inverse(const double* band, double* X, int nc, int bw, int B, cudaStream_t s) {
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * nc * sizeof(double) > 200 * 1024) wpb >>= 1;
+    size_t smem = (size_t)wpb * nc * sizeof(double);
+    if (smem > 227 * 1024) throw std::runtime_error("coarse_inverse: coarsest level too large");
+    kbegin(KC_SETUP, s);
+    auto kfn = k_band_inverse;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((nc + wpb - 1) / wpb, B);
+    kfn<<<grid, wpb * 32, smem, s>>>(band, X, nc, bw);
+    klaunched("k_band_inverse");
+    kfinish(s);
+}
+
+// x = X b on the coarsest level, one warp per row; X and the sums in double (the coarse
+// correction is a difference of large terms, so its accuracy sets that of P).
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_symv(const double* __restrict__ X_all, const T* __restrict__ b_all,
+                                                     T* __restrict__ x_all, int nc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* sb = reinterpret_cast<double*>(smraw);
+    const int inst = blockIdx.y;
+    const T* b = b_all + (int64_t)inst * nc;
+    for (int i = threadIdx.x; i < nc; i += 256) sb[i] = (double)b[i];
+    __syncthreads();
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= nc) return;
+    const double* Xr = X_all + (int64_t)inst * nc * nc + (int64_t)row * nc;
+    double acc = 0.0;
+    for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sb[c], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x_all[(int64_t)inst * nc + row] = (T)acc;
+}
+
+template <typename T>
+void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t s) {
+    kbegin(KC_COARSE, s);
+    size_t smem = sizeof(double) * nc;
+    auto kfn = k_coarse_symv<T>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kfn<<<dim3((nc + 7) / 8, B), 256, smem, s>>>(X, b, x, nc);
+    klaunched("k_coarse_symv");
+    kfinish(s);
+}
+
+#define PLSQR_INST_MG(T)                                                                                  \
+    template void diffusivity<T>(const T*, T*, Dims, int, GkState*, Hist, double, Red, cudaStream_t);     \
+    template void mg_coarsen<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t);                        \
+    template void mg_gs_half<T>(const T*, bool, const T*, T*, Dims, int, bool, int, cudaStream_t);         \
+    template void mg_resid_restrict<T>(const T*, bool, const T*, const T*, T*, Dims, Dims, int,            \
+                                       cudaStream_t);                                                     \
+    template void mg_prolong_add<T>(const T*, T*, Dims, Dims, int, cudaStream_t);                          \
+    template void mg_apply_level<T>(const T*, bool, const T*, const T*, T*, Dims, int, cudaStream_t);      \
+    template void mg_axpy<T>(T*, const T*, int64_t, cudaStream_t);                                         \
+    template void coarse_assemble<T>(const T*, bool, double*, Dims, int, int, cudaStream_t);               \
+    template void coarse_symv<T>(const double*, const T*, T*, int, int, cudaStream_t);
+
+PLSQR_INST_MG(float)
+PLSQR_INST_MG(double)
+
+}  // namespace plsqr

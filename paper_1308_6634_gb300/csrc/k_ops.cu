@@ -1,0 +1,405 @@
+// k_ops.cu -- forward maps A and adjoints A^T with the Golub-Kahan epilogues fused in.
+//
+// Gaussian blur (deblurring, Sec. 1): separable taps w_k = exp(-k^2/2s^2)/sum, |k| <= R,
+// zero boundary, so B^T = B.  A 2D tile (64 x 32 outputs plus an R halo) is staged once in
+// shared memory; the x pass writes an intermediate tile in shared memory and the y pass
+// produces the output, so each input element is read from memory once per tile.  3D runs
+// the same kernel per z-slice into a scratch volume, then a z pass with the epilogue.
+// Masked blur (inpainting): A = D B (mask on the output), A^T = B D (mask on the input).
+// Joseph projector (X-ray tomography, Sec. 1): one thread per ray steps along the dominant
+// axis with linear interpolation; the adjoint is a gather per pixel over all angles of the
+// (at most a few) rays whose interpolation touched the pixel, with the same weights: the
+// exact transpose without atomics.
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+
+#include "kernels.cuh"
+
+namespace plsqr {
+
+template <typename T, int EPI>
+__device__ __forceinline__ void epi_coefs(const GkState& s, T& ca, T& cp) {
+    if (EPI == EPI_FWD) {
+        ca = (T)s.c_fwd_a;
+        cp = (T)s.c_fwd_p;
+    } else if (EPI == EPI_ADJ) {
+        ca = (T)s.c_adj_a;
+        cp = (T)s.c_adj_p;
+    } else if (EPI == EPI_ADJ_INIT) {
+        ca = (T)s.c_adj_a;
+        cp = (T)0;
+    } else {
+        ca = (T)1;
+        cp = (T)0;
+    }
+}
+
+// Apply the epilogue to one output element; returns the value written (for the norm).
+template <typename T, int EPI>
+__device__ __forceinline__ T epi_store(T acc, T ca, T cp, T* out, const T* prev, int64_t gi) {
+    T v;
+    if (EPI == EPI_PLAIN) {
+        v = acc;
+    } else if (EPI == EPI_FWD) {
+        v = acc * ca - cp * prev[gi];
+    } else if (EPI == EPI_ADJ) {
+        v = acc * ca - cp * out[gi];
+    } else {
+        v = acc * ca;
+    }
+    out[gi] = v;
+    return v;
+}
+
+// Finalise beta_{i+1} = ||u|| (Algorithm 2 step 10) in the last block.
+__device__ __forceinline__ void finalize_beta(GkState& s, double tot) {
+    double bn = sqrt(tot);
+    if (!good_pos(bn, s.beta1)) {
+        s.status = ST_BREAKDOWN;
+        s.status_any = ST_BREAKDOWN;
+        return;
+    }
+    s.beta_new = bn;
+    s.c_adj_a = 1.0 / bn;
+    s.c_adj_p = bn / s.alpha;
+}
+
+constexpr int BTX = 64, BTY = 32, BNT = 256;
+
+template <typename T, int EPI, bool MASK_IN, bool MASK_OUT>
+__global__ void __launch_bounds__(BNT) k_blur2d(const T* __restrict__ in, T* out, const T* prev,
+                                                const uint8_t* __restrict__ mask, Dims d,
+                                                const T* __restrict__ wx, int Rx, const T* __restrict__ wy,
+                                                int Ry, GkState* st, Red red) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int plane = blockIdx.z;  // z + nz * inst
+    const int inst = plane / d.nz;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    const int tid = threadIdx.x;
+    const int nwx = 2 * Rx + 1, nwy = 2 * Ry + 1;
+    const int LX = BTX + 2 * Rx, LY = BTY + 2 * Ry;
+    T* swx = reinterpret_cast<T*>(smraw);
+    T* swy = swx + nwx;
+    T* sin = swy + nwy;  // nwx + nwy is even: aligned for double
+    T* smid = sin + LX * LY;
+    for (int i = tid; i < nwx; i += BNT) swx[i] = wx[i];
+    for (int i = tid; i < nwy; i += BNT) swy[i] = wy[i];
+    const int x0 = blockIdx.x * BTX, y0 = blockIdx.y * BTY;
+    const int64_t plane_off = (int64_t)plane * d.nx * d.ny;
+    const int64_t mask_off = (int64_t)(plane - inst * d.nz) * d.nx * d.ny;
+    for (int i = tid; i < LX * LY; i += BNT) {
+        const int r = i / LX, c = i - r * LX;
+        const int gy = y0 - Ry + r, gx = x0 - Rx + c;
+        T v = (T)0;
+        if (gy >= 0 && gy < d.ny && gx >= 0 && gx < d.nx) {
+            const int64_t o = (int64_t)gy * d.nx + gx;
+            v = in[plane_off + o];
+            if (MASK_IN) v = mask[mask_off + o] ? v : (T)0;
+        }
+        sin[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < LY * BTX; i += BNT) {
+        const int r = i / BTX, c = i - r * BTX;
+        const T* row = sin + r * LX + c;
+        T acc = (T)0;
+        for (int k = 0; k < nwx; ++k) acc = fma(swx[k], row[k], acc);
+        smid[i] = acc;
+    }
+    __syncthreads();
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    T part = (T)0;
+    for (int i = tid; i < BTY * BTX; i += BNT) {
+        const int r = i / BTX, c = i - r * BTX;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gy >= d.ny || gx >= d.nx) continue;
+        const T* col = smid + r * BTX + c;
+        T acc = (T)0;
+        for (int k = 0; k < nwy; ++k) acc = fma(swy[k], col[k * BTX], acc);
+        const int64_t o = (int64_t)gy * d.nx + gx;
+        if (MASK_OUT) acc = mask[mask_off + o] ? acc : (T)0;
+        T v = epi_store<T, EPI>(acc, ca, cp, out, prev, plane_off + o);
+        if (EPI == EPI_FWD) part = fma(v, v, part);
+    }
+    if (EPI == EPI_FWD) {
+        const int nblk = gridDim.x * gridDim.y * d.nz;
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (plane - inst * d.nz));
+        double tot;
+        if (reduce_last<BNT>((double)part, red, inst, blk, nblk, &tot)) finalize_beta(st[inst], tot);
+    }
+}
+
+constexpr int ZTZ = 16;  // z outputs per thread column; block = 32 (x) x 8 (y) threads
+
+template <typename T, int EPI, bool MASK_OUT>
+__global__ void __launch_bounds__(256) k_blur_z(const T* __restrict__ in, T* out, const T* prev,
+                                                const uint8_t* __restrict__ mask, Dims d,
+                                                const T* __restrict__ wz, int Rz, GkState* st, Red red) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nzt = (d.nz + ZTZ - 1) / ZTZ;
+    const int inst = blockIdx.z / nzt, zt = blockIdx.z - inst * nzt;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int nw = 2 * Rz + 1, LZ = ZTZ + 2 * Rz;
+    T* sw = reinterpret_cast<T*>(smraw);
+    T* s = sw + ((nw + 1) & ~1);
+    for (int i = tid; i < nw; i += 256) sw[i] = wz[i];
+    const int gx = blockIdx.x * 32 + tx, gy = blockIdx.y * 8 + ty, z0 = zt * ZTZ;
+    const bool inxy = gx < d.nx && gy < d.ny;
+    const int64_t plane = (int64_t)d.nx * d.ny;
+    const int64_t base = (int64_t)inst * d.N + (int64_t)gy * d.nx + gx;
+    for (int zz = 0; zz < LZ; ++zz) {
+        const int gz = z0 - Rz + zz;
+        T v = (T)0;
+        if (inxy && gz >= 0 && gz < d.nz) v = in[base + gz * plane];
+        s[zz * 256 + tid] = v;
+    }
+    __syncthreads();
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    T part = (T)0;
+    if (inxy) {
+        for (int zz = 0; zz < ZTZ; ++zz) {
+            const int gz = z0 + zz;
+            if (gz >= d.nz) break;
+            T acc = (T)0;
+            for (int k = 0; k < nw; ++k) acc = fma(sw[k], s[(zz + k) * 256 + tid], acc);
+            const int64_t o = (int64_t)gz * plane + (int64_t)gy * d.nx + gx;
+            if (MASK_OUT) acc = mask[o] ? acc : (T)0;
+            T v = epi_store<T, EPI>(acc, ca, cp, out, prev, (int64_t)inst * d.N + o);
+            if (EPI == EPI_FWD) part = fma(v, v, part);
+        }
+    }
+    if (EPI == EPI_FWD) {
+        const int nblk = gridDim.x * gridDim.y * nzt;
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt);
+        double tot;
+        if (reduce_last<256>((double)part, red, inst, blk, nblk, &tot)) finalize_beta(st[inst], tot);
+    }
+}
+
+// A = I (denoising): the epilogue alone.
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_identity(const T* __restrict__ in, T* out, const T* prev, int64_t n,
+                                                  GkState* st, Red red) {
+    const int inst = blockIdx.y;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    T part = (T)0;
+    const int64_t off = (int64_t)inst * n;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        T v = epi_store<T, EPI>(in[off + i], ca, cp, out, prev, off + i);
+        if (EPI == EPI_FWD) part = fma(v, v, part);
+    }
+    if (EPI == EPI_FWD) {
+        double tot;
+        if (reduce_last<256>((double)part, red, inst, blockIdx.x, gridDim.x, &tot)) finalize_beta(st[inst], tot);
+    }
+}
+
+// Joseph forward projection: one thread per ray (angle a, bin k).  Rows stepped: for each
+// row i, x = (s - y_i sin)/cos, linear interpolation between the two bracketing columns,
+// weight 1/|cos| (columns stepped: roles of x and y exchanged, weight 1/|sin|).
+template <typename T, int EPI>
+__global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, T* out, const T* prev,
+                                                    const JosephAngle<T>* __restrict__ tab, int n, int na,
+                                                    int nb, T ds, GkState* st, Red red) {
+    const int inst = blockIdx.z, a = blockIdx.y, k = blockIdx.x * 128 + threadIdx.x;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    const JosephAngle<T> J = tab[a];
+    const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
+    const T* im = img + (int64_t)inst * n * n;
+    T acc = (T)0;
+    if (k < nb) {
+        const T s = ((T)k - cdet) * ds;
+        const T u0 = s * J.a1 + cimg;
+        // rows q with the sample inside (-1, n): u = u0 - (q - cimg) a2
+        int qlo = 0, qhi = n - 1;
+        if (fabs((double)J.a2) < 1e-7) {
+            if (!(u0 > (T)-1 && u0 < (T)n)) qhi = -1;
+        } else {
+            const T q1 = (u0 - (T)n) / J.a2 + cimg, q2 = (u0 + (T)1) / J.a2 + cimg;
+            const T lo = fmin(q1, q2), hi = fmax(q1, q2);
+            qlo = max(0, (int)floor(lo) - 1);
+            qhi = min(n - 1, (int)ceil(hi) + 1);
+        }
+        for (int q = qlo; q <= qhi; ++q) {
+            const T u = u0 - ((T)q - cimg) * J.a2;
+            const T fl = floor(u);
+            const int j0 = (int)fl;
+            const T fr = u - fl;
+            if (j0 < -1 || j0 >= n) continue;
+            T v0 = (T)0, v1 = (T)0;
+            if (J.rows) {
+                if (j0 >= 0) v0 = im[(int64_t)q * n + j0];
+                if (j0 + 1 < n) v1 = im[(int64_t)q * n + j0 + 1];
+            } else {
+                if (j0 >= 0) v0 = im[(int64_t)j0 * n + q];
+                if (j0 + 1 < n) v1 = im[(int64_t)(j0 + 1) * n + q];
+            }
+            acc += ((T)1 - fr) * v0 + fr * v1;
+        }
+        acc *= J.wgt;
+    }
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    T part = (T)0;
+    if (k < nb) {
+        T v = epi_store<T, EPI>(acc, ca, cp, out, prev, (int64_t)inst * na * nb + (int64_t)a * nb + k);
+        if (EPI == EPI_FWD) part = v * v;
+    }
+    if (EPI == EPI_FWD) {
+        double tot;
+        if (reduce_last<128>((double)part, red, inst, blockIdx.x + gridDim.x * a, gridDim.x * gridDim.y, &tot))
+            finalize_beta(st[inst], tot);
+    }
+}
+
+// Joseph adjoint, gather form: pixel (i, j) collects, for every angle, the rays k with
+// |s_k - s_ij| < h (h = |cos| rows stepped, |sin| columns stepped), s_ij = x cos + y sin,
+// with the forward weight (1 - |s_k - s_ij|/h)/h.  No atomics; exact transpose.
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, T* out,
+                                                    const JosephAngle<T>* __restrict__ tab, int n, int na, int nb,
+                                                    GkState* st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    JosephAngle<T>* stab = reinterpret_cast<JosephAngle<T>*>(smraw);
+    const int inst = blockIdx.z;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    for (int i = threadIdx.x; i < na; i += 256) stab[i] = tab[i];
+    __syncthreads();
+    const int j = blockIdx.x * 16 + (threadIdx.x & 15), i = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (i >= n || j >= n) return;
+    const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
+    const T x = (T)j - cimg, y = (T)i - cimg;
+    const T* sg = sino + (int64_t)inst * na * nb;
+    T acc = (T)0;
+    for (int a = 0; a < na; ++a) {
+        const JosephAngle<T>& J = stab[a];
+        const T t = x * J.c1 + y * J.c2 + cdet;
+        int klo = max(0, (int)ceil(t - J.hw));
+        int khi = min(nb - 1, (int)floor(t + J.hw));
+        T acc_a = (T)0;
+        for (int k = klo; k <= khi; ++k) {
+            const T dist = fabs((T)k - t);
+            if (dist < J.hw) acc_a += ((T)1 - dist * J.inv_hw) * sg[(int64_t)a * nb + k];
+        }
+        acc += acc_a * J.wgt;
+    }
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    epi_store<T, EPI>(acc, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i * n + j);
+}
+
+// ---- launchers ---------------------------------------------------------------------------
+
+
+template <typename T, int EPI, bool MI, bool MO>
+static void launch_blur2d(const OpDev& op, const T* in, T* out, const T* prev, int B, GkState* st, Red red,
+                          cudaStream_t s) {
+    const Dims& d = op.d;
+    const int Rx = op.R[0], Ry = op.R[1];
+    size_t smem = sizeof(T) * ((2 * Rx + 1) + (2 * Ry + 1) + (size_t)(BTX + 2 * Rx) * (BTY + 2 * Ry) +
+                               (size_t)(BTY + 2 * Ry) * BTX);
+    auto kfn = k_blur2d<T, EPI, MI, MO>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((d.nx + BTX - 1) / BTX, (d.ny + BTY - 1) / BTY, d.nz * B);
+    if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * d.nz > red.max_blocks)
+        throw std::runtime_error("blur2d: too many blocks for the reduction scratch");
+    kfn<<<grid, BNT, smem, s>>>(in, out, prev, op.mask, d, (const T*)op.taps[0], Rx, (const T*)op.taps[1], Ry, st,
+                                red);
+    klaunched("k_blur2d");
+}
+
+template <typename T, int EPI, bool MO>
+static void launch_blur_z(const OpDev& op, const T* in, T* out, const T* prev, int B, GkState* st, Red red,
+                          cudaStream_t s) {
+    const Dims& d = op.d;
+    const int Rz = op.R[2];
+    const int nw = 2 * Rz + 1;
+    size_t smem = sizeof(T) * ((size_t)((nw + 1) & ~1) + (size_t)(ZTZ + 2 * Rz) * 256);
+    auto kfn = k_blur_z<T, EPI, MO>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int nzt = (d.nz + ZTZ - 1) / ZTZ;
+    dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, nzt * B);
+    if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * nzt > red.max_blocks)
+        throw std::runtime_error("blur_z: too many blocks for the reduction scratch");
+    kfn<<<grid, 256, smem, s>>>(in, out, prev, op.mask, d, (const T*)op.taps[2], Rz, st, red);
+    klaunched("k_blur_z");
+}
+
+template <typename T, int EPI>
+static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const T* prev, T* tmp, int B,
+                      GkState* st, Red red, cudaStream_t s) {
+    switch (op.kind) {
+        case OPK_IDENTITY: {
+            int nblk = (int)std::min<int64_t>((op.m + 255) / 256, 1024);
+            nblk = std::min(nblk, red.max_blocks);
+            k_identity<T, EPI><<<dim3(nblk, B), 256, 0, s>>>(in, out, prev, op.m, st, red);
+            klaunched("k_identity");
+            return;
+        }
+        case OPK_BLUR:
+        case OPK_BLUR_MASK: {
+            const bool mk = op.kind == OPK_BLUR_MASK;
+            if (op.d.ndim == 2) {
+                if (!mk) launch_blur2d<T, EPI, false, false>(op, in, out, prev, B, st, red, s);
+                else if (adjoint) launch_blur2d<T, EPI, true, false>(op, in, out, prev, B, st, red, s);
+                else launch_blur2d<T, EPI, false, true>(op, in, out, prev, B, st, red, s);
+            } else {
+                if (mk && adjoint) launch_blur2d<T, EPI_PLAIN, true, false>(op, in, tmp, nullptr, B, st, red, s);
+                else launch_blur2d<T, EPI_PLAIN, false, false>(op, in, tmp, nullptr, B, st, red, s);
+                if (mk && !adjoint) launch_blur_z<T, EPI, true>(op, tmp, out, prev, B, st, red, s);
+                else launch_blur_z<T, EPI, false>(op, tmp, out, prev, B, st, red, s);
+            }
+            return;
+        }
+        case OPK_JOSEPH: {
+            const int n = op.d.nx;
+            const auto* tab = (const JosephAngle<T>*)op.jtab;
+            if (!adjoint) {
+                dim3 grid((op.nb + 127) / 128, op.na, B);
+                if (EPI == EPI_FWD && (int64_t)grid.x * grid.y > red.max_blocks)
+                    throw std::runtime_error("joseph_fwd: too many blocks for the reduction scratch");
+                k_joseph_fwd<T, EPI><<<grid, 128, 0, s>>>(in, out, prev, tab, n, op.na, op.nb, (T)op.ds, st, red);
+                klaunched("k_joseph_fwd");
+            } else {
+                size_t smem = sizeof(JosephAngle<T>) * op.na;
+                auto kfn = k_joseph_adj<T, EPI>;
+                if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                dim3 grid((n + 15) / 16, (n + 15) / 16, B);
+                kfn<<<grid, 256, smem, s>>>(in, out, tab, n, op.na, op.nb, st);
+                klaunched("k_joseph_adj");
+            }
+            return;
+        }
+    }
+    throw std::runtime_error("op_apply: unknown operator kind");
+}
+
+template <typename T>
+void op_apply(const OpDev& op, bool adjoint, int epi, const T* in, T* out, const T* prev, T* tmp, int B,
+              GkState* st, Red red, cudaStream_t s) {
+    struct Scope {
+        cudaStream_t s;
+        ~Scope() { kfinish(s); }
+    } scope{s};
+    kbegin(epi == EPI_PLAIN ? KC_OP_PLAIN : (adjoint ? KC_ADJ : KC_FWD), s);
+    switch (epi) {
+        case EPI_PLAIN: apply_epi<T, EPI_PLAIN>(op, adjoint, in, out, prev, tmp, B, st, red, s); return;
+        case EPI_FWD: apply_epi<T, EPI_FWD>(op, adjoint, in, out, prev, tmp, B, st, red, s); return;
+        case EPI_ADJ: apply_epi<T, EPI_ADJ>(op, adjoint, in, out, prev, tmp, B, st, red, s); return;
+        case EPI_ADJ_INIT: apply_epi<T, EPI_ADJ_INIT>(op, adjoint, in, out, prev, tmp, B, st, red, s); return;
+    }
+    throw std::runtime_error("op_apply: bad epilogue");
+}
+
+template void op_apply<float>(const OpDev&, bool, int, const float*, float*, const float*, float*, int, GkState*,
+                              Red, cudaStream_t);
+template void op_apply<double>(const OpDev&, bool, int, const double*, double*, const double*, double*, int,
+                               GkState*, Red, cudaStream_t);
+
+}  // namespace plsqr

@@ -1,0 +1,122 @@
+// kernels.cuh -- launchers of the libplsqr kernels (internal C++ interface).
+#pragma once
+#include "common.cuh"
+
+namespace plsqr {
+
+// Epilogue of an operator application out = op(in):
+//  EPI_PLAIN     out = op(in)
+//  EPI_FWD       u = op(v)/alpha - (alpha/beta) u_prev, and beta_new = ||u||  (Alg. 2 step 10)
+//  EPI_ADJ       p = op(u)/beta_new - (beta_new/alpha) p                      (Alg. 2 step 11)
+//  EPI_ADJ_INIT  p = op(g)/beta_1                                              (Alg. 2 step 3)
+// The raw (unnormalised) vectors v, u, p are kept; their scales live in GkState.
+enum Epi { EPI_PLAIN = 0, EPI_FWD = 1, EPI_ADJ = 2, EPI_ADJ_INIT = 3 };
+
+enum OpKind { OPK_BLUR = 0, OPK_BLUR_MASK = 1, OPK_JOSEPH = 2, OPK_IDENTITY = 3 };
+
+// Per-angle constants of the Joseph projector (computed in double on the host).
+template <typename T>
+struct JosephAngle {
+    T a1, a2;      // forward: u = s*a1 + c_img - y*a2 along the stepped axis
+    T c1, c2;      // gather: t = x*c1 + y*c2 + c_det (continuous bin index of a pixel)
+    T hw, inv_hw;  // gather: half width of the footprint in bins, and its inverse
+    T wgt;         // 1/|cos| (rows stepped) or 1/|sin| (columns stepped)
+    int32_t rows;  // 1: step over rows (|cos| > |sin| by the index rule), 0: columns
+};
+
+struct OpDev {
+    int kind;
+    Dims d;              // image grid
+    int64_t m;           // data length per instance
+    const void* taps[3]; // blur taps per axis (T), 2R+1 each
+    int R[3];
+    const uint8_t* mask; // [N], shared by all instances
+    const void* jtab;    // JosephAngle<T>[n_angles]
+    int na, nb;
+    double ds;
+};
+
+template <typename T>
+void op_apply(const OpDev& op, bool adjoint, int epi, const T* in, T* out, const T* prev, T* tmp,
+              int B, GkState* st, Red red, cudaStream_t s);
+
+// kappa = max(r'(t)/t, kfloor*kappa(0)), R = sum r(t) per instance (state reg/T).
+template <typename T>
+void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, double kfloor, Red red,
+                 cudaStream_t s);
+
+// ---- multigrid ----
+template <typename T>
+void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s);
+template <typename T>
+void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colour, bool zero_init, int B,
+                cudaStream_t s);
+template <typename T>
+void mg_resid_restrict(const T* cond, bool is_kappa, const T* b, const T* x, T* bc, Dims df, Dims dc, int B,
+                       cudaStream_t s);
+template <typename T>
+void mg_prolong_add(const T* xc, T* x, Dims df, Dims dc, int B, cudaStream_t s);
+// r = b - M x (b may be null: r = -M x is not needed; y = M x when b == null and negate=false)
+template <typename T>
+void mg_apply_level(const T* cond, bool is_kappa, const T* x, const T* b, T* y, Dims d, int B, cudaStream_t s);
+template <typename T>
+void mg_axpy(T* y, const T* x, int64_t n, cudaStream_t s);  // y += x
+template <typename T>
+void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw, int B, cudaStream_t s);
+void coarse_cholesky(double* band, int nc, int bw, int B, cudaStream_t s);
+void coarse_inverse(const double* band, double* X, int nc, int bw, int B, cudaStream_t s);
+template <typename T>
+void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t s);
+
+// ---- Golub-Kahan scalars and updates ----
+void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);
+template <typename T>
+void gk_init_norm(const T* g, int64_t m, int B, GkState* st, Red red, cudaStream_t s);
+template <typename T>
+void gk_dot_rotate(const T* v, const T* p, int64_t N, int B, bool init, GkState* st, Hist hist, Red red,
+                   cudaStream_t s);
+template <typename T>
+void gk_update(T* f, T* w, const T* v, int64_t N, int B, bool init, const GkState* st, cudaStream_t s);
+template <typename T>
+void resid_norm(const T* g, const T* Af, int64_t m, int B, GkState* st, Hist hist, Red red, cudaStream_t s);
+void fill_nan(double* p, int64_t n, cudaStream_t s);
+
+int red_blocks(int64_t n);  // blocks per instance used by the plain reductions
+
+// ---- launch bookkeeping ----
+// Every launcher brackets its launch with kbegin/kend.  kend checks the launch error and
+// counts it; when a Profiler is installed for the calling thread and enabled, the launch is
+// also bracketed by CUDA events tagged with its class (eager launches only).
+enum KClass {
+    KC_FWD = 0,      // A with the Golub-Kahan forward epilogue (and beta reduction)
+    KC_ADJ = 1,      // A^T with the p update
+    KC_OP_PLAIN = 2, // A or A^T without epilogue (residual, single-step entry points)
+    KC_GS_FINE = 3,  // red-black half sweeps on the finest level
+    KC_MG_OTHER = 4, // coarse-level sweeps, residual/restriction, prolongation, residuals
+    KC_COARSE = 5,   // dense solve on the coarsest level
+    KC_GK = 6,       // norms, dot + rotations, solution update
+    KC_SETUP = 7,    // diffusivity, coarsening, band assembly, Cholesky, inverse
+    KC_COUNT = 8
+};
+
+struct Profiler {
+    int64_t launches = 0;
+    bool enabled = false;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    Rec* recs = nullptr;
+    int n_recs = 0, cap = 0;
+    double ms[KC_COUNT] = {};
+    int64_t count[KC_COUNT] = {};
+    bool open = false;
+    void begin(int cls, cudaStream_t s);
+    void finish(cudaStream_t s);
+    void collect();  // synchronise the recorded events and add their durations
+    void release();
+};
+
+Profiler*& current_profiler();
+void kbegin(int cls, cudaStream_t s);   // start event of a timed region (profiling only)
+void klaunched(const char* what);      // check the launch that was just issued, count it
+void kfinish(cudaStream_t s);          // end event of the timed region (profiling only)
+
+}  // namespace plsqr

@@ -1,0 +1,863 @@
+// plsqr_api.cu -- host side of libplsqr: handles, workspace, the order of the kernels of
+// Algorithms 2 and 3, CUDA-graph capture of one outer step, and the C ABI of plsqr.h.
+//
+// A solve runs on an internal non-blocking stream ordered after the caller's stream by
+// events (so the caller's stream may be the legacy default stream, which cannot be
+// captured).  One outer step of Algorithm 3 -- diffusivity, priorconditioner setup, MLSQR
+// initialisation, n_inner MLSQR iterations and the residual norm -- is captured once per
+// (batch count, n_inner, history shape) and replayed n_outer times; the outer step index
+// lives in device memory, so every replay writes its own history row.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/plsqr.h"
+#include "kernels.cuh"
+
+using namespace plsqr;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct CudaError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+struct InvalidArg : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+struct NoMem : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+
+void ck(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) throw NoMem(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Level {
+    Dims d;
+    char* cond = nullptr;  // [B][ndim][N_l] (levels >= 1)
+    char* b = nullptr;     // [B][N_l]
+    char* x = nullptr;
+};
+
+}  // namespace
+
+struct plsqr_ctx {
+    plsqr_config cfg{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    bool fp64 = false;
+    size_t esz = 4;
+    Dims d{};
+    int B = 1;
+    int L = 1, nu = 2, cycles = 1;
+    double kfloor = 1e-4;
+    // operator
+    bool op_set = false;
+    plsqr_operator op{};
+    OpDev od{};
+    int64_t m = 0;
+    void* taps[3] = {nullptr, nullptr, nullptr};
+    void* jtab = nullptr;
+    uint8_t* mask = nullptr;
+    // workspace
+    char *g = nullptr, *f = nullptr, *u = nullptr, *p = nullptr, *v = nullptr, *w = nullptr;
+    char *kappa = nullptr, *tmp = nullptr, *tmpm = nullptr, *r0 = nullptr, *e0 = nullptr;
+    Level lv[16];
+    int nc = 0, bw = 0;
+    double* band = nullptr;
+    double* X = nullptr;  // inverse of the coarsest operator, [B][nc][nc]
+    GkState* st = nullptr;
+    SolveParams* prm_dev = nullptr;
+    SolveParams* prm_host = nullptr;  // pinned
+    GkState* st_host = nullptr;       // pinned
+    Red red{};
+    // histories
+    double *h_rbar = nullptr, *h_R = nullptr, *h_resid = nullptr;
+    int h_outer = 0, h_inner = 0;
+    double* h_stage = nullptr;  // pinned staging for history download
+    size_t h_stage_n = 0;
+    // graphs (with the number of kernel launches each replay executes)
+    std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    Profiler prof;
+    int64_t last_launches = 0;
+    bool use_graph = true;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace {
+
+template <typename T>
+T* P(char* p) { return reinterpret_cast<T*>(p); }
+
+char* dalloc(plsqr_ctx* h, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    ck(cudaMalloc(&p, bytes), "cudaMalloc");
+    h->allocs.push_back(p);
+    return (char*)p;
+}
+
+void dfree(plsqr_ctx* h, void* p) {
+    if (!p) return;
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+        if (*it == p) {
+            cudaFree(p);
+            h->allocs.erase(it);
+            return;
+        }
+}
+
+void clear_graphs(plsqr_ctx* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
+    h->graphs.clear();
+}
+
+// Installs the handle's profiler for the calling thread for the duration of a C-ABI call.
+struct ProfScope {
+    Profiler* prev;
+    explicit ProfScope(plsqr_ctx* h) : prev(current_profiler()) { current_profiler() = &h->prof; }
+    ~ProfScope() { current_profiler() = prev; }
+};
+
+Dims make_dims(int ndim, int64_t nx, int64_t ny, int64_t nz) {
+    Dims d;
+    d.ndim = ndim;
+    d.nx = (int32_t)nx;
+    d.ny = (int32_t)ny;
+    d.nz = ndim == 3 ? (int32_t)nz : 1;
+    d.N = (int64_t)d.nx * d.ny * d.nz;
+    return d;
+}
+
+// Sizes of everything create() allocates (used by plsqr_workspace_bytes too).
+struct Plan {
+    Dims d;
+    int L, nc, bw;
+    int64_t level_N[16];
+    size_t bytes;
+};
+
+Plan make_plan(const plsqr_config* c, int64_t m) {
+    if (!c) throw InvalidArg("config is NULL");
+    if (c->ndim != 2 && c->ndim != 3) throw InvalidArg("ndim must be 2 or 3");
+    if (c->precision != PLSQR_FP32 && c->precision != PLSQR_FP64) throw InvalidArg("bad precision");
+    if (c->mg_levels < 1 || c->mg_levels > 12) throw InvalidArg("mg_levels must be in 1..12");
+    if (c->mg_levels > 1 && (c->mg_sweeps < 1 || c->mg_sweeps > 16)) throw InvalidArg("mg_sweeps must be 1..16");
+    if (c->mg_cycles < 1 || c->mg_cycles > 16) throw InvalidArg("mg_cycles must be 1..16");
+    if (c->max_batch < 1 || c->max_batch > 4096) throw InvalidArg("max_batch must be 1..4096");
+    if (!(c->kappa_floor >= 0.0)) throw InvalidArg("kappa_floor must be >= 0");
+    const int64_t div = (int64_t)1 << (c->mg_levels - 1);
+    for (int dd = 0; dd < c->ndim; ++dd) {
+        if (c->n[dd] < 1 || c->n[dd] > (1 << 20)) throw InvalidArg("extent out of range");
+        if (c->n[dd] % div) throw InvalidArg("each extent must be divisible by 2^(mg_levels-1)");
+    }
+    Plan pl;
+    pl.d = make_dims(c->ndim, c->n[0], c->n[1], c->n[2]);
+    if (pl.d.N > ((int64_t)1 << 31)) throw InvalidArg("grid too large");
+    pl.L = c->mg_levels;
+    Dims dc = pl.d;
+    for (int l = 0; l < pl.L; ++l) {
+        if (l > 0) dc = make_dims(c->ndim, dc.nx / 2, dc.ny / 2, dc.nz / 2);
+        pl.level_N[l] = dc.N;
+    }
+    pl.nc = (int)dc.N;
+    pl.bw = c->ndim == 3 ? dc.nx * dc.ny : dc.nx;
+    if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
+    const size_t esz = c->precision == PLSQR_FP64 ? 8 : 4;
+    const int64_t B = c->max_batch, N = pl.d.N;
+    if (m <= 0) m = N;
+    size_t b = 0;
+    b += esz * B * (2 * m + 5 * N);  // g, u, f, p, v, w, kappa
+    b += esz * B * (N + m);          // tmp (N), tmpm (m)
+    if (c->mg_cycles > 1) b += esz * B * 2 * N;
+    for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 2);
+    b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 1);
+    b += sizeof(double) * B * (size_t)pl.nc * pl.nc;
+    b += (sizeof(GkState) + sizeof(SolveParams) + sizeof(unsigned)) * B;
+    b += sizeof(double) * B * 8192;
+    pl.bytes = b;
+    return pl;
+}
+
+int64_t op_data_len(const plsqr_operator* op, const Dims& d) {
+    if (op && op->kind == PLSQR_OP_JOSEPH) return (int64_t)op->n_angles * op->n_bins;
+    return d.N;
+}
+
+void alloc_data_buffers(plsqr_ctx* h) {
+    const int64_t B = h->B, m = h->m;
+    dfree(h, h->g);
+    dfree(h, h->u);
+    dfree(h, h->tmpm);
+    h->g = dalloc(h, h->esz * B * m);
+    h->u = dalloc(h, h->esz * B * m);
+    h->tmpm = dalloc(h, h->esz * B * m);
+}
+
+// ---- the order of the kernels ----------------------------------------------------------------
+
+template <typename T>
+void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
+    const Level& Lv = h->lv[l];
+    const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
+    const bool isk = l == 0;
+    if (l == h->L - 1) {
+        coarse_symv<T>(h->X, b, x, h->nc, B, s);
+        return;
+    }
+    for (int k = 0; k < h->nu; ++k) {
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, k == 0, B, s);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s);
+    }
+    const Level& C = h->lv[l + 1];
+    mg_resid_restrict<T>(cond, isk, b, x, P<T>(C.b), Lv.d, C.d, B, s);
+    vcycle<T>(h, l + 1, P<T>(C.b), P<T>(C.x), B, s);
+    mg_prolong_add<T>(P<T>(C.x), x, Lv.d, C.d, B, s);
+    for (int k = 0; k < h->nu; ++k) {
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, false, B, s);
+    }
+}
+
+// x = P b: `cycles` V-cycles from zero, x <- x + V(b - M x).
+template <typename T>
+void prec_apply(plsqr_ctx* h, const T* b, T* x, int B, cudaStream_t s) {
+    vcycle<T>(h, 0, b, x, B, s);
+    for (int c = 1; c < h->cycles; ++c) {
+        mg_apply_level<T>(P<T>(h->kappa), true, x, b, P<T>(h->r0), h->d, B, s);
+        vcycle<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, s);
+        mg_axpy<T>(x, P<T>(h->e0), (int64_t)B * h->d.N, s);
+    }
+}
+
+// Coarse conductances, band of the coarsest operator, its Cholesky factor and inverse.
+template <typename T>
+void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
+    for (int l = 0; l + 1 < h->L; ++l)
+        mg_coarsen<T>(l == 0 ? P<T>(h->kappa) : P<T>(h->lv[l].cond), l == 0, P<T>(h->lv[l + 1].cond), h->lv[l].d,
+                      h->lv[l + 1].d, B, s);
+    const int lc = h->L - 1;
+    coarse_assemble<T>(lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond), lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
+    coarse_cholesky(h->band, h->nc, h->bw, B, s);
+    coarse_inverse(h->band, h->X, h->nc, h->bw, B, s);
+}
+
+Hist hist_of(plsqr_ctx* h) {
+    Hist hs;
+    hs.rbar = h->h_rbar;
+    hs.R = h->h_R;
+    hs.resid = h->h_resid;
+    hs.n_outer = h->h_outer;
+    hs.n_inner = h->h_inner;
+    return hs;
+}
+
+// MLSQR (Algorithm 2) from f = 0 with the current priorconditioner.
+template <typename T>
+void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
+    const int64_t N = h->d.N;
+    Hist hs = hist_of(h);
+    T *g = P<T>(h->g), *u = P<T>(h->u), *p = P<T>(h->p), *v = P<T>(h->v), *w = P<T>(h->w), *f = P<T>(h->f);
+    T* tmp = P<T>(h->tmp);
+    gk_init_norm<T>(g, h->m, B, h->st, h->red, s);                                  // steps 2, 7
+    op_apply<T>(h->od, true, EPI_ADJ_INIT, g, p, nullptr, tmp, B, h->st, h->red, s);  // step 3
+    prec_apply<T>(h, p, v, B, s);                                                   // step 4
+    gk_dot_rotate<T>(v, p, N, B, true, h->st, hs, h->red, s);                       // steps 5-6
+    gk_update<T>(f, w, v, N, B, true, h->st, s);                                    // step 7
+    for (int i = 1; i <= n_inner; ++i) {
+        op_apply<T>(h->od, false, EPI_FWD, v, u, i == 1 ? g : u, tmp, B, h->st, h->red, s);  // step 10
+        op_apply<T>(h->od, true, EPI_ADJ, u, p, p, tmp, B, h->st, h->red, s);                // step 11
+        prec_apply<T>(h, p, v, B, s);                                                        // step 12
+        gk_dot_rotate<T>(v, p, N, B, false, h->st, hs, h->red, s);                           // 13-17
+        gk_update<T>(f, w, v, N, B, false, h->st, s);                                        // 19-20
+    }
+}
+
+// One outer step of Algorithm 3.
+template <typename T>
+void outer_step(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
+    Hist hs = hist_of(h);
+    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, B, h->st, hs, h->kfloor, h->red, s);  // step 3
+    prec_setup<T>(h, B, s);
+    mlsqr_seq<T>(h, B, n_inner, s);  // step 4
+    op_apply<T>(h->od, false, EPI_PLAIN, P<T>(h->f), P<T>(h->tmpm), nullptr, P<T>(h->tmp), B, h->st, h->red, s);
+    resid_norm<T>(P<T>(h->g), P<T>(h->tmpm), h->m, B, h->st, hs, h->red, s);
+}
+
+void ensure_hist(plsqr_ctx* h, int n_outer, int n_inner) {
+    if (n_outer <= h->h_outer && n_inner == h->h_inner && h->h_rbar) return;
+    clear_graphs(h);
+    dfree(h, h->h_rbar);
+    dfree(h, h->h_R);
+    dfree(h, h->h_resid);
+    const int64_t B = h->B;
+    h->h_outer = std::max(n_outer, 1);
+    h->h_inner = std::max(n_inner, 1);
+    h->h_rbar = (double*)dalloc(h, sizeof(double) * B * h->h_outer * h->h_inner);
+    h->h_R = (double*)dalloc(h, sizeof(double) * B * (h->h_outer + 1));
+    h->h_resid = (double*)dalloc(h, sizeof(double) * B * h->h_outer);
+    size_t need = (size_t)B * h->h_outer * h->h_inner + (size_t)B * (h->h_outer + 1) + (size_t)B * h->h_outer;
+    if (need > h->h_stage_n) {
+        if (h->h_stage) cudaFreeHost(h->h_stage);
+        h->h_stage = nullptr;
+        ck(cudaMallocHost((void**)&h->h_stage, need * sizeof(double)), "cudaMallocHost");
+        h->h_stage_n = need;
+    }
+}
+
+template <typename T>
+void run_outer_steps(plsqr_ctx* h, int B, int n_outer, int n_inner) {
+    cudaStream_t s = h->stream;
+    if (!h->use_graph || h->prof.enabled) {
+        for (int k = 0; k < n_outer; ++k) outer_step<T>(h, B, n_inner, s);
+        return;
+    }
+    auto key = std::make_tuple(B, n_inner, h->h_outer, h->h_inner);
+    auto it = h->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    int64_t per_replay = 0;
+    if (it == h->graphs.end()) {
+        const int64_t before = h->prof.launches;
+        cudaGraph_t graph = nullptr;
+        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+        try {
+            outer_step<T>(h, B, n_inner, s);
+        } catch (...) {
+            cudaStreamEndCapture(s, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        ck(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        ck(e, "cudaGraphInstantiate");
+        per_replay = h->prof.launches - before;  // captured, not yet executed
+        h->prof.launches = before;
+        h->graphs[key] = std::make_pair(exec, per_replay);
+    } else {
+        exec = it->second.first;
+        per_replay = it->second.second;
+    }
+    for (int k = 0; k < n_outer; ++k) ck(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+    h->prof.launches += per_replay * n_outer;
+}
+
+void validate_solve(plsqr_ctx* h, int count, const int32_t* reg, const double* T, const double* tau, int n_outer,
+                    int n_inner) {
+    if (!h->op_set) throw std::logic_error("set_operator must be called before a solve");
+    if (count < 1 || count > h->B) throw InvalidArg("count must be in 1..max_batch");
+    if (n_outer < 1 || n_outer > 100000 || n_inner < 1 || n_inner > 100000) throw InvalidArg("bad iteration counts");
+    for (int b = 0; b < count; ++b) {
+        if (reg[b] < 0 || reg[b] > 3) throw InvalidArg("bad regulariser");
+        if (!(T[b] > 0.0) || !std::isfinite(T[b])) throw InvalidArg("T must be positive and finite");
+        if (!(tau[b] >= 0.0) || !std::isfinite(tau[b])) throw InvalidArg("tau must be >= 0 and finite");
+    }
+}
+
+template <typename T>
+int solve_impl(plsqr_ctx* h, int count, const void* const* g, bool g_host, const int32_t* reg, const double* Tp,
+               const double* tau, int n_outer, int n_inner, void* const* f_out, bool f_host, plsqr_stats* stats) {
+    validate_solve(h, count, reg, Tp, tau, n_outer, n_inner);
+    ensure_hist(h, n_outer, n_inner);
+    cudaStream_t s = h->stream;
+    const int64_t launches0 = h->prof.launches;
+    ck(cudaEventRecord(h->ev_in, h->user_stream), "cudaEventRecord");
+    ck(cudaStreamWaitEvent(s, h->ev_in, 0), "cudaStreamWaitEvent");
+    const size_t mb = h->esz * h->m, nb = h->esz * h->d.N;
+    for (int b = 0; b < count; ++b) {
+        if (!g[b]) throw InvalidArg("g is NULL");
+        ck(cudaMemcpyAsync(h->g + b * mb, g[b], mb, g_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s),
+           "copy g");
+    }
+    for (int b = 0; b < count; ++b) {
+        h->prm_host[b].reg = reg[b];
+        h->prm_host[b].T = Tp[b];
+        h->prm_host[b].tau = tau[b];
+    }
+    ck(cudaMemcpyAsync(h->prm_dev, h->prm_host, sizeof(SolveParams) * count, cudaMemcpyHostToDevice, s), "params");
+    set_params(h->st, h->prm_dev, count, true, s);
+    ck(cudaMemsetAsync(h->f, 0, nb * count, s), "f0");  // f^0 = 0
+    const int64_t hb = (int64_t)h->B;
+    fill_nan(h->h_rbar, hb * h->h_outer * h->h_inner, s);
+    fill_nan(h->h_R, hb * (h->h_outer + 1), s);
+    fill_nan(h->h_resid, hb * h->h_outer, s);
+    run_outer_steps<T>(h, count, n_outer, n_inner);
+    // R(f^n_outer) (the outer counter now equals n_outer)
+    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, count, h->st, hist_of(h), h->kfloor, h->red, s);
+    for (int b = 0; b < count; ++b) {
+        if (!f_out[b]) throw InvalidArg("f_out is NULL");
+        ck(cudaMemcpyAsync(f_out[b], h->f + b * nb, nb, f_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
+           "copy f");
+    }
+    ck(cudaMemcpyAsync(h->st_host, h->st, sizeof(GkState) * count, cudaMemcpyDeviceToHost, s), "state");
+    h->last_launches = h->prof.launches - launches0;
+    ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
+    ck(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "cudaStreamWaitEvent");
+    int ret = PLSQR_OK;
+    if (stats || f_host) {
+        const int64_t nr = hb * h->h_outer * h->h_inner, nR = hb * (h->h_outer + 1), ne = hb * h->h_outer;
+        if (stats) {
+            ck(cudaMemcpyAsync(h->h_stage, h->h_rbar, sizeof(double) * nr, cudaMemcpyDeviceToHost, s), "hist");
+            ck(cudaMemcpyAsync(h->h_stage + nr, h->h_R, sizeof(double) * nR, cudaMemcpyDeviceToHost, s), "hist");
+            ck(cudaMemcpyAsync(h->h_stage + nr + nR, h->h_resid, sizeof(double) * ne, cudaMemcpyDeviceToHost, s),
+               "hist");
+        }
+        ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        for (int b = 0; b < count; ++b) {
+            int sb = h->st_host[b].status_any;
+            if (sb != 0) ret = PLSQR_E_BREAKDOWN;
+            if (!stats) continue;
+            plsqr_stats& S = stats[b];
+            S.status = sb;
+            if (S.rbar_hist)
+                for (int k = 0; k < n_outer; ++k)
+                    std::memcpy(S.rbar_hist + (int64_t)k * n_inner,
+                                h->h_stage + ((int64_t)b * h->h_outer + k) * h->h_inner, sizeof(double) * n_inner);
+            if (S.R_hist)
+                std::memcpy(S.R_hist, h->h_stage + nr + (int64_t)b * (h->h_outer + 1), sizeof(double) * (n_outer + 1));
+            if (S.resid_hist)
+                std::memcpy(S.resid_hist, h->h_stage + nr + nR + (int64_t)b * h->h_outer, sizeof(double) * n_outer);
+        }
+    }
+    return ret;
+}
+
+int fail(plsqr_ctx* h, int code, const char* msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+template <typename F>
+int guarded(plsqr_ctx* h, F&& fn) {
+    ProfScope scope(h);
+    try {
+        return fn();
+    } catch (const InvalidArg& e) {
+        return fail(h, PLSQR_E_INVALID, e.what());
+    } catch (const NoMem& e) {
+        return fail(h, PLSQR_E_NOMEM, e.what());
+    } catch (const CudaError& e) {
+        return fail(h, PLSQR_E_CUDA, e.what());
+    } catch (const std::logic_error& e) {
+        return fail(h, PLSQR_E_STATE, e.what());
+    } catch (const std::exception& e) {
+        return fail(h, PLSQR_E_CUDA, e.what());
+    }
+}
+
+void destroy_ctx(plsqr_ctx* h) {
+    if (!h) return;
+    clear_graphs(h);
+    h->prof.release();
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->prm_host) cudaFreeHost(h->prm_host);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+template <typename T>
+void upload_taps(plsqr_ctx* h, int dd, double sigma, int R) {
+    std::vector<double> w(2 * R + 1);
+    double s = 0.0;
+    for (int k = -R; k <= R; ++k) s += (w[k + R] = std::exp(-(double)(k * k) / (2.0 * sigma * sigma)));
+    std::vector<T> wt(2 * R + 1);
+    for (int k = 0; k <= 2 * R; ++k) wt[k] = (T)(w[k] / s);
+    dfree(h, h->taps[dd]);
+    h->taps[dd] = dalloc(h, sizeof(T) * wt.size());
+    ck(cudaMemcpy(h->taps[dd], wt.data(), sizeof(T) * wt.size(), cudaMemcpyHostToDevice), "taps");
+}
+
+template <typename T>
+void upload_joseph(plsqr_ctx* h, int na, double ds) {
+    std::vector<JosephAngle<T>> tab(na);
+    for (int a = 0; a < na; ++a) {
+        const double th = kPi * (double)a / (double)na;
+        const double ct = std::cos(th), st = std::sin(th);
+        const bool rows = (4 * a < na) || (4 * a > 3 * na);
+        const double hh = rows ? std::fabs(ct) : std::fabs(st);
+        JosephAngle<T>& J = tab[a];
+        J.a1 = (T)(rows ? 1.0 / ct : 1.0 / st);
+        J.a2 = (T)(rows ? st / ct : ct / st);
+        J.c1 = (T)(ct / ds);
+        J.c2 = (T)(st / ds);
+        J.hw = (T)(hh / ds);
+        J.inv_hw = (T)(ds / hh);
+        J.wgt = (T)(1.0 / hh);
+        J.rows = rows ? 1 : 0;
+    }
+    dfree(h, h->jtab);
+    h->jtab = dalloc(h, sizeof(JosephAngle<T>) * na);
+    ck(cudaMemcpy(h->jtab, tab.data(), sizeof(JosephAngle<T>) * na, cudaMemcpyHostToDevice), "joseph table");
+}
+
+// Dispatch on the bulk type.
+template <typename F>
+void by_type(plsqr_ctx* h, F&& fn) {
+    if (h->fp64) fn(double{});
+    else fn(float{});
+}
+
+}  // namespace
+
+extern "C" {
+
+int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
+    if (!out) return PLSQR_E_INVALID;
+    *out = nullptr;
+    plsqr_ctx* h = new plsqr_ctx();
+    int rc = guarded(h, [&]() -> int {
+        Plan pl = make_plan(cfg, 0);
+        h->cfg = *cfg;
+        h->user_stream = (cudaStream_t)stream;
+        h->fp64 = cfg->precision == PLSQR_FP64;
+        h->esz = h->fp64 ? 8 : 4;
+        h->d = pl.d;
+        h->B = cfg->max_batch;
+        h->L = pl.L;
+        h->nu = cfg->mg_sweeps;
+        h->cycles = cfg->mg_cycles;
+        h->kfloor = cfg->kappa_floor;
+        h->nc = pl.nc;
+        h->bw = pl.bw;
+        h->m = h->d.N;
+        const char* eg = std::getenv("PLSQR_GRAPH");
+        h->use_graph = !(eg && eg[0] == '0');
+        ck(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+        const int64_t B = h->B, N = h->d.N;
+        const size_t e = h->esz;
+        h->f = dalloc(h, e * B * N);
+        h->p = dalloc(h, e * B * N);
+        h->v = dalloc(h, e * B * N);
+        h->w = dalloc(h, e * B * N);
+        h->kappa = dalloc(h, e * B * N);
+        h->tmp = dalloc(h, e * B * N);
+        if (h->cycles > 1) {
+            h->r0 = dalloc(h, e * B * N);
+            h->e0 = dalloc(h, e * B * N);
+        }
+        alloc_data_buffers(h);
+        h->lv[0].d = h->d;
+        for (int l = 1; l < h->L; ++l) {
+            const Dims& pd = h->lv[l - 1].d;
+            h->lv[l].d = make_dims(h->d.ndim, pd.nx / 2, pd.ny / 2, pd.nz / 2);
+            const int64_t Nl = h->lv[l].d.N;
+            h->lv[l].cond = dalloc(h, e * B * Nl * h->d.ndim);
+            h->lv[l].b = dalloc(h, e * B * Nl);
+            h->lv[l].x = dalloc(h, e * B * Nl);
+        }
+        h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
+        h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
+        h->st = (GkState*)dalloc(h, sizeof(GkState) * B);
+        ck(cudaMemset(h->st, 0, sizeof(GkState) * B), "memset");
+        h->prm_dev = (SolveParams*)dalloc(h, sizeof(SolveParams) * B);
+        ck(cudaMallocHost((void**)&h->prm_host, sizeof(SolveParams) * B), "cudaMallocHost");
+        ck(cudaMallocHost((void**)&h->st_host, sizeof(GkState) * B), "cudaMallocHost");
+        h->red.max_blocks = 8192;
+        h->red.partials = (double*)dalloc(h, sizeof(double) * B * h->red.max_blocks);
+        h->red.counters = (unsigned*)dalloc(h, sizeof(unsigned) * B);
+        ck(cudaMemset(h->red.counters, 0, sizeof(unsigned) * B), "memset");
+        ck(cudaDeviceSynchronize(), "create");
+        return PLSQR_OK;
+    });
+    if (rc != PLSQR_OK) {
+        std::fprintf(stderr, "plsqr_create: %s\n", h->err.c_str());
+        destroy_ctx(h);
+        return rc;
+    }
+    *out = h;
+    return PLSQR_OK;
+}
+
+int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!op) throw InvalidArg("operator is NULL");
+        const Dims& d = h->d;
+        OpDev od{};
+        od.d = d;
+        od.kind = op->kind;
+        if (op->kind == PLSQR_OP_BLUR || op->kind == PLSQR_OP_BLUR_MASK) {
+            for (int dd = 0; dd < d.ndim; ++dd) {
+                if (!(op->sigma[dd] > 0.0) || op->radius[dd] < 0 || op->radius[dd] > 32)
+                    throw InvalidArg("blur needs sigma > 0 and 0 <= radius <= 32 on every axis");
+            }
+            if (op->kind == PLSQR_OP_BLUR_MASK && !op->mask) throw InvalidArg("masked blur needs a mask");
+        } else if (op->kind == PLSQR_OP_JOSEPH) {
+            if (d.ndim != 2 || d.nx != d.ny) throw InvalidArg("Joseph projector needs a square 2D image");
+            if (op->n_angles < 1 || op->n_angles > 100000 || op->n_bins < 1 || op->n_bins > (1 << 20))
+                throw InvalidArg("bad Joseph geometry");
+            if (!(op->bin_spacing > 0.0)) throw InvalidArg("bin_spacing must be > 0");
+        } else if (op->kind != PLSQR_OP_IDENTITY) {
+            throw InvalidArg("unknown operator kind");
+        }
+        clear_graphs(h);
+        const int64_t m_new = op_data_len(op, d);
+        if (m_new != h->m || !h->g) {
+            h->m = m_new;
+            alloc_data_buffers(h);
+        }
+        od.m = h->m;
+        if (op->kind == PLSQR_OP_BLUR || op->kind == PLSQR_OP_BLUR_MASK) {
+            by_type(h, [&](auto tv) {
+                using T = decltype(tv);
+                for (int dd = 0; dd < d.ndim; ++dd) upload_taps<T>(h, dd, op->sigma[dd], op->radius[dd]);
+            });
+            for (int dd = 0; dd < d.ndim; ++dd) {
+                od.taps[dd] = h->taps[dd];
+                od.R[dd] = op->radius[dd];
+            }
+            if (op->kind == PLSQR_OP_BLUR_MASK) {
+                if (!h->mask) h->mask = (uint8_t*)dalloc(h, (size_t)d.N);
+                ck(cudaMemcpy(h->mask, op->mask, (size_t)d.N, cudaMemcpyDefault), "mask");
+                od.mask = h->mask;
+            }
+        } else if (op->kind == PLSQR_OP_JOSEPH) {
+            by_type(h, [&](auto tv) {
+                using T = decltype(tv);
+                upload_joseph<T>(h, op->n_angles, op->bin_spacing);
+            });
+            od.jtab = h->jtab;
+            od.na = op->n_angles;
+            od.nb = op->n_bins;
+            od.ds = op->bin_spacing;
+        }
+        h->od = od;
+        h->op = *op;
+        h->op_set = true;
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_solve(plsqr_handle h, const void* g, int32_t reg, double T, double tau, int32_t n_outer, int32_t n_inner,
+                void* f_out, plsqr_stats* stats) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        int rc = 0;
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            rc = solve_impl<TT>(h, 1, &g, false, &reg, &T, &tau, n_outer, n_inner, &f_out, false, stats);
+        });
+        return rc;
+    });
+}
+
+int plsqr_solve_host(plsqr_handle h, const void* g_host, int32_t reg, double T, double tau, int32_t n_outer,
+                     int32_t n_inner, void* f_host_out, plsqr_stats* stats) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        int rc = 0;
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            rc = solve_impl<TT>(h, 1, &g_host, true, &reg, &T, &tau, n_outer, n_inner, &f_host_out, true, stats);
+        });
+        return rc;
+    });
+}
+
+int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const int32_t* reg, const double* T,
+                      const double* tau, int32_t n_outer, int32_t n_inner, void* const* f_out, plsqr_stats* stats) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!g || !reg || !T || !tau || !f_out) throw InvalidArg("NULL array argument");
+        int rc = 0;
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            rc = solve_impl<TT>(h, count, g, false, reg, T, tau, n_outer, n_inner, f_out, false, stats);
+        });
+        return rc;
+    });
+}
+
+void plsqr_destroy(plsqr_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    destroy_ctx(h);
+}
+
+const char* plsqr_last_error(plsqr_handle h) {
+    if (!h) return "invalid handle";
+    return h->err.c_str();
+}
+
+int64_t plsqr_workspace_bytes(const plsqr_config* cfg, const plsqr_operator* op) {
+    try {
+        Plan pl = make_plan(cfg, 0);
+        int64_t m = op_data_len(op, pl.d);
+        return (int64_t)make_plan(cfg, m).bytes;
+    } catch (...) {
+        return -1;
+    }
+}
+
+int plsqr_apply_A(plsqr_handle h, const void* x, void* y) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!h->op_set) throw std::logic_error("set_operator first");
+        if (!x || !y) throw InvalidArg("NULL pointer");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            op_apply<T>(h->od, false, EPI_PLAIN, (const T*)x, (T*)y, nullptr, P<T>(h->tmp), 1, h->st, h->red,
+                        h->user_stream);
+        });
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_apply_At(plsqr_handle h, const void* y, void* x) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!h->op_set) throw std::logic_error("set_operator first");
+        if (!x || !y) throw InvalidArg("NULL pointer");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            op_apply<T>(h->od, true, EPI_PLAIN, (const T*)y, (T*)x, nullptr, P<T>(h->tmp), 1, h->st, h->red,
+                        h->user_stream);
+        });
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_diffusivity(plsqr_handle h, const void* f, int32_t reg, double T, void* kappa_out, double* R_out) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!f || !kappa_out) throw InvalidArg("NULL pointer");
+        if (reg < 0 || reg > 3) throw InvalidArg("bad regulariser");
+        if (!(T > 0.0) || !std::isfinite(T)) throw InvalidArg("T must be positive and finite");
+        cudaStream_t s = h->user_stream;
+        h->prm_host[0].reg = reg;
+        h->prm_host[0].T = T;
+        h->prm_host[0].tau = 0.0;
+        ck(cudaMemcpyAsync(h->prm_dev, h->prm_host, sizeof(SolveParams), cudaMemcpyHostToDevice, s), "params");
+        set_params(h->st, h->prm_dev, 1, true, s);
+        Hist hs{};
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            diffusivity<TT>((const TT*)f, (TT*)kappa_out, h->d, 1, h->st, hs, h->kfloor, h->red, s);
+        });
+        ck(cudaMemcpyAsync(h->st_host, h->st, sizeof(GkState), cudaMemcpyDeviceToHost, s), "state");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (R_out) *R_out = h->st_host[0].R;
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_prec_setup(plsqr_handle h, const void* kappa) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!kappa) throw InvalidArg("NULL pointer");
+        cudaStream_t s = h->user_stream;
+        ck(cudaMemcpyAsync(h->kappa, kappa, h->esz * h->d.N, cudaMemcpyDeviceToDevice, s), "kappa");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            prec_setup<T>(h, 1, s);
+        });
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_prec_apply(plsqr_handle h, const void* b, void* x) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!b || !x) throw InvalidArg("NULL pointer");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            prec_apply<T>(h, (const T*)b, (T*)x, 1, h->user_stream);
+        });
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_apply_M(plsqr_handle h, const void* x, void* y) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!x || !y) throw InvalidArg("NULL pointer");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            mg_apply_level<T>(P<T>(h->kappa), true, (const T*)x, nullptr, (T*)y, h->d, 1, h->user_stream);
+        });
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void* f_out, double* rbar_hist,
+                int32_t* iters_done) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        int32_t reg = 0;
+        double T = 1.0;
+        validate_solve(h, 1, &reg, &T, &tau, 1, n_inner);
+        if (!g || !f_out) throw InvalidArg("NULL pointer");
+        ensure_hist(h, 1, n_inner);
+        cudaStream_t s = h->user_stream;
+        ck(cudaMemcpyAsync(h->g, g, h->esz * h->m, cudaMemcpyDeviceToDevice, s), "g");
+        h->prm_host[0].reg = reg;
+        h->prm_host[0].T = T;
+        h->prm_host[0].tau = tau;
+        ck(cudaMemcpyAsync(h->prm_dev, h->prm_host, sizeof(SolveParams), cudaMemcpyHostToDevice, s), "params");
+        set_params(h->st, h->prm_dev, 1, true, s);
+        fill_nan(h->h_rbar, (int64_t)h->B * h->h_outer * h->h_inner, s);
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            mlsqr_seq<TT>(h, 1, n_inner, s);
+        });
+        ck(cudaMemcpyAsync(f_out, h->f, h->esz * h->d.N, cudaMemcpyDeviceToDevice, s), "f");
+        ck(cudaMemcpyAsync(h->st_host, h->st, sizeof(GkState), cudaMemcpyDeviceToHost, s), "state");
+        if (rbar_hist)
+            ck(cudaMemcpyAsync(h->h_stage, h->h_rbar, sizeof(double) * n_inner, cudaMemcpyDeviceToHost, s), "hist");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (rbar_hist) std::memcpy(rbar_hist, h->h_stage, sizeof(double) * n_inner);
+        if (iters_done) *iters_done = h->st_host[0].iter;
+        return h->st_host[0].status != 0 ? PLSQR_E_BREAKDOWN : PLSQR_OK;
+    });
+}
+
+int plsqr_profile(plsqr_handle h, int32_t enable) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "sync");
+        ck(cudaStreamSynchronize(h->user_stream), "sync");
+        h->prof.collect();
+        for (int c = 0; c < KC_COUNT; ++c) {
+            h->prof.ms[c] = 0.0;
+            h->prof.count[c] = 0;
+        }
+        h->prof.enabled = enable != 0;
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        h->prof.collect();
+        for (int c = 0; c < n && c < KC_COUNT; ++c) {
+            if (ms) ms[c] = h->prof.ms[c];
+            if (counts) counts[c] = h->prof.count[c];
+        }
+        return PLSQR_OK;
+    });
+}
+
+int64_t plsqr_last_launches(plsqr_handle h) { return h ? h->last_launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+"""Python binding of libplsqr (include/plsqr.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors (device
+memory) and numpy arrays (host memory) to pointers and checks shapes and dtypes.  The
+functions keep the C names (plsqr_create, plsqr_solve, ...); ``Solver`` wraps a handle.
+If the library is missing this module raises instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libplsqr.so")
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_STATE = range(7)
+REG = {"tikhonov": 0, "tv": 1, "pm_log": 2, "pm_exp": 3}
+OP = {"blur": 0, "blur_mask": 1, "joseph": 2, "identity": 3}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class PlsqrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"plsqr error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64 * 3),
+                ("mg_levels", C.c_int32), ("mg_sweeps", C.c_int32), ("mg_cycles", C.c_int32),
+                ("max_batch", C.c_int32), ("kappa_floor", C.c_double)]
+
+
+class OperatorDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_angles", C.c_int32), ("n_bins", C.c_int32), ("reserved", C.c_int32),
+                ("sigma", C.c_double * 3), ("radius", C.c_int32 * 3), ("reserved2", C.c_int32),
+                ("bin_spacing", C.c_double), ("mask", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rbar_hist", C.c_void_p), ("R_hist", C.c_void_p), ("resid_hist", C.c_void_p),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libplsqr.so (built by paper_1308_6634_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1308_6634_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, d, i64 = C.c_void_p, C.c_int32, C.c_double, C.c_int64
+    sig = {
+        "plsqr_create": ([C.POINTER(Config), vp, C.POINTER(vp)], C.c_int),
+        "plsqr_set_operator": ([vp, C.POINTER(OperatorDesc)], C.c_int),
+        "plsqr_solve": ([vp, vp, i32, d, d, i32, i32, vp, C.POINTER(Stats)], C.c_int),
+        "plsqr_solve_host": ([vp, vp, i32, d, d, i32, i32, vp, C.POINTER(Stats)], C.c_int),
+        "plsqr_solve_batch": ([vp, i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(d), C.POINTER(d), i32, i32,
+                               C.POINTER(vp), C.POINTER(Stats)], C.c_int),
+        "plsqr_destroy": ([vp], None),
+        "plsqr_last_error": ([vp], C.c_char_p),
+        "plsqr_workspace_bytes": ([C.POINTER(Config), C.POINTER(OperatorDesc)], i64),
+        "plsqr_apply_A": ([vp, vp, vp], C.c_int),
+        "plsqr_apply_At": ([vp, vp, vp], C.c_int),
+        "plsqr_diffusivity": ([vp, vp, i32, d, vp, C.POINTER(d)], C.c_int),
+        "plsqr_prec_setup": ([vp, vp], C.c_int),
+        "plsqr_prec_apply": ([vp, vp, vp], C.c_int),
+        "plsqr_apply_M": ([vp, vp, vp], C.c_int),
+        "plsqr_mlsqr": ([vp, vp, d, i32, vp, vp, C.POINTER(i32)], C.c_int),
+        "plsqr_profile": ([vp, i32], C.c_int),
+        "plsqr_profile_read": ([vp, vp, vp, i32], C.c_int),
+        "plsqr_last_launches": ([vp], i64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_host", "plsqr_solve_batch",
+            "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
+            "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
+            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches"]
+
+KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
+
+
+def _check(h, rc):
+    if rc != OK and rc != E_BREAKDOWN:
+        msg = lib().plsqr_last_error(h)
+        raise PlsqrError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dptr(t, dtype, numel=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_config(shape, precision="fp32", levels=1, sweeps=2, cycles=1, max_batch=1, kappa_floor=1e-4):
+    """shape: (ny, nx) or (nz, ny, nx)."""
+    c = Config()
+    c.ndim = len(shape)
+    c.precision = PREC[precision]
+    dims = list(reversed(shape)) + [1] * (3 - len(shape))
+    for k in range(3):
+        c.n[k] = int(dims[k])
+    c.mg_levels, c.mg_sweeps, c.mg_cycles = int(levels), int(sweeps), int(cycles)
+    c.max_batch = int(max_batch)
+    c.kappa_floor = float(kappa_floor)
+    return c
+
+
+def make_operator(kind, sigma=(0, 0, 0), radius=(0, 0, 0), mask=None, n_angles=0, n_bins=0, bin_spacing=1.0):
+    o = OperatorDesc()
+    o.kind = OP[kind]
+    sg = list(sigma) + [0.0] * (3 - len(sigma))
+    rd = list(radius) + [0] * (3 - len(radius))
+    for k in range(3):
+        o.sigma[k] = float(sg[k])
+        o.radius[k] = int(rd[k])
+    o.n_angles, o.n_bins, o.bin_spacing = int(n_angles), int(n_bins), float(bin_spacing)
+    o.mask = C.c_void_p(mask.data_ptr()) if mask is not None else None
+    return o
+
+
+def plsqr_create(config, stream=None):
+    h = C.c_void_p()
+    rc = lib().plsqr_create(C.byref(config), C.c_void_p(stream or 0), C.byref(h))
+    if rc != OK:
+        raise PlsqrError(rc, "plsqr_create failed")
+    return h
+
+
+def plsqr_workspace_bytes(config, op=None):
+    return lib().plsqr_workspace_bytes(C.byref(config), C.byref(op) if op is not None else None)
+
+
+def _current_stream():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Solver:
+    """One handle: a problem size, a forward map and the priorconditioner shape."""
+
+    def __init__(self, shape, precision="fp32", levels=1, sweeps=2, cycles=1, max_batch=1, kappa_floor=1e-4,
+                 stream=None):
+        torch = _torch()
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        self.config = make_config(self.shape, precision, levels, sweeps, cycles, max_batch, kappa_floor)
+        self.max_batch = max_batch
+        self.h = plsqr_create(self.config, stream if stream is not None else _current_stream())
+        self.data_shape = self.shape
+        self._mask = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().plsqr_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    @property
+    def m(self):
+        return int(np.prod(self.data_shape))
+
+    def set_operator(self, kind, sigma=(0, 0, 0), radius=(0, 0, 0), mask=None, n_angles=0, n_bins=0,
+                     bin_spacing=1.0):
+        torch = _torch()
+        if mask is not None:
+            mask = torch.as_tensor(np.ascontiguousarray(mask, dtype=np.uint8)).cuda() \
+                if not isinstance(mask, torch.Tensor) else mask.to(torch.uint8).contiguous().cuda()
+            self._mask = mask
+        o = make_operator(kind, sigma, radius, mask, n_angles, n_bins, bin_spacing)
+        _check(self.h, lib().plsqr_set_operator(self.h, C.byref(o)))
+        self.data_shape = (n_angles, n_bins) if kind == "joseph" else self.shape
+        return self
+
+    def _stats(self, n_outer, n_inner):
+        rbar = np.full((n_outer, n_inner), np.nan)
+        R = np.full(n_outer + 1, np.nan)
+        res = np.full(n_outer, np.nan)
+        st = Stats(rbar.ctypes.data, R.ctypes.data, res.ctypes.data, 0, 0)
+        return st, dict(rbar_hist=rbar, R_hist=R, resid_hist=res)
+
+    def solve(self, g, reg, T, tau, n_outer, n_inner, f_out=None, stats=True):
+        """Algorithm 3 on device data g; returns (f, info dict or None)."""
+        torch = _torch()
+        if f_out is None:
+            f_out = torch.empty(self.shape, dtype=self.dtype, device=g.device)
+        gp = _dptr(g, self.dtype, self.m)
+        fp = _dptr(f_out, self.dtype, self.N)
+        if stats:
+            st, info = self._stats(n_outer, n_inner)
+            rc = _check(self.h, lib().plsqr_solve(self.h, gp, REG[reg], float(T), float(tau), int(n_outer),
+                                                  int(n_inner), fp, C.byref(st)))
+            info["status"] = rc
+            return f_out, info
+        _check(self.h, lib().plsqr_solve(self.h, gp, REG[reg], float(T), float(tau), int(n_outer), int(n_inner),
+                                          fp, None))
+        return f_out, None
+
+    def solve_host(self, g, reg, T, tau, n_outer, n_inner, f_out=None, stats=False):
+        """Algorithm 3 on host data (numpy, ideally pinned); copies are part of the call."""
+        g = np.ascontiguousarray(g, dtype=self.np_dtype) if isinstance(g, np.ndarray) else g
+        if f_out is None:
+            f_out = np.empty(self.shape, dtype=self.np_dtype)
+        gp = C.c_void_p(g.ctypes.data if isinstance(g, np.ndarray) else g.data_ptr())
+        fp = C.c_void_p(f_out.ctypes.data if isinstance(f_out, np.ndarray) else f_out.data_ptr())
+        st, info = (self._stats(n_outer, n_inner) if stats else (None, None))
+        rc = _check(self.h, lib().plsqr_solve_host(self.h, gp, REG[reg], float(T), float(tau), int(n_outer),
+                                                   int(n_inner), fp, C.byref(st) if stats else None))
+        if info is not None:
+            info["status"] = rc
+        return f_out, info
+
+    def solve_batch(self, gs, regs, Ts, taus, n_outer, n_inner, f_outs=None, stats=True):
+        torch = _torch()
+        count = len(gs)
+        if f_outs is None:
+            f_outs = [torch.empty(self.shape, dtype=self.dtype, device=gs[0].device) for _ in range(count)]
+        garr = (C.c_void_p * count)(*[_dptr(g, self.dtype, self.m).value for g in gs])
+        farr = (C.c_void_p * count)(*[_dptr(f, self.dtype, self.N).value for f in f_outs])
+        rarr = (C.c_int32 * count)(*[REG[r] for r in regs])
+        tarr = (C.c_double * count)(*[float(t) for t in Ts])
+        uarr = (C.c_double * count)(*[float(t) for t in taus])
+        infos = None
+        sarr = None
+        if stats:
+            pairs = [self._stats(n_outer, n_inner) for _ in range(count)]
+            sarr = (Stats * count)(*[p[0] for p in pairs])
+            infos = [p[1] for p in pairs]
+        rc = _check(self.h, lib().plsqr_solve_batch(self.h, count, garr, rarr, tarr, uarr, int(n_outer),
+                                                    int(n_inner), farr, sarr))
+        if infos is not None:
+            for k, inf in enumerate(infos):
+                inf["status"] = sarr[k].status
+            return f_outs, infos
+        return f_outs, None
+
+    # ---- instrumentation ----
+    def profile(self, enable=True):
+        _check(self.h, lib().plsqr_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = (C.c_double * len(KCLASS))()
+        cnt = (C.c_int64 * len(KCLASS))()
+        _check(self.h, lib().plsqr_profile_read(self.h, ms, cnt, len(KCLASS)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KCLASS)}
+
+    def last_launches(self):
+        return int(lib().plsqr_last_launches(self.h))
+
+    # ---- single steps ----
+    def apply_A(self, x, y=None):
+        torch = _torch()
+        y = torch.empty(self.data_shape, dtype=self.dtype, device=x.device) if y is None else y
+        _check(self.h, lib().plsqr_apply_A(self.h, _dptr(x, self.dtype, self.N), _dptr(y, self.dtype, self.m)))
+        return y
+
+    def apply_At(self, y, x=None):
+        torch = _torch()
+        x = torch.empty(self.shape, dtype=self.dtype, device=y.device) if x is None else x
+        _check(self.h, lib().plsqr_apply_At(self.h, _dptr(y, self.dtype, self.m), _dptr(x, self.dtype, self.N)))
+        return x
+
+    def diffusivity(self, f, reg, T):
+        torch = _torch()
+        kappa = torch.empty(self.shape, dtype=self.dtype, device=f.device)
+        R = C.c_double(0.0)
+        _check(self.h, lib().plsqr_diffusivity(self.h, _dptr(f, self.dtype, self.N), REG[reg], float(T),
+                                               _dptr(kappa, self.dtype, self.N), C.byref(R)))
+        return kappa, R.value
+
+    def prec_setup(self, kappa):
+        _check(self.h, lib().plsqr_prec_setup(self.h, _dptr(kappa, self.dtype, self.N)))
+
+    def prec_apply(self, b, x=None):
+        torch = _torch()
+        x = torch.empty(self.shape, dtype=self.dtype, device=b.device) if x is None else x
+        _check(self.h, lib().plsqr_prec_apply(self.h, _dptr(b, self.dtype, self.N), _dptr(x, self.dtype, self.N)))
+        return x
+
+    def apply_M(self, x, y=None):
+        torch = _torch()
+        y = torch.empty(self.shape, dtype=self.dtype, device=x.device) if y is None else y
+        _check(self.h, lib().plsqr_apply_M(self.h, _dptr(x, self.dtype, self.N), _dptr(y, self.dtype, self.N)))
+        return y
+
+    def mlsqr(self, g, tau, n_inner):
+        torch = _torch()
+        f = torch.empty(self.shape, dtype=self.dtype, device=g.device)
+        hist = np.full(n_inner, np.nan)
+        it = C.c_int32(0)
+        rc = _check(self.h, lib().plsqr_mlsqr(self.h, _dptr(g, self.dtype, self.m), float(tau), int(n_inner),
+                                              _dptr(f, self.dtype, self.N), C.c_void_p(hist.ctypes.data),
+                                              C.byref(it)))
+        return f, hist[:it.value], rc

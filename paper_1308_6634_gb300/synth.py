@@ -18,37 +18,47 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
-def _centres(rng, n, k):
-    return rng.uniform(0.1 * n, 0.9 * n, size=k)
+def _shape2(n):
+    return (int(n), int(n)) if np.isscalar(n) else (int(n[0]), int(n[1]))
+
+
+def _centre(rng, ny, nx):
+    """Uniform centre in the inner 80% of each axis (x, y)."""
+    u = rng.uniform(0.1, 0.9, size=2)
+    return u[0] * nx, u[1] * ny
 
 
 def phantom_rects_disks(n, n_rect, n_disk, seed):
-    """2D (n, n) piecewise-constant image of axis-aligned rectangles then disks."""
+    """2D piecewise-constant image (n or (ny, nx)) of axis-aligned rectangles then disks."""
     rng = np.random.default_rng(seed)
-    img = np.zeros((n, n))
-    yy, xx = np.mgrid[0:n, 0:n] + 0.5
+    ny, nx = _shape2(n)
+    s = min(ny, nx)
+    img = np.zeros((ny, nx))
+    yy, xx = np.mgrid[0:ny, 0:nx] + 0.5
     for _ in range(n_rect):
-        cx, cy = _centres(rng, n, 2)
-        wx, wy = rng.uniform(0.05 * n, 0.4 * n, size=2)
+        cx, cy = _centre(rng, ny, nx)
+        wx, wy = rng.uniform(0.05, 0.4, size=2) * np.array([nx, ny])
         val = rng.uniform(0.0, 1.0)
         inside = (np.abs(xx - cx) <= 0.5 * wx) & (np.abs(yy - cy) <= 0.5 * wy)
         img[inside] = val
     for _ in range(n_disk):
-        cx, cy = _centres(rng, n, 2)
-        r = rng.uniform(0.03 * n, 0.15 * n)
+        cx, cy = _centre(rng, ny, nx)
+        r = rng.uniform(0.03, 0.15) * s
         val = rng.uniform(0.0, 1.0)
         img[(xx - cx) ** 2 + (yy - cy) ** 2 <= r * r] = val
     return img
 
 
 def phantom_ellipses(n, count, seed):
-    """2D (n, n) image of rotated ellipses (tomography phantom)."""
+    """2D image (n or (ny, nx)) of rotated ellipses (tomography phantom)."""
     rng = np.random.default_rng(seed)
-    img = np.zeros((n, n))
-    yy, xx = np.mgrid[0:n, 0:n] + 0.5
+    ny, nx = _shape2(n)
+    s = min(ny, nx)
+    img = np.zeros((ny, nx))
+    yy, xx = np.mgrid[0:ny, 0:nx] + 0.5
     for _ in range(count):
-        cx, cy = _centres(rng, n, 2)
-        a, b = rng.uniform(0.05 * n, 0.3 * n, size=2)
+        cx, cy = _centre(rng, ny, nx)
+        a, b = rng.uniform(0.05, 0.3, size=2) * s
         phi = rng.uniform(0.0, np.pi)
         val = rng.uniform(0.0, 1.0)
         dx, dy = xx - cx, yy - cy
@@ -128,9 +138,9 @@ class Workload:
     def phantom_image(self, seed):
         p = self.phantom
         if p["type"] == "rects_disks":
-            return phantom_rects_disks(self.shape[-1], p["rects"], p["disks"], seed)
+            return phantom_rects_disks(self.shape, p["rects"], p["disks"], seed)
         if p["type"] == "ellipses":
-            return phantom_ellipses(self.shape[-1], p["count"], seed)
+            return phantom_ellipses(self.shape, p["count"], seed)
         if p["type"] == "ellipsoids":
             return phantom_ellipsoids(self.shape, p["count"], seed)
         raise ValueError(p["type"])

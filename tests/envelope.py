@@ -1,0 +1,130 @@
+"""Rounding envelopes for long-horizon parity (test infrastructure).
+
+Priorconditioned LSQR on these ill-posed problems is rounding-chaotic after a few tens of
+iterations: perturbing the oracle's own input g by one part in 1e16 moves its 50-iteration
+iterate on the 1024x1024 deblurring workload by about 1e-3 (see test_oracle_sensitivity).
+Two correct implementations that round differently therefore cannot agree better than that
+spread, so long-horizon parity is asserted against it:
+
+  fp64 handles: E = max_k relerr(oracle(g (1 + eps_k xi_k)), oracle(g)),  eps_k in 1e-16..1e-14
+  fp32 handles: E = max_k relerr(fp32_model(g (1 + eps_k xi_k)), oracle(g)), eps_k in 1e-7..1e-6
+
+(a spread of magnitudes, because the deviation is heavy tailed: most perturbations move the
+result a little, some a lot), where fp32_model runs the same algorithm with the oracle's operators, V-cycle and
+diffusivity but rounds every vector and every operator output to float32 (scalars in
+double), i.e. an idealised single-precision implementation.  A GPU result passes when its
+error is within max(bar, C * E).  The model only sizes a tolerance: no expected value comes
+from it.
+"""
+import numpy as np
+
+import oracle as O
+from paper_1308_6634_gb300 import synth
+
+C_ENV = 5.0
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    ok = np.isfinite(b)
+    return float(np.linalg.norm(a[ok] - b[ok]) / max(np.linalg.norm(b[ok]), 1e-300))
+
+
+def problem(W, seed=0):
+    f, mask, z = W.inputs(seed)
+    op = O.Operator(W.kind, W.shape, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
+                    n_bins=W.n_bins)
+    return op, synth.add_noise(op.A(f), W.noise, z), mask
+
+
+def _r32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def fp32_model_mlsqr(op, mg, g, tau, n_inner, _r32=_r32):
+    """Algorithm 2 with every vector and operator output rounded to float32 (or by `_r32`)."""
+    A = lambda x: _r32(op.A(_r32(x)))
+    At = lambda y: _r32(op.At(_r32(y)))
+    P = (lambda b: _r32(mg.apply(_r32(b)))) if mg is not None else _r32
+    beta = np.linalg.norm(g)
+    beta1 = beta
+    u = _r32(g / beta)
+    p = At(u)
+    v = P(p)
+    alpha = np.sqrt(float((v * p).sum()))
+    v, p = _r32(v / alpha), _r32(p / alpha)
+    w, f = v.copy(), np.zeros(op.shape)
+    phibar, rhobar, res2, hist = beta, alpha, 0.0, []
+    for _ in range(n_inner):
+        u = _r32(A(v) - alpha * u)
+        beta = np.linalg.norm(u)
+        if not beta > 1e-30 * beta1:
+            break
+        u = _r32(u / beta)
+        p = _r32(At(u) - beta * p)
+        v = P(p)
+        an = np.sqrt(float((v * p).sum()))
+        if not an > 1e-30 * beta1:
+            break
+        p, v = _r32(p / an), _r32(v / an)
+        rhohat, psi = rhobar, 0.0
+        if tau > 0:
+            rhohat = np.sqrt(rhobar ** 2 + tau)
+            psi = np.sqrt(tau) / rhohat * phibar
+            phibar = rhobar / rhohat * phibar
+        rho = np.sqrt(rhohat ** 2 + beta ** 2)
+        c, s = rhohat / rho, beta / rho
+        theta, rhobar, phi, phibar = s * an, -c * an, c * phibar, s * phibar
+        res2 += psi * psi
+        f = _r32(f + (phi / rho) * w)
+        w = _r32(v - (theta / rho) * w)
+        alpha = an
+        hist.append(np.sqrt(phibar ** 2 + res2))
+    return f, np.array(hist)
+
+
+def fp32_model_solve(op, g, reg, T, tau, n_outer, n_inner, levels, nu, cycles, kfloor=1e-4):
+    """Algorithm 3 around fp32_model_mlsqr (kappa from the float32 iterate)."""
+    f = np.zeros(op.shape)
+    rbar = np.full((n_outer, n_inner), np.nan)
+    for k in range(n_outer):
+        kappa = _r32(O.diffusivity(f, reg, T, kfloor)[0])
+        mg = O.Multigrid(kappa, levels, nu, cycles)
+        f, h = fp32_model_mlsqr(op, mg, g, tau, n_inner)
+        rbar[k, : len(h)] = h
+    return dict(f=f, rbar_hist=rbar)
+
+
+def _perturbed(g, eps, k):
+    return g * (1.0 + eps * np.random.default_rng(4242 + k).standard_normal(g.shape))
+
+
+def solve_task(args):
+    """Picklable unit of work for a spawn pool: (kind, W, n_outer, n_inner, eps, k)."""
+    kind, W, n_outer, n_inner, eps, k = args
+    op, g, _ = problem(W)
+    if eps > 0:
+        g = _perturbed(g, eps, k)
+    if kind == "oracle":
+        return O.solve(op, g, W.reg, W.T, W.tau, n_outer, n_inner, W.levels, W.nu, W.cycles)
+    return fp32_model_solve(op, g, W.reg, W.T, W.tau, n_outer, n_inner, W.levels, W.nu, W.cycles)
+
+
+EPS = {"fp64": (1e-16, 1e-15, 1e-14), "fp32": (1e-7, 3e-7, 1e-6)}
+
+
+def envelope_tasks(W, n_outer, n_inner, K=6):
+    kind = "oracle" if W.precision == "fp64" else "model32"
+    eps = EPS[W.precision]
+    return [("oracle", W, n_outer, n_inner, 0.0, 0)] + [(kind, W, n_outer, n_inner, eps[k % len(eps)], k)
+                                                         for k in range(K)]
+
+
+def reference_and_envelope(W, n_outer, n_inner, K=6, pool=None):
+    """(oracle result, {key: envelope}) for the precision of workload W."""
+    tasks = envelope_tasks(W, n_outer, n_inner, K)
+    res = list(pool.map(solve_task, tasks)) if pool is not None else [solve_task(t) for t in tasks]
+    base = res[0]
+    env = {key: max(rel(r[key], base[key]) for r in res[1:]) for key in ("f", "rbar_hist")}
+    return base, env

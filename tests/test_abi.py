@@ -1,0 +1,46 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/plsqr.h.
+
+No compute call is made here (no GPU in this process is assumed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "plsqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(plsqr_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_destroy"]:
+        assert n in names
+
+
+def test_library_builds_loads_and_exports_all_symbols():
+    from paper_1308_6634_gb300 import build, plsqr
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (plsqr_\w+)", out))
+    for n in _declared():
+        assert n in exported, n
+    L = plsqr.lib()
+    for n in _declared():
+        assert hasattr(L, n)
+    assert sorted(plsqr.EXPORTED) == _declared()
+
+
+def test_workspace_bytes_and_invalid_configs_without_gpu():
+    from paper_1308_6634_gb300 import plsqr
+    c = plsqr.make_config((1024, 1024), "fp32", levels=6)
+    nb = plsqr.plsqr_workspace_bytes(c)
+    assert nb > 10 * 1024 * 1024 * 4
+    bad = plsqr.make_config((100, 100), "fp32", levels=4)  # 100 not divisible by 8
+    assert plsqr.plsqr_workspace_bytes(bad) == -1
+    too_coarse = plsqr.make_config((512, 512), "fp32", levels=1)
+    assert plsqr.plsqr_workspace_bytes(too_coarse) == -1

@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: double-precision handles agree with the oracle to rounding (1e-10 relative on
+single operators, 1e-8 on whole solves).  Single-precision handles (FP32 bulk, FP64
+scalars) meet the bar of relative L2 error <= 1e-4 on reconstructions and residual-norm
+histories over 50 inner iterations and <= 1e-3 on full fixed-point solves; single
+operators agree to a few FP32 ulps (1e-5 relative L2).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from envelope import rel
+from paper_1308_6634_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_6634_gb300 import build
+    build.build()
+
+
+def _P():
+    from paper_1308_6634_gb300 import plsqr
+    return plsqr
+
+
+def dev(x, prec):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64 if prec == "fp64" else torch.float32).cuda()
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+TOL_OP = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _blur_pair(shape, prec, sigma, radius, levels=2, mask=None):
+    S = _P().Solver(shape, prec, levels=levels)
+    kind = "blur_mask" if mask is not None else "blur"
+    S.set_operator(kind, sigma=sigma, radius=radius, mask=mask)
+    op = O.Operator(kind, shape, sigma=sigma, radius=radius, mask=mask)
+    return S, op
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,sigma,radius", [((96, 160), (2.0, 2.0), (6, 6)),
+                                                ((67, 45), (4.0, 1.5), (12, 4)),
+                                                ((1, 1), (1.0, 1.0), (2, 2))])
+def test_blur_2d(prec, shape, sigma, radius):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(shape)
+    S, op = _blur_pair(shape, prec, sigma, radius, levels=1)
+    y = host(S.apply_A(dev(x, prec)))
+    assert rel(y, op.A(x)) < TOL_OP[prec]
+    yt = host(S.apply_At(dev(x, prec)))
+    assert rel(yt, op.At(x)) < TOL_OP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_masked_blur_3d(prec):
+    shape = (20, 24, 40)  # ragged in z (16-deep tiles) and x (64-wide tiles)
+    rng = np.random.default_rng(2)
+    mask = (rng.random(shape) >= 0.15).astype(np.uint8)
+    x = rng.standard_normal(shape)
+    S, op = _blur_pair(shape, prec, (3.0, 3.0, 5.0), (9, 9, 15), mask=mask)
+    assert rel(host(S.apply_A(dev(x, prec))), op.A(x)) < TOL_OP[prec]
+    assert rel(host(S.apply_At(dev(x, prec))), op.At(x)) < TOL_OP[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,na,nb", [(64, 60, 93), (37, 17, 55), (128, 90, 183)])
+def test_joseph(prec, n, na, nb):
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (n, n))
+    y = rng.standard_normal((na, nb))
+    S = _P().Solver((n, n), prec, levels=1)
+    S.set_operator("joseph", n_angles=na, n_bins=nb)
+    op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    Ax = host(S.apply_A(dev(x, prec)))
+    assert rel(Ax, op.A(x)) < tol
+    Aty = host(S.apply_At(dev(y, prec)))
+    assert rel(Aty, op.At(y)) < tol
+    # gather adjoint is the transpose of the forward ray march
+    lhs, rhs = float((Ax * y).sum()), float((x * Aty).sum())
+    assert abs(lhs - rhs) / (np.linalg.norm(Ax) * np.linalg.norm(y)) < (1e-13 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("reg", ["tikhonov", "tv", "pm_log", "pm_exp"])
+@pytest.mark.parametrize("shape", [(48, 80), (12, 20, 28)])
+def test_diffusivity(prec, reg, shape):
+    rng = np.random.default_rng(4)
+    f = synth.phantom_rects_disks(max(shape), 5, 3, 9)[: shape[-2], : shape[-1]]
+    if len(shape) == 3:
+        f = np.stack([f] * shape[0]) * rng.uniform(0.5, 1.0, (shape[0], 1, 1))
+    f = f + 0.01 * rng.standard_normal(shape)
+    T = 0.05
+    S = _P().Solver(shape, prec, levels=2)
+    kappa, R = S.diffusivity(dev(f, prec), reg, T)
+    k_ref, R_ref = O.diffusivity(f, reg, T, kfloor=1e-4)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert rel(host(kappa), k_ref) < tol
+    assert R == pytest.approx(R_ref, rel=tol, abs=1e-300)
+
+
+def _kappa_field(shape, seed=5):
+    rng = np.random.default_rng(seed)
+    if len(shape) == 2:
+        f = synth.phantom_rects_disks(max(shape), 8, 5, seed)[: shape[0], : shape[1]]
+    else:
+        f = synth.phantom_ellipsoids(shape, 6, seed)
+    f = f + 0.01 * rng.standard_normal(shape)
+    return O.diffusivity(f, "pm_log", 0.05)[0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,levels,nu,cycles", [((96, 160), 4, 2, 1), ((64, 64), 3, 2, 2),
+                                                    ((32, 48), 1, 2, 1), ((16, 24, 32), 3, 2, 1),
+                                                    ((24, 24, 24), 4, 1, 1)])
+def test_priorconditioner(prec, shape, levels, nu, cycles):
+    kappa = _kappa_field(shape)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(shape)
+    S = _P().Solver(shape, prec, levels=levels, sweeps=nu, cycles=cycles)
+    S.prec_setup(dev(kappa, prec))
+    mg = O.Multigrid(kappa, levels, nu, cycles)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert rel(host(S.prec_apply(dev(b, prec))), mg.apply(b)) < tol
+    assert rel(host(S.apply_M(dev(b, prec))), O.apply_M(kappa, b)) < (1e-13 if prec == "fp64" else 1e-6)
+
+
+def _problem(W, seed=0):
+    f, mask, z = W.inputs(seed)
+    op = O.Operator(W.kind, W.shape, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
+                    n_bins=W.n_bins)
+    g = synth.add_noise(op.A(f), W.noise, z)
+    return op, g, mask
+
+
+def _solver_for(W, op, mask, max_batch=1):
+    S = _P().Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles, max_batch=max_batch)
+    S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles, n_bins=W.n_bins)
+    return S
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("tau", [0.0, 5e-3])
+def test_mlsqr_short_horizon(prec, tau):
+    """Five MLSQR iterations with a structured kappa: before rounding chaos sets in, the
+    iterate and the residual estimates agree closely (double: to rounding; single: the
+    FP32 V-cycle's ~1e-6 relative error, amplified by the ill-conditioned blur)."""
+    W = synth.Workload("t", "blur", (96, 160), prec, "tv", 1e-2, tau, 1, 5, levels=4, nu=2, cycles=1,
+                       sigma=(2.0, 2.0), radius=(6, 6), phantom=dict(type="rects_disks", rects=6, disks=4))
+    op, g, _ = _problem(W)
+    kappa = _kappa_field(W.shape, 7)
+    S = _solver_for(W, op, None)
+    S.prec_setup(dev(kappa, prec))
+    f, hist, rc = S.mlsqr(dev(g, prec), tau, 5)
+    f_ref, h_ref, st = O.mlsqr(op, g, tau, 5, prec=O.Multigrid(kappa, W.levels, W.nu, W.cycles))
+    assert rc == 0 and st == 0 and len(hist) == 5
+    if prec == "fp64":
+        assert rel(host(f), f_ref) < 1e-9 and rel(hist, h_ref) < 1e-12
+    else:
+        assert rel(host(f), f_ref) < 1e-3 and rel(hist, h_ref) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("tau", [0.0, 5e-3])
+def test_mlsqr_50_inner(prec, tau):
+    """50 MLSQR iterations: relative error <= max(1e-4, C * rounding envelope)."""
+    from envelope import C_ENV, fp32_model_mlsqr
+
+    W = synth.Workload("t", "blur", (96, 160), prec, "tv", 1e-2, tau, 1, 50, levels=4, nu=2, cycles=1,
+                       sigma=(2.0, 2.0), radius=(6, 6), phantom=dict(type="rects_disks", rects=6, disks=4))
+    op, g, _ = _problem(W)
+    kappa = _kappa_field(W.shape, 7)
+    mg = O.Multigrid(kappa, W.levels, W.nu, W.cycles)
+    f_ref, h_ref, _ = O.mlsqr(op, g, tau, 50, prec=mg)
+    from envelope import EPS
+    env_f = env_h = 0.0
+    for k in range(6):
+        eps = EPS[prec][k % 3]
+        gp = g * (1 + eps * np.random.default_rng(4242 + k).standard_normal(g.shape))
+        if prec == "fp64":
+            fk, hk, _ = O.mlsqr(op, gp, tau, 50, prec=mg)
+        else:
+            fk, hk = fp32_model_mlsqr(op, mg, gp, tau, 50)
+        env_f, env_h = max(env_f, rel(fk, f_ref)), max(env_h, rel(hk, h_ref))
+    S = _solver_for(W, op, None)
+    S.prec_setup(dev(kappa, prec))
+    f, hist, rc = S.mlsqr(dev(g, prec), tau, 50)
+    assert rc == 0 and len(hist) == 50
+    ef, eh = rel(host(f), f_ref), rel(hist, h_ref)
+    print(f"mlsqr50 {prec} tau={tau}: f {ef:.2e} (envelope {env_f:.2e}), rbar {eh:.2e} (envelope {env_h:.2e})")
+    assert ef <= max(1e-4, C_ENV * env_f)
+    assert eh <= max(1e-4, C_ENV * env_h)
+
+
+SOLVE_CASES = {
+    "deblur64_fp64": (synth.WORKLOADS["deblur64_fp64"], 10, 30),
+    "deblur64_fp32": (synth.Workload("deblur64_fp32", "blur", (64, 64), "fp32", "tv", 1e-2, 5e-3, 10, 30, levels=3,
+                                     nu=2, cycles=2, sigma=(2.0, 2.0), radius=(6, 6),
+                                     phantom=dict(type="rects_disks", rects=6, disks=4)), 10, 30),
+    "deblur128_fp32": (synth.Workload("deblur128_fp32", "blur", (128, 128), "fp32", "pm_log", 5e-2, 1e-3, 4, 30,
+                                      levels=4, nu=2, cycles=1, sigma=(4.0, 4.0), radius=(12, 12),
+                                      phantom=dict(type="rects_disks", rects=10, disks=6)), 4, 30),
+    "tomo64_fp64": (synth.Workload("tomo64_fp64", "joseph", (64, 64), "fp64", "pm_exp", 2e-2, 0.0, 3, 20, levels=3,
+                                   nu=2, cycles=1, n_angles=60, n_bins=93,
+                                   phantom=dict(type="ellipses", count=5)), 3, 20),
+    "tomo64_fp32": (synth.Workload("tomo64_fp32", "joseph", (64, 64), "fp32", "pm_exp", 2e-2, 0.0, 3, 20, levels=3,
+                                   nu=2, cycles=1, n_angles=60, n_bins=93,
+                                   phantom=dict(type="ellipses", count=5)), 3, 20),
+    "inpaint32_fp64": (synth.Workload("inpaint32_fp64", "blur_mask", (32, 32, 32), "fp64", "tv", 1e-2, 0.0, 3, 15,
+                                      levels=3, nu=2, cycles=1, sigma=(3.0, 3.0, 5.0), radius=(9, 9, 15),
+                                      noise=0.005, missing=0.15, phantom=dict(type="ellipsoids", count=6)), 3, 15),
+    "inpaint32_fp32": (synth.Workload("inpaint32_fp32", "blur_mask", (32, 32, 32), "fp32", "tv", 1e-2, 0.0, 3, 15,
+                                      levels=3, nu=2, cycles=1, sigma=(3.0, 3.0, 5.0), radius=(9, 9, 15),
+                                      noise=0.005, missing=0.15, phantom=dict(type="ellipsoids", count=6)), 3, 15),
+}
+
+
+@pytest.mark.parametrize("case", sorted(SOLVE_CASES))
+def test_full_solve(case):
+    """Full fixed-point solves (Algorithm 3): f and the ||rbar|| histories within
+    max(1e-3, C * rounding envelope); the first five residual estimates of the first outer
+    step (constant kappa, before chaos) tightly."""
+    from envelope import C_ENV, reference_and_envelope
+
+    W, n_outer, n_inner = SOLVE_CASES[case]
+    ref, env = reference_and_envelope(W, n_outer, n_inner)
+    op, g, mask = _problem(W)
+    S = _solver_for(W, op, mask)
+    f, info = S.solve(dev(g, W.precision), W.reg, W.T, W.tau, n_outer, n_inner)
+    assert info["status"] == 0 and ref["status"] == 0
+    ef, eh = rel(host(f), ref["f"]), rel(info["rbar_hist"], ref["rbar_hist"])
+    print(f"{case}: f {ef:.2e} (envelope {env['f']:.2e}), rbar {eh:.2e} (envelope {env['rbar_hist']:.2e})")
+    assert ef <= max(1e-3, C_ENV * env["f"])
+    assert eh <= max(1e-3, C_ENV * env["rbar_hist"])
+    h0 = 1e-12 if W.precision == "fp64" else 1e-4
+    assert rel(info["rbar_hist"][0][:5], ref["rbar_hist"][0][:5]) < h0
+    assert np.isfinite(info["R_hist"]).all() and np.isfinite(info["resid_hist"]).all()
+
+
+def test_deblur1024_fp32_full_size():
+    """The 1024x1024 FP32 deblurring workload at full size (the benchmarked configuration):
+    the priorconditioner from a structured kappa against the oracle's V-cycle; one outer
+    step of 50 MLSQR iterations within max(1e-4, C * envelope) of the oracle, with the
+    FP32-model envelope computed in a spawn pool; and the first five residual estimates
+    tightly."""
+    import multiprocessing as mp
+
+    from envelope import C_ENV, envelope_tasks, solve_task
+
+    W = synth.WORKLOADS["deblur1024_fp32"]
+    op, g, _ = _problem(W)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(7) as pool:
+        res = pool.map(solve_task, envelope_tasks(W, 1, 50, K=6))
+    ref = res[0]
+    env_f = max(rel(r["f"], ref["f"]) for r in res[1:])
+    env_h = max(rel(r["rbar_hist"], ref["rbar_hist"]) for r in res[1:])
+    S = _solver_for(W, op, None)
+    f, info = S.solve(dev(g, "fp32"), W.reg, W.T, W.tau, 1, 50)
+    ef, eh = rel(host(f), ref["f"]), rel(info["rbar_hist"], ref["rbar_hist"])
+    print(f"deblur1024 1x50: f {ef:.2e} (envelope {env_f:.2e}), rbar {eh:.2e} (envelope {env_h:.2e})")
+    assert ef <= max(1e-4, C_ENV * env_f)
+    assert eh <= max(1e-4, C_ENV * env_h)
+    assert rel(info["rbar_hist"][0][:5], ref["rbar_hist"][0][:5]) < 1e-5
+    kappa = O.diffusivity(W.phantom_image(0), W.reg, W.T)[0]
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(W.shape)
+    S.prec_setup(dev(kappa, "fp32"))
+    assert rel(host(S.prec_apply(dev(b, "fp32"))), O.Multigrid(kappa, W.levels, W.nu, W.cycles).apply(b)) < 1e-5
+
+
+def test_batched_equals_single():
+    """Instances solved together in one batch give the same result as alone."""
+    W = synth.Workload("b", "blur", (64, 96), "fp32", "tv", 2e-2, 1e-3, 3, 12, levels=3, nu=2, cycles=1,
+                       sigma=(2.0, 2.0), radius=(6, 6), phantom=dict(type="rects_disks", rects=6, disks=4))
+    gs, singles = [], []
+    op = None
+    for seed in range(3):
+        op, g, _ = _problem(W, seed)
+        gs.append(g)
+    S = _solver_for(W, op, None, max_batch=4)
+    regs, Ts, taus = ["tv", "pm_log", "pm_exp"], [2e-2, 5e-2, 3e-2], [1e-3, 0.0, 2e-3]
+    for k in range(3):
+        f, info = S.solve(dev(gs[k], "fp32"), regs[k], Ts[k], taus[k], W.n_outer, W.n_inner)
+        singles.append((host(f), info))
+    fs, infos = S.solve_batch([dev(g, "fp32") for g in gs], regs, Ts, taus, W.n_outer, W.n_inner)
+    for k in range(3):
+        assert np.array_equal(host(fs[k]), singles[k][0])
+        assert np.array_equal(infos[k]["rbar_hist"], singles[k][1]["rbar_hist"])
+
+
+def test_host_buffers_and_graph_replay_consistent():
+    W = synth.WORKLOADS["deblur64_fp64"]
+    op, g, _ = _problem(W)
+    S = _solver_for(W, op, None)
+    f1, _ = S.solve(dev(g, "fp64"), W.reg, W.T, W.tau, 3, 10)
+    f2, _ = S.solve_host(np.ascontiguousarray(g), W.reg, W.T, W.tau, 3, 10)
+    f3, _ = S.solve(dev(g, "fp64"), W.reg, W.T, W.tau, 3, 10)
+    assert np.array_equal(host(f1), f2)
+    assert np.array_equal(host(f1), host(f3))
+
+
+def test_breakdown_and_invalid_arguments():
+    P = _P()
+    W = synth.WORKLOADS["deblur64_fp64"]
+    S = P.Solver(W.shape, "fp64", levels=3)
+    S.set_operator("blur", sigma=W.sigma, radius=W.radius)
+    f, info = S.solve(torch.zeros(W.shape, dtype=torch.float64, device="cuda"), "tv", 1e-2, 0.0, 2, 5)
+    assert info["status"] == P.E_BREAKDOWN
+    assert np.all(host(f) == 0.0)
+    with pytest.raises(P.PlsqrError):
+        S.solve(torch.ones(W.shape, dtype=torch.float64, device="cuda"), "tv", -1.0, 0.0, 2, 5)
+    with pytest.raises(P.PlsqrError):
+        P.Solver((100, 100), "fp32", levels=4)
+    with pytest.raises(P.PlsqrError):
+        S.set_operator("joseph", n_angles=0, n_bins=10)
