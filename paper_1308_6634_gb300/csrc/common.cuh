@@ -128,4 +128,52 @@ __device__ __forceinline__ bool good_pos(double x, double ref) {
     return isfinite(x) && x > 1e-30 * ref;
 }
 
+// alpha_{i+1} = sqrt(v~ . p~) (Algorithm 2 steps 5 / 13) from the reduced dot product, then
+// (INIT = false) the orthogonal transformation: the Paige-Saunders damping rotation that
+// eliminates sqrt(tau) I (eq. 3.6) and Algorithm 1 steps 10-16, the coefficients of the
+// pending update (steps 19-20) and ||rbar_i||.  Runs on one thread.
+template <bool INIT>
+__device__ __forceinline__ void finalize_alpha(GkState& s, double tot, const Hist& hist, int inst) {
+    const double an = sqrt(tot);
+    if (!good_pos(an, s.beta1)) {
+        s.status = ST_BREAKDOWN;
+        s.status_any = ST_BREAKDOWN;
+        return;
+    }
+    if (INIT) {  // step 7: rhobar_1 = alpha_1, w~_1 = v~_1
+        s.alpha = an;
+        s.rhobar = an;
+        s.c_upd_v = 1.0 / an;
+        s.c_fwd_a = 1.0 / an;
+        s.c_fwd_p = an / s.beta;
+        return;
+    }
+    double rhohat = s.rhobar, psi = 0.0;
+    if (s.tau > 0.0) {
+        rhohat = sqrt(s.rhobar * s.rhobar + s.tau);
+        const double c1 = s.rhobar / rhohat, s1 = s.sqrt_tau / rhohat;
+        psi = s1 * s.phibar;
+        s.phibar = c1 * s.phibar;
+    }
+    const double beta = s.beta_new;
+    const double rho = sqrt(rhohat * rhohat + beta * beta);
+    const double c = rhohat / rho, sn = beta / rho;
+    const double theta = sn * an;
+    s.rhobar = -c * an;
+    const double phi = c * s.phibar;
+    s.phibar = sn * s.phibar;
+    s.res2 += psi * psi;
+    s.cf = phi / rho;
+    s.cw = theta / rho;
+    s.iter += 1;
+    if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
+        hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] =
+            sqrt(s.phibar * s.phibar + s.res2);
+    s.alpha = an;
+    s.beta = beta;
+    s.c_upd_v = 1.0 / an;
+    s.c_fwd_a = 1.0 / an;
+    s.c_fwd_p = an / beta;
+}
+
 }  // namespace plsqr

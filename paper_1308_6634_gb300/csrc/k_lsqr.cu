@@ -10,7 +10,12 @@
 #include <stdexcept>
 #include <string>
 
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace plsqr {
 
@@ -80,6 +85,40 @@ void klaunched(const char* what) {
 
 void kfinish(cudaStream_t s) {
     if (Profiler* p = current_profiler()) p->finish(s);
+}
+
+bool tma_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("PLSQR_TMA");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+bool tma_map_3d(CUtensorMap* map, const void* base, int esz, int64_t nx, int64_t ny, int64_t planes, int bx, int by,
+                int bz) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || !base) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (nx * esz) % 16 || ((int64_t)bx * esz) % 16) return false;
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256 || nx < 1 || ny < 1 || planes < 1) return false;
+    if (planes > (int64_t(1) << 31) - 1 || nx > (int64_t(1) << 31) - 1 || ny > (int64_t(1) << 31) - 1) return false;
+    cuuint64_t gdim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    cuuint64_t gstride[2] = {(cuuint64_t)(nx * esz), (cuuint64_t)(nx * ny * esz)};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                              const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 1024)); }
@@ -158,49 +197,7 @@ __global__ void __launch_bounds__(256) k_dot_rotate(const T* __restrict__ v, con
         part = fma(vi[i], pi[i], part);
     double tot;
     if (!reduce_last<256>((double)part, red, inst, blockIdx.x, gridDim.x, &tot)) return;
-    GkState& s = st[inst];
-    const double an = sqrt(tot);
-    if (!good_pos(an, s.beta1)) {
-        s.status = ST_BREAKDOWN;
-        s.status_any = ST_BREAKDOWN;
-        return;
-    }
-    if (INIT) {  // step 7: rhobar_1 = alpha_1, w~_1 = v~_1
-        s.alpha = an;
-        s.rhobar = an;
-        s.c_upd_v = 1.0 / an;
-        s.c_fwd_a = 1.0 / an;
-        s.c_fwd_p = an / s.beta;
-        return;
-    }
-    // damping rotation: eliminate sqrt(tau) below rhobar (Paige-Saunders, eq. 3.6)
-    double rhohat = s.rhobar, psi = 0.0;
-    if (s.tau > 0.0) {
-        rhohat = sqrt(s.rhobar * s.rhobar + s.tau);
-        const double c1 = s.rhobar / rhohat, s1 = s.sqrt_tau / rhohat;
-        psi = s1 * s.phibar;
-        s.phibar = c1 * s.phibar;
-    }
-    // Algorithm 1 steps 10-16
-    const double beta = s.beta_new;
-    const double rho = sqrt(rhohat * rhohat + beta * beta);
-    const double c = rhohat / rho, sn = beta / rho;
-    const double theta = sn * an;
-    s.rhobar = -c * an;
-    const double phi = c * s.phibar;
-    s.phibar = sn * s.phibar;
-    s.res2 += psi * psi;
-    s.cf = phi / rho;
-    s.cw = theta / rho;
-    s.iter += 1;
-    if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
-        hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] =
-            sqrt(s.phibar * s.phibar + s.res2);
-    s.alpha = an;
-    s.beta = beta;
-    s.c_upd_v = 1.0 / an;
-    s.c_fwd_a = 1.0 / an;
-    s.c_fwd_p = an / beta;
+    finalize_alpha<INIT>(st[inst], tot, hist, inst);
 }
 
 template <typename T>

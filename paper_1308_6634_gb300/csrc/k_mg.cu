@@ -337,61 +337,205 @@ void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw,
     kfinish(s);
 }
 
-// In-place banded Cholesky M = L L^T, one block of 1024 threads per instance.  Column j's
-// trailing update uses the unscaled column and the pivot a_j (L(i,k) -= L(i,j) L(k,j)/a_j),
-// and the column is scaled by 1/sqrt(a_j) during the next column's update, which touches
-// disjoint entries: one barrier per column.
-__global__ void __launch_bounds__(1024) k_chol_band(double* band_all, int nc, int bw) {
-    double* band = band_all + (int64_t)blockIdx.x * nc * (bw + 1);
-    const int W = bw + 1;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    double a_prev = 1.0;
+// 1/sqrt(a) for a > 0 in double: single-precision seed, then two Newton-Raphson steps for
+// the reciprocal square root, r <- r (3/2 - a r^2 / 2) (each step squares the relative error:
+// ~2e-7 -> ~1e-13 -> rounding level).  Six dependent multiply-adds instead of a division and
+// a square root on the critical path of the factorisation.  Non-positive or non-finite a
+// gives NaN, which propagates into the inverse and surfaces as a breakdown.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+    if (!(a > 0.0) || !isfinite(a)) return nan("");
+    double r = (double)rsqrtf((float)a);
+    r = r * fma(-0.5 * a * r, r, 1.5);
+    r = r * fma(-0.5 * a * r, r, 1.5);
+    return r;
+}
+
+// In-place banded Cholesky M = L L^T, one block of 1024 threads per instance.  The rows that
+// column j touches live in a sliding window of bw+4 rows in shared memory.  Iteration j:
+//  - scales column j-1 by 1/sqrt(a_{j-1}) and sets L(j-1,j-1) = sqrt(a_{j-1}),
+//  - writes the finished row j-2 back and loads row j+bw+1 into the slot row j-3 left,
+//  - applies the trailing update of column j with the unscaled column and pivot a_j:
+//    L(i,k) -= L(i,j) L(k,j) / a_j,  j < k <= i <= j+bw,
+// all on disjoint entries, so one barrier per column.  The thread that updates the next
+// pivot also forms 1/a, sqrt(a) and 1/sqrt(a) once (triple-buffered in shared memory), so
+// no other thread divides or takes a root in double.  rdiag receives 1/L(j,j).
+__global__ void __launch_bounds__(1024) k_chol_band(double* band_all, double* rdiag_all, int nc, int bw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* win = reinterpret_cast<double*>(smraw);
+    __shared__ double s_inv[3], s_sq[3], s_rsq[3];
+    const int W = bw + 1, S = bw + 4;
+    double* band = band_all + (int64_t)blockIdx.x * nc * W;
+    double* rdiag = rdiag_all + (int64_t)blockIdx.x * nc;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int nload = min(bw + 1, nc);
+    for (int e = tid; e < nload * W; e += 1024) {
+        const int r = e / W, k = e - r * W;
+        win[(r % S) * W + k] = band[(int64_t)r * W + k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double a = win[0], r = rsqrt_nr(a);
+        s_inv[0] = r * r;
+        s_sq[0] = a * r;
+        s_rsq[0] = r;
+    }
+    __syncthreads();
     for (int j = 0; j <= nc; ++j) {
-        if (j > 0) {  // scale column j-1
-            const double r = sqrt(a_prev);
-            for (int t = threadIdx.x; t < W; t += 1024) {
+        if (j >= 1) {  // scale column j-1
+            const int c = (j - 1) % 3;
+            const double rs = s_rsq[c];
+            for (int t = tid; t < W; t += 1024) {
                 const int i = j - 1 + t;
                 if (i >= nc) break;
-                if (t == 0) band[(int64_t)i * W] = r;
-                else band[(int64_t)i * W + t] /= r;
+                double* Ri = win + (i % S) * W;
+                if (t == 0) {
+                    Ri[0] = s_sq[c];
+                    rdiag[i] = rs;
+                } else {
+                    Ri[t] *= rs;
+                }
             }
         }
-        if (j == nc) break;
-        const double a = band[(int64_t)j * W];
-        const double inv_a = 1.0 / a;
-        for (int ii = ty; ii < bw; ii += 32) {
-            const int i = j + 1 + ii;
-            if (i >= nc) break;
-            const double lij = band[(int64_t)i * W + (i - j)];
-            if (lij == 0.0) continue;
-            const double f = lij * inv_a;
-            for (int kk = tx; kk <= ii; kk += 32) {
-                const int k = j + 1 + kk;
-                const double lkj = band[(int64_t)k * W + (k - j)];
-                band[(int64_t)i * W + (i - k)] -= f * lkj;
+        if (j >= 2) {  // row j-2 is final
+            const int r = j - 2;
+            for (int k = tid; k < W; k += 1024) band[(int64_t)r * W + k] = win[(r % S) * W + k];
+        }
+        {
+            const int r = j + bw + 1;
+            if (r < nc)
+                for (int k = tid; k < W; k += 1024) win[(r % S) * W + k] = band[(int64_t)r * W + k];
+        }
+        if (j < nc) {
+            const double inv_a = s_inv[j % 3];
+            const int base = (j + 1) % S;  // slot of row j+1; rows j+1.. follow cyclically
+            for (int ii = ty; ii < bw; ii += 32) {
+                const int i = j + 1 + ii;
+                if (i >= nc) break;
+                int si = base + ii;
+                if (si >= S) si -= S;
+                double* Ri = win + si * W;
+                double f = 0.0;
+                if (tx == 0) f = Ri[ii + 1] * inv_a;  // L(i, j) / a_j, once per row
+                f = __shfl_sync(0xffffffffu, f, 0);
+                if (f == 0.0) continue;
+                for (int kk = tx; kk <= ii; kk += 32) {
+                    int sk = base + kk;
+                    if (sk >= S) sk -= S;
+                    Ri[ii - kk] -= f * win[sk * W + kk + 1];  // L(i,k) -= f L(k,j), k = j+1+kk
+                }
+            }
+            if (tid == 0 && j + 1 < nc) {  // thread 0 updated L(j+1,j+1) (ii = kk = 0)
+                const double a = win[((j + 1) % S) * W], r = rsqrt_nr(a);
+                const int c = (j + 1) % 3;
+                s_inv[c] = r * r;
+                s_sq[c] = a * r;
+                s_rsq[c] = r;
             }
         }
-        a_prev = a;
         __syncthreads();
+    }
+    {
+        const int r = nc - 1;
+        for (int k = tid; k < W; k += 1024) band[(int64_t)r * W + k] = win[(r % S) * W + k];
     }
 }
 
-void coarse_cholesky(double* band, int nc, int bw, int B, cudaStream_t s) {
+void coarse_cholesky(double* band, double* rdiag, int nc, int bw, int B, cudaStream_t s) {
     kbegin(KC_SETUP, s);
-    k_chol_band<<<B, 1024, 0, s>>>(band, nc, bw);
+    const size_t smem = sizeof(double) * (size_t)(bw + 4) * (bw + 1);
+    if (smem > 227 * 1024) throw std::runtime_error("coarse_cholesky: band too wide for shared memory");
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chol_band<<<B, 1024, smem, s>>>(band, rdiag, nc, bw);
     klaunched("k_chol_band");
     kfinish(s);
 }
 
-// Inverse of the coarsest operator from its band factor: one warp per column j solves
-// L y = e_j (rows j..nc-1), then L^T x = y (rows nc-1..j); X(i,j) = X(j,i) = x_i, i >= j.
-__global__ void k_band_inverse(const double* __restrict__ band_all, double* __restrict__ X_all, int nc, int bw) {
+// Inverse of the coarsest operator from its band factor, X = L^{-T} L^{-1}, stored full and
+// exactly symmetric: for each column c,
+//   forward  y_i = (delta_ic - sum_m L(i, i-m) y_{i-m}) / L(i,i),      i = c .. nc-1
+//   backward x_i = (y_i      - sum_m L(i+m, i) x_{i+m}) / L(i,i),      i = nc-1 .. c
+// y is parked in X(i, c); x overwrites it and is mirrored to X(c, i).  The rows are walked by a
+// whole warp together, so the band row read is the same for all its lanes (broadcast).
+// Narrow-band inverse with four lanes per column: lane q of the quad keeps window entries
+// m = 8q .. 8q+7 and their partial sum; the quad adds the four partial sums (two butterfly
+// shuffles) and passes the entry that leaves one lane's part of the window to the next lane
+// (shuffle up within the quad).  Four times the parallelism of one lane per column, so the
+// double-precision pipe stays busy even for one instance.
+__device__ __forceinline__ double quad_sum(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2, 4);
+    return v;
+}
+
+__global__ void __launch_bounds__(128) k_band_inverse_quad(const double* __restrict__ band_all,
+                                                           const double* __restrict__ rdiag_all,
+                                                           double* __restrict__ X_all, int nc, int bw) {
+    const int inst = blockIdx.y;
+    const int q = threadIdx.x & 3;
+    const int c = blockIdx.x * 32 + (threadIdx.x >> 2);       // column of this quad
+    const int c0 = blockIdx.x * 32 + ((threadIdx.x & ~31) >> 2);  // first column of this warp
+    if (c0 >= nc) return;
+    const int W = bw + 1;
+    const double* band = band_all + (int64_t)inst * nc * W;
+    const double* rdiag = rdiag_all + (int64_t)inst * nc;
+    double* X = X_all + (int64_t)inst * nc * nc;
+    const bool live = c < nc;
+    const int mb = 8 * q;  // first window index of this lane
+    double win[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) win[t] = 0.0;
+    // forward: y_i = (delta_ic - sum_m L(i, i-1-m) y_{i-1-m}) / L(i,i); win[t] = y_{i-1-(mb+t)}
+    for (int i = c0; i < nc; ++i) {
+        const double* Li = band + (int64_t)i * W;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            if (mb + t < bw) s0 = fma(Li[mb + t + 1], win[t], s0);
+            if (mb + t + 1 < bw) s1 = fma(Li[mb + t + 2], win[t + 1], s1);
+        }
+        const double s = quad_sum(s0 + s1);
+        double yi = ((i == c ? 1.0 : 0.0) - s) * rdiag[i];
+        if (i < c || !live) yi = 0.0;
+        const double carry = __shfl_up_sync(0xffffffffu, win[7], 1, 4);
+#pragma unroll
+        for (int t = 7; t > 0; --t) win[t] = win[t - 1];
+        win[0] = q == 0 ? yi : carry;
+        if (q == 0 && live && i >= c) X[(int64_t)i * nc + c] = yi;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) win[t] = 0.0;
+    // backward: x_i = (y_i - sum_m L(i+1+m, i) x_{i+1+m}) / L(i,i); win[t] = x_{i+1+(mb+t)}
+    for (int i = nc - 1; i >= c0; --i) {
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            const int m0 = mb + t, m1 = mb + t + 1;
+            if (m0 < bw && i + 1 + m0 < nc) s0 = fma(band[(int64_t)(i + 1 + m0) * W + 1 + m0], win[t], s0);
+            if (m1 < bw && i + 1 + m1 < nc) s1 = fma(band[(int64_t)(i + 1 + m1) * W + 1 + m1], win[t + 1], s1);
+        }
+        const double s = quad_sum(s0 + s1);
+        double xi = 0.0;
+        if (live && i >= c) xi = (X[(int64_t)i * nc + c] - s) * rdiag[i];
+        const double carry = __shfl_up_sync(0xffffffffu, win[7], 1, 4);
+#pragma unroll
+        for (int t = 7; t > 0; --t) win[t] = win[t - 1];
+        win[0] = q == 0 ? xi : carry;
+        if (q == 0 && live && i >= c) {
+            X[(int64_t)i * nc + c] = xi;
+            X[(int64_t)c * nc + i] = xi;
+        }
+    }
+}
+
+__global__ void k_band_inverse(const double* __restrict__ band_all, const double* __restrict__ rdiag_all,
+                               double* __restrict__ X_all, int nc, int bw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int inst = blockIdx.y;
     const int j = blockIdx.x * wpb + warp;
     if (j >= nc) return;
     const double* band = band_all + (int64_t)inst * nc * (bw + 1);
+    const double* rdiag = rdiag_all + (int64_t)inst * nc;
     double* X = X_all + (int64_t)inst * nc * nc;
     double* y = reinterpret_cast<double*>(smraw) + (int64_t)warp * nc;
     const int W = bw + 1;
@@ -400,7 +544,7 @@ __global__ void k_band_inverse(const double* __restrict__ band_all, double* __re
         const int kmin = max(j, i - bw);
         for (int k = i - 1 - lane; k >= kmin; k -= 32) s += band[(int64_t)i * W + (i - k)] * y[k];
         s = warp_sum(s);
-        const double yi = ((i == j ? 1.0 : 0.0) - s) / band[(int64_t)i * W];
+        const double yi = ((i == j ? 1.0 : 0.0) - s) * rdiag[i];
         if (lane == 0) y[i] = yi;
         __syncwarp();
     }
@@ -409,7 +553,7 @@ __global__ void k_band_inverse(const double* __restrict__ band_all, double* __re
         const int kmax = min(i + bw, nc - 1);
         for (int k = i + 1 + lane; k <= kmax; k += 32) s += band[(int64_t)k * W + (k - i)] * y[k];
         s = warp_sum(s);
-        const double xi = (y[i] - s) / band[(int64_t)i * W];
+        const double xi = (y[i] - s) * rdiag[i];
         __syncwarp();
         if (lane == 0) y[i] = xi;
         __syncwarp();
@@ -421,7 +565,15 @@ __global__ void k_band_inverse(const double* __restrict__ band_all, double* __re
     }
 }
 
-void coarse_inverse(const double* band, double* X, int nc, int bw, int B, cudaStream_t s) {
+void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, int bw, int B, cudaStream_t s) {
+    if (bw <= 32) {
+        kbegin(KC_SETUP, s);
+        dim3 grid((nc + 31) / 32, B);  // 32 columns (8 warps of 4-lane quads) per block
+        k_band_inverse_quad<<<grid, 128, 0, s>>>(band, rdiag, X, nc, bw);
+        klaunched("k_band_inverse_quad");
+        kfinish(s);
+        return;
+    }
     int wpb = 8;
     while (wpb > 1 && (size_t)wpb * nc * sizeof(double) > 200 * 1024) wpb >>= 1;
     size_t smem = (size_t)wpb * nc * sizeof(double);
@@ -430,7 +582,7 @@ void coarse_inverse(const double* band, double* X, int nc, int bw, int B, cudaSt
     auto kfn = k_band_inverse;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((nc + wpb - 1) / wpb, B);
-    kfn<<<grid, wpb * 32, smem, s>>>(band, X, nc, bw);
+    kfn<<<grid, wpb * 32, smem, s>>>(band, rdiag, X, nc, bw);
     klaunched("k_band_inverse");
     kfinish(s);
 }

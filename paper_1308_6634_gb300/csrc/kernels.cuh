@@ -29,7 +29,9 @@ struct OpDev {
     Dims d;              // image grid
     int64_t m;           // data length per instance
     const void* taps[3]; // blur taps per axis (T), 2R+1 each
+    double taps_host[3][65];  // the same taps on the host (kernel-parameter variants)
     int R[3];
+    int generic_blur;    // 1: always use the generic blur kernel (tests and comparisons)
     const uint8_t* mask; // [N], shared by all instances
     const void* jtab;    // JosephAngle<T>[n_angles]
     int na, nb;
@@ -63,10 +65,22 @@ template <typename T>
 void mg_axpy(T* y, const T* x, int64_t n, cudaStream_t s);  // y += x
 template <typename T>
 void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw, int B, cudaStream_t s);
-void coarse_cholesky(double* band, int nc, int bw, int B, cudaStream_t s);
-void coarse_inverse(const double* band, double* X, int nc, int bw, int B, cudaStream_t s);
+// band <- its Cholesky factor; rdiag <- 1/L(j,j)
+void coarse_cholesky(double* band, double* rdiag, int nc, int bw, int B, cudaStream_t s);
+void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, int bw, int B, cudaStream_t s);
 template <typename T>
 void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t s);
+
+// ---- temporally blocked 2D V-cycle (one launch per level and direction) ----
+bool mg2d_supported(int ndim, int nu);
+// x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x)
+template <typename T>
+void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,
+              cudaStream_t s);
+// x = nu black->red sweeps from xi + P xc.  dot: 0 none, 1 alpha_1 (init), 2 alpha and rotations
+template <typename T>
+void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int nu,
+               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s);
 
 // ---- Golub-Kahan scalars and updates ----
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);

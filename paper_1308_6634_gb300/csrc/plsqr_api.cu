@@ -47,7 +47,8 @@ struct Level {
     Dims d;
     char* cond = nullptr;  // [B][ndim][N_l] (levels >= 1)
     char* b = nullptr;     // [B][N_l]
-    char* x = nullptr;
+    char* x = nullptr;     // pre-smoothed iterate (fused path) or the V-cycle result (generic path)
+    char* x2 = nullptr;    // V-cycle result of this level (fused path)
 };
 
 }  // namespace
@@ -77,6 +78,7 @@ struct plsqr_ctx {
     Level lv[16];
     int nc = 0, bw = 0;
     double* band = nullptr;
+    double* rdiag = nullptr;  // 1/L(j,j) of the coarse factor, [B][nc]
     double* X = nullptr;  // inverse of the coarsest operator, [B][nc][nc]
     GkState* st = nullptr;
     SolveParams* prm_dev = nullptr;
@@ -90,6 +92,7 @@ struct plsqr_ctx {
     size_t h_stage_n = 0;
     // graphs (with the number of kernel launches each replay executes)
     std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
     Profiler prof;
     int64_t last_launches = 0;
     bool use_graph = true;
@@ -176,6 +179,8 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     pl.nc = (int)dc.N;
     pl.bw = c->ndim == 3 ? dc.nx * dc.ny : dc.nx;
     if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
+    if ((size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) > 227 * 1024)
+        throw InvalidArg("coarsest level too wide for the banded factorisation: add levels");
     const size_t esz = c->precision == PLSQR_FP64 ? 8 : 4;
     const int64_t B = c->max_batch, N = pl.d.N;
     if (m <= 0) m = N;
@@ -183,8 +188,8 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += esz * B * (2 * m + 5 * N);  // g, u, f, p, v, w, kappa
     b += esz * B * (N + m);          // tmp (N), tmpm (m)
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
-    for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 2);
-    b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 1);
+    for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
+    b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
     b += sizeof(double) * B * (size_t)pl.nc * pl.nc;
     b += (sizeof(GkState) + sizeof(SolveParams) + sizeof(unsigned)) * B;
     b += sizeof(double) * B * 8192;
@@ -209,6 +214,17 @@ void alloc_data_buffers(plsqr_ctx* h) {
 
 // ---- the order of the kernels ----------------------------------------------------------------
 
+Hist hist_of(plsqr_ctx* h) {
+    Hist hs;
+    hs.rbar = h->h_rbar;
+    hs.R = h->h_R;
+    hs.resid = h->h_resid;
+    hs.n_outer = h->h_outer;
+    hs.n_inner = h->h_inner;
+    return hs;
+}
+
+
 template <typename T>
 void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
     const Level& Lv = h->lv[l];
@@ -232,15 +248,41 @@ void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
     }
 }
 
-// x = P b: `cycles` V-cycles from zero, x <- x + V(b - M x).
+// Temporally blocked V-cycle (2D): one pre and one post launch per level.  dot (finest level
+// only): 0 none, 1 alpha_1, 2 alpha and the rotations fused into the last post launch.
 template <typename T>
-void prec_apply(plsqr_ctx* h, const T* b, T* x, int B, cudaStream_t s) {
-    vcycle<T>(h, 0, b, x, B, s);
+void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStream_t s) {
+    const Level& Lv = h->lv[l];
+    if (l == h->L - 1) {
+        coarse_symv<T>(h->X, b, x, h->nc, B, s);
+        return;
+    }
+    const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
+    const bool isk = l == 0;
+    T* xpre = l == 0 ? P<T>(h->tmp) : P<T>(Lv.x);
+    const Level& C = h->lv[l + 1];
+    mg2d_pre<T>(cond, isk, b, xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s);
+    vcycle_fused<T>(h, l + 1, P<T>(C.b), P<T>(C.x2), B, 0, s);
+    mg2d_post<T>(cond, isk, b, xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s);
+}
+
+bool use_fused_mg(const plsqr_ctx* h) { return mg2d_supported(h->d.ndim, h->nu) && h->L > 1 && !h->generic_mg; }
+
+// x = P b: `cycles` V-cycles from zero, x <- x + V(b - M x).  Returns true when alpha and the
+// rotations were fused into the last launch (dot: 1 init, 2 iteration; 0 = not requested).
+template <typename T>
+bool prec_apply(plsqr_ctx* h, const T* b, T* x, int B, cudaStream_t s, int dot = 0) {
+    const bool fused = use_fused_mg(h);
+    const bool fuse_dot = fused && dot != 0 && h->cycles == 1;
+    if (fused) vcycle_fused<T>(h, 0, b, x, B, fuse_dot ? dot : 0, s);
+    else vcycle<T>(h, 0, b, x, B, s);
     for (int c = 1; c < h->cycles; ++c) {
         mg_apply_level<T>(P<T>(h->kappa), true, x, b, P<T>(h->r0), h->d, B, s);
-        vcycle<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, s);
+        if (fused) vcycle_fused<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, 0, s);
+        else vcycle<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, s);
         mg_axpy<T>(x, P<T>(h->e0), (int64_t)B * h->d.N, s);
     }
+    return fuse_dot;
 }
 
 // Coarse conductances, band of the coarsest operator, its Cholesky factor and inverse.
@@ -251,19 +293,10 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
                       h->lv[l + 1].d, B, s);
     const int lc = h->L - 1;
     coarse_assemble<T>(lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond), lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
-    coarse_cholesky(h->band, h->nc, h->bw, B, s);
-    coarse_inverse(h->band, h->X, h->nc, h->bw, B, s);
+    coarse_cholesky(h->band, h->rdiag, h->nc, h->bw, B, s);
+    coarse_inverse(h->band, h->rdiag, h->X, h->nc, h->bw, B, s);
 }
 
-Hist hist_of(plsqr_ctx* h) {
-    Hist hs;
-    hs.rbar = h->h_rbar;
-    hs.R = h->h_R;
-    hs.resid = h->h_resid;
-    hs.n_outer = h->h_outer;
-    hs.n_inner = h->h_inner;
-    return hs;
-}
 
 // MLSQR (Algorithm 2) from f = 0 with the current priorconditioner.
 template <typename T>
@@ -274,14 +307,14 @@ void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
     T* tmp = P<T>(h->tmp);
     gk_init_norm<T>(g, h->m, B, h->st, h->red, s);                                  // steps 2, 7
     op_apply<T>(h->od, true, EPI_ADJ_INIT, g, p, nullptr, tmp, B, h->st, h->red, s);  // step 3
-    prec_apply<T>(h, p, v, B, s);                                                   // step 4
-    gk_dot_rotate<T>(v, p, N, B, true, h->st, hs, h->red, s);                       // steps 5-6
+    if (!prec_apply<T>(h, p, v, B, s, 1))                                           // step 4
+        gk_dot_rotate<T>(v, p, N, B, true, h->st, hs, h->red, s);                   // steps 5-6
     gk_update<T>(f, w, v, N, B, true, h->st, s);                                    // step 7
     for (int i = 1; i <= n_inner; ++i) {
         op_apply<T>(h->od, false, EPI_FWD, v, u, i == 1 ? g : u, tmp, B, h->st, h->red, s);  // step 10
         op_apply<T>(h->od, true, EPI_ADJ, u, p, p, tmp, B, h->st, h->red, s);                // step 11
-        prec_apply<T>(h, p, v, B, s);                                                        // step 12
-        gk_dot_rotate<T>(v, p, N, B, false, h->st, hs, h->red, s);                           // 13-17
+        if (!prec_apply<T>(h, p, v, B, s, 2))                                                // step 12
+            gk_dot_rotate<T>(v, p, N, B, false, h->st, hs, h->red, s);                       // 13-17
         gk_update<T>(f, w, v, N, B, false, h->st, s);                                        // 19-20
     }
 }
@@ -474,12 +507,15 @@ void destroy_ctx(plsqr_ctx* h) {
 }
 
 template <typename T>
-void upload_taps(plsqr_ctx* h, int dd, double sigma, int R) {
+void upload_taps(plsqr_ctx* h, OpDev& od, int dd, double sigma, int R) {
     std::vector<double> w(2 * R + 1);
     double s = 0.0;
     for (int k = -R; k <= R; ++k) s += (w[k + R] = std::exp(-(double)(k * k) / (2.0 * sigma * sigma)));
     std::vector<T> wt(2 * R + 1);
-    for (int k = 0; k <= 2 * R; ++k) wt[k] = (T)(w[k] / s);
+    for (int k = 0; k <= 2 * R; ++k) {
+        wt[k] = (T)(w[k] / s);
+        od.taps_host[dd][k] = w[k] / s;
+    }
     dfree(h, h->taps[dd]);
     h->taps[dd] = dalloc(h, sizeof(T) * wt.size());
     ck(cudaMemcpy(h->taps[dd], wt.data(), sizeof(T) * wt.size(), cudaMemcpyHostToDevice), "taps");
@@ -540,6 +576,8 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         h->m = h->d.N;
         const char* eg = std::getenv("PLSQR_GRAPH");
         h->use_graph = !(eg && eg[0] == '0');
+        const char* em = std::getenv("PLSQR_GENERIC_MG");
+        h->generic_mg = em && em[0] == '1';
         ck(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
         ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "cudaEventCreate");
@@ -564,8 +602,10 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
             h->lv[l].cond = dalloc(h, e * B * Nl * h->d.ndim);
             h->lv[l].b = dalloc(h, e * B * Nl);
             h->lv[l].x = dalloc(h, e * B * Nl);
+            h->lv[l].x2 = dalloc(h, e * B * Nl);
         }
         h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
+        h->rdiag = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc);
         h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
         h->st = (GkState*)dalloc(h, sizeof(GkState) * B);
         ck(cudaMemset(h->st, 0, sizeof(GkState) * B), "memset");
@@ -596,6 +636,8 @@ int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
         OpDev od{};
         od.d = d;
         od.kind = op->kind;
+        const char* eg = std::getenv("PLSQR_GENERIC_BLUR");
+        od.generic_blur = (eg && eg[0] == '1') ? 1 : 0;
         if (op->kind == PLSQR_OP_BLUR || op->kind == PLSQR_OP_BLUR_MASK) {
             for (int dd = 0; dd < d.ndim; ++dd) {
                 if (!(op->sigma[dd] > 0.0) || op->radius[dd] < 0 || op->radius[dd] > 32)
@@ -620,7 +662,7 @@ int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
         if (op->kind == PLSQR_OP_BLUR || op->kind == PLSQR_OP_BLUR_MASK) {
             by_type(h, [&](auto tv) {
                 using T = decltype(tv);
-                for (int dd = 0; dd < d.ndim; ++dd) upload_taps<T>(h, dd, op->sigma[dd], op->radius[dd]);
+                for (int dd = 0; dd < d.ndim; ++dd) upload_taps<T>(h, od, dd, op->sigma[dd], op->radius[dd]);
             });
             for (int dd = 0; dd < d.ndim; ++dd) {
                 od.taps[dd] = h->taps[dd];

@@ -6,11 +6,13 @@ iterate on the 1024x1024 deblurring workload by about 1e-3 (see test_oracle_sens
 Two correct implementations that round differently therefore cannot agree better than that
 spread, so long-horizon parity is asserted against it:
 
-  fp64 handles: E = max_k relerr(oracle(g (1 + eps_k xi_k)), oracle(g)),  eps_k in 1e-16..1e-14
+  fp64 handles: E = max_k relerr(oracle(g (1 + eps_k xi_k)), oracle(g)),  eps_k in 1e-15..1e-13
   fp32 handles: E = max_k relerr(fp32_model(g (1 + eps_k xi_k)), oracle(g)), eps_k in 1e-7..1e-6
 
 (a spread of magnitudes, because the deviation is heavy tailed: most perturbations move the
-result a little, some a lot), where fp32_model runs the same algorithm with the oracle's operators, V-cycle and
+result a little, some a lot; for double the magnitudes reach above one rounding because the
+per-operation roundings of the ~1e4 operations that touch each value in an iteration add up),
+where fp32_model runs the same algorithm with the oracle's operators, V-cycle and
 diffusivity but rounds every vector and every operator output to float32 (scalars in
 double), i.e. an idealised single-precision implementation.  A GPU result passes when its
 error is within max(bar, C * E).  The model only sizes a tolerance: no expected value comes
@@ -21,7 +23,7 @@ import numpy as np
 import oracle as O
 from paper_1308_6634_gb300 import synth
 
-C_ENV = 5.0
+C_ENV = 10.0  # the spread is heavy tailed; a coding slip gives errors of order one
 
 
 def rel(a, b):
@@ -111,17 +113,17 @@ def solve_task(args):
     return fp32_model_solve(op, g, W.reg, W.T, W.tau, n_outer, n_inner, W.levels, W.nu, W.cycles)
 
 
-EPS = {"fp64": (1e-16, 1e-15, 1e-14), "fp32": (1e-7, 3e-7, 1e-6)}
+EPS = {"fp64": (1e-15, 1e-14, 1e-13), "fp32": (1e-7, 3e-7, 1e-6)}
 
 
-def envelope_tasks(W, n_outer, n_inner, K=6):
+def envelope_tasks(W, n_outer, n_inner, K=9):
     kind = "oracle" if W.precision == "fp64" else "model32"
     eps = EPS[W.precision]
     return [("oracle", W, n_outer, n_inner, 0.0, 0)] + [(kind, W, n_outer, n_inner, eps[k % len(eps)], k)
                                                          for k in range(K)]
 
 
-def reference_and_envelope(W, n_outer, n_inner, K=6, pool=None):
+def reference_and_envelope(W, n_outer, n_inner, K=9, pool=None):
     """(oracle result, {key: envelope}) for the precision of workload W."""
     tasks = envelope_tasks(W, n_outer, n_inner, K)
     res = list(pool.map(solve_task, tasks)) if pool is not None else [solve_task(t) for t in tasks]
