@@ -34,12 +34,17 @@ L2_BYTES = 126 * 1024 * 1024
 METRIC = "solves/s and p50/p99 ms at <=1e-4 rel err vs FP64 oracle; HBM GB/s vs peak"
 
 # Algorithmic bytes per instance and per launch of each kernel class, in units of
-# (vector element size x N): the minimum reads and writes each pass forces.
-#   fwd:     v~ in, u_prev in, u out                         3
-#   adj:     u in, p~ in, p~ out                             3
-#   gs_fine: x of the other colour in (1/2), kappa in (1), b of this colour in (1/2),
-#            x of this colour out (1/2)                      2.5
-ALG_UNITS = {"fwd": 3.0, "adj": 3.0, "gs_fine": 2.5}
+# (vector element size x N): the minimum reads and writes each pass forces, for the kernels the
+# 2D single-precision blur workload runs.
+#   fwd:  first iteration v~ in, u_prev in, u out (3); later iterations also apply the previous
+#         iteration's update on the same cells: + w~, f in and out (7)      -> (3 + 7 (n-1)) / n
+#   adj:  u in, p~ in, p~ out                                               3
+#   gs_fine (finest-level V-cycle launches, pre and post alternate):
+#         pre:  p~ (rhs), kappa in, x out, restricted residual out (1/4)    3.25
+#         post: x_in, p~, kappa, coarse correction (1/4) in, v~ out         4.25  -> mean 3.75
+def alg_units(W):
+    n = W.n_inner
+    return {"fwd": (3.0 + 7.0 * (n - 1)) / n, "adj": 3.0, "gs_fine": 3.75}
 
 
 def parse():
@@ -317,6 +322,7 @@ def main():
         torch.cuda.synchronize()
         prof = S.profile_read()
         S.profile(False)
+        ALG_UNITS = alg_units(W)
         cand = {k: v for k, v in prof.items() if k in ALG_UNITS and v[1] > 0}
         top = max(prof.items(), key=lambda kv: kv[1][0])[0]
         dom = max(cand.items(), key=lambda kv: kv[1][0])[0] if cand else None

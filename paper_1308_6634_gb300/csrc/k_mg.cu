@@ -350,25 +350,37 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     return r;
 }
 
-// In-place banded Cholesky M = L L^T, one block of 1024 threads per instance.  The rows that
-// column j touches live in a sliding window of bw+4 rows in shared memory.  Iteration j:
-//  - scales column j-1 by 1/sqrt(a_{j-1}) and sets L(j-1,j-1) = sqrt(a_{j-1}),
-//  - writes the finished row j-2 back and loads row j+bw+1 into the slot row j-3 left,
-//  - applies the trailing update of column j with the unscaled column and pivot a_j:
-//    L(i,k) -= L(i,j) L(k,j) / a_j,  j < k <= i <= j+bw,
-// all on disjoint entries, so one barrier per column.  The thread that updates the next
-// pivot also forms 1/a, sqrt(a) and 1/sqrt(a) once (triple-buffered in shared memory), so
-// no other thread divides or takes a root in double.  rdiag receives 1/L(j,j).
+// In-place banded Cholesky M = L L^T, one block per instance.  The rows that column j touches
+// live in a sliding window of bw+4 rows in shared memory.  Column j:
+//  phase 1: the factors f_i = L(i,j)/a_j of the column (one per row), scaling of column j-1 by
+//           1/sqrt(a_{j-1}) with L(j-1,j-1) = sqrt(a_{j-1}), write-back of the finished row j-2
+//           and load of row j+bw+1 into the slot row j-3 left (all on disjoint entries);
+//  phase 2: the trailing update L(i,k) -= f_i L(k,j), j < k <= i <= j+bw, with the
+//           bw(bw+1)/2 pairs packed densely over the threads (the double-precision pipe is
+//           narrow, so lanes that would sit predicated off cost as much as busy ones).
+// The thread that updates the next pivot forms 1/a, sqrt(a) and 1/sqrt(a) once (triple-
+// buffered in shared memory).  rdiag receives 1/L(j,j).
 __global__ void __launch_bounds__(1024) k_chol_band(double* band_all, double* rdiag_all, int nc, int bw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* win = reinterpret_cast<double*>(smraw);
-    __shared__ double s_inv[3], s_sq[3], s_rsq[3];
     const int W = bw + 1, S = bw + 4;
+    const int P = bw * (bw + 1) / 2;
+    double* win = reinterpret_cast<double*>(smraw);
+    double* sf = win + (size_t)S * W;                            // bw factors
+    unsigned short* pii = reinterpret_cast<unsigned short*>(sf + bw);  // pair table
+    unsigned short* pkk = pii + P;
+    __shared__ double s_inv[3], s_sq[3], s_rsq[3];
     double* band = band_all + (int64_t)blockIdx.x * nc * W;
     double* rdiag = rdiag_all + (int64_t)blockIdx.x * nc;
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int ii = tid; ii < bw; ii += nt) {  // pairs of row ii: (ii, 0..ii) at ii(ii+1)/2
+        const int base = ii * (ii + 1) / 2;
+        for (int kk = 0; kk <= ii; ++kk) {
+            pii[base + kk] = (unsigned short)ii;
+            pkk[base + kk] = (unsigned short)kk;
+        }
+    }
     const int nload = min(bw + 1, nc);
-    for (int e = tid; e < nload * W; e += 1024) {
+    for (int e = tid; e < nload * W; e += nt) {
         const int r = e / W, k = e - r * W;
         win[(r % S) * W + k] = band[(int64_t)r * W + k];
     }
@@ -381,10 +393,21 @@ __global__ void __launch_bounds__(1024) k_chol_band(double* band_all, double* rd
     }
     __syncthreads();
     for (int j = 0; j <= nc; ++j) {
-        if (j >= 1) {  // scale column j-1
+        // phase 1
+        if (j < nc) {
+            const double inv_a = s_inv[j % 3];
+            const int base = (j + 1) % S;
+            for (int ii = tid; ii < bw; ii += nt) {
+                const int i = j + 1 + ii;
+                int si = base + ii;
+                if (si >= S) si -= S;
+                sf[ii] = i < nc ? win[si * W + ii + 1] * inv_a : 0.0;  // L(i, j) / a_j
+            }
+        }
+        if (j >= 1) {
             const int c = (j - 1) % 3;
             const double rs = s_rsq[c];
-            for (int t = tid; t < W; t += 1024) {
+            for (int t = tid; t < W; t += nt) {
                 const int i = j - 1 + t;
                 if (i >= nc) break;
                 double* Ri = win + (i % S) * W;
@@ -396,36 +419,31 @@ __global__ void __launch_bounds__(1024) k_chol_band(double* band_all, double* rd
                 }
             }
         }
-        if (j >= 2) {  // row j-2 is final
+        if (j >= 2) {
             const int r = j - 2;
-            for (int k = tid; k < W; k += 1024) band[(int64_t)r * W + k] = win[(r % S) * W + k];
+            for (int k = tid; k < W; k += nt) band[(int64_t)r * W + k] = win[(r % S) * W + k];
         }
         {
             const int r = j + bw + 1;
             if (r < nc)
-                for (int k = tid; k < W; k += 1024) win[(r % S) * W + k] = band[(int64_t)r * W + k];
+                for (int k = tid; k < W; k += nt) win[(r % S) * W + k] = band[(int64_t)r * W + k];
         }
+        __syncthreads();
+        // phase 2
         if (j < nc) {
-            const double inv_a = s_inv[j % 3];
-            const int base = (j + 1) % S;  // slot of row j+1; rows j+1.. follow cyclically
-            for (int ii = ty; ii < bw; ii += 32) {
-                const int i = j + 1 + ii;
-                if (i >= nc) break;
-                int si = base + ii;
-                if (si >= S) si -= S;
-                double* Ri = win + si * W;
-                double f = 0.0;
-                if (tx == 0) f = Ri[ii + 1] * inv_a;  // L(i, j) / a_j, once per row
-                f = __shfl_sync(0xffffffffu, f, 0);
+            const int base = (j + 1) % S;
+            for (int pidx = tid; pidx < P; pidx += nt) {
+                const int ii = pii[pidx], kk = pkk[pidx];
+                if (j + 1 + ii >= nc) continue;
+                const double f = sf[ii];
                 if (f == 0.0) continue;
-                for (int kk = tx; kk <= ii; kk += 32) {
-                    int sk = base + kk;
-                    if (sk >= S) sk -= S;
-                    Ri[ii - kk] -= f * win[sk * W + kk + 1];  // L(i,k) -= f L(k,j), k = j+1+kk
-                }
+                int si = base + ii, sk = base + kk;
+                if (si >= S) si -= S;
+                if (sk >= S) sk -= S;
+                win[si * W + (ii - kk)] -= f * win[sk * W + kk + 1];  // L(i,k) -= f_i L(k,j)
             }
-            if (tid == 0 && j + 1 < nc) {  // thread 0 updated L(j+1,j+1) (ii = kk = 0)
-                const double a = win[((j + 1) % S) * W], r = rsqrt_nr(a);
+            if (tid == 0 && j + 1 < nc) {  // thread 0 owns the pair (0, 0): L(j+1, j+1)
+                const double a = win[base * W], r = rsqrt_nr(a);
                 const int c = (j + 1) % 3;
                 s_inv[c] = r * r;
                 s_sq[c] = a * r;
@@ -436,16 +454,18 @@ __global__ void __launch_bounds__(1024) k_chol_band(double* band_all, double* rd
     }
     {
         const int r = nc - 1;
-        for (int k = tid; k < W; k += 1024) band[(int64_t)r * W + k] = win[(r % S) * W + k];
+        for (int k = tid; k < W; k += nt) band[(int64_t)r * W + k] = win[(r % S) * W + k];
     }
 }
 
 void coarse_cholesky(double* band, double* rdiag, int nc, int bw, int B, cudaStream_t s) {
     kbegin(KC_SETUP, s);
-    const size_t smem = sizeof(double) * (size_t)(bw + 4) * (bw + 1);
+    const int P = bw * (bw + 1) / 2;
+    const size_t smem = sizeof(double) * ((size_t)(bw + 4) * (bw + 1) + bw) + sizeof(unsigned short) * 2 * P;
     if (smem > 227 * 1024) throw std::runtime_error("coarse_cholesky: band too wide for shared memory");
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chol_band<<<B, 1024, smem, s>>>(band, rdiag, nc, bw);
+    const int nt = std::min(1024, std::max(64, ((P + 31) / 32) * 32));
+    k_chol_band<<<B, nt, smem, s>>>(band, rdiag, nc, bw);
     klaunched("k_chol_band");
     kfinish(s);
 }

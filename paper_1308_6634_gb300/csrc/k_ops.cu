@@ -144,11 +144,15 @@ struct TapsF {
 };
 
 // TMA (R % 4 == 0): the whole halo tile arrives with one tensor copy (zero fill outside).
-template <int R, int EPI, bool MASK_IN, bool MASK_OUT, bool TMA>
+// UPD (with EPI_FWD): also the pending solution update of the previous iteration on the same
+// cells, f += (phi/rho) w~, w~ = v~ - (theta/rho) w~ (Algorithm 2 steps 19-20), with v~ taken
+// from the staged input tile.
+template <int R, int EPI, bool MASK_IN, bool MASK_OUT, bool TMA, bool UPD>
 __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUtensorMap map_in,
                                                    const float* __restrict__ in, float* out, const float* prev,
                                                    const uint8_t* __restrict__ mask, Dims d, const TapsF<R> wx,
-                                                   const TapsF<R> wy, GkState* st, Red red) {
+                                                   const TapsF<R> wy, GkState* st, Red red, float* __restrict__ fu,
+                                                   float* __restrict__ wu) {
     constexpr int LX = ((BTX + 2 * R) + 3) & ~3;  // row pitch (floats), multiple of 4
     constexpr int LY = BTY + 2 * R;
     constexpr int NW4 = (4 + 2 * R + 3) / 4;       // float4 loads per x-pass window
@@ -163,6 +167,25 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     const int x0 = blockIdx.x * BTX, y0 = blockIdx.y * BTY;
     const int64_t plane_off = (int64_t)plane * d.nx * d.ny;
     const int64_t mask_off = (int64_t)(plane - inst * d.nz) * d.nx * d.ny;
+    // this thread's outputs: column c, rows srow..srow+7 of the tile; their previous values
+    // (and w~, f for UPD) are fetched now so the loads overlap the staging and the x pass
+    const int oc = tid & (BTX - 1), srow = 8 * (tid / BTX);
+    const int ogx = x0 + oc;
+    float pv[8], wv[8], fv[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        pv[o] = wv[o] = fv[o] = 0.f;
+        const int gy = y0 + srow + o;
+        if (gy < d.ny && ogx < d.nx) {
+            const int64_t gi = plane_off + (int64_t)gy * d.nx + ogx;
+            if (EPI == EPI_FWD) pv[o] = prev[gi];
+            if (EPI == EPI_ADJ) pv[o] = out[gi];
+            if (UPD) {
+                wv[o] = wu[gi];
+                fv[o] = fu[gi];
+            }
+        }
+    }
     if constexpr (TMA) {
         if (tid == 0) mbar_init(&bar, 1);
         __syncthreads();
@@ -211,7 +234,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     if (EPI != EPI_PLAIN) epi_coefs<float, EPI>(st[inst], ca, cp);
     float part = 0.f;
     {  // y pass: column c, outputs rows 8s..8s+7
-        const int c = tid & (BTX - 1), srow = 8 * (tid / BTX);
+        const int c = oc;
         float win[8 + 2 * R];
 #pragma unroll
         for (int k = 0; k < 8 + 2 * R; ++k) win[k] = smid[(srow + k) * BTX + c];
@@ -222,7 +245,13 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
         for (int k = 0; k <= 2 * R; ++k)
 #pragma unroll
             for (int o = 0; o < 8; ++o) acc[o] = fmaf(wy.w[k], win[o + k], acc[o]);
-        const int gx = x0 + c;
+        const int gx = ogx;
+        float cv = 0.f, cf = 0.f, cw = 0.f;
+        if (UPD) {
+            cv = (float)st[inst].c_upd_v;
+            cf = (float)st[inst].cf;
+            cw = (float)st[inst].cw;
+        }
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             const int gy = y0 + srow + o;
@@ -230,8 +259,17 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
                 const int64_t oo = (int64_t)gy * d.nx + gx;
                 float a = acc[o];
                 if (MASK_OUT) a = mask[mask_off + oo] ? a : 0.f;
-                const float v = epi_store<float, EPI>(a, ca, cp, out, prev, plane_off + oo);
+                float v;
+                if (EPI == EPI_PLAIN) v = a;
+                else if (EPI == EPI_ADJ_INIT) v = a * ca;
+                else v = a * ca - cp * pv[o];
+                out[plane_off + oo] = v;
                 if (EPI == EPI_FWD) part = fmaf(v, v, part);
+                if (UPD) {
+                    const float vin = sin[(srow + o + R) * LX + c + R];
+                    fu[plane_off + oo] = fmaf(cf, wv[o], fv[o]);
+                    wu[plane_off + oo] = vin * cv - cw * wv[o];
+                }
             }
         }
     }
@@ -409,9 +447,9 @@ __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, 
 // ---- launchers ---------------------------------------------------------------------------
 
 
-template <int R, int EPI, bool MI, bool MO>
+template <int R, int EPI, bool MI, bool MO, bool UPD = false>
 static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const float* prev, int B, GkState* st,
-                             Red red, cudaStream_t s) {
+                             Red red, cudaStream_t s, float* fu = nullptr, float* wu = nullptr) {
     const Dims& d = op.d;
     TapsF<R> wx, wy;
     for (int k = 0; k <= 2 * R; ++k) {
@@ -426,9 +464,13 @@ static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const
     if constexpr (R % 4 == 0 && !MI) {
         tma = tma_enabled() &&
               tma_map_3d(&map, in, 4, d.nx, d.ny, (int64_t)d.nz * B, BTX + 2 * R, BTY + 2 * R, 1);
-        if (tma) k_blur2d_rb<R, EPI, MI, MO, true><<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red);
+        if (tma)
+            k_blur2d_rb<R, EPI, MI, MO, true, UPD>
+                <<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red, fu, wu);
     }
-    if (!tma) k_blur2d_rb<R, EPI, MI, MO, false><<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red);
+    if (!tma)
+        k_blur2d_rb<R, EPI, MI, MO, false, UPD>
+            <<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red, fu, wu);
     klaunched("k_blur2d_rb");
 }
 
@@ -541,6 +583,36 @@ void op_apply(const OpDev& op, bool adjoint, int epi, const T* in, T* out, const
         case EPI_ADJ_INIT: apply_epi<T, EPI_ADJ_INIT>(op, adjoint, in, out, prev, tmp, B, st, red, s); return;
     }
     throw std::runtime_error("op_apply: bad epilogue");
+}
+
+// Forward step fused with the previous iteration's solution update (2D float blur with a
+// register-blocked radius); returns false when not applicable (caller runs them separately).
+bool op_fwd_update(const OpDev& op, const float* v, float* u, float* f, float* w, int B, GkState* st, Red red,
+                   cudaStream_t s) {
+    if ((op.kind != OPK_BLUR && op.kind != OPK_BLUR_MASK) || op.d.ndim != 2 || op.R[0] != op.R[1] ||
+        op.generic_blur)
+        return false;
+    const bool mo = op.kind == OPK_BLUR_MASK;
+    struct Scope {
+        cudaStream_t s;
+        ~Scope() { kfinish(s); }
+    } scope{s};
+    kbegin(KC_FWD, s);
+#define FU_CASE(R_)                                                                                      \
+    case R_:                                                                                             \
+        if (mo) launch_blur2d_rb<R_, EPI_FWD, false, true, true>(op, v, u, u, B, st, red, s, f, w);     \
+        else launch_blur2d_rb<R_, EPI_FWD, false, false, true>(op, v, u, u, B, st, red, s, f, w);       \
+        return true;
+    switch (op.R[0]) {
+        FU_CASE(6)
+        FU_CASE(9)
+        FU_CASE(12)
+        FU_CASE(15)
+        default: break;
+    }
+#undef FU_CASE
+    kfinish(s);
+    return false;
 }
 
 template void op_apply<float>(const OpDev&, bool, int, const float*, float*, const float*, float*, int, GkState*,

@@ -42,6 +42,11 @@ template <typename T>
 void op_apply(const OpDev& op, bool adjoint, int epi, const T* in, T* out, const T* prev, T* tmp,
               int B, GkState* st, Red red, cudaStream_t s);
 
+// u = A v / alpha - (alpha/beta) u with beta_new = ||u||, fused with the pending update
+// f += cf w, w = v c_upd_v - cw w; false if not available for this operator (then nothing ran).
+bool op_fwd_update(const OpDev& op, const float* v, float* u, float* f, float* w, int B, GkState* st, Red red,
+                   cudaStream_t s);
+
 // kappa = max(r'(t)/t, kfloor*kappa(0)), R = sum r(t) per instance (state reg/T).
 template <typename T>
 void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, double kfloor, Red red,

@@ -17,6 +17,7 @@
 #include <stdexcept>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/plsqr.h"
@@ -93,6 +94,7 @@ struct plsqr_ctx {
     // graphs (with the number of kernel launches each replay executes)
     std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
+    bool no_fuse_update = false;  // PLSQR_FUSE_UPDATE=0: separate update kernel (comparisons)
     Profiler prof;
     int64_t last_launches = 0;
     bool use_graph = true;
@@ -179,7 +181,8 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     pl.nc = (int)dc.N;
     pl.bw = c->ndim == 3 ? dc.nx * dc.ny : dc.nx;
     if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
-    if ((size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) > 227 * 1024)
+    if ((size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 + pl.bw * 8 >
+        227 * 1024)
         throw InvalidArg("coarsest level too wide for the banded factorisation: add levels");
     const size_t esz = c->precision == PLSQR_FP64 ? 8 : 4;
     const int64_t B = c->max_batch, N = pl.d.N;
@@ -310,13 +313,21 @@ void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
     if (!prec_apply<T>(h, p, v, B, s, 1))                                           // step 4
         gk_dot_rotate<T>(v, p, N, B, true, h->st, hs, h->red, s);                   // steps 5-6
     gk_update<T>(f, w, v, N, B, true, h->st, s);                                    // step 7
+    bool pending = false;  // update (steps 19-20) of the previous iteration not yet applied
     for (int i = 1; i <= n_inner; ++i) {
-        op_apply<T>(h->od, false, EPI_FWD, v, u, i == 1 ? g : u, tmp, B, h->st, h->red, s);  // step 10
+        bool fused = false;
+        if (pending) {
+            if constexpr (std::is_same<T, float>::value)
+                fused = !h->no_fuse_update && op_fwd_update(h->od, v, u, f, w, B, h->st, h->red, s);
+            if (!fused) gk_update<T>(f, w, v, N, B, false, h->st, s);                        // 19-20
+        }
+        if (!fused) op_apply<T>(h->od, false, EPI_FWD, v, u, i == 1 ? g : u, tmp, B, h->st, h->red, s);  // 10
         op_apply<T>(h->od, true, EPI_ADJ, u, p, p, tmp, B, h->st, h->red, s);                // step 11
         if (!prec_apply<T>(h, p, v, B, s, 2))                                                // step 12
             gk_dot_rotate<T>(v, p, N, B, false, h->st, hs, h->red, s);                       // 13-17
-        gk_update<T>(f, w, v, N, B, false, h->st, s);                                        // 19-20
+        pending = true;
     }
+    if (pending) gk_update<T>(f, w, v, N, B, false, h->st, s);                               // 19-20
 }
 
 // One outer step of Algorithm 3.
@@ -578,6 +589,8 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         h->use_graph = !(eg && eg[0] == '0');
         const char* em = std::getenv("PLSQR_GENERIC_MG");
         h->generic_mg = em && em[0] == '1';
+        const char* eu = std::getenv("PLSQR_FUSE_UPDATE");
+        h->no_fuse_update = eu && eu[0] == '0';
         ck(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
         ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "cudaEventCreate");
