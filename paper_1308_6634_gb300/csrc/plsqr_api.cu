@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <tuple>
@@ -564,6 +565,41 @@ void by_type(plsqr_ctx* h, F&& fn) {
 
 }  // namespace
 
+// ---- separable blur without any device allocation ------------------------------------------
+// Scratch of plsqr_blur_noalloc: the blur taps (first 2 KiB) and the intermediate volume of the
+// 3D blur.  A file-scope array, so every GPU that loads this library holds it until exit; its
+// device address is looked up once per device (the host-side name is only a stand-in).
+constexpr size_t kNoallocTapsBytes = 2048;
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch on the current device (first call per device looks it up).
+void* noalloc_scratch(int* err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        *err = PLSQR_E_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            *err = PLSQR_E_CUDA;
+            return nullptr;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
 extern "C" {
 
 int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
@@ -914,5 +950,62 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n) {
 }
 
 int64_t plsqr_last_launches(plsqr_handle h) { return h ? h->last_launches : -1; }
+
+int plsqr_blur_noalloc(int32_t ndim, const int64_t* n, int32_t precision, const double* sigma, const int32_t* radius,
+                       const void* x, void* y, void* stream) {
+    if (!n || !sigma || !radius || !x || !y || (ndim != 2 && ndim != 3)) return PLSQR_E_INVALID;
+    if (precision != PLSQR_FP32 && precision != PLSQR_FP64) return PLSQR_E_INVALID;
+    const size_t esz = precision == PLSQR_FP64 ? 8 : 4;
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (n[d] < 1 || n[d] > (1 << 20)) return PLSQR_E_INVALID;
+        if (!(sigma[d] > 0.0) || radius[d] < 0 || radius[d] > 32) return PLSQR_E_INVALID;
+        N *= n[d];
+    }
+    if ((size_t)N * esz > kNoallocScratchBytes - kNoallocTapsBytes) return PLSQR_E_INVALID;  // beyond the maximum
+    int err = PLSQR_OK;
+    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(&err));
+    if (!scratch) return err;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        OpDev od{};
+        od.kind = OPK_BLUR;
+        od.d = make_dims(ndim, n[0], n[1], ndim == 3 ? n[2] : 1);
+        od.m = od.d.N;
+        // taps of every axis, in the element type, packed into the first 2 KiB of the scratch
+        double taps_bytes[kNoallocTapsBytes / sizeof(double)];
+        unsigned char* tb = reinterpret_cast<unsigned char*>(taps_bytes);
+        size_t off = 0;
+        for (int d = 0; d < ndim; ++d) {
+            const int R = radius[d];
+            double sum = 0.0;
+            for (int k = -R; k <= R; ++k) sum += std::exp(-(double)(k * k) / (2.0 * sigma[d] * sigma[d]));
+            od.R[d] = R;
+            od.taps[d] = scratch + off;
+            for (int k = -R; k <= R; ++k) {
+                const double w = std::exp(-(double)(k * k) / (2.0 * sigma[d] * sigma[d])) / sum;
+                od.taps_host[d][k + R] = w;
+                if (esz == 8) std::memcpy(tb + off + (k + R) * 8, &w, 8);
+                else {
+                    const float wf = (float)w;
+                    std::memcpy(tb + off + (k + R) * 4, &wf, 4);
+                }
+            }
+            off += ((2 * R + 1) * esz + 15) & ~(size_t)15;
+        }
+        ck(cudaMemcpyAsync(scratch, taps_bytes, off, cudaMemcpyHostToDevice, s), "taps");
+        Red red{};
+        if (esz == 8)
+            op_apply<double>(od, false, EPI_PLAIN, (const double*)x, (double*)y, nullptr,
+                             reinterpret_cast<double*>(scratch + kNoallocTapsBytes), 1, nullptr, red, s);
+        else
+            op_apply<float>(od, false, EPI_PLAIN, (const float*)x, (float*)y, nullptr,
+                            reinterpret_cast<float*>(scratch + kNoallocTapsBytes), 1, nullptr, red, s);
+        return PLSQR_OK;
+    } catch (const std::exception& e) {
+        std::fprintf(stderr, "plsqr_blur_noalloc: %s\n", e.what());
+        return PLSQR_E_CUDA;
+    }
+}
 
 }  // extern "C"

@@ -74,6 +74,7 @@ def lib():
         "plsqr_profile": ([vp, i32], C.c_int),
         "plsqr_profile_read": ([vp, vp, vp, i32], C.c_int),
         "plsqr_last_launches": ([vp], i64),
+        "plsqr_blur_noalloc": ([i32, C.POINTER(i64), i32, C.POINTER(d), C.POINTER(i32), vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -86,7 +87,7 @@ def lib():
 EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_host", "plsqr_solve_batch",
             "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
-            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches"]
+            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
 
@@ -151,6 +152,25 @@ def plsqr_create(config, stream=None):
 
 def plsqr_workspace_bytes(config, op=None):
     return lib().plsqr_workspace_bytes(C.byref(config), C.byref(op) if op is not None else None)
+
+
+def plsqr_blur_noalloc(x, sigma, radius, y=None, stream=None):
+    """y = B x for a contiguous float32/float64 CUDA tensor of shape (ny, nx) or (nz, ny, nx),
+    without any device allocation inside the library (sigma, radius in x, y(, z) order)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(x)
+    prec = PREC["fp64"] if x.dtype == torch.float64 else PREC["fp32"]
+    nd = x.dim()
+    dims = list(reversed(x.shape)) + [1] * (3 - nd)
+    n = (C.c_int64 * 3)(*[int(v) for v in dims])
+    sg = (C.c_double * 3)(*(list(map(float, sigma)) + [0.0] * (3 - len(sigma))))
+    rd = (C.c_int32 * 3)(*(list(map(int, radius)) + [0] * (3 - len(radius))))
+    rc = lib().plsqr_blur_noalloc(nd, n, prec, sg, rd, _dptr(x, x.dtype), _dptr(y, x.dtype, x.numel()),
+                                  C.c_void_p(stream if stream is not None else _current_stream()))
+    if rc != OK:
+        raise PlsqrError(rc, "plsqr_blur_noalloc failed")
+    return y
 
 
 def _current_stream():
