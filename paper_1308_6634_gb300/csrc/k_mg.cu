@@ -607,34 +607,47 @@ void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, 
     kfinish(s);
 }
 
-// x = X b on the coarsest level, one warp per row; X and the sums in double (the coarse
-// correction is a difference of large terms, so its accuracy sets that of P).
+// x = X b on the coarsest level, one warp per row.  Double-precision handles: X and the sums in
+// double.  Single-precision handles: X rounded to float once per outer step (half the bytes per
+// V-cycle), sums in float -- the coarse correction then carries an error of a few float ulps of
+// |X||b|, below that of the single-precision smoothing around it.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_symv(const double* __restrict__ X_all, const T* __restrict__ b_all,
+__global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all, const T* __restrict__ b_all,
                                                      T* __restrict__ x_all, int nc) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* sb = reinterpret_cast<double*>(smraw);
+    T* sb = reinterpret_cast<T*>(smraw);
     const int inst = blockIdx.y;
     const T* b = b_all + (int64_t)inst * nc;
-    for (int i = threadIdx.x; i < nc; i += 256) sb[i] = (double)b[i];
+    for (int i = threadIdx.x; i < nc; i += 256) sb[i] = b[i];
     __syncthreads();
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= nc) return;
-    const double* Xr = X_all + (int64_t)inst * nc * nc + (int64_t)row * nc;
-    double acc = 0.0;
+    const T* Xr = X_all + (int64_t)inst * nc * nc + (int64_t)row * nc;
+    T acc = (T)0;
     for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sb[c], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) x_all[(int64_t)inst * nc + row] = (T)acc;
+    acc = warp_sum_t<T>(acc);
+    if (lane == 0) x_all[(int64_t)inst * nc + row] = acc;
 }
 
 template <typename T>
-void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t s) {
+void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s) {
     kbegin(KC_COARSE, s);
-    size_t smem = sizeof(double) * nc;
+    size_t smem = sizeof(T) * nc;
     auto kfn = k_coarse_symv<T>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kfn<<<dim3((nc + 7) / 8, B), 256, smem, s>>>(X, b, x, nc);
     klaunched("k_coarse_symv");
+    kfinish(s);
+}
+
+__global__ void k_round_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) b[i] = (float)a[i];
+}
+
+void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    k_round_to_float<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(a, b, n);
+    klaunched("k_round_to_float");
     kfinish(s);
 }
 
@@ -648,7 +661,7 @@ void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t 
     template void mg_apply_level<T>(const T*, bool, const T*, const T*, T*, Dims, int, cudaStream_t);      \
     template void mg_axpy<T>(T*, const T*, int64_t, cudaStream_t);                                         \
     template void coarse_assemble<T>(const T*, bool, double*, Dims, int, int, cudaStream_t);               \
-    template void coarse_symv<T>(const double*, const T*, T*, int, int, cudaStream_t);
+    template void coarse_symv<T>(const T*, const T*, T*, int, int, cudaStream_t);
 
 PLSQR_INST_MG(float)
 PLSQR_INST_MG(double)

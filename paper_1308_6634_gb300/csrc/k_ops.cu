@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <stdexcept>
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -353,15 +355,17 @@ __global__ void __launch_bounds__(256) k_identity(const T* __restrict__ in, T* o
 // Joseph forward projection: one thread per ray (angle a, bin k).  Rows stepped: for each
 // row i, x = (s - y_i sin)/cos, linear interpolation between the two bracketing columns,
 // weight 1/|cos| (columns stepped: roles of x and y exchanged, weight 1/|sin|).
+// Columns-stepped angles read the transposed image imgT (imgT[x][y] = img[y][x]), so that the
+// lanes of a warp (neighbouring rays) gather from one row instead of 32 rows.
 template <typename T, int EPI>
-__global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, T* out, const T* prev,
-                                                    const JosephAngle<T>* __restrict__ tab, int n, int na,
-                                                    int nb, T ds, GkState* st, Red red) {
+__global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, const T* __restrict__ imgT, T* out,
+                                                    const T* prev, const JosephAngle<T>* __restrict__ tab, int n,
+                                                    int na, int nb, T ds, GkState* st, Red red) {
     const int inst = blockIdx.z, a = blockIdx.y, k = blockIdx.x * 128 + threadIdx.x;
     if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
     const JosephAngle<T> J = tab[a];
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
-    const T* im = img + (int64_t)inst * n * n;
+    const T* im = (J.rows ? img : imgT) + (int64_t)inst * n * n;
     T acc = (T)0;
     if (k < nb) {
         const T s = ((T)k - cdet) * ds;
@@ -383,13 +387,8 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, T
             const T fr = u - fl;
             if (j0 < -1 || j0 >= n) continue;
             T v0 = (T)0, v1 = (T)0;
-            if (J.rows) {
-                if (j0 >= 0) v0 = im[(int64_t)q * n + j0];
-                if (j0 + 1 < n) v1 = im[(int64_t)q * n + j0 + 1];
-            } else {
-                if (j0 >= 0) v0 = im[(int64_t)j0 * n + q];
-                if (j0 + 1 < n) v1 = im[(int64_t)(j0 + 1) * n + q];
-            }
+            if (j0 >= 0) v0 = im[(int64_t)q * n + j0];
+            if (j0 + 1 < n) v1 = im[(int64_t)q * n + j0 + 1];
             acc += ((T)1 - fr) * v0 + fr * v1;
         }
         acc *= J.wgt;
@@ -408,40 +407,95 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, T
     }
 }
 
+// imgT[x][y] = img[y][x] for each n x n instance, through 32 x 32 shared-memory tiles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ img, T* __restrict__ imgT, int n) {
+    __shared__ T tile[32][33];
+    const int inst = blockIdx.z;
+    const T* a = img + (int64_t)inst * n * n;
+    T* b = imgT + (int64_t)inst * n * n;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
+        const int y = y0 + r, x = x0 + (threadIdx.x & 31);
+        if (y < n && x < n) tile[r][threadIdx.x & 31] = a[(int64_t)y * n + x];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x >> 5; r < 32; r += 8) {
+        const int x = x0 + r, y = y0 + (threadIdx.x & 31);
+        if (y < n && x < n) b[(int64_t)x * n + y] = tile[threadIdx.x & 31][r];
+    }
+}
+
 // Joseph adjoint, gather form: pixel (i, j) collects, for every angle, the rays k with
 // |s_k - s_ij| < h (h = |cos| rows stepped, |sin| columns stepped), s_ij = x cos + y sin,
 // with the forward weight (1 - |s_k - s_ij|/h)/h.  No atomics; exact transpose.
 template <typename T, int EPI>
 __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, T* out,
                                                     const JosephAngle<T>* __restrict__ tab, int n, int na, int nb,
-                                                    GkState* st) {
+                                                    int KB, GkState* st) {
+    // A 16 x 16 pixel tile touches, per angle, at most KB consecutive bins: they are staged in
+    // shared memory (zeros outside the detector) together with the angle table, so the loop over
+    // angles reads only shared memory.
     extern __shared__ __align__(16) unsigned char smraw[];
     JosephAngle<T>* stab = reinterpret_cast<JosephAngle<T>*>(smraw);
+    int* sk0 = reinterpret_cast<int*>(stab + na);
+    T* sbin = reinterpret_cast<T*>(smraw + ((sizeof(JosephAngle<T>) * na + sizeof(int) * na + 15) & ~(size_t)15));
     const int inst = blockIdx.z;
     if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
-    for (int i = threadIdx.x; i < na; i += 256) stab[i] = tab[i];
-    __syncthreads();
-    const int j = blockIdx.x * 16 + (threadIdx.x & 15), i = blockIdx.y * 16 + (threadIdx.x >> 4);
-    if (i >= n || j >= n) return;
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
-    const T x = (T)j - cimg, y = (T)i - cimg;
+    const int tj = blockIdx.x * 16, ti = blockIdx.y * 16;
+    const T xa = (T)tj - cimg, xb = (T)min(tj + 15, n - 1) - cimg;
+    const T ya = (T)ti - cimg, yb = (T)min(ti + 15, n - 1) - cimg;
+    for (int a = threadIdx.x; a < na; a += 256) {
+        const JosephAngle<T> J = tab[a];
+        stab[a] = J;
+        const T tmin = fmin(xa * J.c1, xb * J.c1) + fmin(ya * J.c2, yb * J.c2) + cdet;
+        sk0[a] = (int)floor(tmin - J.hw) - 1;
+    }
+    __syncthreads();
     const T* sg = sino + (int64_t)inst * na * nb;
+    for (int e = threadIdx.x; e < na * KB; e += 256) {
+        const int a = e / KB, kk = e - a * KB;
+        const int k = sk0[a] + kk;
+        sbin[e] = (k >= 0 && k < nb) ? sg[(int64_t)a * nb + k] : (T)0;
+    }
+    __syncthreads();
+    const int j = tj + (threadIdx.x & 15), i = ti + (threadIdx.x >> 4);
+    if (i >= n || j >= n) return;
+    const T x = (T)j - cimg, y = (T)i - cimg;
     T acc = (T)0;
     for (int a = 0; a < na; ++a) {
         const JosephAngle<T>& J = stab[a];
         const T t = x * J.c1 + y * J.c2 + cdet;
-        int klo = max(0, (int)ceil(t - J.hw));
-        int khi = min(nb - 1, (int)floor(t + J.hw));
+        const int k0 = sk0[a];
+        const int klo = (int)ceil(t - J.hw), khi = (int)floor(t + J.hw);
+        const T* row = sbin + a * KB - k0;
         T acc_a = (T)0;
         for (int k = klo; k <= khi; ++k) {
             const T dist = fabs((T)k - t);
-            if (dist < J.hw) acc_a += ((T)1 - dist * J.inv_hw) * sg[(int64_t)a * nb + k];
+            if (dist < J.hw) acc_a += ((T)1 - dist * J.inv_hw) * row[k];
         }
         acc += acc_a * J.wgt;
     }
     T ca, cp;
     if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
     epi_store<T, EPI>(acc, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i * n + j);
+}
+
+// Bins a 16 x 16 tile can touch for one angle: 15 (|cos| + |sin|)/ds + 2 hw + 2 of slack, maximised
+// over the angles.
+template <typename T>
+static int joseph_tile_bins(const OpDev& op) {
+    const double ds = op.ds;
+    double w = 0.0;
+    for (int a = 0; a < op.na; ++a) {
+        const double th = 3.14159265358979323846 * (double)a / (double)op.na;
+        const double c = std::fabs(std::cos(th)), sn = std::fabs(std::sin(th));
+        const bool rows = (4 * a < op.na) || (4 * a > 3 * op.na);
+        const double hw = (rows ? c : sn) / ds;
+        w = std::max(w, 15.0 * (c + sn) / ds + 2.0 * hw);
+    }
+    return (int)std::ceil(w) + 4;
 }
 
 // ---- launchers ---------------------------------------------------------------------------
@@ -549,17 +603,24 @@ static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const 
             const int n = op.d.nx;
             const auto* tab = (const JosephAngle<T>*)op.jtab;
             if (!adjoint) {
+                if (!tmp) throw std::runtime_error("joseph_fwd: scratch for the transposed image missing");
+                dim3 tg((n + 31) / 32, (n + 31) / 32, B);
+                k_transpose<T><<<tg, 256, 0, s>>>(in, tmp, n);
+                klaunched("k_transpose");
                 dim3 grid((op.nb + 127) / 128, op.na, B);
                 if (EPI == EPI_FWD && (int64_t)grid.x * grid.y > red.max_blocks)
                     throw std::runtime_error("joseph_fwd: too many blocks for the reduction scratch");
-                k_joseph_fwd<T, EPI><<<grid, 128, 0, s>>>(in, out, prev, tab, n, op.na, op.nb, (T)op.ds, st, red);
+                k_joseph_fwd<T, EPI><<<grid, 128, 0, s>>>(in, tmp, out, prev, tab, n, op.na, op.nb, (T)op.ds, st, red);
                 klaunched("k_joseph_fwd");
             } else {
-                size_t smem = sizeof(JosephAngle<T>) * op.na;
+                const int KB = joseph_tile_bins<T>(op);
+                const size_t head = (sizeof(JosephAngle<T>) * op.na + sizeof(int) * op.na + 15) & ~(size_t)15;
+                const size_t smem = head + sizeof(T) * (size_t)op.na * KB;
+                if (smem > 227 * 1024) throw std::runtime_error("joseph_adj: too many angles for shared memory");
                 auto kfn = k_joseph_adj<T, EPI>;
                 if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 dim3 grid((n + 15) / 16, (n + 15) / 16, B);
-                kfn<<<grid, 256, smem, s>>>(in, out, tab, n, op.na, op.nb, st);
+                kfn<<<grid, 256, smem, s>>>(in, out, tab, n, op.na, op.nb, KB, st);
                 klaunched("k_joseph_adj");
             }
             return;

@@ -74,7 +74,8 @@ void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw,
 void coarse_cholesky(double* band, double* rdiag, int nc, int bw, int B, cudaStream_t s);
 void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, int bw, int B, cudaStream_t s);
 template <typename T>
-void coarse_symv(const double* X, const T* b, T* x, int nc, int B, cudaStream_t s);
+void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s);
+void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
 
 // ---- temporally blocked 2D V-cycle (one launch per level and direction) ----
 bool mg2d_supported(int ndim, int nu);

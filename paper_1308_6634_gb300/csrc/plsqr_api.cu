@@ -82,6 +82,7 @@ struct plsqr_ctx {
     double* band = nullptr;
     double* rdiag = nullptr;  // 1/L(j,j) of the coarse factor, [B][nc]
     double* X = nullptr;  // inverse of the coarsest operator, [B][nc][nc]
+    float* Xf = nullptr;  // the same rounded to float (single-precision handles)
     GkState* st = nullptr;
     SolveParams* prm_dev = nullptr;
     SolveParams* prm_host = nullptr;  // pinned
@@ -194,7 +195,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
     for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
     b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
-    b += sizeof(double) * B * (size_t)pl.nc * pl.nc;
+    b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
     b += (sizeof(GkState) + sizeof(SolveParams) + sizeof(unsigned)) * B;
     b += sizeof(double) * B * 8192;
     pl.bytes = b;
@@ -218,6 +219,14 @@ void alloc_data_buffers(plsqr_ctx* h) {
 
 // ---- the order of the kernels ----------------------------------------------------------------
 
+// Inverse of the coarsest operator in the handle's element type.
+template <typename T>
+const T* coarse_inverse_of(plsqr_ctx* h);
+template <>
+const double* coarse_inverse_of<double>(plsqr_ctx* h) { return h->X; }
+template <>
+const float* coarse_inverse_of<float>(plsqr_ctx* h) { return h->Xf; }
+
 Hist hist_of(plsqr_ctx* h) {
     Hist hs;
     hs.rbar = h->h_rbar;
@@ -235,7 +244,7 @@ void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
     const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
     const bool isk = l == 0;
     if (l == h->L - 1) {
-        coarse_symv<T>(h->X, b, x, h->nc, B, s);
+        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, s);
         return;
     }
     for (int k = 0; k < h->nu; ++k) {
@@ -258,7 +267,7 @@ template <typename T>
 void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStream_t s) {
     const Level& Lv = h->lv[l];
     if (l == h->L - 1) {
-        coarse_symv<T>(h->X, b, x, h->nc, B, s);
+        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, s);
         return;
     }
     const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
@@ -299,6 +308,7 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     coarse_assemble<T>(lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond), lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
     coarse_cholesky(h->band, h->rdiag, h->nc, h->bw, B, s);
     coarse_inverse(h->band, h->rdiag, h->X, h->nc, h->bw, B, s);
+    if (!h->fp64) round_to_float(h->X, h->Xf, (int64_t)B * h->nc * h->nc, s);
 }
 
 
@@ -656,6 +666,7 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
         h->rdiag = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc);
         h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
+        if (!h->fp64) h->Xf = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * h->nc);
         h->st = (GkState*)dalloc(h, sizeof(GkState) * B);
         ck(cudaMemset(h->st, 0, sizeof(GkState) * B), "memset");
         h->prm_dev = (SolveParams*)dalloc(h, sizeof(SolveParams) * B);
