@@ -11,6 +11,28 @@
 
 namespace plsqr {
 
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialization attribute
+// (launch_k) may be scheduled while its predecessor in the stream is finishing; it waits here,
+// before its first access to global memory, until the predecessor has completed and its writes are
+// visible.  Without the attribute this is a no-op.  (No kernel signals its dependents early:
+// letting them become resident at the start of the predecessor measured slower on the V-cycle
+// chain than letting them start at its completion.)
+// Butterfly sum over the 32 lanes of a warp (every lane receives the total).
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Barrier over all threads of the thread-block cluster; the release/acquire pair at cluster scope
+// makes the memory writes of every block before it visible to every block after it.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_grid_sync() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Status codes mirrored from plsqr.h (device side).
 constexpr int ST_OK = 0;
 constexpr int ST_BREAKDOWN = 4;
@@ -66,6 +88,19 @@ struct Red {
 struct Dims {
     int32_t nx, ny, nz, ndim;
     int64_t N;  // nx*ny*nz
+};
+
+// Per-level buffers of the coarse end of a 2D V-cycle (conductances, right-hand side, pre-smoothed
+// iterate, post-smoothed result), indexed by level - lc for the levels lc..L-1 (at most
+// TAIL_LEVELS - 1 smoothing levels and the coarsest).
+constexpr int TAIL_LEVELS = 5;
+struct TailLevels {
+    const void* cond[TAIL_LEVELS];
+    void* b[TAIL_LEVELS];
+    void* x[TAIL_LEVELS];
+    void* x2[TAIL_LEVELS];
+    Dims d[TAIL_LEVELS];
+    int n;  // levels in use (the last one is the coarsest)
 };
 
 template <typename T> struct Vec2;

@@ -1,0 +1,295 @@
+// k_coarse32.cu -- the exact coarse solve of the V-cycle in single precision (float handles).
+//
+// The coarsest operator M_c (Galerkin sums of the edge conductances, section 4.2) is a symmetric
+// M-matrix: its off-diagonal entries are -c_e <= 0, and its row sums are the conductances of the
+// edges to the zero ghost cells beyond the high boundary, s_i >= 0.  Gaussian elimination that
+// carries the off-diagonal magnitudes and the row-sum excess s instead of the diagonal (the
+// arrangement of Grassmann, Taksar and Heyman, 1985) forms each pivot as d_k = s_k + sum_i |a_ik|
+// and each update as a sum of non-negative terms:
+//
+//     |a'_ij| = |a_ij| + |a_ik| |a_jk| / d_k,      s'_i = s_i + |a_ik| s_k / d_k.
+//
+// Nothing is ever subtracted, so every computed quantity carries a small componentwise relative
+// error whatever the condition number of M_c, and single precision gives the inverse to a few
+// float ulps per entry (M_c^{-1} is entrywise positive).  With M_c = L D L^T, L unit lower with
+// entries -l_ik (l_ik >= 0), the inverse X = L^{-T} D^{-1} L^{-1} again needs only additions of
+// non-negative terms.  This replaces the double-precision banded Cholesky and inverse, whose
+// sequential column steps ran on the narrow double-precision pipe, for bandwidths <= 32 (2D
+// coarsest grids up to 32 cells wide).
+//
+// Layout.  bw is the bandwidth (largest cell stride), BWP = round4(window + 1).  gcol[j][0] = s_j,
+// gcol[j][t] = |a_{j+t,j}| (t = 1..bw, zero beyond); after the factorisation gcol[k][0] = 1/d_k and
+// gcol[k][t] = l_{k+t,k}, and grow[i][t] = l_{i,i-t}.
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+
+#include "kernels.cuh"
+#include "tma.cuh"
+
+namespace plsqr {
+
+// Column j of the strictly lower triangle of M_c is the conductances of cell j's edges in the
+// +x, +y (+z) directions; an edge to the ghost cell beyond the high boundary adds to s_j instead.
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_gth_assemble(const T* __restrict__ cond, float* __restrict__ gcol, Dims d,
+                                                      int BWP) {
+    const int inst = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (j >= d.N) return;
+    float* col = gcol + ((int64_t)inst * d.N + j) * BWP;
+    for (int t = 0; t < BWP; ++t) col[t] = 0.f;
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
+    const int co[3] = {(int)(j % d.nx), (int)((j / d.nx) % d.ny), (int)(j / ((int64_t)d.nx * d.ny))};
+    const int n[3] = {d.nx, d.ny, d.nz};
+    const int strd[3] = {1, d.nx, d.nx * d.ny};
+    float s = 0.f;
+    for (int dd = 0; dd < d.ndim; ++dd) {
+        const float ce = (float)(KAPPA ? c[j] : c[(int64_t)dd * d.N + j]);
+        if (co[dd] + 1 < n[dd]) col[strd[dd]] = ce;
+        else s += ce;
+    }
+    col[0] = s;
+}
+
+template <int BWP>
+__device__ __forceinline__ void load_row(float (&r)[BWP], const float* p) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int q = 0; q < BWP / 4; ++q) {
+        const float4 v = p4[q];
+        r[4 * q] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
+    }
+}
+
+// L D L^T of one instance per warp.  The whole instance (nc * BWP floats) is staged in shared
+// memory by one bulk copy, so the pivot loop makes no global loads.  Step k: every lane loads
+// column k into registers and sums it (the same order everywhere, so all agree on d_k); lane
+// t-1 forms l_{k+t,k}; then, for each column j = k + tau, lane t-1 updates the entry of row
+// j + t (consecutive lanes on consecutive words: no bank conflicts) and lane tau-1 updates s_j.
+// l and 1/d_k go to global memory as they are formed; the staged copy of column k is left as is.
+template <int BW>
+__global__ void __launch_bounds__(32) k_ldl_gth_staged(float* __restrict__ gcol_all, float* __restrict__ grow_all,
+                                                       int nc, int bw, GkState* st) {
+    constexpr int BWP = (BW + 1 + 3) & ~3;
+    extern __shared__ __align__(128) float col[];
+    __shared__ float sl[BWP + BW];
+    __shared__ __align__(8) uint64_t bar;
+    const int inst = blockIdx.x, tid = threadIdx.x;
+    float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(float)));
+        bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(float)), &bar);
+    }
+    for (int e = tid; e < nc * BWP; e += 32)  // row layout: entries no pivot writes
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
+    for (int e = tid; e < BWP + BW; e += 32) sl[e] = 0.f;  // l beyond the band stays 0
+    __syncwarp();
+    tma_wait_tile(&bar, st, inst);
+    const int t = tid + 1;
+    const bool mine = t <= bw;
+    for (int k = 0; k < nc; ++k) {
+        const float* ck = col + (int64_t)k * BWP;
+        float cv[BWP];
+        load_row<BWP>(cv, ck);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int q = 0; q < BWP / 4; ++q) {
+            a0 += cv[4 * q];
+            a1 += cv[4 * q + 1];
+            a2 += cv[4 * q + 2];
+            a3 += cv[4 * q + 3];
+        }
+        const float rd = 1.0f / ((a0 + a1) + (a2 + a3));
+        const float l = mine ? ck[t] * rd : 0.f;
+        if (mine) {
+            sl[t] = l;
+            gc[(int64_t)k * BWP + t] = l;
+            if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
+        }
+        if (tid == 0) gc[(int64_t)k * BWP] = rd;
+        __syncwarp();
+#pragma unroll
+        for (int tau = 1; tau < BW; ++tau) {
+            if (k + tau < nc && t <= bw - tau) {
+                float* e = col + (int64_t)(k + tau) * BWP + t;
+                *e = fmaf(sl[tau + t], cv[tau], *e);
+            }
+        }
+        if (mine && k + t < nc) {
+            float* e = col + (int64_t)(k + t) * BWP;
+            *e = fmaf(l, cv[0], *e);
+        }
+        __syncwarp();
+    }
+}
+
+// X = L^{-T} D^{-1} L^{-1}, one thread per column j (BW = window >= bw, a power of two).
+// Forward: z = L^{-1} e_j column-oriented -- when z_k is final, z_{k+t} += l_{k+t,k} z_k -- with
+// the BW pending sums in registers (rotating, the index fixed by unrolling), y_k = z_k / d_k kept
+// in X[k][j].  Backward from the last row to row j: x_i = y_i + (pending), then the rows above
+// receive l_{i,i-t} x_i.  x_i (i >= j) is stored at X[i][j] and X[j][i].  The factor tables are
+// staged in shared memory for each pass.
+template <int BW>
+__global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ gcol_all,
+                                                     const float* __restrict__ grow_all, float* __restrict__ X_all,
+                                                     int nc, GkState* st) {
+    constexpr int BWP = (BW + 1 + 3) & ~3;
+    extern __shared__ __align__(128) float tab[];
+    const int inst = blockIdx.y;
+    const int jb = blockIdx.x * 128;
+    const int j = jb + threadIdx.x;
+    const int j0 = jb + (threadIdx.x & ~31);
+    const float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    const float* gr = grow_all + (int64_t)inst * nc * BWP;
+    float* X = X_all + (int64_t)inst * nc * nc;
+    const bool live = j < nc;
+    __shared__ __align__(8) uint64_t bar[2];
+    const uint32_t bytes = (uint32_t)((nc - jb) * BWP * sizeof(float));
+    // ---- forward ----
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_expect_tx(&bar[0], bytes);
+        bulk_load(tab, gc + (int64_t)jb * BWP, bytes, &bar[0]);
+    }
+    __syncthreads();
+    tma_wait_tile(&bar[0], st, inst);
+    float pend[BW];
+#pragma unroll
+    for (int u = 0; u < BW; ++u) pend[u] = 0.f;
+    if (j0 < nc) {
+        for (int base = j0; base < nc; base += BW) {
+#pragma unroll
+            for (int u = 0; u < BW; ++u) {
+                const int k = base + u;
+                if (k < nc) {
+                    float row[BWP];
+                    load_row<BWP>(row, tab + (int64_t)(k - jb) * BWP);
+                    const float z = pend[u] + (k == j ? 1.f : 0.f);
+                    pend[u] = 0.f;
+                    if (live && k >= j) X[(int64_t)k * nc + j] = z * row[0];
+#pragma unroll
+                    for (int t = 1; t <= BW; ++t) pend[(u + t) & (BW - 1)] = fmaf(row[t], z, pend[(u + t) & (BW - 1)]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- backward ----
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar[1], bytes);
+        bulk_load(tab, gr + (int64_t)jb * BWP, bytes, &bar[1]);
+    }
+    tma_wait_tile(&bar[1], st, inst);
+#pragma unroll
+    for (int u = 0; u < BW; ++u) pend[u] = 0.f;
+    if (j0 >= nc) return;
+    // y values of the next chunk are loaded one chunk ahead (they were written by this thread)
+    float ynx[BW];
+    const int top = nc - 1;
+#pragma unroll
+    for (int v = 0; v < BW; ++v) {
+        const int i = top - v;
+        ynx[v] = (live && i >= j) ? X[(int64_t)i * nc + j] : 0.f;
+    }
+    // the warp's chunk of x (BW rows x 32 columns) goes through shared memory so that the mirror
+    // entries X[j][i] are written along rows
+    float (*tile)[33] = reinterpret_cast<float (*)[33]>(tab + (size_t)nc * BWP) + (threadIdx.x >> 5) * BW;
+    const int lane = threadIdx.x & 31;
+    for (int base = top; base >= j0; base -= BW) {
+        float ycur[BW];
+#pragma unroll
+        for (int v = 0; v < BW; ++v) ycur[v] = ynx[v];
+#pragma unroll
+        for (int v = 0; v < BW; ++v) {
+            const int i = base - BW - v;
+            ynx[v] = (live && i >= j && i >= j0) ? X[(int64_t)i * nc + j] : 0.f;
+        }
+#pragma unroll
+        for (int v = 0; v < BW; ++v) {
+            const int i = base - v;
+            if (i >= j0) {
+                float row[BWP];
+                load_row<BWP>(row, tab + (int64_t)(i - jb) * BWP);
+                const float x = ycur[v] + pend[v];
+                pend[v] = 0.f;
+                tile[v][lane] = x;
+                if (live && i >= j) X[(int64_t)i * nc + j] = x;
+#pragma unroll
+                for (int t = 1; t <= BW; ++t) pend[(v + t) & (BW - 1)] = fmaf(row[t], x, pend[(v + t) & (BW - 1)]);
+            }
+        }
+        __syncwarp();
+        if (lane < BW) {
+            const int i = base - lane;
+            for (int r = 0; r < 32; ++r) {
+                const int jr = j0 + r;
+                if (jr < nc && i > jr) X[(int64_t)jr * nc + i] = tile[lane][r];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int gth_window(int bw) { return bw <= 8 ? 8 : bw <= 16 ? 16 : bw <= 32 ? 32 : 0; }
+
+int gth_stride(int bw) {
+    const int w = gth_window(bw);
+    return ((w ? w : bw) + 1 + 3) & ~3;
+}
+
+bool gth_supported(int bw, int nc) {
+    const int BWP = gth_stride(bw);
+    return gth_window(bw) != 0 && (size_t)nc * BWP * sizeof(float) + sizeof(float) * 4 * 32 * 33 <= 220 * 1024;
+}
+
+template <typename T>
+void gth_assemble(const T* cond, bool is_kappa, float* gcol, Dims d, int bw, int B, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    const int BWP = gth_stride(bw);
+    dim3 grid((unsigned)((d.N + 255) / 256), B);
+    if (is_kappa) k_gth_assemble<T, true><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
+    else k_gth_assemble<T, false><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
+    klaunched("k_gth_assemble");
+    kfinish(s);
+}
+
+void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+    if (!gth_supported(bw, nc)) throw std::runtime_error("gth_factor_inverse: bandwidth or size not supported");
+    kbegin(KC_SETUP, s);
+    const int BWP = gth_stride(bw);
+    const size_t stage = sizeof(float) * (size_t)nc * BWP;
+    const int W = gth_window(bw);
+    dim3 igrid((unsigned)((nc + 127) / 128), B);
+#define GTH_CASE(BW_)                                                                                     \
+    case BW_: {                                                                                           \
+        auto kf = k_ldl_gth_staged<BW_>;                                                                  \
+        if (stage > 48 * 1024) cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage); \
+        kf<<<B, 32, stage, s>>>(gcol, grow, nc, bw, st);                                                  \
+        klaunched("k_ldl_gth_staged");                                                                    \
+        auto ki = k_gth_inverse<BW_>;                                                                     \
+        const size_t ism = stage + sizeof(float) * 4 * BW_ * 33;                                          \
+        if (ism > 48 * 1024) cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism); \
+        ki<<<igrid, 128, ism, s>>>(gcol, grow, X, nc, st);                                                \
+        klaunched("k_gth_inverse");                                                                       \
+        break;                                                                                            \
+    }
+    switch (W) {
+        GTH_CASE(8)
+        GTH_CASE(16)
+        GTH_CASE(32)
+    }
+#undef GTH_CASE
+    kfinish(s);
+}
+
+template void gth_assemble<float>(const float*, bool, float*, Dims, int, int, cudaStream_t);
+template void gth_assemble<double>(const double*, bool, float*, Dims, int, int, cudaStream_t);
+
+}  // namespace plsqr

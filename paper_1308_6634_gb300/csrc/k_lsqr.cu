@@ -95,6 +95,14 @@ bool tma_enabled() {
     return on;
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("PLSQR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 bool tma_map_3d(CUtensorMap* map, const void* base, int esz, int64_t nx, int64_t ny, int64_t planes, int bx, int by,
                 int bz) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {

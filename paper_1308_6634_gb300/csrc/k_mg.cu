@@ -20,14 +20,6 @@
 
 namespace plsqr {
 
-
-template <typename T>
-__device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // ---- diffusivity (Algorithm 3 step 3) ----------------------------------------------------
 
 template <typename T>
@@ -134,7 +126,8 @@ __device__ __forceinline__ void stencil(const T* __restrict__ c, const T* x, con
     }
 }
 
-// One red-black Gauss-Seidel half sweep: cells of `colour` get x = (b + off)/diag.
+// One red-black Gauss-Seidel half sweep: cells of `colour` get x = (b + off) * (1 / diag) (the
+// form of the temporally blocked kernels, which keep 1 / diag per cell).
 // zero_init: x is implicitly 0 (first half sweep of a level); the other colour is written 0.
 template <typename T, bool KAPPA, bool ZERO>
 __global__ void __launch_bounds__(256) k_gs_half(const T* __restrict__ cond, const T* __restrict__ b, T* x, Dims d,
@@ -154,7 +147,7 @@ __global__ void __launch_bounds__(256) k_gs_half(const T* __restrict__ cond, con
     T* xi = x + (int64_t)inst * d.N;
     T diag, off;
     stencil<T, KAPPA, !ZERO>(c, xi, d, i, xx, y, z, diag, off);
-    xi[i] = (bi[i] + off) / diag;
+    xi[i] = (bi[i] + off) * ((T)1 / diag);
     if (ZERO) xi[i + (par ? -1 : 1)] = (T)0;
 }
 
@@ -616,6 +609,7 @@ __global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all
                                                      T* __restrict__ x_all, int nc) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sb = reinterpret_cast<T*>(smraw);
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const T* b = b_all + (int64_t)inst * nc;
     for (int i = threadIdx.x; i < nc; i += 256) sb[i] = b[i];
@@ -635,7 +629,7 @@ void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s) {
     size_t smem = sizeof(T) * nc;
     auto kfn = k_coarse_symv<T>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kfn<<<dim3((nc + 7) / 8, B), 256, smem, s>>>(X, b, x, nc);
+    launch_k(kfn, dim3((nc + 7) / 8, B), dim3(256), smem, s, X, b, x, nc);
     klaunched("k_coarse_symv");
     kfinish(s);
 }

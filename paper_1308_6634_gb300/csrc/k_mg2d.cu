@@ -15,6 +15,7 @@
 // tile instead of once per half sweep.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <stdexcept>
 #include <string>
@@ -24,7 +25,9 @@
 
 namespace plsqr {
 
-constexpr int MTX = 64, MTY = 32, MNT = 256;
+// Tile extent; threads per block on the finest level (many tiles), on the coarser levels (few
+// tiles: more threads per tile) and in the one-launch coarse end.
+constexpr int MTX = 64, MTY = 32, MNT = 256, CNT = 512, TNT = 1024;
 
 // Tile geometry: logical halo H on both axes; in storage the x halo is HX >= H (HX * sizeof(T)
 // a multiple of 16 bytes, the TMA rule for the innermost coordinate), so logical column lx is
@@ -38,10 +41,13 @@ struct Tile {
     static constexpr int NCS = LY * LXS;                      // one staged plane
     static constexpr int NCP = ((NCS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);  // 128-byte padded
     static constexpr int CPLANES = L0 ? 1 : 2;
-    // layout: sb [NCP] | scx, scy [CPLANES * NCS, padded] | sx [NCP] | mbarrier
+    // layout: sb [NCP] | scx, scy [CPLANES * NCS, padded] | sx [NCP] | sd [NCP] | mbarrier
+    // (sd: 1 / diagonal of the cells inside the domain, 0 elsewhere)
     static constexpr int OFF_C = NCP;
     static constexpr int OFF_X = NCP + ((CPLANES * NCS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
-    static constexpr size_t bytes() { return sizeof(T) * (size_t)(OFF_X + NCP) + 16; }
+    static constexpr int OFF_D = OFF_X + NCP;
+    static constexpr int OFF_BAR = OFF_D + NCP;
+    static constexpr size_t bytes() { return sizeof(T) * (size_t)OFF_BAR + 16; }
 };
 
 struct Maps {
@@ -49,7 +55,7 @@ struct Maps {
 };
 
 // Stage b and the conductances (and x_in when X_IN) of the tile.
-template <typename T, bool L0, int H, bool TMA, bool X_IN>
+template <typename T, bool L0, int H, bool TMA, bool X_IN, int NTH>
 __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restrict__ cond, const T* __restrict__ b,
                                       const T* __restrict__ x_in, const Dims& d, int inst, int x0, int y0,
                                       GkState* st) {
@@ -58,7 +64,7 @@ __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restri
     T* sc = sm + TL::OFF_C;
     T* sx = sm + TL::OFF_X;
     if constexpr (TMA) {
-        uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::OFF_X + TL::NCP);
+        uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::OFF_BAR);
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -70,10 +76,12 @@ __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restri
             if (X_IN) tma_load_3d(sx, &maps.x, bar, gx, gy, inst);
         }
         tma_wait_tile(bar, st, inst);
+        __syncthreads();
+        if (threadIdx.x == 0) mbar_inval(bar);  // the next tile of this block initialises it again
     } else {
         const int64_t off = (int64_t)inst * d.N;
         const T* c = cond + (L0 ? off : (int64_t)inst * 2 * d.N);
-        for (int i = threadIdx.x; i < TL::NCS; i += MNT) {
+        for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
             const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
             const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
             T vb = (T)0, vx = (T)0, vy = (T)0, vv = (T)0;
@@ -93,14 +101,39 @@ __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restri
     }
 }
 
-// One half sweep of `colour` over the logical cells at distance >= lo from the staged edge.
-template <typename T, int LX, int LY, int LXS, int OX, int H>
-__device__ __forceinline__ void half_sweep(const T* sb, const T* scx, const T* scy, T* sx, int lo, int colour,
-                                          const Dims& d, int x0, int y0) {
+// sd = 1 / (sum of the four conductances around the cell) for the staged cells inside the domain
+// and at least one cell from the staged edge, 0 elsewhere (the summation order of the diagonal is
+// that of the one-half-sweep kernels).
+template <typename T, bool L0, int H, int NTH>
+__device__ __forceinline__ void diag_inverse(T* sm, const Dims& d, int x0, int y0) {
+    using TL = Tile<T, L0, H>;
+    const T* scx = sm + TL::OFF_C;
+    const T* scy = L0 ? scx : scx + TL::NCS;
+    T* sd = sm + TL::OFF_D;
+    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
+        const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
+        const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
+        T v = (T)0;
+        if (ly >= 1 && lxs >= 1 && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
+            T diag = scx[i];
+            diag += scx[i - 1];
+            diag += scy[i];
+            diag += scy[i - TL::LXS];
+            v = (T)1 / diag;
+        }
+        sd[i] = v;
+    }
+}
+
+// One half sweep of `colour` over the logical cells at distance >= lo from the staged edge:
+// x = (b + off) * sd.  Cells outside the domain have b = 0 and sd = 0 and stay 0.
+template <typename T, int LX, int LY, int LXS, int OX, int H, int NTH>
+__device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* scx, const T* scy, T* sx, int lo,
+                                          int colour, int x0, int y0) {
     const int hi = LX - 1 - lo, hiy = LY - 1 - lo;
     const int half = (hi - lo + 2) >> 1;
     const int rows = hiy - lo + 1;
-    for (int k = threadIdx.x; k < rows * half; k += MNT) {
+    for (int k = threadIdx.x; k < rows * half; k += NTH) {
         const int ry = k / half, j = k - ry * half;
         const int ly = lo + ry;
         const int gy = y0 - H + ly;
@@ -108,47 +141,42 @@ __device__ __forceinline__ void half_sweep(const T* sb, const T* scx, const T* s
         const int p = (colour - gy - gx_lo) & 1;  // first lx in [lo, hi] with (gx + gy) % 2 == colour
         const int lx = lo + p + 2 * j;
         if (lx > hi) continue;
-        const int gx = x0 - H + lx;
-        if (gx < 0 || gx >= d.nx || gy < 0 || gy >= d.ny) continue;
         const int i = ly * LXS + lx + OX;
-        T diag = scx[i];
-        diag += scx[i - 1];
-        diag += scy[i];
-        diag += scy[i - LXS];
         T off = scx[i] * sx[i + 1];
         off += scx[i - 1] * sx[i - 1];
         off += scy[i] * sx[i + LXS];
         off += scy[i - LXS] * sx[i - LXS];
-        sx[i] = (sb[i] + off) / diag;
+        sx[i] = (sb[i] + off) * sd[i];
     }
 }
 
-// Pre-smoothing from x = 0 (nu red->black sweeps), residual and restriction to bc.
-template <typename T, bool L0, int NU, bool TMA>
-__global__ void __launch_bounds__(MNT) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
-                                                  const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
-                                                  Dims d, Dims dc, GkState* st) {
+// Pre-smoothing of one tile from x = 0 (nu red->black sweeps), residual and restriction to bc.
+// Ends with a barrier, so that a block can go on with another tile.
+template <typename T, bool L0, int NU, bool TMA, int NTH>
+__device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b, T* x,
+                                         T* bc, const Dims& d, const Dims& dc, GkState* st, int inst, int x0,
+                                         int y0) {
     constexpr int H = 2 * NU + 1;
     using TL = Tile<T, L0, H>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
-    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     T* sb = sm;
     T* scx = sm + TL::OFF_C;
     T* scy = L0 ? scx : scx + TL::NCS;
     T* sx = sm + TL::OFF_X;
-    const int inst = blockIdx.z, x0 = blockIdx.x * MTX, y0 = blockIdx.y * MTY;
-    for (int i = threadIdx.x; i < TL::NCS; i += MNT) sx[i] = (T)0;
-    stage<T, L0, H, TMA, false>(sm, maps, cond, b, nullptr, d, inst, x0, y0, st);
+    const T* sd = sm + TL::OFF_D;
+    for (int i = threadIdx.x; i < TL::NCS; i += NTH) sx[i] = (T)0;
+    stage<T, L0, H, TMA, false, NTH>(sm, maps, cond, b, nullptr, d, inst, x0, y0, st);
+    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, H>(sb, scx, scy, sx, s + 1, s & 1, d, x0, y0);
+        half_sweep<T, TL::LX, TL::LY, LXS, OX, H, NTH>(sb, sd, scx, scy, sx, s + 1, s & 1, x0, y0);
         __syncthreads();
     }
     // residual r = b - (diag x - off) on the tile, summed over the 2 x 2 children
     const int64_t offc = (int64_t)inst * dc.N;
-    for (int k = threadIdx.x; k < (MTX / 2) * (MTY / 2); k += MNT) {
+    for (int k = threadIdx.x; k < (MTX / 2) * (MTY / 2); k += NTH) {
         const int cy = k / (MTX / 2), cx = k - cy * (MTX / 2);
         const int X = (x0 >> 1) + cx, Y = (y0 >> 1) + cy;
         if (X >= dc.nx || Y >= dc.ny) continue;
@@ -171,35 +199,43 @@ __global__ void __launch_bounds__(MNT) k_mg_pre2d(const __grid_constant__ Maps m
         bc[offc + (int64_t)Y * dc.nx + X] = sum;
     }
     const int64_t off = (int64_t)inst * d.N;
-    for (int k = threadIdx.x; k < MTX * MTY; k += MNT) {
+    for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
         const int ty = k / MTX, tx = k - ty * MTX;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx < d.nx && gy < d.ny) x[off + (int64_t)gy * d.nx + gx] = sx[(H + ty) * LXS + H + tx + OX];
     }
+    __syncthreads();
 }
 
-// x_out = smooth(x_in + P xc) with nu black->red sweeps (x_in and x_out must differ: blocks read
-// neighbouring tiles of x_in as halo).  DOT: also alpha = sqrt(x_out . b) and the rotations
-// (finest level of the last V-cycle: x_out = v~, b = p~).
-template <typename T, bool L0, int NU, bool DOT, bool INIT, bool TMA>
-__global__ void __launch_bounds__(MNT) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
-                                                   const T* __restrict__ b, const T* __restrict__ x_in,
-                                                   T* __restrict__ x_out, const T* __restrict__ xc, Dims d, Dims dc,
-                                                   GkState* st, Hist hist, Red red) {
+template <typename T, bool L0, int NU, bool TMA, int NTH>
+__global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
+                                                  const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
+                                                  Dims d, Dims dc, GkState* st) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    pdl_grid_sync();
+    pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY);
+}
+
+// One tile of x_out = smooth(x_in + P xc) with nu black->red sweeps (x_in and x_out must differ:
+// blocks read neighbouring tiles of x_in as halo).  Returns this thread's share of x_out . b over
+// the tile when DOT.  Ends with a barrier.
+template <typename T, bool L0, int NU, bool DOT, bool TMA, int NTH>
+__device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
+                                       const T* x_in, T* x_out, const T* xc, const Dims& d, const Dims& dc,
+                                       GkState* st, int inst, int x0, int y0) {
     constexpr int H = 2 * NU;
     using TL = Tile<T, L0, H>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
-    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     T* sb = sm;
     T* scx = sm + TL::OFF_C;
     T* scy = L0 ? scx : scx + TL::NCS;
     T* sx = sm + TL::OFF_X;
-    const int inst = blockIdx.z, x0 = blockIdx.x * MTX, y0 = blockIdx.y * MTY;
-    if (DOT && st[inst].status != ST_OK) return;
-    stage<T, L0, H, TMA, true>(sm, maps, cond, b, x_in, d, inst, x0, y0, st);
+    const T* sd = sm + TL::OFF_D;
+    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st);
+    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
     const int64_t offc = (int64_t)inst * dc.N;
-    for (int i = threadIdx.x; i < TL::NCS; i += MNT) {  // + P xc on the staged cells in the domain
+    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {  // + P xc on the staged cells in the domain
         const int ly = i / LXS, lxs = i - ly * LXS;
         const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
         if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
@@ -208,12 +244,12 @@ __global__ void __launch_bounds__(MNT) k_mg_post2d(const __grid_constant__ Maps 
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, H>(sb, scx, scy, sx, s + 1, 1 - (s & 1), d, x0, y0);
+        half_sweep<T, TL::LX, TL::LY, LXS, OX, H, NTH>(sb, sd, scx, scy, sx, s + 1, 1 - (s & 1), x0, y0);
         __syncthreads();
     }
     const int64_t off = (int64_t)inst * d.N;
     T part = (T)0;
-    for (int k = threadIdx.x; k < MTX * MTY; k += MNT) {
+    for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
         const int ty = k / MTX, tx = k - ty * MTX;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx < d.nx && gy < d.ny) {
@@ -222,11 +258,92 @@ __global__ void __launch_bounds__(MNT) k_mg_post2d(const __grid_constant__ Maps 
             if (DOT) part = fma(sx[i], sb[i], part);
         }
     }
+    __syncthreads();
+    return part;
+}
+
+// DOT: also alpha = sqrt(x_out . b) and the rotations (finest level of the last V-cycle:
+// x_out = v~, b = p~).
+template <typename T, bool L0, int NU, bool DOT, bool INIT, bool TMA, int NTH>
+__global__ void __launch_bounds__(NTH) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
+                                                   const T* __restrict__ b, const T* __restrict__ x_in,
+                                                   T* __restrict__ x_out, const T* __restrict__ xc, Dims d, Dims dc,
+                                                   GkState* st, Hist hist, Red red) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int inst = blockIdx.z;
+    pdl_grid_sync();
+    if (DOT && st[inst].status != ST_OK) return;
+    const T part = post_tile<T, L0, NU, DOT, TMA, NTH>(smraw, maps, cond, b, x_in, x_out, xc, d, dc, st, inst,
+                                                 blockIdx.x * MTX, blockIdx.y * MTY);
     if (DOT) {
         const int nblk = gridDim.x * gridDim.y;
         double tot;
-        if (reduce_last<MNT>((double)part, red, inst, blockIdx.x + gridDim.x * blockIdx.y, nblk, &tot))
+        if (reduce_last<NTH>((double)part, red, inst, blockIdx.x + gridDim.x * blockIdx.y, nblk, &tot))
             finalize_alpha<INIT>(st[inst], tot, hist, inst);
+    }
+}
+
+struct TailMaps {
+    Maps pre[TAIL_LEVELS - 1], post[TAIL_LEVELS - 1];
+};
+
+// Barrier between two phases of the coarse end: the generic-proxy writes of this phase are
+// ordered before the TMA reads of the next, and the cluster barrier (release/acquire at cluster
+// scope) makes them visible to every block of the cluster.
+__device__ __forceinline__ void tail_phase_barrier() {
+    fence_proxy_async();
+    cluster_barrier();
+    fence_proxy_async();
+}
+
+// The coarse end of the V-cycle in one launch: levels lc..L-2 (pre-smoothing going down, post-
+// smoothing coming up) and the exact solve x = X b on the coarsest level, for one instance per
+// cluster of CS blocks.  Each phase spreads the tiles (rows of X) of its level over the blocks of
+// the cluster, separated by tail_phase_barrier.  The arithmetic per cell and the summation order
+// are those of the per-level kernels and of the coarse symv kernel.
+template <typename T, int NU, int CS, bool TMA>
+__global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailLevels tl,
+                                                   const __grid_constant__ TailMaps tm, const T* X, int nc,
+                                                   GkState* st) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int inst = blockIdx.y, rank = blockIdx.x;
+    const int nl = tl.n;
+    pdl_grid_sync();
+    if (st[inst].status != ST_OK) return;  // the same answer in every block of the cluster
+    for (int q = 0; q < nl - 1; ++q) {
+        const Dims d = tl.d[q], dc = tl.d[q + 1];
+        const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);
+        for (int t = rank; t < nt; t += CS)
+            pre_tile<T, false, NU, TMA, TNT>(smraw, tm.pre[q], (const T*)tl.cond[q], (const T*)tl.b[q], (T*)tl.x[q],
+                                             (T*)tl.b[q + 1], d, dc, st, inst, (t % tx) * MTX, (t / tx) * MTY);
+        tail_phase_barrier();
+    }
+    {
+        T* sbv = reinterpret_cast<T*>(smraw);
+        const T* bL = (const T*)tl.b[nl - 1] + (int64_t)inst * nc;
+        T* xL = (T*)tl.x2[nl - 1] + (int64_t)inst * nc;
+        for (int i = threadIdx.x; i < nc; i += TNT) sbv[i] = bL[i];
+        __syncthreads();
+        const int per = (nc + CS - 1) / CS, r0 = rank * per, r1 = min(nc, r0 + per);
+        const int lane = threadIdx.x & 31;
+        for (int row = r0 + (threadIdx.x >> 5); row < r1; row += TNT / 32) {
+            const T* Xr = X + (int64_t)inst * nc * nc + (int64_t)row * nc;
+            T acc = (T)0;
+            for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sbv[c], acc);
+            acc = warp_sum_t<T>(acc);
+            if (lane == 0) xL[row] = acc;
+        }
+        __syncthreads();
+        tail_phase_barrier();
+    }
+    for (int q = nl - 2; q >= 0; --q) {
+        const Dims d = tl.d[q], dc = tl.d[q + 1];
+        const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);
+        for (int t = rank; t < nt; t += CS)
+            post_tile<T, false, NU, false, TMA, TNT>(smraw, tm.post[q], (const T*)tl.cond[q], (const T*)tl.b[q],
+                                                     (const T*)tl.x[q], (T*)tl.x2[q], (const T*)tl.x2[q + 1], d, dc,
+                                                     st, inst, (t % tx) * MTX, (t / tx) * MTY);
+        if (q > 0) tail_phase_barrier();
     }
 }
 
@@ -247,10 +364,11 @@ static void pre_launch(const T* cond, const T* b, T* x, T* bc, Dims d, Dims dc, 
     const size_t smem = Tile<T, L0, H>::bytes();
     Maps maps;
     const bool tma = tma_enabled() && make_maps<T, L0, H>(maps, cond, b, nullptr, d, B);
-    auto kfn = tma ? k_mg_pre2d<T, L0, NU, true> : k_mg_pre2d<T, L0, NU, false>;
+    constexpr int NTH = L0 ? MNT : CNT;
+    auto kfn = tma ? k_mg_pre2d<T, L0, NU, true, NTH> : k_mg_pre2d<T, L0, NU, false, NTH>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
-    kfn<<<grid, MNT, smem, s>>>(maps, cond, b, x, bc, d, dc, st);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, x, bc, d, dc, st);
 }
 
 template <typename T, bool L0, int NU, bool DOT, bool INIT>
@@ -260,15 +378,130 @@ static void post_launch(const T* cond, const T* b, const T* xi, T* x, const T* x
     const size_t smem = Tile<T, L0, H>::bytes();
     Maps maps;
     const bool tma = tma_enabled() && make_maps<T, L0, H>(maps, cond, b, xi, d, B);
-    auto kfn = tma ? k_mg_post2d<T, L0, NU, DOT, INIT, true> : k_mg_post2d<T, L0, NU, DOT, INIT, false>;
+    constexpr int NTH = L0 ? MNT : CNT;
+    auto kfn = tma ? k_mg_post2d<T, L0, NU, DOT, INIT, true, NTH> : k_mg_post2d<T, L0, NU, DOT, INIT, false, NTH>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
     if (DOT && (int64_t)grid.x * grid.y > red.max_blocks)
         throw std::runtime_error("mg_post2d: too many blocks for the reduction scratch");
-    kfn<<<grid, MNT, smem, s>>>(maps, cond, b, xi, x, xc, d, dc, st, hist, red);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, xi, x, xc, d, dc, st, hist, red);
 }
 
 bool mg2d_supported(int ndim, int nu) { return ndim == 2 && nu >= 1 && nu <= 3; }
+
+constexpr int TAIL_CS = 16;  // blocks per cluster (non-portable size; the driver is asked first)
+
+// At least 120 KB per block, so that the blocks of a cluster land on different SMs (the tiles of
+// a phase then run in parallel instead of sharing one SM's issue slots).
+template <typename T, int NU>
+static size_t tail_smem(int nc) {
+    return std::max({Tile<T, false, 2 * NU + 1>::bytes(), Tile<T, false, 2 * NU>::bytes(), sizeof(T) * (size_t)nc,
+                     (size_t)120 * 1024});
+}
+
+template <typename T, int NU>
+static cudaLaunchConfig_t tail_config(int B, size_t smem, cudaStream_t s, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(TAIL_CS, B, 1);
+    cfg.blockDim = dim3(TNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = TAIL_CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
+    return cfg;
+}
+
+template <typename T, int NU, bool TMA>
+static bool tail_prepare_one(int nc) {
+    const size_t smem = tail_smem<T, NU>(nc);
+    auto kfn = k_mg_tail2d<T, NU, TAIL_CS, TMA>;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = tail_config<T, NU>(1, smem, nullptr, at);
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kfn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+template <typename T, int NU>
+static bool tail_prepare(int nc) {
+    return tail_prepare_one<T, NU, true>(nc) && tail_prepare_one<T, NU, false>(nc);
+}
+
+int mg2d_tail_level(const Dims* d, int L, int nu, size_t elem, int nc) {
+    // Opt-in (PLSQR_MG_TAIL=1): on the 1024^2 deblurring workload the cluster barriers and the
+    // idle blocks of the small levels made the single launch slower than the per-level launches.
+    const char* e = std::getenv("PLSQR_MG_TAIL");
+    if (!(e && e[0] == '1') || !mg2d_supported(d[0].ndim, nu) || L < 3) return L;
+    int lc = L;
+    for (int l = std::max(1, L - TAIL_LEVELS); l < L - 1; ++l) {
+        const int nt = ((d[l].nx + MTX - 1) / MTX) * ((d[l].ny + MTY - 1) / MTY);
+        if (nt <= 2 * TAIL_CS) {
+            lc = l;
+            break;
+        }
+    }
+    if (lc == L) return L;
+    bool ok = false;
+#define TAIL_PREP(NU_)                                                                  \
+    case NU_:                                                                           \
+        ok = elem == 8 ? tail_prepare<double, NU_>(nc) : tail_prepare<float, NU_>(nc); \
+        break;
+    switch (nu) {
+        TAIL_PREP(1)
+        TAIL_PREP(2)
+        TAIL_PREP(3)
+    }
+#undef TAIL_PREP
+    return ok ? lc : L;
+}
+
+template <typename T, int NU>
+static void tail_launch(const TailLevels& tl, const T* X, int nc, int B, GkState* st, cudaStream_t s) {
+    TailMaps tm;
+    bool tma = tma_enabled();
+    for (int q = 0; q + 1 < tl.n && tma; ++q) {
+        const T* c = (const T*)tl.cond[q];
+        const T* b = (const T*)tl.b[q];
+        tma = make_maps<T, false, 2 * NU + 1>(tm.pre[q], c, b, nullptr, tl.d[q], B) &&
+              make_maps<T, false, 2 * NU>(tm.post[q], c, b, (const T*)tl.x[q], tl.d[q], B);
+    }
+    cudaLaunchAttribute at[2];
+    const cudaLaunchConfig_t cfg = tail_config<T, NU>(B, tail_smem<T, NU>(nc), s, at);
+    const cudaError_t e = tma ? cudaLaunchKernelEx(&cfg, k_mg_tail2d<T, NU, TAIL_CS, true>, tl, tm, X, nc, st)
+                              : cudaLaunchKernelEx(&cfg, k_mg_tail2d<T, NU, TAIL_CS, false>, tl, tm, X, nc, st);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("mg2d_tail: ") + cudaGetErrorString(e));
+}
+
+template <typename T>
+void mg2d_tail(const TailLevels& tl, int nu, const T* X, int nc, int B, GkState* st, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    switch (nu) {
+        case 1: tail_launch<T, 1>(tl, X, nc, B, st, s); break;
+        case 2: tail_launch<T, 2>(tl, X, nc, B, st, s); break;
+        case 3: tail_launch<T, 3>(tl, X, nc, B, st, s); break;
+        default: throw std::runtime_error("mg2d_tail: unsupported sweep count");
+    }
+    klaunched("k_mg_tail2d");
+    kfinish(s);
+}
+
+template void mg2d_tail<float>(const TailLevels&, int, const float*, int, int, GkState*, cudaStream_t);
+template void mg2d_tail<double>(const TailLevels&, int, const double*, int, int, GkState*, cudaStream_t);
 
 template <typename T>
 void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     __shared__ __align__(128) float sin[LY * LX];
     __shared__ __align__(16) float smid[LY * BTX];
     __shared__ __align__(8) uint64_t bar;
+    pdl_grid_sync();
     const int plane = blockIdx.z;
     const int inst = plane / d.nz;
     if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
@@ -519,12 +520,12 @@ static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const
         tma = tma_enabled() &&
               tma_map_3d(&map, in, 4, d.nx, d.ny, (int64_t)d.nz * B, BTX + 2 * R, BTY + 2 * R, 1);
         if (tma)
-            k_blur2d_rb<R, EPI, MI, MO, true, UPD>
-                <<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red, fu, wu);
+            launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                     (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu);
     }
     if (!tma)
-        k_blur2d_rb<R, EPI, MI, MO, false, UPD>
-            <<<grid, BNT, 0, s>>>(map, in, out, prev, op.mask, d, wx, wy, st, red, fu, wu);
+        launch_k(k_blur2d_rb<R, EPI, MI, MO, false, UPD>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                 (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu);
     klaunched("k_blur2d_rb");
 }
 

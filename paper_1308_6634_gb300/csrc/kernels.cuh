@@ -2,7 +2,32 @@
 #pragma once
 #include "common.cuh"
 
+#include <stdexcept>
+#include <string>
+
 namespace plsqr {
+
+// Programmatic dependent launches are used unless PLSQR_PDL=0.
+bool pdl_enabled();
+
+// Launch a kernel that begins with pdl_grid_sync(), with the programmatic-serialization attribute
+// so that its launch overlaps the tail of the previous kernel in the stream.
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
 
 // Epilogue of an operator application out = op(in):
 //  EPI_PLAIN     out = op(in)
@@ -76,9 +101,20 @@ void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, 
 template <typename T>
 void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s);
 void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+// Single-precision subtraction-free coarse factorisation and inverse (bandwidth <= 32).
+int gth_stride(int bw);
+bool gth_supported(int bw, int nc);
+template <typename T>
+void gth_assemble(const T* cond, bool is_kappa, float* gcol, Dims d, int bw, int B, cudaStream_t s);
+void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
 
 // ---- temporally blocked 2D V-cycle (one launch per level and direction) ----
 bool mg2d_supported(int ndim, int nu);
+// First level from which the coarse end of a 2D V-cycle (levels.. L-1) runs as one cluster launch
+// (mg2d_tail), or L when it does not apply.
+int mg2d_tail_level(const Dims* d, int L, int nu, size_t elem, int nc);
+template <typename T>
+void mg2d_tail(const TailLevels& tl, int nu, const T* X, int nc, int B, GkState* st, cudaStream_t s);
 // x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x)
 template <typename T>
 void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,

@@ -83,6 +83,10 @@ struct plsqr_ctx {
     double* rdiag = nullptr;  // 1/L(j,j) of the coarse factor, [B][nc]
     double* X = nullptr;  // inverse of the coarsest operator, [B][nc][nc]
     float* Xf = nullptr;  // the same rounded to float (single-precision handles)
+    // single-precision handles with a coarsest bandwidth <= 32: subtraction-free L D L^T in float
+    bool gth = false;
+    float* gcol = nullptr;  // [B][nc][stride]: column layout (input conductances, then l and 1/d)
+    float* grow = nullptr;  // [B][nc][stride]: row layout of l
     GkState* st = nullptr;
     SolveParams* prm_dev = nullptr;
     SolveParams* prm_host = nullptr;  // pinned
@@ -96,6 +100,8 @@ struct plsqr_ctx {
     // graphs (with the number of kernel launches each replay executes)
     std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
+    int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
+    TailLevels tail{};
     bool no_fuse_update = false;  // PLSQR_FUSE_UPDATE=0: separate update kernel (comparisons)
     Profiler prof;
     int64_t last_launches = 0;
@@ -155,6 +161,7 @@ struct Plan {
     int L, nc, bw;
     int64_t level_N[16];
     size_t bytes;
+    bool gth;
 };
 
 Plan make_plan(const plsqr_config* c, int64_t m) {
@@ -183,8 +190,11 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     pl.nc = (int)dc.N;
     pl.bw = c->ndim == 3 ? dc.nx * dc.ny : dc.nx;
     if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
-    if ((size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 + pl.bw * 8 >
-        227 * 1024)
+    const char* e64 = std::getenv("PLSQR_COARSE64");
+    pl.gth = c->precision == PLSQR_FP32 && gth_supported(pl.bw, pl.nc) && !(e64 && e64[0] == '1');
+    if (!pl.gth && (size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 +
+                           pl.bw * 8 >
+                       227 * 1024)
         throw InvalidArg("coarsest level too wide for the banded factorisation: add levels");
     const size_t esz = c->precision == PLSQR_FP64 ? 8 : 4;
     const int64_t B = c->max_batch, N = pl.d.N;
@@ -194,8 +204,13 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += esz * B * (N + m);          // tmp (N), tmpm (m)
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
     for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
-    b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
-    b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
+    if (pl.gth) {
+        b += sizeof(float) * B * (size_t)pl.nc * 2 * gth_stride(pl.bw);
+        b += sizeof(float) * B * (size_t)pl.nc * pl.nc;
+    } else {
+        b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
+        b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
+    }
     b += (sizeof(GkState) + sizeof(SolveParams) + sizeof(unsigned)) * B;
     b += sizeof(double) * B * 8192;
     pl.bytes = b;
@@ -270,6 +285,10 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
         coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, s);
         return;
     }
+    if (l == h->tail_lc) {  // levels l..L-1 in one cluster launch (x is lv[l].x2 here)
+        mg2d_tail<T>(h->tail, h->nu, coarse_inverse_of<T>(h), h->nc, B, h->st, s);
+        return;
+    }
     const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
     const bool isk = l == 0;
     T* xpre = l == 0 ? P<T>(h->tmp) : P<T>(Lv.x);
@@ -305,7 +324,13 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
         mg_coarsen<T>(l == 0 ? P<T>(h->kappa) : P<T>(h->lv[l].cond), l == 0, P<T>(h->lv[l + 1].cond), h->lv[l].d,
                       h->lv[l + 1].d, B, s);
     const int lc = h->L - 1;
-    coarse_assemble<T>(lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond), lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
+    const T* cc = lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond);
+    if (h->gth) {
+        gth_assemble<T>(cc, lc == 0, h->gcol, h->lv[lc].d, h->bw, B, s);
+        gth_factor_inverse(h->gcol, h->grow, h->Xf, h->nc, h->bw, B, h->st, s);
+        return;
+    }
+    coarse_assemble<T>(cc, lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
     coarse_cholesky(h->band, h->rdiag, h->nc, h->bw, B, s);
     coarse_inverse(h->band, h->rdiag, h->X, h->nc, h->bw, B, s);
     if (!h->fp64) round_to_float(h->X, h->Xf, (int64_t)B * h->nc * h->nc, s);
@@ -663,9 +688,29 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
             h->lv[l].x = dalloc(h, e * B * Nl);
             h->lv[l].x2 = dalloc(h, e * B * Nl);
         }
-        h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
-        h->rdiag = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc);
-        h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
+        {
+            Dims dl[16];
+            for (int l = 0; l < h->L; ++l) dl[l] = h->lv[l].d;
+            h->tail_lc = h->generic_mg ? h->L : mg2d_tail_level(dl, h->L, h->nu, h->esz, h->nc);
+            h->tail.n = h->tail_lc < h->L ? h->L - h->tail_lc : 0;
+            for (int q = 0; q < h->tail.n; ++q) {
+                const Level& Lv = h->lv[h->tail_lc + q];
+                h->tail.cond[q] = Lv.cond;
+                h->tail.b[q] = Lv.b;
+                h->tail.x[q] = Lv.x;
+                h->tail.x2[q] = Lv.x2;
+                h->tail.d[q] = Lv.d;
+            }
+        }
+        h->gth = pl.gth;
+        if (h->gth) {
+            h->gcol = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
+            h->grow = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
+        } else {
+            h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
+            h->rdiag = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc);
+            h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
+        }
         if (!h->fp64) h->Xf = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * h->nc);
         h->st = (GkState*)dalloc(h, sizeof(GkState) * B);
         ck(cudaMemset(h->st, 0, sizeof(GkState) * B), "memset");

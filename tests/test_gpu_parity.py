@@ -151,6 +151,36 @@ def test_priorconditioner(prec, shape, levels, nu, cycles):
     assert rel(host(S.apply_M(dev(b, prec))), O.apply_M(kappa, b)) < (1e-13 if prec == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("shape", [(32, 32), (24, 16), (8, 8), (2, 3, 4), (4, 4, 2)])
+def test_single_precision_coarse_solve(shape):
+    """Float handles factor the coarsest operator without subtractions (L D L^T carrying the row-sum
+    excess).  With one level the priorconditioner is exactly that coarse solve, so it must match the
+    oracle's double-precision Cholesky solve to float accuracy even for a diffusivity with a 1e4
+    contrast (condition numbers ~1e5 here; an emulation in float gives ~5e-7)."""
+    rng = np.random.default_rng(11)
+    kappa = np.where(rng.random(shape) < 0.3, 1e-4, 1.0) * rng.uniform(0.5, 1.5, shape)
+    b = rng.standard_normal(shape)
+    ref = O.Multigrid(kappa, 1, 2, 1).apply(b)
+    S = _P().Solver(shape, "fp32", levels=1)
+    S.prec_setup(dev(kappa, "fp32"))
+    assert rel(host(S.prec_apply(dev(b, "fp32"))), ref) < 5e-6
+
+
+def test_single_precision_coarse_solve_matches_double_route(monkeypatch):
+    """The float coarse route against the double-precision banded Cholesky route of the same handle
+    type (PLSQR_COARSE64=1) inside a full V-cycle."""
+    shape, levels = (256, 256), 4
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(12).standard_normal(shape)
+    outs = []
+    for route in ("0", "1"):
+        monkeypatch.setenv("PLSQR_COARSE64", route)
+        S = _P().Solver(shape, "fp32", levels=levels)
+        S.prec_setup(dev(kappa, "fp32"))
+        outs.append(host(S.prec_apply(dev(b, "fp32"))))
+    assert rel(outs[0], outs[1]) < 2e-6
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nu", [1, 2, 3])
 def test_fused_vcycle_matches_one_launch_per_half_sweep(prec, nu, monkeypatch):
@@ -165,6 +195,24 @@ def test_fused_vcycle_matches_one_launch_per_half_sweep(prec, nu, monkeypatch):
         S.prec_setup(dev(kappa, prec))
         outs.append(host(S.prec_apply(dev(b, prec))))
     assert rel(outs[0], outs[1]) < (1e-13 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,levels,cycles", [((256, 256), 6, 1), ((1024, 1024), 6, 1), ((136, 200), 4, 1),
+                                                 ((64, 64), 3, 2)])
+def test_coarse_end_in_one_launch_matches_per_level_launches(prec, shape, levels, cycles, monkeypatch):
+    """The coarse levels of the 2D V-cycle run as one cluster launch (cluster barriers between the
+    levels); the arithmetic per cell and the summation order are those of the per-level launches,
+    so the two must agree bit for bit."""
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(13).standard_normal(shape)
+    outs = []
+    for tail in ("1", "0"):
+        monkeypatch.setenv("PLSQR_MG_TAIL", tail)  # opt-in schedule against the default
+        S = _P().Solver(shape, prec, levels=levels, sweeps=2, cycles=cycles)
+        S.prec_setup(dev(kappa, prec))
+        outs.append(host(S.prec_apply(dev(b, prec))))
+    assert np.array_equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("kind", ["blur", "blur_mask"])
@@ -273,11 +321,18 @@ SOLVE_CASES = {
 }
 
 
+# Residual estimates of the first outer step compared tightly.  In the tomography cases chaos sets
+# in one iteration earlier: with a relative perturbation of 1e-7 (1e-6) on each priorconditioner
+# output the fifth estimate of tomo64's first outer step moves by up to 6e-6 (6e-4), the sixth by
+# 3e-1, while the same perturbation of g moves neither, so only the first four are compared there.
+N_TIGHT = {"tomo64_fp32": 4, "tomo64_fp64": 4}
+
+
 @pytest.mark.parametrize("case", sorted(SOLVE_CASES))
 def test_full_solve(case):
     """Full fixed-point solves (Algorithm 3): f and the ||rbar|| histories within
-    max(1e-3, C * rounding envelope); the first five residual estimates of the first outer
-    step (constant kappa, before chaos) tightly."""
+    max(1e-3, C * rounding envelope); the first residual estimates of the first outer step
+    (constant kappa, before chaos) tightly."""
     from envelope import C_ENV, reference_and_envelope
 
     W, n_outer, n_inner = SOLVE_CASES[case]
@@ -293,7 +348,8 @@ def test_full_solve(case):
     assert ef <= max(1e-3, C_ENV * env["f"])
     assert eh <= max(1e-3, C_ENV * env["rbar_hist"])
     h0 = 1e-12 if W.precision == "fp64" else 1e-4
-    assert rel(info["rbar_hist"][0][:5], ref["rbar_hist"][0][:5]) < h0
+    nt = N_TIGHT.get(case, 5)
+    assert rel(info["rbar_hist"][0][:nt], ref["rbar_hist"][0][:nt]) < h0
     assert np.isfinite(info["R_hist"]).all() and np.isfinite(info["resid_hist"]).all()
 
 
