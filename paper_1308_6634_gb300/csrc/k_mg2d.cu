@@ -232,14 +232,26 @@ __device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, c
     T* scy = L0 ? scx : scx + TL::NCS;
     T* sx = sm + TL::OFF_X;
     const T* sd = sm + TL::OFF_D;
-    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st);
-    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
+    // P xc for this thread's staged cells (inside the domain), loaded before the tile so that the
+    // loads overlap the staging
+    constexpr int NPT = (TL::NCS + NTH - 1) / NTH;
     const int64_t offc = (int64_t)inst * dc.N;
-    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {  // + P xc on the staged cells in the domain
+    T xcv[NPT];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const int i = threadIdx.x + q * NTH;
         const int ly = i / LXS, lxs = i - ly * LXS;
         const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
-        if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
-            sx[i] = sx[i] + xc[offc + (int64_t)(gy >> 1) * dc.nx + (gx >> 1)];
+        xcv[q] = (i < TL::NCS && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
+                     ? xc[offc + (int64_t)(gy >> 1) * dc.nx + (gx >> 1)]
+                     : (T)0;
+    }
+    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st);
+    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {  // + P xc (cells outside the domain add 0 and stay 0)
+        const int i = threadIdx.x + q * NTH;
+        if (i < TL::NCS) sx[i] = sx[i] + xcv[q];
     }
     __syncthreads();
 #pragma unroll
