@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-fp64-single", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="serving: device-memory budget")
     return ap.parse_args()
 
 
@@ -233,8 +237,50 @@ def run_reference(args, W):
     return 0
 
 
+def run_serving(args):
+    """The serving stream: Poisson arrivals of deblurring and tomography requests of mixed sizes
+    served by the continuous-batching engine; value = completed solves / (last completion - first
+    arrival); per-request latency percentiles over --requests requests."""
+    import torch
+    from paper_1308_6634_gb300 import serving
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    count = args.requests
+    reqs = serving.make_stream(count, rate=args.rate, seed=rank)
+    data = {r.rid: serving.make_data(r, torch, dev)[0] for r in reqs}
+    warm = serving.make_stream(max(8, args.warmup * 4), rate=1000.0, seed=10_000 + rank)
+    wdata = {r.rid: serving.make_data(r, torch, dev)[0] for r in warm}
+    eng = serving.Engine(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
+    eng.run(warm, wdata, realtime=False)  # creates and warms buckets (graph capture)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        eng.run(reqs, data)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    sm = serving.summarize(reqs)
+    if rank == 0:
+        line = {
+            "metric": "solves/s and p50/p99 ms (serving stream)", "value": sm["solves_per_s"] * world,
+            "unit": "solves/s", "n_gpus": world, "steps": count, "warmup": len(warm),
+            "ms_per_step": 1e3 * wall / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve_stream_{count}_poisson{args.rate:g}", "sizes": list(serving.SIZES),
+                       "size_p": list(serving.SIZE_P), "angles": list(serving.ANGLES), "n_outer": 10,
+                       "n_inner": 30, "parallelism": f"replicas x{world}", "hbm_budget_gb": args.hbm_budget_gb},
+            "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "serving": sm,
+            "buckets": len(eng.buckets), "bucket_bytes": eng.bytes_used, "admission_refusals": eng.refused,
+            "clocks": clk.summary(), "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serve":
+        return run_serving(args)
     from paper_1308_6634_gb300 import synth
     W = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -348,6 +394,12 @@ def main():
                         "share_of_eager_device_time": ms / total_prof, "largest_class": top,
                         "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
 
+    # the plain form beside it: the same workload with the same kernels instantiated in double,
+    # one instance per call, no CUDA graph
+    fp64_single = None
+    if rank == 0 and world == 1 and not args.no_fp64_single and W.precision == "fp32":
+        fp64_single = time_fp64_single(W, plsqr, torch, dev, gs[0])
+
     cpu = None
     acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -378,6 +430,7 @@ def main():
             "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
             "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "accuracy": acc,
+            "fp64_single": fp64_single,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -387,6 +440,36 @@ def main():
 
 def W_N(W):
     return int(np.prod(W.shape))
+
+
+def time_fp64_single(W, plsqr, torch, dev, g32, steps=2):
+    """solves/s of the double-precision single-instance form without graph replay, and the
+    relative difference of its reconstruction from the single-precision one on the same data."""
+    os.environ["PLSQR_GRAPH"] = "0"
+    try:
+        S = plsqr.Solver(W.shape, "fp64", levels=W.levels, sweeps=W.nu, cycles=W.cycles)
+    finally:
+        os.environ.pop("PLSQR_GRAPH", None)
+    S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=W.inputs(0)[1], n_angles=W.n_angles,
+                   n_bins=W.n_bins)
+    g = g32.double()
+    f = torch.empty(W.shape, dtype=torch.float64, device=dev)
+    S.solve(g, W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=f)  # warm-up
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        S.solve(g, W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=f)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    S32 = plsqr.Solver(W.shape, "fp32", levels=W.levels, sweeps=W.nu, cycles=W.cycles)
+    S32.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=W.inputs(0)[1], n_angles=W.n_angles,
+                     n_bins=W.n_bins)
+    f32, _ = S32.solve(g32, W.reg, W.T, W.tau, W.n_outer, W.n_inner)
+    diff = float(torch.linalg.vector_norm(f32.double() - f) / torch.linalg.vector_norm(f))
+    return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_solve": ms, "batch": 1, "graph": False,
+            "dtype": "f64", "steps": steps, "rel_diff_fp32_vs_fp64_f": diff}
 
 
 if __name__ == "__main__":

@@ -185,6 +185,36 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
 
+/* ---- slots: continuous batching ---------------------------------------------------------------
+ * Algorithm 3 advanced one lagged-diffusivity step at a time (Sec. 4.1: steps 3-5 of one outer
+ * iteration), with the handle's max_batch instances used as slots that requests enter and leave
+ * independently.  A slot's iterates, Krylov state and histories stay on the device between
+ * steps.  Each slot's arithmetic is that of plsqr_solve on a one-instance handle with the same
+ * operator: the instances of a launch never mix, so a request gives the same result alone and in
+ * any mix.  The first plsqr_slot_start puts the handle in slot mode, where plsqr_solve*,
+ * plsqr_solve_batch and plsqr_set_operator return PLSQR_E_STATE.
+ *
+ * plsqr_slot_start: copies g (device, m values) into `slot` (0 <= slot < max_batch, not busy),
+ *   sets f = 0, the slot's r, T, tau and target n_outer.  n_inner must equal, and n_outer must
+ *   not exceed, those of the slots already running (history storage is shared).  sigma: NULL
+ *   (the operator's blur) or, for a 2D single-precision PLSQR_OP_BLUR handle whose radius is 6, 9,
+ *   12 or 15 on both axes, this slot's own sigma[0..1] (x, y): taps exp(-k^2/(2 sigma^2)) for
+ *   |k| <= ceil(3 sigma) <= radius, zero beyond, unit sum.  Ordered after the work already on the
+ *   caller's stream; the caller's stream then waits for the copy.
+ * plsqr_step: enqueues one outer step for every running slot that has not reached its target
+ *   (the others are skipped) and returns without waiting.
+ * plsqr_query: 1 while the last enqueued slot operation runs, 0 when done, < 0 on a CUDA error.
+ * plsqr_slot_progress: outer steps done by `slot` and whether it is running (host-side counts).
+ * plsqr_slot_finish: copies the slot's f (device, N values) to f_out, fills stats (histories of
+ *   the steps done, R of the final f), empties the slot; waits for the handle's stream.
+ *   Returns PLSQR_E_BREAKDOWN when the slot broke down (f holds its last complete iterate). */
+int plsqr_slot_start(plsqr_handle h, int32_t slot, const void* g, int32_t r, double T, double tau,
+                     int32_t n_outer, int32_t n_inner, const double* sigma);
+int plsqr_step(plsqr_handle h);
+int plsqr_query(plsqr_handle h);
+int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32_t* active);
+int plsqr_slot_finish(plsqr_handle h, int32_t slot, void* f_out, plsqr_stats* stats);
+
 /* ---- blur without device allocation ---------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
  * device memory: a serving process that hands all device memory to its own pool and admits work

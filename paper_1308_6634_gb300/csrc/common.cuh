@@ -11,6 +11,9 @@
 
 namespace plsqr {
 
+constexpr int ST_IDLE = 7;  // an empty slot of a serving handle: kernels skip the instance
+
+
 // Programmatic dependent launch.  A kernel launched with the programmatic-serialization attribute
 // (launch_k) may be scheduled while its predecessor in the stream is finishing; it waits here,
 // before its first access to global memory, until the predecessor has completed and its writes are

@@ -146,6 +146,37 @@ __global__ void k_set_params(GkState* st, const SolveParams* prm, int B, int res
     }
 }
 
+// Slot states of a serving handle.  slot < 0: every slot empty.  idle: the slot is empty (or parked:
+// kernels skip it).  Otherwise the slot takes its parameters from prm[slot] and starts afresh
+// (outer counter 0, no breakdown), or, with keep_outer, a parked slot is only made runnable again.
+__global__ void k_slots_state(GkState* st, const SolveParams* prm, int B, int slot, int idle, int keep_outer) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || (slot >= 0 && b != slot)) return;
+    GkState& s = st[b];
+    if (idle) {
+        s.status = ST_IDLE;
+        return;
+    }
+    if (keep_outer) {
+        if (s.status == ST_IDLE) s.status = ST_OK;
+        return;
+    }
+    s.reg = prm[b].reg;
+    s.T = prm[b].T;
+    s.tau = prm[b].tau;
+    s.sqrt_tau = sqrt(prm[b].tau);
+    s.outer = 0;
+    s.status = ST_OK;
+    s.status_any = ST_OK;
+}
+
+void slots_state(GkState* st, const SolveParams* prm, int B, int slot, bool idle, cudaStream_t s, bool keep_outer) {
+    kbegin(KC_GK, s);
+    k_slots_state<<<(B + 63) / 64, 64, 0, s>>>(st, prm, B, slot, idle ? 1 : 0, keep_outer ? 1 : 0);
+    klaunched("k_slots_state");
+    kfinish(s);
+}
+
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s) {
     kbegin(KC_GK, s);
     k_set_params<<<(B + 63) / 64, 64, 0, s>>>(st, prm, B, reset_outer ? 1 : 0);
@@ -256,6 +287,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ g, const T* __restrict__ Af, int64_t m,
                                                     GkState* st, Hist hist, Red red) {
     const int inst = blockIdx.y;
+    if (st[inst].status == ST_IDLE) return;
     const T* gi = g + (int64_t)inst * m;
     const T* ai = Af + (int64_t)inst * m;
     T part = (T)0;

@@ -48,6 +48,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T* __restrict__ kappa, Dims d,
                                                      GkState* st, Hist hist, double kfloor, Red red) {
     const int inst = blockIdx.y;
+    if (st[inst].status == ST_IDLE) return;
     const int reg = st[inst].reg;
     const T Tp = (T)st[inst].T;
     const T kmin = (T)kfloor * kappa_of<T>(reg, Tp, (T)0);
@@ -606,11 +607,12 @@ void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, 
 // |X||b|, below that of the single-precision smoothing around it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all, const T* __restrict__ b_all,
-                                                     T* __restrict__ x_all, int nc) {
+                                                     T* __restrict__ x_all, int nc, const GkState* st) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sb = reinterpret_cast<T*>(smraw);
     pdl_grid_sync();
     const int inst = blockIdx.y;
+    if (st && st[inst].status == ST_IDLE) return;
     const T* b = b_all + (int64_t)inst * nc;
     for (int i = threadIdx.x; i < nc; i += 256) sb[i] = b[i];
     __syncthreads();
@@ -624,12 +626,12 @@ __global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all
 }
 
 template <typename T>
-void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s) {
+void coarse_symv(const T* X, const T* b, T* x, int nc, int B, const GkState* st, cudaStream_t s) {
     kbegin(KC_COARSE, s);
     size_t smem = sizeof(T) * nc;
     auto kfn = k_coarse_symv<T>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    launch_k(kfn, dim3((nc + 7) / 8, B), dim3(256), smem, s, X, b, x, nc);
+    launch_k(kfn, dim3((nc + 7) / 8, B), dim3(256), smem, s, X, b, x, nc, st);
     klaunched("k_coarse_symv");
     kfinish(s);
 }
@@ -655,7 +657,7 @@ void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
     template void mg_apply_level<T>(const T*, bool, const T*, const T*, T*, Dims, int, cudaStream_t);      \
     template void mg_axpy<T>(T*, const T*, int64_t, cudaStream_t);                                         \
     template void coarse_assemble<T>(const T*, bool, double*, Dims, int, int, cudaStream_t);               \
-    template void coarse_symv<T>(const T*, const T*, T*, int, int, cudaStream_t);
+    template void coarse_symv<T>(const T*, const T*, T*, int, int, const GkState*, cudaStream_t);
 
 PLSQR_INST_MG(float)
 PLSQR_INST_MG(double)

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps m
                                                   Dims d, Dims dc, GkState* st) {
     extern __shared__ __align__(128) unsigned char smraw[];
     pdl_grid_sync();
+    if (st[blockIdx.z].status == ST_IDLE) return;
     pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY);
 }
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(NTH) k_mg_post2d(const __grid_constant__ Maps 
     extern __shared__ __align__(128) unsigned char smraw[];
     const int inst = blockIdx.z;
     pdl_grid_sync();
-    if (DOT && st[inst].status != ST_OK) return;
+    if (DOT ? st[inst].status != ST_OK : st[inst].status == ST_IDLE) return;
     const T part = post_tile<T, L0, NU, DOT, TMA, NTH>(smraw, maps, cond, b, x_in, x_out, xc, d, dc, st, inst,
                                                  blockIdx.x * MTX, blockIdx.y * MTY);
     if (DOT) {

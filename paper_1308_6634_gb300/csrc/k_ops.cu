@@ -149,12 +149,14 @@ struct TapsF {
 // UPD (with EPI_FWD): also the pending solution update of the previous iteration on the same
 // cells, f += (phi/rho) w~, w~ = v~ - (theta/rho) w~ (Algorithm 2 steps 19-20), with v~ taken
 // from the staged input tile.
-template <int R, int EPI, bool MASK_IN, bool MASK_OUT, bool TMA, bool UPD>
+// PI: the taps of each instance come from tapt[inst] ([2][2R+1], x then y) through shared memory
+// instead of the kernel parameters.
+template <int R, int EPI, bool MASK_IN, bool MASK_OUT, bool TMA, bool UPD, bool PI>
 __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUtensorMap map_in,
                                                    const float* __restrict__ in, float* out, const float* prev,
                                                    const uint8_t* __restrict__ mask, Dims d, const TapsF<R> wx,
                                                    const TapsF<R> wy, GkState* st, Red red, float* __restrict__ fu,
-                                                   float* __restrict__ wu) {
+                                                   float* __restrict__ wu, const float* __restrict__ tapt) {
     constexpr int LX = ((BTX + 2 * R) + 3) & ~3;  // row pitch (floats), multiple of 4
     constexpr int LY = BTY + 2 * R;
     constexpr int NW4 = (4 + 2 * R + 3) / 4;       // float4 loads per x-pass window
@@ -162,11 +164,14 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     __shared__ __align__(128) float sin[LY * LX];
     __shared__ __align__(16) float smid[LY * BTX];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ float stap[PI ? 2 * (2 * R + 1) : 1];
     pdl_grid_sync();
     const int plane = blockIdx.z;
     const int inst = plane / d.nz;
     if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
     const int tid = threadIdx.x;
+    if (PI)  // made visible by the barrier that follows the tile staging
+        for (int k = tid; k < 2 * (2 * R + 1); k += BNT) stap[k] = tapt[(int64_t)inst * 2 * (2 * R + 1) + k];
     const int x0 = blockIdx.x * BTX, y0 = blockIdx.y * BTY;
     const int64_t plane_off = (int64_t)plane * d.nx * d.ny;
     const int64_t mask_off = (int64_t)(plane - inst * d.nz) * d.nx * d.ny;
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
 #pragma unroll
             for (int k = 0; k <= 2 * R; ++k)
 #pragma unroll
-                for (int o = 0; o < 4; ++o) acc[o] = fmaf(wx.w[k], win[o + k], acc[o]);
+                for (int o = 0; o < 4; ++o) acc[o] = fmaf(PI ? stap[k] : wx.w[k], win[o + k], acc[o]);
             *reinterpret_cast<float4*>(smid + r * BTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
         }
     }
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
 #pragma unroll
         for (int k = 0; k <= 2 * R; ++k)
 #pragma unroll
-            for (int o = 0; o < 8; ++o) acc[o] = fmaf(wy.w[k], win[o + k], acc[o]);
+            for (int o = 0; o < 8; ++o) acc[o] = fmaf(PI ? stap[2 * R + 1 + k] : wy.w[k], win[o + k], acc[o]);
         const int gx = ogx;
         float cv = 0.f, cf = 0.f, cw = 0.f;
         if (UPD) {
@@ -519,13 +524,31 @@ static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const
     if constexpr (R % 4 == 0 && !MI) {
         tma = tma_enabled() &&
               tma_map_3d(&map, in, 4, d.nx, d.ny, (int64_t)d.nz * B, BTX + 2 * R, BTY + 2 * R, 1);
-        if (tma)
-            launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD>, grid, dim3(BNT), 0, s, map, in, out, prev,
-                     (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu);
+        if (tma) {
+            if constexpr (!MI && !MO) {
+                if (op.tapt) {
+                    launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD, true>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                             (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, op.tapt);
+                    klaunched("k_blur2d_rb");
+                    return;
+                }
+            }
+            launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD, false>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                     (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, (const float*)nullptr);
+        }
     }
-    if (!tma)
-        launch_k(k_blur2d_rb<R, EPI, MI, MO, false, UPD>, grid, dim3(BNT), 0, s, map, in, out, prev,
-                 (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu);
+    if (!tma) {
+        if constexpr (!MI && !MO) {
+            if (op.tapt) {
+                launch_k(k_blur2d_rb<R, EPI, MI, MO, false, UPD, true>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                         (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, op.tapt);
+                klaunched("k_blur2d_rb");
+                return;
+            }
+        }
+        launch_k(k_blur2d_rb<R, EPI, MI, MO, false, UPD, false>, grid, dim3(BNT), 0, s, map, in, out, prev,
+                 (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, (const float*)nullptr);
+    }
     klaunched("k_blur2d_rb");
 }
 

@@ -61,6 +61,9 @@ struct OpDev {
     const void* jtab;    // JosephAngle<T>[n_angles]
     int na, nb;
     double ds;
+    // per-instance blur taps (2D single precision, no mask): [B][2][2R+1] (x then y), or null when
+    // every instance uses taps[] (slots of a serving handle may each have their own width)
+    const float* tapt;
 };
 
 template <typename T>
@@ -99,7 +102,7 @@ void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw,
 void coarse_cholesky(double* band, double* rdiag, int nc, int bw, int B, cudaStream_t s);
 void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, int bw, int B, cudaStream_t s);
 template <typename T>
-void coarse_symv(const T* X, const T* b, T* x, int nc, int B, cudaStream_t s);
+void coarse_symv(const T* X, const T* b, T* x, int nc, int B, const GkState* st, cudaStream_t s);
 void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
 // Single-precision subtraction-free coarse factorisation and inverse (bandwidth <= 32).
 int gth_stride(int bw);
@@ -126,6 +129,8 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, cons
 
 // ---- Golub-Kahan scalars and updates ----
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);
+void slots_state(GkState* st, const SolveParams* prm, int B, int slot, bool idle, cudaStream_t s,
+                 bool keep_outer = false);
 template <typename T>
 void gk_init_norm(const T* g, int64_t m, int B, GkState* st, Red red, cudaStream_t s);
 template <typename T>

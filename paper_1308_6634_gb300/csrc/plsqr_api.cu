@@ -99,6 +99,11 @@ struct plsqr_ctx {
     size_t h_stage_n = 0;
     // graphs (with the number of kernel launches each replay executes)
     std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    // slots (continuous batching): host bookkeeping, per-slot blur taps
+    bool serving = false;
+    std::vector<int> slot_active, slot_outer, slot_target;
+    float* taps_inst = nullptr;       // device [B][2][2R+1]
+    float* taps_inst_host = nullptr;  // pinned staging, same shape
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
     TailLevels tail{};
@@ -259,7 +264,7 @@ void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
     const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
     const bool isk = l == 0;
     if (l == h->L - 1) {
-        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, s);
+        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, h->st, s);
         return;
     }
     for (int k = 0; k < h->nu; ++k) {
@@ -282,7 +287,7 @@ template <typename T>
 void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStream_t s) {
     const Level& Lv = h->lv[l];
     if (l == h->L - 1) {
-        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, s);
+        coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, h->st, s);
         return;
     }
     if (l == h->tail_lc) {  // levels l..L-1 in one cluster launch (x is lv[l].x2 here)
@@ -392,6 +397,7 @@ void ensure_hist(plsqr_ctx* h, int n_outer, int n_inner) {
     size_t need = (size_t)B * h->h_outer * h->h_inner + (size_t)B * (h->h_outer + 1) + (size_t)B * h->h_outer;
     if (need > h->h_stage_n) {
         if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->taps_inst_host) cudaFreeHost(h->taps_inst_host);
         h->h_stage = nullptr;
         ck(cudaMallocHost((void**)&h->h_stage, need * sizeof(double)), "cudaMallocHost");
         h->h_stage_n = need;
@@ -547,6 +553,7 @@ void destroy_ctx(plsqr_ctx* h) {
     if (h->prm_host) cudaFreeHost(h->prm_host);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->taps_inst_host) cudaFreeHost(h->taps_inst_host);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -737,6 +744,7 @@ int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
         if (!op) throw InvalidArg("operator is NULL");
+        if (h->serving) throw std::logic_error("set_operator on a handle in slot mode");
         const Dims& d = h->d;
         OpDev od{};
         od.d = d;
@@ -798,6 +806,7 @@ int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
 int plsqr_solve(plsqr_handle h, const void* g, int32_t reg, double T, double tau, int32_t n_outer, int32_t n_inner,
                 void* f_out, plsqr_stats* stats) {
     if (!h) return PLSQR_E_INVALID;
+    if (h->serving) return fail(h, PLSQR_E_STATE, "the handle is in slot mode");
     return guarded(h, [&]() -> int {
         int rc = 0;
         by_type(h, [&](auto tv) {
@@ -811,6 +820,7 @@ int plsqr_solve(plsqr_handle h, const void* g, int32_t reg, double T, double tau
 int plsqr_solve_host(plsqr_handle h, const void* g_host, int32_t reg, double T, double tau, int32_t n_outer,
                      int32_t n_inner, void* f_host_out, plsqr_stats* stats) {
     if (!h) return PLSQR_E_INVALID;
+    if (h->serving) return fail(h, PLSQR_E_STATE, "the handle is in slot mode");
     return guarded(h, [&]() -> int {
         int rc = 0;
         by_type(h, [&](auto tv) {
@@ -824,6 +834,7 @@ int plsqr_solve_host(plsqr_handle h, const void* g_host, int32_t reg, double T, 
 int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const int32_t* reg, const double* T,
                       const double* tau, int32_t n_outer, int32_t n_inner, void* const* f_out, plsqr_stats* stats) {
     if (!h) return PLSQR_E_INVALID;
+    if (h->serving) return fail(h, PLSQR_E_STATE, "the handle is in slot mode");
     return guarded(h, [&]() -> int {
         if (!g || !reg || !T || !tau || !f_out) throw InvalidArg("NULL array argument");
         int rc = 0;
@@ -832,6 +843,191 @@ int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const
             rc = solve_impl<TT>(h, count, g, false, reg, T, tau, n_outer, n_inner, f_out, false, stats);
         });
         return rc;
+    });
+}
+
+// ---- slots: continuous batching -----------------------------------------------------------
+
+namespace {
+
+// Taps of one slot on the handle's radius R: exp(-k^2 / (2 sigma^2)) for |k| <= ceil(3 sigma),
+// zero beyond, normalised to unit sum over the nonzero part.
+void slot_taps(float* dst, double sigma, int R) {
+    const int r = (int)std::ceil(3.0 * sigma);
+    if (!(sigma > 0.0) || !std::isfinite(sigma) || r > R) throw InvalidArg("slot sigma: ceil(3 sigma) must be <= the handle's radius");
+    double sum = 0.0;
+    for (int k = -r; k <= r; ++k) sum += std::exp(-(double)(k * k) / (2.0 * sigma * sigma));
+    for (int k = -R; k <= R; ++k)
+        dst[k + R] = std::abs(k) <= r ? (float)(std::exp(-(double)(k * k) / (2.0 * sigma * sigma)) / sum) : 0.0f;
+}
+
+void enter_slot_mode(plsqr_ctx* h) {
+    if (h->serving) return;
+    h->serving = true;
+    h->slot_active.assign(h->B, 0);
+    h->slot_outer.assign(h->B, 0);
+    h->slot_target.assign(h->B, 0);
+    slots_state(h->st, h->prm_dev, h->B, -1, true, h->stream);  // every slot empty
+}
+
+}  // namespace
+
+int plsqr_slot_start(plsqr_handle h, int32_t slot, const void* g, int32_t reg, double T, double tau, int32_t n_outer,
+                     int32_t n_inner, const double* sigma) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!h->op_set) throw std::logic_error("set_operator must be called before plsqr_slot_start");
+        if (slot < 0 || slot >= h->B) throw InvalidArg("slot out of range");
+        if (!g) throw InvalidArg("g is NULL");
+        validate_solve(h, 1, &reg, &T, &tau, n_outer, n_inner);
+        enter_slot_mode(h);
+        if (h->slot_active[slot]) throw std::logic_error("slot is busy");
+        bool any = false;
+        for (int b = 0; b < h->B; ++b) any = any || h->slot_active[b];
+        if (!any) ensure_hist(h, n_outer, n_inner);
+        else if (n_inner != h->h_inner || n_outer > h->h_outer)
+            throw InvalidArg("n_inner must equal, and n_outer not exceed, those of the running slots");
+        const bool blur2d = h->op.kind == PLSQR_OP_BLUR && h->d.ndim == 2;
+        if (sigma) {
+            if (!blur2d || h->fp64 || h->od.R[0] != h->od.R[1] || h->od.generic_blur ||
+                (h->od.R[0] != 6 && h->od.R[0] != 9 && h->od.R[0] != 12 && h->od.R[0] != 15))
+                throw InvalidArg("per-slot sigma needs a 2D single-precision blur with radius 6, 9, 12 or 15 on both axes");
+        }
+        cudaStream_t s = h->stream;
+        ck(cudaEventRecord(h->ev_in, h->user_stream), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(s, h->ev_in, 0), "cudaStreamWaitEvent");
+        const int R = h->od.R[0], W = 2 * (2 * R + 1);
+        if (sigma && !h->taps_inst) {  // from now on every slot reads its own taps
+            h->taps_inst = (float*)dalloc(h, sizeof(float) * W * h->B);
+            ck(cudaMallocHost((void**)&h->taps_inst_host, sizeof(float) * W * h->B), "cudaMallocHost");
+            for (int b = 0; b < h->B; ++b)
+                for (int k = 0; k < W; ++k) h->taps_inst_host[b * W + k] = (float)h->od.taps_host[k < W / 2 ? 0 : 1][k % (W / 2)];
+            ck(cudaMemcpyAsync(h->taps_inst, h->taps_inst_host, sizeof(float) * W * h->B, cudaMemcpyHostToDevice, s),
+               "taps");
+            h->od.tapt = h->taps_inst;
+            clear_graphs(h);
+        }
+        if (h->taps_inst) {
+            float* row = h->taps_inst_host + (size_t)slot * W;
+            if (sigma) {
+                slot_taps(row, sigma[0], R);
+                slot_taps(row + W / 2, sigma[1], R);
+            } else {
+                for (int k = 0; k < W; ++k) row[k] = (float)h->od.taps_host[k < W / 2 ? 0 : 1][k % (W / 2)];
+            }
+            ck(cudaMemcpyAsync(h->taps_inst + (size_t)slot * W, row, sizeof(float) * W, cudaMemcpyHostToDevice, s),
+               "taps");
+        }
+        const size_t mb = h->esz * h->m, nb = h->esz * h->d.N;
+        ck(cudaMemcpyAsync(h->g + slot * mb, g, mb, cudaMemcpyDeviceToDevice, s), "copy g");
+        ck(cudaMemsetAsync(h->f + slot * nb, 0, nb, s), "f0");
+        h->prm_host[slot].reg = reg;
+        h->prm_host[slot].T = T;
+        h->prm_host[slot].tau = tau;
+        ck(cudaMemcpyAsync(h->prm_dev + slot, h->prm_host + slot, sizeof(SolveParams), cudaMemcpyHostToDevice, s),
+           "params");
+        slots_state(h->st, h->prm_dev, h->B, slot, false, s);
+        fill_nan(h->h_rbar + (int64_t)slot * h->h_outer * h->h_inner, (int64_t)h->h_outer * h->h_inner, s);
+        fill_nan(h->h_R + (int64_t)slot * (h->h_outer + 1), h->h_outer + 1, s);
+        fill_nan(h->h_resid + (int64_t)slot * h->h_outer, h->h_outer, s);
+        h->slot_active[slot] = 1;
+        h->slot_outer[slot] = 0;
+        h->slot_target[slot] = n_outer;
+        ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "cudaStreamWaitEvent");
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_step(plsqr_handle h) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!h->serving) throw std::logic_error("no slot has been started");
+        int n = 0;
+        for (int b = 0; b < h->B; ++b)
+            if (h->slot_active[b] && h->slot_outer[b] < h->slot_target[b]) ++n;
+        if (n == 0) return PLSQR_OK;
+        cudaStream_t s = h->stream;
+        const int64_t launches0 = h->prof.launches;
+        // a slot that has reached its target is parked (skipped) until it is finished
+        for (int b = 0; b < h->B; ++b)
+            if (h->slot_active[b] && h->slot_outer[b] >= h->slot_target[b]) slots_state(h->st, h->prm_dev, h->B, b, true, s);
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            run_outer_steps<TT>(h, h->B, 1, h->h_inner);
+        });
+        for (int b = 0; b < h->B; ++b)
+            if (h->slot_active[b] && h->slot_outer[b] < h->slot_target[b]) ++h->slot_outer[b];
+        h->last_launches = h->prof.launches - launches0;
+        ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_query(plsqr_handle h) {
+    if (!h) return PLSQR_E_INVALID;
+    const cudaError_t e = cudaEventQuery(h->ev_out);
+    if (e == cudaErrorNotReady) return 1;
+    if (e != cudaSuccess) {
+        fail(h, PLSQR_E_CUDA, cudaGetErrorString(e));
+        return -PLSQR_E_CUDA;
+    }
+    return 0;
+}
+
+int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32_t* active) {
+    if (!h) return PLSQR_E_INVALID;
+    if (slot < 0 || slot >= h->B) return fail(h, PLSQR_E_INVALID, "slot out of range");
+    const bool on = h->serving && h->slot_active[slot];
+    if (outer_done) *outer_done = on ? h->slot_outer[slot] : 0;
+    if (active) *active = on ? 1 : 0;
+    return PLSQR_OK;
+}
+
+int plsqr_slot_finish(plsqr_handle h, int32_t slot, void* f_out, plsqr_stats* stats) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (slot < 0 || slot >= h->B) throw InvalidArg("slot out of range");
+        if (!h->serving || !h->slot_active[slot]) throw std::logic_error("slot is not running");
+        if (!f_out) throw InvalidArg("f_out is NULL");
+        cudaStream_t s = h->stream;
+        const size_t nb = h->esz * h->d.N;
+        const int no = h->slot_outer[slot], ni = h->h_inner;
+        // R(f^k) of this slot alone: the diffusivity pass on instance `slot` through shifted bases
+        Hist hs = hist_of(h);
+        hs.R = h->h_R + (int64_t)slot * (h->h_outer + 1);
+        hs.rbar = nullptr;
+        hs.resid = nullptr;
+        slots_state(h->st, h->prm_dev, h->B, slot, false, s, /*keep_outer=*/true);
+        by_type(h, [&](auto tv) {
+            using TT = decltype(tv);
+            diffusivity<TT>(P<TT>(h->f) + (int64_t)slot * h->d.N, P<TT>(h->kappa) + (int64_t)slot * h->d.N, h->d, 1,
+                            h->st + slot, hs, h->kfloor, h->red, s);
+        });
+        ck(cudaMemcpyAsync(f_out, h->f + slot * nb, nb, cudaMemcpyDeviceToDevice, s), "copy f");
+        ck(cudaMemcpyAsync(h->st_host + slot, h->st + slot, sizeof(GkState), cudaMemcpyDeviceToHost, s), "state");
+        const int64_t nr = (int64_t)h->h_outer * ni, nR = h->h_outer + 1, ne = h->h_outer;
+        if (stats) {
+            ck(cudaMemcpyAsync(h->h_stage, h->h_rbar + (int64_t)slot * nr, sizeof(double) * nr, cudaMemcpyDeviceToHost,
+                               s), "hist");
+            ck(cudaMemcpyAsync(h->h_stage + nr, h->h_R + (int64_t)slot * nR, sizeof(double) * nR,
+                               cudaMemcpyDeviceToHost, s), "hist");
+            ck(cudaMemcpyAsync(h->h_stage + nr + nR, h->h_resid + (int64_t)slot * ne, sizeof(double) * ne,
+                               cudaMemcpyDeviceToHost, s), "hist");
+        }
+        slots_state(h->st, h->prm_dev, h->B, slot, true, s);  // empty again
+        ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "cudaStreamWaitEvent");
+        ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        h->slot_active[slot] = 0;
+        const int sb = h->st_host[slot].status_any;
+        if (stats) {
+            stats->status = sb;
+            if (stats->rbar_hist) std::memcpy(stats->rbar_hist, h->h_stage, sizeof(double) * (size_t)no * ni);
+            if (stats->R_hist) std::memcpy(stats->R_hist, h->h_stage + nr, sizeof(double) * (size_t)(no + 1));
+            if (stats->resid_hist) std::memcpy(stats->resid_hist, h->h_stage + nr + nR, sizeof(double) * (size_t)no);
+        }
+        return sb != 0 ? PLSQR_E_BREAKDOWN : PLSQR_OK;
     });
 }
 

@@ -75,6 +75,11 @@ def lib():
         "plsqr_profile_read": ([vp, vp, vp, i32], C.c_int),
         "plsqr_last_launches": ([vp], i64),
         "plsqr_blur_noalloc": ([i32, C.POINTER(i64), i32, C.POINTER(d), C.POINTER(i32), vp, vp, vp], C.c_int),
+        "plsqr_slot_start": ([vp, i32, vp, i32, d, d, i32, i32, C.POINTER(d)], C.c_int),
+        "plsqr_step": ([vp], C.c_int),
+        "plsqr_query": ([vp], C.c_int),
+        "plsqr_slot_progress": ([vp, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "plsqr_slot_finish": ([vp, i32, vp, C.POINTER(Stats)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -87,7 +92,8 @@ def lib():
 EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_host", "plsqr_solve_batch",
             "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
-            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc"]
+            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
+            "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
 
@@ -292,6 +298,37 @@ class Solver:
 
     def last_launches(self):
         return int(lib().plsqr_last_launches(self.h))
+
+    # ---- slots (continuous batching) ----
+    def slot_start(self, slot, g, reg, T, tau, n_outer, n_inner, sigma=None):
+        sg = None if sigma is None else (C.c_double * 2)(*[float(x) for x in sigma])
+        _check(self.h, lib().plsqr_slot_start(self.h, int(slot), _dptr(g, self.dtype, self.m), REG[reg], float(T),
+                                              float(tau), int(n_outer), int(n_inner), sg))
+
+    def step(self):
+        _check(self.h, lib().plsqr_step(self.h))
+
+    def busy(self):
+        rc = lib().plsqr_query(self.h)
+        if rc < 0:
+            _check(self.h, -rc)
+        return rc == 1
+
+    def slot_progress(self, slot):
+        done, act = C.c_int32(0), C.c_int32(0)
+        _check(self.h, lib().plsqr_slot_progress(self.h, int(slot), C.byref(done), C.byref(act)))
+        return done.value, bool(act.value)
+
+    def slot_finish(self, slot, n_outer, n_inner, f_out=None):
+        """Returns (f, info) for a slot that ran n_outer steps of n_inner iterations."""
+        torch = _torch()
+        if f_out is None:
+            f_out = torch.empty(self.shape, dtype=self.dtype, device=torch.device("cuda", torch.cuda.current_device()))
+        st, info = self._stats(n_outer, n_inner)
+        rc = _check(self.h, lib().plsqr_slot_finish(self.h, int(slot), _dptr(f_out, self.dtype, self.N),
+                                                    C.byref(st)))
+        info["status"] = rc
+        return f_out, info
 
     # ---- single steps ----
     def apply_A(self, x, y=None):

@@ -1,0 +1,152 @@
+"""Slots and the continuous-batching serving loop.
+
+A slot of a serving handle runs Algorithm 3 one lagged-diffusivity step at a time; its
+arithmetic is that of a one-instance solve (instances of a launch never mix), so a request must
+give the same result alone and in any mix of other requests, buckets and arrival times.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_6634_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _deblur_data(n, sigma, R, seed):
+    from paper_1308_6634_gb300 import plsqr, synth
+    f = synth.phantom_rects_disks(n, 6, 4, seed)
+    x = torch.as_tensor(f, dtype=torch.float32, device="cuda")
+    Af = plsqr.plsqr_blur_noalloc(x, (sigma, sigma), (R, R))
+    z = torch.as_tensor(synth.standard_noise((n, n), seed + 1), device="cuda")
+    return (Af.double() + 0.01 * float(Af.double().norm()) / n * z).float().contiguous()
+
+
+@pytest.mark.parametrize("per_slot_sigma", [False, True])
+def test_slot_steps_equal_one_instance_solve(per_slot_sigma):
+    """n_outer plsqr_step calls on one slot (the other slots empty) reproduce plsqr_solve on a
+    one-instance handle bit for bit; with a per-slot sigma equal to the operator's (ceil(3 sigma)
+    = radius) the per-slot taps equal the operator's taps."""
+    from paper_1308_6634_gb300 import plsqr
+    n, sigma, R, n_outer, n_inner = 96, 4.0, 12, 3, 8
+    g = _deblur_data(n, sigma, R, 3)
+    S1 = plsqr.Solver((n, n), "fp32", levels=3, max_batch=1)
+    S1.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    f1, info1 = S1.solve(g, "pm_log", 5e-2, 1e-3, n_outer, n_inner)
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=4)
+    S.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    S.slot_start(2, g, "pm_log", 5e-2, 1e-3, n_outer, n_inner, sigma=(sigma, sigma) if per_slot_sigma else None)
+    for _ in range(n_outer):
+        S.step()
+    f2, info2 = S.slot_finish(2, n_outer, n_inner)
+    torch.cuda.synchronize()
+    assert info2["status"] == 0
+    assert torch.equal(f1, f2)
+    assert np.array_equal(info1["rbar_hist"], info2["rbar_hist"])
+    assert np.array_equal(info1["resid_hist"], info2["resid_hist"])
+    assert np.allclose(info1["R_hist"], info2["R_hist"], rtol=0, atol=0, equal_nan=True)
+
+
+def test_slot_with_own_sigma_matches_oracle():
+    """A slot with sigma 2.3 (support ceil(6.9) = 7, zero-padded to the handle's radius 9) against
+    the oracle's blur of radius 7: the first residual estimates before rounding chaos."""
+    import oracle as O
+    from paper_1308_6634_gb300 import plsqr, synth
+    n, sigma = 64, 2.3
+    f = synth.phantom_rects_disks(n, 6, 4, 5)
+    op = O.Operator("blur", (n, n), sigma=(sigma, sigma), radius=(7, 7))
+    g = synth.add_noise(op.A(f), 0.01, synth.standard_noise((n, n), 6))
+    ref = O.solve(op, g, "tv", 1e-2, 1e-3, 1, 5, 3, 2, 1)
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=2)
+    S.set_operator("blur", sigma=(3.0, 3.0), radius=(9, 9))
+    S.slot_start(1, torch.as_tensor(g, dtype=torch.float32, device="cuda"), "tv", 1e-2, 1e-3, 1, 5,
+                 sigma=(sigma, sigma))
+    S.step()
+    fs, info = S.slot_finish(1, 1, 5)
+    assert _rel(info["rbar_hist"][0], ref["rbar_hist"][0]) < 1e-4
+    assert _rel(fs.double().cpu().numpy(), ref["f"]) < 1e-3
+
+
+def test_slot_api_errors():
+    from paper_1308_6634_gb300 import plsqr
+    n = 64
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=2)
+    S.set_operator("blur", sigma=(2.0, 2.0), radius=(6, 6))
+    g = torch.zeros((n, n), dtype=torch.float32, device="cuda") + 1.0
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_start(2, g, "tv", 1e-2, 0.0, 2, 4)            # no such slot
+    assert e.value.code == plsqr.E_INVALID
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_start(0, g, "tv", 1e-2, 0.0, 2, 4, sigma=(2.5, 2.5))   # ceil(7.5) = 8 > radius 6
+    assert e.value.code == plsqr.E_INVALID
+    S.slot_start(0, g, "tv", 1e-2, 0.0, 2, 4)
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_start(0, g, "tv", 1e-2, 0.0, 2, 4)             # busy
+    assert e.value.code == plsqr.E_STATE
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_start(1, g, "tv", 1e-2, 0.0, 2, 5)             # different n_inner
+    assert e.value.code == plsqr.E_INVALID
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.solve(g, "tv", 1e-2, 0.0, 2, 4)                     # slot mode
+    assert e.value.code == plsqr.E_STATE
+    S.step()
+    S.step()
+    S.step()  # the slot has reached its target: nothing left to run
+    f, info = S.slot_finish(0, 2, 4)
+    assert info["status"] == 0 and torch.isfinite(f).all()
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_finish(0, 2, 4)                                # not running
+    assert e.value.code == plsqr.E_STATE
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    """A stream of deblurring and tomography requests of two sizes, different blur widths,
+    regularisers and angle counts, arriving while others run (continuous batching over several
+    buckets whose steps overlap on the device), against each request served alone."""
+    from paper_1308_6634_gb300 import serving
+    reqs = serving.make_stream(14, rate=400.0, seed=3, n_outer=3, n_inner=6, sizes=(64, 128), size_p=(0.5, 0.5),
+                               angles=(60, 90))
+    data = {r.rid: serving.make_data(r, torch, torch.device("cuda"))[0] for r in reqs}
+    eng = serving.Engine(keep_results=True, slots_for_size={64: 4, 128: 2})
+    eng.run(reqs, data)
+    mixed = eng.results()
+    summary = serving.summarize(reqs)
+    assert summary["requests"] == 14 and summary["breakdowns"] == 0
+    assert len({r.bucket for r in reqs}) >= 3
+    assert max(b.steps for b in eng.buckets.values()) > 3  # some bucket admitted requests mid-run
+    for r in reqs:
+        alone = serving.Engine(keep_results=True, slots_for_size={64: 4, 128: 2})
+        r2 = serving.Request(**{k: getattr(r, k) for k in ("rid", "kind", "n", "reg", "T", "tau", "n_outer",
+                                                            "n_inner", "seed", "sigma", "n_angles")})
+        alone.run([r2], data, realtime=False)
+        f_alone, info_alone = alone.results()[r.rid]
+        f_mix, info_mix = mixed[r.rid]
+        assert torch.equal(f_alone, f_mix), r
+        assert np.array_equal(info_alone["rbar_hist"], info_mix["rbar_hist"]), r
+
+
+def test_admission_waits_for_memory():
+    """With a budget that holds one bucket, requests of a second bucket wait until the first is
+    idle and released, and all complete."""
+    from paper_1308_6634_gb300 import serving
+    reqs = serving.make_stream(6, rate=1000.0, seed=4, n_outer=2, n_inner=4, sizes=(64,), size_p=(1.0,),
+                               angles=(60,))
+    data = {r.rid: serving.make_data(r, torch, torch.device("cuda"))[0] for r in reqs}
+    keys = {serving.bucket_key(r) for r in reqs}
+    one = max(serving.bucket_bytes(k, 4) for k in keys)
+    eng = serving.Engine(hbm_budget_bytes=one, slots_for_size={64: 4})
+    eng.run(reqs, data)
+    assert all(np.isfinite(r.t_done) for r in reqs)
+    assert len(eng.buckets) == 1
