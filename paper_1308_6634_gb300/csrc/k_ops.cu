@@ -386,15 +386,14 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, c
             qlo = max(0, (int)floor(lo) - 1);
             qhi = min(n - 1, (int)ceil(hi) + 1);
         }
+        // samples outside the image add an exact 0
         for (int q = qlo; q <= qhi; ++q) {
             const T u = u0 - ((T)q - cimg) * J.a2;
             const T fl = floor(u);
             const int j0 = (int)fl;
             const T fr = u - fl;
-            if (j0 < -1 || j0 >= n) continue;
-            T v0 = (T)0, v1 = (T)0;
-            if (j0 >= 0) v0 = im[(int64_t)q * n + j0];
-            if (j0 + 1 < n) v1 = im[(int64_t)q * n + j0 + 1];
+            const T v0 = (j0 >= 0 && j0 < n) ? im[(int64_t)q * n + j0] : (T)0;
+            const T v1 = (j0 + 1 >= 0 && j0 + 1 < n) ? im[(int64_t)q * n + j0 + 1] : (T)0;
             acc += ((T)1 - fr) * v0 + fr * v1;
         }
         acc *= J.wgt;
@@ -410,6 +409,125 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, c
         double tot;
         if (reduce_last<128>((double)part, red, inst, blockIdx.x + gridDim.x * a, gridDim.x * gridDim.y, &tot))
             finalize_beta(st[inst], tot);
+    }
+}
+
+// Joseph forward projection, band-staged: one block per (angle, instance), a thread per ray
+// (bins tid, tid + 256, ...).  The image (img for rows-stepped angles, imgT for columns-stepped
+// ones) is streamed through shared memory in bands of QB rows with cp.async double buffering, and
+// every ray takes its samples of the band from shared memory, rows in increasing order, with the
+// interpolation written x0 + fr (x1 - x0).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int JF_RAYS = 4;  // rays per thread (nb <= 1024)
+constexpr int JF_PAD = 4;   // zero elements on each side of a staged row
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_joseph_fwd_band(const T* __restrict__ img, const T* __restrict__ imgT,
+                                                         T* out, const T* prev,
+                                                         const JosephAngle<T>* __restrict__ tab, int n, int na,
+                                                         int nb, T ds, int QB, GkState* st, Red red) {
+    // band rows are stored with JF_PAD zero elements on each side (pitch n + 2 JF_PAD), so that the
+    // samples just outside the image (u in (-4, n + 3) for the conservative row ranges below, as
+    // |a2| <= 1) read zeros without a bounds test
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sbuf = reinterpret_cast<T*>(smraw);  // two bands of QB x pitch
+    const int pitch = n + 2 * JF_PAD;
+    const int inst = blockIdx.y, a = blockIdx.x;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    const JosephAngle<T> J = tab[a];
+    const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
+    const T* im = (J.rows ? img : imgT) + (int64_t)inst * n * n;
+    for (int i = threadIdx.x; i < 2 * QB * 2 * JF_PAD; i += 256) {  // the pads of both buffers
+        const int r = i / (2 * JF_PAD), c = i - r * (2 * JF_PAD);
+        sbuf[(size_t)r * pitch + (c < JF_PAD ? c : n + c)] = (T)0;
+    }
+    T u0[JF_RAYS], acc[JF_RAYS];
+    int qlo[JF_RAYS], qhi[JF_RAYS];
+#pragma unroll
+    for (int r = 0; r < JF_RAYS; ++r) {
+        const int k = threadIdx.x + 256 * r;
+        acc[r] = (T)0;
+        qlo[r] = 0;
+        qhi[r] = -1;
+        u0[r] = (T)0;
+        if (k < nb) {
+            const T s = ((T)k - cdet) * ds;
+            u0[r] = s * J.a1 + cimg;
+            qhi[r] = n - 1;
+            if (fabs((double)J.a2) < 1e-7) {
+                if (!(u0[r] > (T)-1 && u0[r] < (T)n)) qhi[r] = -1;
+            } else {
+                const T q1 = (u0[r] - (T)n) / J.a2 + cimg, q2 = (u0[r] + (T)1) / J.a2 + cimg;
+                const T lo = fmin(q1, q2), hi = fmax(q1, q2);
+                qlo[r] = max(0, (int)floor(lo) - 1);
+                qhi[r] = min(n - 1, (int)ceil(hi) + 1);
+            }
+        }
+    }
+    const int nband = (n + QB - 1) / QB;
+    const int vec = n * (int)sizeof(T) / 16;  // 16-byte chunks per row
+    auto stage = [&](int b) {
+        T* dst = sbuf + (size_t)(b & 1) * QB * pitch + JF_PAD;
+        const int rows = min(QB, n - b * QB);
+        const T* src = im + (int64_t)b * QB * n;
+        for (int c = threadIdx.x; c < rows * vec; c += 256) {
+            const int r = c / vec, v = c - r * vec;
+            cp_async16(reinterpret_cast<char*>(dst + (size_t)r * pitch) + 16 * v,
+                       reinterpret_cast<const char*>(src + (int64_t)r * n) + 16 * v);
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    const T a2 = J.a2;
+    for (int b = 0; b < nband; ++b) {
+        if (b + 1 < nband) {
+            stage(b + 1);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();
+        const T* band = sbuf + (size_t)(b & 1) * QB * pitch + JF_PAD;
+        const int q0 = b * QB, q1 = min(n, q0 + QB) - 1;
+#pragma unroll
+        for (int r = 0; r < JF_RAYS; ++r) {
+            const int lo = max(qlo[r], q0), hi = min(qhi[r], q1);
+            T qc = (T)lo - cimg;  // q - cimg, exact
+            const T* rowp = band + (size_t)(lo - q0) * pitch;
+#pragma unroll 4
+            for (int q = lo; q <= hi; ++q) {
+                const T u = u0[r] - qc * a2;
+                const T fl = floor(u);
+                const int j0 = (int)fl;
+                const T fr = u - fl;
+                const T x0 = rowp[j0], x1 = rowp[j0 + 1];
+                acc[r] += x0 + fr * (x1 - x0);
+                qc += (T)1;
+                rowp += pitch;
+            }
+        }
+        __syncthreads();  // the buffer of band b is refilled with band b + 2
+    }
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    T part = (T)0;
+#pragma unroll
+    for (int r = 0; r < JF_RAYS; ++r) {
+        const int k = threadIdx.x + 256 * r;
+        if (k < nb) {
+            const T v = epi_store<T, EPI>(acc[r] * J.wgt, ca, cp, out, prev, (int64_t)inst * na * nb + (int64_t)a * nb + k);
+            if (EPI == EPI_FWD) part = fma(v, v, part);
+        }
+    }
+    if (EPI == EPI_FWD) {
+        double tot;
+        if (reduce_last<256>((double)part, red, inst, a, na, &tot)) finalize_beta(st[inst], tot);
     }
 }
 
@@ -486,6 +604,114 @@ __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, 
     T ca, cp;
     if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
     epi_store<T, EPI>(acc, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i * n + j);
+}
+
+// Gather adjoint when every half-width is at most one bin (ds >= max(|cos|, |sin|)): the rays that
+// reach a pixel are the two bins around s_ij, floor(t) and floor(t) + 1, with weights
+// max(0, 1 - |k - t| / h).  Tiles of 16 (x) x 32 (y) pixels, two pixels per thread (rows y and
+// y + 16); per angle the tile's bin band (KB bins from k0) is staged in shared memory together
+// with (c1, c2, cdet - k0, 1/h) and the weight 1/h.
+constexpr int JAX = 16, JAY = 32;
+
+template <typename T>
+struct __align__(4 * sizeof(T)) JosephAdjAngle {
+    T c1, c2, off, ih;  // t - k0 = x c1 + y c2 + off; 1 / h
+};
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino, T* out,
+                                                     const JosephAngle<T>* __restrict__ tab, int n, int na, int nb,
+                                                     int KB, GkState* st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    using T4 = JosephAdjAngle<T>;
+    T4* sp = reinterpret_cast<T4*>(smraw);                 // (c1, c2, cdet - k0, 1/h)
+    T* sw = reinterpret_cast<T*>(sp + na);                 // 1/h (forward weight)
+    int* sk0 = reinterpret_cast<int*>(sw + na);
+    T* sbin = reinterpret_cast<T*>(smraw + ((sizeof(T4) * na + sizeof(T) * na + sizeof(int) * na + 15) & ~(size_t)15));
+    const int inst = blockIdx.z;
+    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
+    const int tj = blockIdx.x * JAX, ti = blockIdx.y * JAY;
+    const T xa = (T)tj - cimg, xb = (T)min(tj + JAX - 1, n - 1) - cimg;
+    const T ya = (T)ti - cimg, yb = (T)min(ti + JAY - 1, n - 1) - cimg;
+    for (int a = threadIdx.x; a < na; a += 256) {
+        const JosephAngle<T> J = tab[a];
+        const T tmin = fmin(xa * J.c1, xb * J.c1) + fmin(ya * J.c2, yb * J.c2) + cdet;
+        const int k0 = (int)floor(tmin - J.hw) - 1;
+        sk0[a] = k0;
+        T4 pv;
+        pv.c1 = J.c1;
+        pv.c2 = J.c2;
+        pv.off = cdet - (T)k0;
+        pv.ih = J.inv_hw;
+        sp[a] = pv;
+        sw[a] = J.wgt;
+    }
+    __syncthreads();
+    const T* sg = sino + (int64_t)inst * na * nb;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < na * KB; e += 256) {
+        const int a = e / KB, kk = e - a * KB;
+        const int k = sk0[a] + kk;
+        sbin[e] = (k >= 0 && k < nb) ? sg[(int64_t)a * nb + k] : (T)0;
+    }
+    __syncthreads();
+    const int j = tj + (threadIdx.x & (JAX - 1)), i0 = ti + (threadIdx.x / JAX), i1 = i0 + JAY / 2;
+    // pixels beyond a ragged edge are evaluated at the edge (inside the staged band), not stored
+    const T x = (T)min(j, n - 1) - cimg, y0 = (T)min(i0, n - 1) - cimg, y1 = (T)min(i1, n - 1) - cimg;
+    T acc0 = (T)0, acc1 = (T)0;
+    for (int a = 0; a < na; ++a) {
+        const T4 pv = sp[a];
+        const T wa = sw[a];
+        const T* row = sbin + a * KB;
+        const T ux = fma(x, pv.c1, pv.off);
+        {
+            const T u = fma(y0, pv.c2, ux);  // t - k0
+            const T fu = floor(u);
+            const int q = (int)fu;
+            const T fr = u - fu;
+            const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
+            acc0 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+        }
+        {
+            const T u = fma(y1, pv.c2, ux);
+            const T fu = floor(u);
+            const int q = (int)fu;
+            const T fr = u - fu;
+            const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
+            acc1 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+        }
+    }
+    T ca, cp;
+    if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
+    if (j < n && i0 < n) epi_store<T, EPI>(acc0, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i0 * n + j);
+    if (j < n && i1 < n) epi_store<T, EPI>(acc1, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i1 * n + j);
+}
+
+// Bins a JAX x JAY tile can touch for one angle (two-tap kernel), and whether every half-width
+// is at most one bin.
+static int joseph_tile_bins2(const OpDev& op, bool* two_tap) {
+    const double ds = op.ds;
+    double w = 0.0, hmax = 0.0;
+    for (int a = 0; a < op.na; ++a) {
+        const double th = 3.14159265358979323846 * (double)a / (double)op.na;
+        const double c = std::fabs(std::cos(th)), sn = std::fabs(std::sin(th));
+        const bool rows = (4 * a < op.na) || (4 * a > 3 * op.na);
+        const double hw = (rows ? c : sn) / ds;
+        hmax = std::max(hmax, hw);
+        w = std::max(w, ((JAX - 1) * c + (JAY - 1) * sn) / ds + 2.0 * hw);
+    }
+    *two_tap = hmax <= 1.0;
+    return (int)std::ceil(w) + 4;
+}
+
+// PLSQR_JOSEPH_GENERIC=1: the per-ray global-memory forward kernel (comparisons).
+static bool op_generic_joseph() {
+    static const bool on = [] {
+        const char* e = std::getenv("PLSQR_JOSEPH_GENERIC");
+        return e && e[0] == '1';
+    }();
+    return on;
 }
 
 // Bins a 16 x 16 tile can touch for one angle: 15 (|cos| + |sin|)/ds + 2 hw + 2 of slack, maximised
@@ -631,12 +857,39 @@ static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const 
                 dim3 tg((n + 31) / 32, (n + 31) / 32, B);
                 k_transpose<T><<<tg, 256, 0, s>>>(in, tmp, n);
                 klaunched("k_transpose");
+                // band-staged form: rows of 16-byte multiples, at most JF_RAYS * 256 bins
+                const int QB = std::max(1, std::min(64, (int)(32768 / ((size_t)n * sizeof(T)))));
+                if ((n * sizeof(T)) % 16 == 0 && op.nb <= JF_RAYS * 256 && !op_generic_joseph()) {
+                    const size_t smem = 2 * sizeof(T) * (size_t)QB * (n + 2 * JF_PAD);
+                    auto kfn = k_joseph_fwd_band<T, EPI>;
+                    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (EPI == EPI_FWD && op.na > red.max_blocks)
+                        throw std::runtime_error("joseph_fwd: too many blocks for the reduction scratch");
+                    kfn<<<dim3(op.na, B), 256, smem, s>>>(in, tmp, out, prev, tab, n, op.na, op.nb, (T)op.ds, QB, st,
+                                                          red);
+                    klaunched("k_joseph_fwd_band");
+                    return;
+                }
                 dim3 grid((op.nb + 127) / 128, op.na, B);
                 if (EPI == EPI_FWD && (int64_t)grid.x * grid.y > red.max_blocks)
                     throw std::runtime_error("joseph_fwd: too many blocks for the reduction scratch");
                 k_joseph_fwd<T, EPI><<<grid, 128, 0, s>>>(in, tmp, out, prev, tab, n, op.na, op.nb, (T)op.ds, st, red);
                 klaunched("k_joseph_fwd");
             } else {
+                bool two = false;
+                const int KB2 = joseph_tile_bins2(op, &two);
+                const size_t head2 =
+                    (sizeof(T) * 4 * op.na + sizeof(T) * op.na + sizeof(int) * op.na + 15) & ~(size_t)15;
+                const size_t smem2 = head2 + sizeof(T) * (size_t)op.na * KB2;
+                if (two && smem2 <= 227 * 1024) {
+                    auto kfn = k_joseph_adj2<T, EPI>;
+                    if (smem2 > 48 * 1024)
+                        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+                    dim3 grid((n + JAX - 1) / JAX, (n + JAY - 1) / JAY, B);
+                    kfn<<<grid, 256, smem2, s>>>(in, out, tab, n, op.na, op.nb, KB2, st);
+                    klaunched("k_joseph_adj2");
+                    return;
+                }
                 const int KB = joseph_tile_bins<T>(op);
                 const size_t head = (sizeof(JosephAngle<T>) * op.na + sizeof(int) * op.na + 15) & ~(size_t)15;
                 const size_t smem = head + sizeof(T) * (size_t)op.na * KB;

@@ -88,14 +88,17 @@ def test_masked_blur_3d(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n,na,nb", [(64, 60, 93), (37, 17, 55), (128, 90, 183)])
-def test_joseph(prec, n, na, nb):
+@pytest.mark.parametrize("n,na,nb,ds", [(64, 60, 93, 1.0), (37, 17, 55, 1.0), (128, 90, 183, 1.0),
+                                        (48, 30, 101, 0.7), (50, 45, 121, 0.6)])
+def test_joseph(prec, n, na, nb, ds):
+    """Bin spacing 1 takes the two-tap gather adjoint (every half-width <= one bin); finer bins
+    the general one."""
     rng = np.random.default_rng(3)
     x = rng.uniform(0, 1, (n, n))
     y = rng.standard_normal((na, nb))
     S = _P().Solver((n, n), prec, levels=1)
-    S.set_operator("joseph", n_angles=na, n_bins=nb)
-    op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb)
+    S.set_operator("joseph", n_angles=na, n_bins=nb, bin_spacing=ds)
+    op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb, bin_spacing=ds)
     tol = 1e-11 if prec == "fp64" else 2e-5
     Ax = host(S.apply_A(dev(x, prec)))
     assert rel(Ax, op.A(x)) < tol
