@@ -45,6 +45,10 @@ def lib():
         _lib.oracle_mlsqr.argtypes = [vp, vp, d, i, vp, vp, vp, P(i)]
         _lib.oracle_solve.restype = i
         _lib.oracle_solve.argtypes = [vp, i, d, d, d, i, i, i, i, i, vp, vp, vp, vp, vp]
+        _lib.oracle_mlsqr_s4.restype = i
+        _lib.oracle_mlsqr_s4.argtypes = [vp, vp, d, i, vp, vp, vp, P(i), d]
+        _lib.oracle_solve_stop.restype = i
+        _lib.oracle_solve_stop.argtypes = [vp, i, d, d, d, i, i, i, i, i, d, d, vp, vp, vp, vp, vp, P(i)]
     return _lib
 
 
@@ -223,4 +227,30 @@ def solve(op: Operator, g, reg, T, tau, n_outer, n_inner, levels, nu=2, cycles=1
 
 
 __all__ = ["REG", "OP", "Operator", "Multigrid", "r_of", "kappa_of", "blur_taps",
-           "diffusivity", "apply_M", "mlsqr", "solve", "lib"]
+           "diffusivity", "apply_M", "mlsqr", "solve", "lib", "mlsqr_s4", "solve_stop"]
+
+
+def mlsqr_s4(op: Operator, g, tau, n_inner, eta_delta, prec: Multigrid = None):
+    """Algorithm 2 stopped by S4 (residual estimate <= eta_delta). Returns (f, rbar_hist, status)."""
+    g = _f64(g)
+    f = np.empty(op.shape)
+    hist = np.full(n_inner, np.nan)
+    st = C.c_int(0)
+    it = lib().oracle_mlsqr_s4(C.byref(op.struct()), prec.h if prec is not None else None, float(tau), int(n_inner),
+                               _ptr(g), _ptr(f), _ptr(hist), C.byref(st), float(eta_delta))
+    return f, hist[:it], st.value
+
+
+def solve_stop(op: Operator, g, reg, T, tau, n_outer, n_inner, levels, eta_delta, r_rel, nu=2, cycles=1,
+               kfloor=1e-4):
+    """Algorithm 3 with S4 inner stops and the relative-R outer stop."""
+    g = _f64(g)
+    f = np.empty(op.shape)
+    rbar = np.full((n_outer, n_inner), np.nan)
+    R = np.full(n_outer + 1, np.nan)
+    res = np.full(n_outer, np.nan)
+    done = C.c_int(0)
+    st = lib().oracle_solve_stop(C.byref(op.struct()), REG[reg], float(T), float(tau), float(kfloor), int(levels),
+                                 int(nu), int(cycles), int(n_outer), int(n_inner), float(eta_delta), float(r_rel),
+                                 _ptr(g), _ptr(f), _ptr(rbar), _ptr(R), _ptr(res), C.byref(done))
+    return dict(f=f, rbar_hist=rbar, R_hist=R, resid_hist=res, status=st, outer_done=done.value)

@@ -583,8 +583,24 @@ enum { PREC_MG = 0, PREC_IDENTITY = 1 };
 /* Returns the number of iterations completed; *status = 0 ok, 4 breakdown.
  * rbar_hist[i-1] = ||rbar_i|| = sqrt(phibar_{i+1}^2 + sum psi^2) (the LSQR estimate of
  * the residual of the damped problem, Sec. 3.4). prec = NULL applies P = I. */
+/* Algorithm 2; with eta_delta > 0 it stops after the first iteration i whose residual estimate
+ * ||rbar_i|| = sqrt(phibar_{i+1}^2 + sum psi^2) is <= eta_delta (the discrepancy principle S4,
+ * Sec. 3.4, with eta delta given; at tau = 0 the estimate equals ||g - A f_i||), keeping f_i. */
+static int mlsqr_impl(const op_t* op, void* prec, double tau, int n_inner, const double* g, double* f,
+                      double* rbar_hist, int* status, double eta_delta);
+
 int oracle_mlsqr(const op_t* op, void* prec, double tau, int n_inner, const double* g,
                  double* f, double* rbar_hist, int* status) {
+    return mlsqr_impl(op, prec, tau, n_inner, g, f, rbar_hist, status, 0.0);
+}
+
+int oracle_mlsqr_s4(const op_t* op, void* prec, double tau, int n_inner, const double* g, double* f,
+                    double* rbar_hist, int* status, double eta_delta) {
+    return mlsqr_impl(op, prec, tau, n_inner, g, f, rbar_hist, status, eta_delta);
+}
+
+static int mlsqr_impl(const op_t* op, void* prec, double tau, int n_inner, const double* g, double* f,
+                      double* rbar_hist, int* status, double eta_delta) {
     mg_t* mg = (mg_t*)prec;
     int64_t N = op_unknowns(op), m = oracle_op_data_len(op);
     double* u = (double*)malloc((size_t)m * sizeof(double));
@@ -645,8 +661,10 @@ int oracle_mlsqr(const op_t* op, void* prec, double tau, int n_inner, const doub
             w[i] = v[i] - (theta / rho) * w[i];
         }
         alpha = alpha_new;
-        if (rbar_hist) rbar_hist[it - 1] = sqrt(phibar * phibar + res2);
+        const double rbar = sqrt(phibar * phibar + res2);
+        if (rbar_hist) rbar_hist[it - 1] = rbar;
         done = it;
+        if (eta_delta > 0.0 && rbar <= eta_delta) break; /* S4 */
     }
 out:
     free(u); free(Av); free(p); free(Atu); free(v); free(w);
@@ -661,6 +679,47 @@ out:
  * breakdown stay as given), R_hist (n_outer+1: R(f^0..f^n_outer)), resid_hist (n_outer:
  * ||g - A f^k||). Returns 0, 4 (breakdown in some inner solve; the loop continues with
  * the iterate reached) or 1 (invalid multigrid sizes / factorisation failure). */
+/* Algorithm 3 with its stopping rules (Sec. 4.1): each MLSQR solve stops by S4 with eta_delta
+ * (0: never) within the cap of n_inner iterations, and the fixed point stops at f^j (j >= 2) when
+ * R(f^j) did not decrease by more than the fraction r_rel of R(f^{j-1}) (r_rel <= 0: never).
+ * *outer_done receives the number of MLSQR solves run.  Histories as oracle_solve; entries of
+ * iterations and steps not run stay as given. */
+int oracle_solve_stop(const op_t* op, int reg, double T, double tau, double kfloor, int levels, int nu,
+                      int cycles, int n_outer, int n_inner, double eta_delta, double r_rel, const double* g,
+                      double* f, double* rbar_hist, double* R_hist, double* resid_hist, int* outer_done) {
+    int64_t N = op_unknowns(op), m = oracle_op_data_len(op);
+    double* kappa = (double*)malloc((size_t)N * sizeof(double));
+    double* Af = (double*)malloc((size_t)m * sizeof(double));
+    int ret = 0, k = 1, stopped = 0;
+    double R_prev = 0.0;
+    for (int64_t i = 0; i < N; ++i) f[i] = 0.0;
+    *outer_done = 0;
+    for (; k <= n_outer; ++k) {
+        double R = oracle_diffusivity(op->ndim, op->n, reg, T, kfloor, f, kappa); /* R(f^{k-1}) */
+        if (R_hist) R_hist[k - 1] = R;
+        if (r_rel > 0.0 && k - 1 >= 2 && R_prev > 0.0 && (R - R_prev) / R_prev > -r_rel) { stopped = 1; break; }
+        R_prev = R;
+        void* mg = oracle_mg_create(op->ndim, op->n, kappa, levels, nu, cycles);
+        if (!mg) { ret = 1; break; }
+        int st = 0;
+        mlsqr_impl(op, mg, tau, n_inner, g, f, rbar_hist ? rbar_hist + (int64_t)(k - 1) * n_inner : NULL, &st,
+                   eta_delta);
+        if (st) ret = st;
+        oracle_mg_free(mg);
+        *outer_done = k;
+        if (resid_hist) {
+            oracle_apply_A(op, f, Af);
+            double s = 0.0;
+            for (int64_t i = 0; i < m; ++i) s += (g[i] - Af[i]) * (g[i] - Af[i]);
+            resid_hist[k - 1] = sqrt(s);
+        }
+    }
+    if (R_hist && ret != 1 && !stopped) R_hist[n_outer] = oracle_diffusivity(op->ndim, op->n, reg, T, kfloor, f, kappa);
+    free(kappa);
+    free(Af);
+    return ret;
+}
+
 int oracle_solve(const op_t* op, int reg, double T, double tau, double kfloor, int levels,
                  int nu, int cycles, int n_outer, int n_inner, const double* g, double* f,
                  double* rbar_hist, double* R_hist, double* resid_hist) {
