@@ -185,6 +185,19 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
 
+/* ---- stopping rules --------------------------------------------------------------------------
+ * The paper's stopping logic for later solves, slots and batch instances (Sec. 3.4, Sec. 4.1):
+ *   inner: MLSQR stops after the first iteration i with ||rbar_i|| <= eta * delta (S4, the
+ *     Morozov discrepancy principle; ||rbar_i|| is the LSQR residual estimate, which equals
+ *     ||g - A f_i|| at tau = 0 and bounds it from above for tau > 0), within the cap n_inner;
+ *   outer: Algorithm 3 stops at f^k (k >= 2) when (R(f^k) - R(f^{k-1})) / R(f^{k-1}) > -r_rel
+ *     (R did not decrease by the fraction r_rel), within the cap n_outer.
+ * index: -1 = every instance, else one instance of solve_batch / one slot.  eta * delta = 0 turns
+ * S4 off, r_rel = 0 the outer stop (the defaults).  eta, delta >= 0 and finite; 0 <= r_rel < 1.
+ * The histories of iterations and steps not run stay NaN; f is the iterate where the solve
+ * stopped.  Kernels skip a stopped instance, so a batch finishes when its slowest instance does. */
+int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, double r_rel);
+
 /* ---- slots: continuous batching ---------------------------------------------------------------
  * Algorithm 3 advanced one lagged-diffusivity step at a time (Sec. 4.1: steps 3-5 of one outer
  * iteration), with the handle's max_batch instances used as slots that requests enter and leave

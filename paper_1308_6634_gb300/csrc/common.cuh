@@ -11,7 +11,8 @@
 
 namespace plsqr {
 
-constexpr int ST_IDLE = 7;  // an empty slot of a serving handle: kernels skip the instance
+constexpr int ST_IDLE = 7;       // an empty slot of a serving handle: kernels skip the instance
+constexpr int ST_CONVERGED = 8;  // the fixed point stopped (Algorithm 3 step 5): kernels skip it
 
 
 // Programmatic dependent launch.  A kernel launched with the programmatic-serialization attribute
@@ -58,17 +59,25 @@ struct GkState {
     double c_fwd_a, c_fwd_p, c_adj_a, c_adj_p, c_upd_v;
     double tau, sqrt_tau, T;
     double R;            // R(f) from the last diffusivity pass
+    double eta_delta;    // S4: stop the inner solve once ||rbar_i|| <= eta delta (0: never)
+    double r_rel;        // outer stop: R decreased by less than this fraction (0: never)
     int32_t reg;
-    int32_t status;      // ST_OK or ST_BREAKDOWN for the current inner solve
+    int32_t status;      // ST_OK, ST_BREAKDOWN (current inner solve), ST_IDLE, ST_CONVERGED
     int32_t status_any;  // sticky over the whole solve
     int32_t iter;        // completed inner iterations of the current inner solve
     int32_t outer;       // current outer step (0-based), history row
-    int32_t pad_;
+    int32_t frozen;      // S4: 0 running, 1 met at the last iteration, 2 inner solve finished
 };
+
+// The instance takes no part in the current outer step (empty slot, or converged).
+__device__ __forceinline__ bool parked(const GkState& s) { return s.status == ST_IDLE || s.status == ST_CONVERGED; }
+// The instance takes no part in the remaining inner iterations.
+__device__ __forceinline__ bool inner_off(const GkState& s) { return s.status != ST_OK || s.frozen >= 2; }
 
 // Per-instance solve parameters written by the host before a solve.
 struct SolveParams {
     double T, tau;
+    double eta_delta, r_rel;  // stopping rules (0: off)
     int32_t reg, pad_;
 };
 
@@ -203,10 +212,18 @@ __device__ __forceinline__ void finalize_alpha(GkState& s, double tot, const His
     s.res2 += psi * psi;
     s.cf = phi / rho;
     s.cw = theta / rho;
-    s.iter += 1;
-    if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
-        hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] =
-            sqrt(s.phibar * s.phibar + s.res2);
+    if (s.frozen) {
+        // S4 held after the previous iteration: its update was the last one; this iteration's
+        // is void and the remaining iterations of the inner solve are skipped
+        s.cf = 0.0;
+        s.frozen = 2;
+    } else {
+        s.iter += 1;
+        const double rb = sqrt(s.phibar * s.phibar + s.res2);
+        if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
+            hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] = rb;
+        if (s.eta_delta > 0.0 && rb <= s.eta_delta) s.frozen = 1;  // S4 (Sec. 3.4)
+    }
     s.alpha = an;
     s.beta = beta;
     s.c_upd_v = 1.0 / an;

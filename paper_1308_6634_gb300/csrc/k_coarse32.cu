@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(32) k_ldl_gth_staged(float* __restrict__ gcol_
     __shared__ float sl[BWP + BW];
     __shared__ __align__(8) uint64_t bar;
     const int inst = blockIdx.x, tid = threadIdx.x;
-    if (st[inst].status == ST_IDLE) return;
+    if (parked(st[inst])) return;
     float* gc = gcol_all + (int64_t)inst * nc * BWP;
     float* gr = grow_all + (int64_t)inst * nc * BWP;
     if (tid == 0) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ g
     constexpr int BWP = (BW + 1 + 3) & ~3;
     extern __shared__ __align__(128) float tab[];
     const int inst = blockIdx.y;
-    if (st[inst].status == ST_IDLE) return;
+    if (parked(st[inst])) return;
     const int jb = blockIdx.x * 128;
     const int j = jb + threadIdx.x;
     const int j0 = jb + (threadIdx.x & ~31);

@@ -139,6 +139,9 @@ __global__ void k_set_params(GkState* st, const SolveParams* prm, int B, int res
     s.T = prm[b].T;
     s.tau = prm[b].tau;
     s.sqrt_tau = sqrt(prm[b].tau);
+    s.eta_delta = prm[b].eta_delta;
+    s.r_rel = prm[b].r_rel;
+    s.frozen = 0;
     if (reset_outer) {
         s.outer = 0;
         s.status_any = ST_OK;
@@ -165,6 +168,10 @@ __global__ void k_slots_state(GkState* st, const SolveParams* prm, int B, int sl
     s.T = prm[b].T;
     s.tau = prm[b].tau;
     s.sqrt_tau = sqrt(prm[b].tau);
+    s.eta_delta = prm[b].eta_delta;
+    s.r_rel = prm[b].r_rel;
+    s.frozen = 0;
+    s.R = 0.0;
     s.outer = 0;
     s.status = ST_OK;
     s.status_any = ST_OK;
@@ -188,6 +195,7 @@ void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cu
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_norm(const T* __restrict__ g, int64_t m, GkState* st, Red red) {
     const int inst = blockIdx.y;
+    if (parked(st[inst])) return;
     const T* gi = g + (int64_t)inst * m;
     T part = (T)0;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < m; i += (int64_t)gridDim.x * 256)
@@ -202,6 +210,7 @@ __global__ void __launch_bounds__(256) k_init_norm(const T* __restrict__ g, int6
         s.phibar = b1;
         s.res2 = 0.0;
         s.iter = 0;
+        s.frozen = 0;
         s.cf = 0.0;
         s.cw = 0.0;
         if (!(isfinite(b1) && b1 > 0.0)) {
@@ -228,7 +237,7 @@ template <typename T, bool INIT>
 __global__ void __launch_bounds__(256) k_dot_rotate(const T* __restrict__ v, const T* __restrict__ p, int64_t N,
                                                     GkState* st, Hist hist, Red red) {
     const int inst = blockIdx.y;
-    if (st[inst].status != ST_OK) return;
+    if (inner_off(st[inst])) return;
     const T* vi = v + (int64_t)inst * N;
     const T* pi = p + (int64_t)inst * N;
     T part = (T)0;
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(256) k_update(T* __restrict__ f, T* __restrict
                                                 int64_t N, const GkState* st) {
     const int inst = blockIdx.y;
     const GkState& s = st[inst];
-    if (!INIT && s.status != ST_OK) return;
+    if (parked(s) || (!INIT && inner_off(s))) return;
     const T cv = (T)s.c_upd_v, cf = (T)s.cf, cw = (T)s.cw;
     const int64_t off = (int64_t)inst * N;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
@@ -287,7 +296,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ g, const T* __restrict__ Af, int64_t m,
                                                     GkState* st, Hist hist, Red red) {
     const int inst = blockIdx.y;
-    if (st[inst].status == ST_IDLE) return;
+    if (parked(st[inst])) return;
     const T* gi = g + (int64_t)inst * m;
     const T* ai = Af + (int64_t)inst * m;
     T part = (T)0;

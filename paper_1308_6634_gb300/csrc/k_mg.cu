@@ -48,7 +48,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T* __restrict__ kappa, Dims d,
                                                      GkState* st, Hist hist, double kfloor, Red red) {
     const int inst = blockIdx.y;
-    if (st[inst].status == ST_IDLE) return;
+    if (parked(st[inst])) return;
     const int reg = st[inst].reg;
     const T Tp = (T)st[inst].T;
     const T kmin = (T)kfloor * kappa_of<T>(reg, Tp, (T)0);
@@ -77,8 +77,12 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T*
     double tot;
     if (reduce_last<256>(part, red, inst, blockIdx.x, gridDim.x, &tot)) {
         GkState& s = st[inst];
+        const double R_prev = s.R;
         s.R = tot;
         if (hist.R) hist.R[(int64_t)inst * (hist.n_outer + 1) + s.outer] = tot;
+        // Algorithm 3 step 5: stop at f^k (k >= 2) when R(f^k) fell by less than r_rel R(f^{k-1})
+        if (s.r_rel > 0.0 && s.outer >= 2 && R_prev > 0.0 && (tot - R_prev) / R_prev > -s.r_rel)
+            s.status = ST_CONVERGED;
     }
 }
 
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all
     T* sb = reinterpret_cast<T*>(smraw);
     pdl_grid_sync();
     const int inst = blockIdx.y;
-    if (st && st[inst].status == ST_IDLE) return;
+    if (st && (parked(st[inst]) || st[inst].frozen >= 2)) return;
     const T* b = b_all + (int64_t)inst * nc;
     for (int i = threadIdx.x; i < nc; i += 256) sb[i] = b[i];
     __syncthreads();

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps m
                                                   Dims d, Dims dc, GkState* st) {
     extern __shared__ __align__(128) unsigned char smraw[];
     pdl_grid_sync();
-    if (st[blockIdx.z].status == ST_IDLE) return;
+    if (parked(st[blockIdx.z]) || st[blockIdx.z].frozen >= 2) return;
     pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY);
 }
 
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(NTH) k_mg_post2d(const __grid_constant__ Maps 
     extern __shared__ __align__(128) unsigned char smraw[];
     const int inst = blockIdx.z;
     pdl_grid_sync();
-    if (DOT ? st[inst].status != ST_OK : st[inst].status == ST_IDLE) return;
+    if (DOT ? inner_off(st[inst]) : (parked(st[inst]) || st[inst].frozen >= 2)) return;
     const T part = post_tile<T, L0, NU, DOT, TMA, NTH>(smraw, maps, cond, b, x_in, x_out, xc, d, dc, st, inst,
                                                  blockIdx.x * MTX, blockIdx.y * MTY);
     if (DOT) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
     const int inst = blockIdx.y, rank = blockIdx.x;
     const int nl = tl.n;
     pdl_grid_sync();
-    if (st[inst].status != ST_OK) return;  // the same answer in every block of the cluster
+    if (inner_off(st[inst])) return;  // the same answer in every block of the cluster
     for (int q = 0; q < nl - 1; ++q) {
         const Dims d = tl.d[q], dc = tl.d[q + 1];
         const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);

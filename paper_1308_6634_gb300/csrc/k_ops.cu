@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d(const T* __restrict__ in, T* out
     extern __shared__ __align__(16) unsigned char smraw[];
     const int plane = blockIdx.z;  // z + nz * inst
     const int inst = plane / d.nz;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const int tid = threadIdx.x;
     const int nwx = 2 * Rx + 1, nwy = 2 * Ry + 1;
     const int LX = BTX + 2 * Rx, LY = BTY + 2 * Ry;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     pdl_grid_sync();
     const int plane = blockIdx.z;
     const int inst = plane / d.nz;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const int tid = threadIdx.x;
     if (PI)  // made visible by the barrier that follows the tile staging
         for (int k = tid; k < 2 * (2 * R + 1); k += BNT) stap[k] = tapt[(int64_t)inst * 2 * (2 * R + 1) + k];
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_blur_z(const T* __restrict__ in, T* out
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nzt = (d.nz + ZTZ - 1) / ZTZ;
     const int inst = blockIdx.z / nzt, zt = blockIdx.z - inst * nzt;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int nw = 2 * Rz + 1, LZ = ZTZ + 2 * Rz;
     T* sw = reinterpret_cast<T*>(smraw);
@@ -343,7 +343,7 @@ template <typename T, int EPI>
 __global__ void __launch_bounds__(256) k_identity(const T* __restrict__ in, T* out, const T* prev, int64_t n,
                                                   GkState* st, Red red) {
     const int inst = blockIdx.y;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     T ca, cp;
     if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
     T part = (T)0;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, c
                                                     const T* prev, const JosephAngle<T>* __restrict__ tab, int n,
                                                     int na, int nb, T ds, GkState* st, Red red) {
     const int inst = blockIdx.z, a = blockIdx.y, k = blockIdx.x * 128 + threadIdx.x;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const JosephAngle<T> J = tab[a];
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
     const T* im = (J.rows ? img : imgT) + (int64_t)inst * n * n;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(256) k_joseph_fwd_band(const T* __restrict__ i
     T* sbuf = reinterpret_cast<T*>(smraw);  // two bands of QB x pitch
     const int pitch = n + 2 * JF_PAD;
     const int inst = blockIdx.y, a = blockIdx.x;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const JosephAngle<T> J = tab[a];
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
     const T* im = (J.rows ? img : imgT) + (int64_t)inst * n * n;
@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, 
     int* sk0 = reinterpret_cast<int*>(stab + na);
     T* sbin = reinterpret_cast<T*>(smraw + ((sizeof(JosephAngle<T>) * na + sizeof(int) * na + 15) & ~(size_t)15));
     const int inst = blockIdx.z;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
     const int tj = blockIdx.x * 16, ti = blockIdx.y * 16;
     const T xa = (T)tj - cimg, xb = (T)min(tj + 15, n - 1) - cimg;
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino,
     int* sk0 = reinterpret_cast<int*>(sw + na);
     T* sbin = reinterpret_cast<T*>(smraw + ((sizeof(T4) * na + sizeof(T) * na + sizeof(int) * na + 15) & ~(size_t)15));
     const int inst = blockIdx.z;
-    if (EPI != EPI_PLAIN && st[inst].status != ST_OK) return;
+    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
     const int tj = blockIdx.x * JAX, ti = blockIdx.y * JAY;
     const T xa = (T)tj - cimg, xb = (T)min(tj + JAX - 1, n - 1) - cimg;

@@ -723,6 +723,7 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         ck(cudaMemset(h->st, 0, sizeof(GkState) * B), "memset");
         h->prm_dev = (SolveParams*)dalloc(h, sizeof(SolveParams) * B);
         ck(cudaMallocHost((void**)&h->prm_host, sizeof(SolveParams) * B), "cudaMallocHost");
+        std::memset(h->prm_host, 0, sizeof(SolveParams) * B);  // stopping rules off
         ck(cudaMallocHost((void**)&h->st_host, sizeof(GkState) * B), "cudaMallocHost");
         h->red.max_blocks = 8192;
         h->red.partials = (double*)dalloc(h, sizeof(double) * B * h->red.max_blocks);
@@ -843,6 +844,23 @@ int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const
             rc = solve_impl<TT>(h, count, g, false, reg, T, tau, n_outer, n_inner, f_out, false, stats);
         });
         return rc;
+    });
+}
+
+// ---- stopping rules ----------------------------------------------------------------------------
+
+int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, double r_rel) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (index < -1 || index >= h->B) throw InvalidArg("index must be -1 (all) or an instance in 0..max_batch-1");
+        if (!(eta >= 0.0) || !std::isfinite(eta) || !(delta >= 0.0) || !std::isfinite(delta))
+            throw InvalidArg("eta and delta must be finite and >= 0");
+        if (!(r_rel >= 0.0) || !(r_rel < 1.0)) throw InvalidArg("r_rel must be in [0, 1)");
+        for (int b = (index < 0 ? 0 : index); b < (index < 0 ? h->B : index + 1); ++b) {
+            h->prm_host[b].eta_delta = eta * delta;
+            h->prm_host[b].r_rel = r_rel;
+        }
+        return PLSQR_OK;
     });
 }
 
