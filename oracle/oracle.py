@@ -45,6 +45,10 @@ def lib():
         _lib.oracle_mlsqr.argtypes = [vp, vp, d, i, vp, vp, vp, P(i)]
         _lib.oracle_solve.restype = i
         _lib.oracle_solve.argtypes = [vp, i, d, d, d, i, i, i, i, i, vp, vp, vp, vp, vp]
+        _lib.oracle_set_kappa_rounding.argtypes = [i]
+        _lib.oracle_set_kappa_rounding.restype = None
+        _lib.oracle_round_bf16.argtypes = [d]
+        _lib.oracle_round_bf16.restype = d
         _lib.oracle_mlsqr_s4.restype = i
         _lib.oracle_mlsqr_s4.argtypes = [vp, vp, d, i, vp, vp, vp, P(i), d]
         _lib.oracle_solve_stop.restype = i
@@ -227,7 +231,7 @@ def solve(op: Operator, g, reg, T, tau, n_outer, n_inner, levels, nu=2, cycles=1
 
 
 __all__ = ["REG", "OP", "Operator", "Multigrid", "r_of", "kappa_of", "blur_taps",
-           "diffusivity", "apply_M", "mlsqr", "solve", "lib", "mlsqr_s4", "solve_stop"]
+           "diffusivity", "apply_M", "mlsqr", "solve", "lib", "mlsqr_s4", "solve_stop", "set_kappa_rounding", "round_bf16"]
 
 
 def mlsqr_s4(op: Operator, g, tau, n_inner, eta_delta, prec: Multigrid = None):
@@ -254,3 +258,13 @@ def solve_stop(op: Operator, g, reg, T, tau, n_outer, n_inner, levels, eta_delta
                                  int(nu), int(cycles), int(n_outer), int(n_inner), float(eta_delta), float(r_rel),
                                  _ptr(g), _ptr(f), _ptr(rbar), _ptr(R), _ptr(res), C.byref(done))
     return dict(f=f, rbar_hist=rbar, R_hist=R, resid_hist=res, status=st, outer_done=done.value)
+
+
+def set_kappa_rounding(mode):
+    """None: kappa as computed; "bf16": kappa rounded to float then bfloat16 (nearest, ties to
+    even) where the diffusivity stores it, as the GPU's bfloat16-kappa variant does."""
+    lib().oracle_set_kappa_rounding({None: 0, "bf16": 1}[mode])
+
+
+def round_bf16(x):
+    return lib().oracle_round_bf16(float(x))

@@ -110,6 +110,25 @@ static double fwd_diff(const grid_t* G, const double* f, int64_t idx, const int6
 
 /* Diffusivity (Algorithm 3 step 3, eqs. 1.12-1.13): t_i = |(D f)_i|, kappa_i =
  * max(kappa(t_i), kfloor*kappa(0)); returns R(f) = sum_i r(t_i) (discrete eq. 1.2). */
+/* Storage rounding of kappa, for the variant that keeps kappa in bfloat16: 0 none; 1 the value
+ * rounded to single precision and then to bfloat16 (8 significant bits), both to nearest with
+ * ties to even.  The second rounding is the usual bit form: add 0x7fff plus the lowest kept bit
+ * to the single-precision pattern and clear the 16 low bits. */
+static int kappa_rounding = 0;
+
+void oracle_set_kappa_rounding(int mode) { kappa_rounding = mode; }
+
+double oracle_round_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf, nan */
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
 double oracle_diffusivity(int ndim, const int64_t* n, int reg, double T, double kfloor,
                           const double* f, double* kappa) {
     grid_t G = {ndim, {n[0], ndim > 1 ? n[1] : 1, ndim > 2 ? n[2] : 1}};
@@ -126,7 +145,8 @@ double oracle_diffusivity(int ndim, const int64_t* n, int reg, double T, double 
         }
         double t = sqrt(t2);
         double k = oracle_kappa_of(reg, T, t);
-        kappa[idx] = k > kmin ? k : kmin;
+        k = k > kmin ? k : kmin;
+        kappa[idx] = kappa_rounding == 1 ? oracle_round_bf16(k) : k;
         R += oracle_r_of(reg, T, t);
     }
     return R;
