@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-fp64-single", action="store_true")
+    ap.add_argument("--kappa-bf16", action="store_true", help="keep kappa in bfloat16 (2D single precision)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="serving: device-memory budget")
@@ -300,6 +301,8 @@ def main():
     seeds = [rank * B + b for b in range(B)]
     mask = W.inputs(seeds[0])[1]
     S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles, n_bins=W.n_bins)
+    if args.kappa_bf16:
+        S.set_kappa_bf16(True)
     gs = make_inputs(W, S, seeds, torch, dev)
     fs = [torch.empty(W.shape, dtype=S.dtype, device=dev) for _ in range(B)]
     regs, Ts, taus = [W.reg] * B, [W.T] * B, [W.tau] * B
@@ -410,6 +413,8 @@ def main():
         S1 = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles)
         S1.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=cb["mask"], n_angles=W.n_angles,
                         n_bins=W.n_bins)
+        if args.kappa_bf16:
+            S1.set_kappa_bf16(True)
         _, inf1 = S1.solve(torch.as_tensor(cb["g"], dtype=S1.dtype, device=dev), W.reg, W.T, W.tau, 1, cb["i2"])
         got = inf1["rbar_hist"][0]
         acc = {"rbar_first_iters_rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
@@ -426,6 +431,7 @@ def main():
             "config": {"workload": W.name, "shape": list(W.shape), "operator": W.kind, "n_outer": W.n_outer,
                        "n_inner": W.n_inner, "reg": W.reg, "T": W.T, "tau": W.tau, "levels": W.levels,
                        "sweeps": W.nu, "cycles": W.cycles, "batch": B, "parallelism": f"replicas x{world}",
+                       "kappa": "bf16" if args.kappa_bf16 else W.precision,
                        "l2": "flushed between steps" if flush is not None else "working set larger than L2"},
             "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
             "gpu_launches": int(launches_per_step * args.steps),

@@ -185,6 +185,15 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
 
+/* ---- bfloat16 kappa ----------------------------------------------------------------------------
+ * on != 0: later solves keep the diffusivity kappa (eq. 1.13) only in bfloat16 (8 significant bits,
+ * rounded to nearest even from the single-precision value); the finest level of the V-cycle and
+ * the first coarsening read it and widen it to float.  Everything else is unchanged, so P is the
+ * V-cycle of the rounded kappa.  Needs a 2D PLSQR_FP32 handle with mg_levels >= 2 and 1..3
+ * sweeps; otherwise PLSQR_E_INVALID.  plsqr_prec_setup rounds the kappa it is given.  on = 0
+ * returns to float kappa (the default). */
+int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on);
+
 /* ---- stopping rules --------------------------------------------------------------------------
  * The paper's stopping logic for later solves, slots and batch instances (Sec. 3.4, Sec. 4.1):
  *   inner: MLSQR stops after the first iteration i with ||rbar_i|| <= eta * delta (S4, the

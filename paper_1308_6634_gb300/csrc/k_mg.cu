@@ -46,7 +46,8 @@ __device__ __forceinline__ T r_of(int reg, T Tp, T t) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T* __restrict__ kappa, Dims d,
-                                                     GkState* st, Hist hist, double kfloor, Red red) {
+                                                     GkState* st, Hist hist, double kfloor, Red red,
+                                                     __nv_bfloat16* __restrict__ k16) {
     const int inst = blockIdx.y;
     if (parked(st[inst])) return;
     const int reg = st[inst].reg;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T*
     const T kmin = (T)kfloor * kappa_of<T>(reg, Tp, (T)0);
     const T* fi = f + (int64_t)inst * d.N;
     T* ki = kappa + (int64_t)inst * d.N;
+    __nv_bfloat16* k16i = k16 ? k16 + (int64_t)inst * d.N : nullptr;
     double part = 0.0;
     const int64_t plane = (int64_t)d.nx * d.ny;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * 256) {
@@ -71,7 +73,9 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T*
         }
         const T t = sqrt(t2);
         const T k = kappa_of<T>(reg, Tp, t);
-        ki[i] = k > kmin ? k : kmin;
+        const T kc = k > kmin ? k : kmin;
+        if (k16i) k16i[i] = __float2bfloat16_rn((float)kc);  // bfloat16 storage: the only copy
+        else ki[i] = kc;
         part += (double)r_of<T>(reg, Tp, t);
     }
     double tot;
@@ -88,10 +92,10 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T*
 
 template <typename T>
 void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, double kfloor, Red red,
-                 cudaStream_t s) {
+                 cudaStream_t s, __nv_bfloat16* k16) {
     kbegin(KC_SETUP, s);
     int nblk = std::min(red_blocks(d.N), red.max_blocks);
-    k_diffusivity<T><<<dim3(nblk, B), 256, 0, s>>>(f, kappa, d, st, hist, kfloor, red);
+    k_diffusivity<T><<<dim3(nblk, B), 256, 0, s>>>(f, kappa, d, st, hist, kfloor, red, k16);
     klaunched("k_diffusivity");
     kfinish(s);
 }
@@ -271,7 +275,8 @@ void mg_axpy(T* y, const T* x, int64_t n, cudaStream_t s) {
 // Galerkin coarsening: c_{l+1,d}(I) = sum of c_{l,d}(i) over the fine cells i of coarse
 // cell I with i_d = 2 I_d + 1 (their edge i -> i+e_d crosses the high face of I).
 template <typename T, bool KAPPA>
-__global__ void __launch_bounds__(256) k_coarsen(const T* __restrict__ cf, T* __restrict__ cc, Dims df, Dims dc) {
+__global__ void __launch_bounds__(256) k_coarsen(const T* __restrict__ cf, T* __restrict__ cc, Dims df, Dims dc,
+                                                 const __nv_bfloat16* __restrict__ k16) {
     const int inst = blockIdx.y;
     const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (I >= dc.N) return;
@@ -286,18 +291,22 @@ __global__ void __launch_bounds__(256) k_coarsen(const T* __restrict__ cf, T* __
         T s = (T)0;
         for (int fz = zlo; fz <= zhi; ++fz)
             for (int fy = ylo; fy <= yhi; ++fy)
-                for (int fx = xlo; fx <= xhi; ++fx)
-                    s += cond_at<T, KAPPA>(c, dd, df.N, fx + (int64_t)df.nx * (fy + (int64_t)df.ny * fz));
+                for (int fx = xlo; fx <= xhi; ++fx) {
+                    const int64_t i = fx + (int64_t)df.nx * (fy + (int64_t)df.ny * fz);
+                    s += (KAPPA && k16) ? (T)__bfloat162float(k16[(int64_t)inst * df.N + i])
+                                        : cond_at<T, KAPPA>(c, dd, df.N, i);
+                }
         o[(int64_t)dd * dc.N + I] = s;
     }
 }
 
 template <typename T>
-void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s) {
+void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s,
+                const __nv_bfloat16* k16) {
     kbegin(KC_SETUP, s);
     dim3 grid((unsigned)((dc.N + 255) / 256), B);
-    if (fine_is_kappa) k_coarsen<T, true><<<grid, 256, 0, s>>>(cf, cc, df, dc);
-    else k_coarsen<T, false><<<grid, 256, 0, s>>>(cf, cc, df, dc);
+    if (fine_is_kappa) k_coarsen<T, true><<<grid, 256, 0, s>>>(cf, cc, df, dc, k16);
+    else k_coarsen<T, false><<<grid, 256, 0, s>>>(cf, cc, df, dc, nullptr);
     klaunched("k_coarsen");
     kfinish(s);
 }
@@ -644,6 +653,18 @@ __global__ void k_round_to_float(const double* __restrict__ a, float* __restrict
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) b[i] = (float)a[i];
 }
 
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+void to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s) {
+    kbegin(KC_SETUP, s);
+    k_to_bf16<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(a, b, n);
+    klaunched("k_to_bf16");
+    kfinish(s);
+}
+
 void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
     kbegin(KC_SETUP, s);
     k_round_to_float<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(a, b, n);
@@ -652,8 +673,9 @@ void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
 }
 
 #define PLSQR_INST_MG(T)                                                                                  \
-    template void diffusivity<T>(const T*, T*, Dims, int, GkState*, Hist, double, Red, cudaStream_t);     \
-    template void mg_coarsen<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t);                        \
+    template void diffusivity<T>(const T*, T*, Dims, int, GkState*, Hist, double, Red, cudaStream_t,         \
+                                 __nv_bfloat16*);                                                         \
+    template void mg_coarsen<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t, const __nv_bfloat16*);  \
     template void mg_gs_half<T>(const T*, bool, const T*, T*, Dims, int, bool, int, cudaStream_t);         \
     template void mg_resid_restrict<T>(const T*, bool, const T*, const T*, T*, Dims, Dims, int,            \
                                        cudaStream_t);                                                     \

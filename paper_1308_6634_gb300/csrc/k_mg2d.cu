@@ -54,11 +54,12 @@ struct Maps {
     CUtensorMap b, c, x;
 };
 
-// Stage b and the conductances (and x_in when X_IN) of the tile.
+// Stage b and the conductances (and x_in when X_IN) of the tile.  k16 (finest level only, may be
+// null): kappa stored in bfloat16, read with plain loads and widened in shared memory.
 template <typename T, bool L0, int H, bool TMA, bool X_IN, int NTH>
 __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restrict__ cond, const T* __restrict__ b,
                                       const T* __restrict__ x_in, const Dims& d, int inst, int x0, int y0,
-                                      GkState* st) {
+                                      GkState* st, const __nv_bfloat16* __restrict__ k16 = nullptr) {
     using TL = Tile<T, L0, H>;
     T* sb = sm;
     T* sc = sm + TL::OFF_C;
@@ -67,13 +68,24 @@ __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restri
         uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::OFF_BAR);
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
+        const bool kb = L0 && k16;
         if (threadIdx.x == 0) {
             const uint32_t plane = TL::NCS * sizeof(T);
-            mbar_expect_tx(bar, plane * (1 + TL::CPLANES + (X_IN ? 1 : 0)));
+            mbar_expect_tx(bar, plane * (1 + (kb ? 0 : TL::CPLANES) + (X_IN ? 1 : 0)));
             const int gx = x0 - TL::HX, gy = y0 - H;
             tma_load_3d(sb, &maps.b, bar, gx, gy, inst);
-            tma_load_3d(sc, &maps.c, bar, gx, gy, L0 ? inst : 2 * inst);
+            if (!kb) tma_load_3d(sc, &maps.c, bar, gx, gy, L0 ? inst : 2 * inst);
             if (X_IN) tma_load_3d(sx, &maps.x, bar, gx, gy, inst);
+        }
+        if (kb) {  // meanwhile, kappa from bfloat16 (zero outside the domain, like the TMA fill)
+            const __nv_bfloat16* k = k16 + (int64_t)inst * d.N;
+            for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
+                const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
+                const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
+                sc[i] = (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
+                            ? (T)__bfloat162float(k[(int64_t)gy * d.nx + gx])
+                            : (T)0;
+            }
         }
         tma_wait_tile(bar, st, inst);
         __syncthreads();
@@ -88,7 +100,7 @@ __device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restri
             if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
                 const int64_t g = (int64_t)gy * d.nx + gx;
                 vb = b[off + g];
-                vx = c[g];
+                vx = (L0 && k16) ? (T)__bfloat162float(k16[off + g]) : c[g];
                 if (!L0) vy = c[d.N + g];
                 if (X_IN) vv = x_in[off + g];
             }
@@ -155,7 +167,7 @@ __device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* sc
 template <typename T, bool L0, int NU, bool TMA, int NTH>
 __device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b, T* x,
                                          T* bc, const Dims& d, const Dims& dc, GkState* st, int inst, int x0,
-                                         int y0) {
+                                         int y0, const __nv_bfloat16* k16 = nullptr) {
     constexpr int H = 2 * NU + 1;
     using TL = Tile<T, L0, H>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
@@ -166,7 +178,7 @@ __device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps,
     T* sx = sm + TL::OFF_X;
     const T* sd = sm + TL::OFF_D;
     for (int i = threadIdx.x; i < TL::NCS; i += NTH) sx[i] = (T)0;
-    stage<T, L0, H, TMA, false, NTH>(sm, maps, cond, b, nullptr, d, inst, x0, y0, st);
+    stage<T, L0, H, TMA, false, NTH>(sm, maps, cond, b, nullptr, d, inst, x0, y0, st, k16);
     diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
     __syncthreads();
 #pragma unroll
@@ -210,11 +222,12 @@ __device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps,
 template <typename T, bool L0, int NU, bool TMA, int NTH>
 __global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
                                                   const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
-                                                  Dims d, Dims dc, GkState* st) {
+                                                  Dims d, Dims dc, GkState* st, const __nv_bfloat16* __restrict__ k16) {
     extern __shared__ __align__(128) unsigned char smraw[];
     pdl_grid_sync();
     if (parked(st[blockIdx.z]) || st[blockIdx.z].frozen >= 2) return;
-    pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY);
+    pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY,
+                                  k16);
 }
 
 // One tile of x_out = smooth(x_in + P xc) with nu black->red sweeps (x_in and x_out must differ:
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps m
 template <typename T, bool L0, int NU, bool DOT, bool TMA, int NTH>
 __device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
                                        const T* x_in, T* x_out, const T* xc, const Dims& d, const Dims& dc,
-                                       GkState* st, int inst, int x0, int y0) {
+                                       GkState* st, int inst, int x0, int y0, const __nv_bfloat16* k16 = nullptr) {
     constexpr int H = 2 * NU;
     using TL = Tile<T, L0, H>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
@@ -247,7 +260,7 @@ __device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, c
                      ? xc[offc + (int64_t)(gy >> 1) * dc.nx + (gx >> 1)]
                      : (T)0;
     }
-    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st);
+    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st, k16);
     diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {  // + P xc (cells outside the domain add 0 and stay 0)
@@ -281,13 +294,14 @@ template <typename T, bool L0, int NU, bool DOT, bool INIT, bool TMA, int NTH>
 __global__ void __launch_bounds__(NTH) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
                                                    const T* __restrict__ b, const T* __restrict__ x_in,
                                                    T* __restrict__ x_out, const T* __restrict__ xc, Dims d, Dims dc,
-                                                   GkState* st, Hist hist, Red red) {
+                                                   GkState* st, Hist hist, Red red,
+                                                   const __nv_bfloat16* __restrict__ k16) {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int inst = blockIdx.z;
     pdl_grid_sync();
     if (DOT ? inner_off(st[inst]) : (parked(st[inst]) || st[inst].frozen >= 2)) return;
     const T part = post_tile<T, L0, NU, DOT, TMA, NTH>(smraw, maps, cond, b, x_in, x_out, xc, d, dc, st, inst,
-                                                 blockIdx.x * MTX, blockIdx.y * MTY);
+                                                 blockIdx.x * MTX, blockIdx.y * MTY, k16);
     if (DOT) {
         const int nblk = gridDim.x * gridDim.y;
         double tot;
@@ -372,7 +386,8 @@ static bool make_maps(Maps& m, const T* cond, const T* b, const T* x_in, const D
 }
 
 template <typename T, bool L0, int NU>
-static void pre_launch(const T* cond, const T* b, T* x, T* bc, Dims d, Dims dc, int B, GkState* st, cudaStream_t s) {
+static void pre_launch(const T* cond, const T* b, T* x, T* bc, Dims d, Dims dc, int B, GkState* st, cudaStream_t s,
+                       const __nv_bfloat16* k16) {
     constexpr int H = 2 * NU + 1;
     const size_t smem = Tile<T, L0, H>::bytes();
     Maps maps;
@@ -381,12 +396,12 @@ static void pre_launch(const T* cond, const T* b, T* x, T* bc, Dims d, Dims dc, 
     auto kfn = tma ? k_mg_pre2d<T, L0, NU, true, NTH> : k_mg_pre2d<T, L0, NU, false, NTH>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
-    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, x, bc, d, dc, st);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, x, bc, d, dc, st, k16);
 }
 
 template <typename T, bool L0, int NU, bool DOT, bool INIT>
 static void post_launch(const T* cond, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int B,
-                        GkState* st, Hist hist, Red red, cudaStream_t s) {
+                        GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16) {
     constexpr int H = 2 * NU;
     const size_t smem = Tile<T, L0, H>::bytes();
     Maps maps;
@@ -397,7 +412,7 @@ static void post_launch(const T* cond, const T* b, const T* xi, T* x, const T* x
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
     if (DOT && (int64_t)grid.x * grid.y > red.max_blocks)
         throw std::runtime_error("mg_post2d: too many blocks for the reduction scratch");
-    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, xi, x, xc, d, dc, st, hist, red);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, xi, x, xc, d, dc, st, hist, red, k16);
 }
 
 bool mg2d_supported(int ndim, int nu) { return ndim == 2 && nu >= 1 && nu <= 3; }
@@ -518,12 +533,12 @@ template void mg2d_tail<double>(const TailLevels&, int, const double*, int, int,
 
 template <typename T>
 void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,
-              cudaStream_t s) {
+              cudaStream_t s, const __nv_bfloat16* k16) {
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
 #define PRE_CASE(NU_)                                                                   \
     case NU_:                                                                           \
-        if (is_kappa) pre_launch<T, true, NU_>(cond, b, x, bc, d, dc, B, st, s);       \
-        else pre_launch<T, false, NU_>(cond, b, x, bc, d, dc, B, st, s);               \
+        if (is_kappa) pre_launch<T, true, NU_>(cond, b, x, bc, d, dc, B, st, s, k16);  \
+        else pre_launch<T, false, NU_>(cond, b, x, bc, d, dc, B, st, s, nullptr);      \
         break;
     switch (nu) {
         PRE_CASE(1)
@@ -538,14 +553,14 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dim
 
 template <typename T>
 void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int nu,
-               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s) {
+               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16) {
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
 #define POST_CASE(NU_)                                                                                           \
     case NU_:                                                                                                    \
-        if (!is_kappa) post_launch<T, false, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s); \
-        else if (dot == 0) post_launch<T, true, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s); \
-        else if (dot == 1) post_launch<T, true, NU_, true, true>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s); \
-        else post_launch<T, true, NU_, true, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s);             \
+        if (!is_kappa) post_launch<T, false, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, nullptr); \
+        else if (dot == 0) post_launch<T, true, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
+        else if (dot == 1) post_launch<T, true, NU_, true, true>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
+        else post_launch<T, true, NU_, true, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16);             \
         break;
     switch (nu) {
         POST_CASE(1)
@@ -559,12 +574,12 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, cons
 }
 
 template void mg2d_pre<float>(const float*, bool, const float*, float*, float*, Dims, Dims, int, int, GkState*,
-                              cudaStream_t);
+                              cudaStream_t, const __nv_bfloat16*);
 template void mg2d_pre<double>(const double*, bool, const double*, double*, double*, Dims, Dims, int, int, GkState*,
-                               cudaStream_t);
+                               cudaStream_t, const __nv_bfloat16*);
 template void mg2d_post<float>(const float*, bool, const float*, const float*, float*, const float*, Dims, Dims, int,
-                               int, int, GkState*, Hist, Red, cudaStream_t);
+                               int, int, GkState*, Hist, Red, cudaStream_t, const __nv_bfloat16*);
 template void mg2d_post<double>(const double*, bool, const double*, const double*, double*, const double*, Dims, Dims,
-                                int, int, int, GkState*, Hist, Red, cudaStream_t);
+                                int, int, int, GkState*, Hist, Red, cudaStream_t, const __nv_bfloat16*);
 
 }  // namespace plsqr

@@ -2,6 +2,8 @@
 #pragma once
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <stdexcept>
 #include <string>
 
@@ -78,11 +80,14 @@ bool op_fwd_update(const OpDev& op, const float* v, float* u, float* f, float* w
 // kappa = max(r'(t)/t, kfloor*kappa(0)), R = sum r(t) per instance (state reg/T).
 template <typename T>
 void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, double kfloor, Red red,
-                 cudaStream_t s);
+                 cudaStream_t s, __nv_bfloat16* k16 = nullptr);
 
 // ---- multigrid ----
 template <typename T>
-void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s);
+void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s,
+                const __nv_bfloat16* k16 = nullptr);
+// kappa widened to bfloat16 storage (round to nearest even)
+void to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
 template <typename T>
 void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colour, bool zero_init, int B,
                 cudaStream_t s);
@@ -121,11 +126,11 @@ void mg2d_tail(const TailLevels& tl, int nu, const T* X, int nc, int B, GkState*
 // x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x)
 template <typename T>
 void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,
-              cudaStream_t s);
+              cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
 // x = nu black->red sweeps from xi + P xc.  dot: 0 none, 1 alpha_1 (init), 2 alpha and rotations
 template <typename T>
 void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int nu,
-               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s);
+               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
 
 // ---- Golub-Kahan scalars and updates ----
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);

@@ -104,6 +104,9 @@ struct plsqr_ctx {
     std::vector<int> slot_active, slot_outer, slot_target;
     float* taps_inst = nullptr;       // device [B][2][2R+1]
     float* taps_inst_host = nullptr;  // pinned staging, same shape
+    // kappa stored in bfloat16 (the diffusivity's only output; the finest-level V-cycle widens it)
+    bool kbf16 = false;
+    __nv_bfloat16* kappa16 = nullptr;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
     TailLevels tail{};
@@ -119,6 +122,8 @@ namespace {
 
 template <typename T>
 T* P(char* p) { return reinterpret_cast<T*>(p); }
+
+__nv_bfloat16* K16(plsqr_ctx* h) { return h->kbf16 ? h->kappa16 : nullptr; }
 
 char* dalloc(plsqr_ctx* h, size_t bytes) {
     void* p = nullptr;
@@ -298,9 +303,10 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
     const bool isk = l == 0;
     T* xpre = l == 0 ? P<T>(h->tmp) : P<T>(Lv.x);
     const Level& C = h->lv[l + 1];
-    mg2d_pre<T>(cond, isk, b, xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s);
+    mg2d_pre<T>(cond, isk, b, xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s, isk ? K16(h) : nullptr);
     vcycle_fused<T>(h, l + 1, P<T>(C.b), P<T>(C.x2), B, 0, s);
-    mg2d_post<T>(cond, isk, b, xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s);
+    mg2d_post<T>(cond, isk, b, xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s,
+                 isk ? K16(h) : nullptr);
 }
 
 bool use_fused_mg(const plsqr_ctx* h) { return mg2d_supported(h->d.ndim, h->nu) && h->L > 1 && !h->generic_mg; }
@@ -327,7 +333,7 @@ template <typename T>
 void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     for (int l = 0; l + 1 < h->L; ++l)
         mg_coarsen<T>(l == 0 ? P<T>(h->kappa) : P<T>(h->lv[l].cond), l == 0, P<T>(h->lv[l + 1].cond), h->lv[l].d,
-                      h->lv[l + 1].d, B, s);
+                      h->lv[l + 1].d, B, s, l == 0 ? K16(h) : nullptr);
     const int lc = h->L - 1;
     const T* cc = lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond);
     if (h->gth) {
@@ -375,7 +381,7 @@ void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
 template <typename T>
 void outer_step(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
     Hist hs = hist_of(h);
-    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, B, h->st, hs, h->kfloor, h->red, s);  // step 3
+    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, B, h->st, hs, h->kfloor, h->red, s, K16(h));  // step 3
     prec_setup<T>(h, B, s);
     mlsqr_seq<T>(h, B, n_inner, s);  // step 4
     op_apply<T>(h->od, false, EPI_PLAIN, P<T>(h->f), P<T>(h->tmpm), nullptr, P<T>(h->tmp), B, h->st, h->red, s);
@@ -482,7 +488,7 @@ int solve_impl(plsqr_ctx* h, int count, const void* const* g, bool g_host, const
     fill_nan(h->h_resid, hb * h->h_outer, s);
     run_outer_steps<T>(h, count, n_outer, n_inner);
     // R(f^n_outer) (the outer counter now equals n_outer)
-    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, count, h->st, hist_of(h), h->kfloor, h->red, s);
+    diffusivity<T>(P<T>(h->f), P<T>(h->kappa), h->d, count, h->st, hist_of(h), h->kfloor, h->red, s, K16(h));
     for (int b = 0; b < count; ++b) {
         if (!f_out[b]) throw InvalidArg("f_out is NULL");
         ck(cudaMemcpyAsync(f_out[b], h->f + b * nb, nb, f_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
@@ -847,6 +853,20 @@ int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const
     });
 }
 
+// ---- bfloat16 kappa -----------------------------------------------------------------------------
+
+int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (on && (h->fp64 || h->d.ndim != 2 || !use_fused_mg(h)))
+            throw InvalidArg("bfloat16 kappa needs a 2D single-precision handle with the temporally blocked V-cycle");
+        if (on && !h->kappa16) h->kappa16 = (__nv_bfloat16*)dalloc(h, sizeof(__nv_bfloat16) * h->B * h->d.N);
+        if ((on != 0) != h->kbf16) clear_graphs(h);
+        h->kbf16 = on != 0;
+        return PLSQR_OK;
+    });
+}
+
 // ---- stopping rules ----------------------------------------------------------------------------
 
 int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, double r_rel) {
@@ -1128,6 +1148,7 @@ int plsqr_prec_setup(plsqr_handle h, const void* kappa) {
         if (!kappa) throw InvalidArg("NULL pointer");
         cudaStream_t s = h->user_stream;
         ck(cudaMemcpyAsync(h->kappa, kappa, h->esz * h->d.N, cudaMemcpyDeviceToDevice, s), "kappa");
+        if (h->kbf16) to_bf16(P<float>(h->kappa), h->kappa16, h->d.N, s);
         by_type(h, [&](auto tv) {
             using T = decltype(tv);
             prec_setup<T>(h, 1, s);

@@ -76,6 +76,7 @@ def lib():
         "plsqr_last_launches": ([vp], i64),
         "plsqr_blur_noalloc": ([i32, C.POINTER(i64), i32, C.POINTER(d), C.POINTER(i32), vp, vp, vp], C.c_int),
         "plsqr_set_stopping": ([vp, i32, d, d, d], C.c_int),
+        "plsqr_set_kappa_bf16": ([vp, i32], C.c_int),
         "plsqr_slot_start": ([vp, i32, vp, i32, d, d, i32, i32, C.POINTER(d)], C.c_int),
         "plsqr_step": ([vp], C.c_int),
         "plsqr_query": ([vp], C.c_int),
@@ -94,7 +95,7 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
-            "plsqr_set_stopping", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish"]
+            "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
 
@@ -304,6 +305,10 @@ class Solver:
         """S4 with eta * delta (0: off) and the outer stop on a relative R decrease below r_rel
         (0: off) for later solves; index -1 = every instance."""
         _check(self.h, lib().plsqr_set_stopping(self.h, int(index), float(eta), float(delta), float(r_rel)))
+
+    def set_kappa_bf16(self, on=True):
+        """Keep kappa in bfloat16 for later solves (2D single precision, temporally blocked V-cycle)."""
+        _check(self.h, lib().plsqr_set_kappa_bf16(self.h, 1 if on else 0))
 
     # ---- slots (continuous batching) ----
     def slot_start(self, slot, g, reg, T, tau, n_outer, n_inner, sigma=None):
