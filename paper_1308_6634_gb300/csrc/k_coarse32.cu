@@ -65,34 +65,41 @@ __device__ __forceinline__ void load_row(float (&r)[BWP], const float* p) {
     }
 }
 
-// L D L^T of one instance per warp.  The whole instance (nc * BWP floats) is staged in shared
-// memory by one bulk copy, so the pivot loop makes no global loads.  Step k: every lane loads
-// column k into registers and sums it (the same order everywhere, so all agree on d_k); lane
-// t-1 forms l_{k+t,k}; then, for each column j = k + tau, lane t-1 updates the entry of row
-// j + t (consecutive lanes on consecutive words: no bank conflicts) and lane tau-1 updates s_j.
-// l and 1/d_k go to global memory as they are formed; the staged copy of column k is left as is.
+// L D L^T of one instance per block of GW warps.  The whole instance (nc * BWP floats) is staged
+// in shared memory by one bulk copy, so the pivot loop makes no global loads.  Step k: every warp
+// loads column k into registers and sums it (the same order everywhere, so all agree on d_k) and
+// forms its own copy of l_{k+t,k} (lane t-1); warp w then updates the columns j = k + tau with
+// tau = w + 1 (mod GW): lane t-1 the entry of row j + t (consecutive lanes on consecutive words,
+// no bank conflicts), and warp 0 the excess s_j.  A block barrier closes the step.  l and 1/d_k
+// go to global memory as they are formed; the staged copy of column k is left as is.
+constexpr int GTH_GW = 1;  // more warps (4 measured) only added a block barrier per step
+
 template <int BW>
-__global__ void __launch_bounds__(32) k_ldl_gth_staged(float* __restrict__ gcol_all, float* __restrict__ grow_all,
-                                                       int nc, int bw, GkState* st) {
+__global__ void __launch_bounds__(32 * GTH_GW) k_ldl_gth_staged(float* __restrict__ gcol_all,
+                                                                float* __restrict__ grow_all, int nc, int bw,
+                                                                GkState* st) {
     constexpr int BWP = (BW + 1 + 3) & ~3;
+    constexpr int SLW = BWP + BW;  // one l buffer per warp
     extern __shared__ __align__(128) float col[];
-    __shared__ float sl[BWP + BW];
+    __shared__ float sl_all[GTH_GW * SLW];
     __shared__ __align__(8) uint64_t bar;
     const int inst = blockIdx.x, tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     if (parked(st[inst])) return;
     float* gc = gcol_all + (int64_t)inst * nc * BWP;
     float* gr = grow_all + (int64_t)inst * nc * BWP;
+    float* sl = sl_all + warp * SLW;
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(float)));
         bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(float)), &bar);
     }
-    for (int e = tid; e < nc * BWP; e += 32)  // row layout: entries no pivot writes
+    for (int e = tid; e < nc * BWP; e += 32 * GTH_GW)  // row layout: entries no pivot writes
         if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
-    for (int e = tid; e < BWP + BW; e += 32) sl[e] = 0.f;  // l beyond the band stays 0
-    __syncwarp();
+    for (int e = tid; e < GTH_GW * SLW; e += 32 * GTH_GW) sl_all[e] = 0.f;  // l beyond the band stays 0
+    __syncthreads();
     tma_wait_tile(&bar, st, inst);
-    const int t = tid + 1;
+    const int t = lane + 1;
     const bool mine = t <= bw;
     for (int k = 0; k < nc; ++k) {
         const float* ck = col + (int64_t)k * BWP;
@@ -108,25 +115,28 @@ __global__ void __launch_bounds__(32) k_ldl_gth_staged(float* __restrict__ gcol_
         }
         const float rd = 1.0f / ((a0 + a1) + (a2 + a3));
         const float l = mine ? ck[t] * rd : 0.f;
-        if (mine) {
-            sl[t] = l;
-            gc[(int64_t)k * BWP + t] = l;
-            if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
+        if (mine) sl[t] = l;
+        if (warp == 0) {
+            if (mine) {
+                gc[(int64_t)k * BWP + t] = l;
+                if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
+            }
+            if (lane == 0) gc[(int64_t)k * BWP] = rd;
         }
-        if (tid == 0) gc[(int64_t)k * BWP] = rd;
         __syncwarp();
+        const int lim = min(bw - t, nc - 1 - k);  // the columns k + tau this lane updates: tau <= lim
 #pragma unroll
         for (int tau = 1; tau < BW; ++tau) {
-            if (k + tau < nc && t <= bw - tau) {
+            if ((tau - 1) % GTH_GW == warp && tau <= lim) {
                 float* e = col + (int64_t)(k + tau) * BWP + t;
                 *e = fmaf(sl[tau + t], cv[tau], *e);
             }
         }
-        if (mine && k + t < nc) {
+        if (warp == 0 && mine && k + t < nc) {
             float* e = col + (int64_t)(k + t) * BWP;
             *e = fmaf(l, cv[0], *e);
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -273,7 +283,7 @@ void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int 
     case BW_: {                                                                                           \
         auto kf = k_ldl_gth_staged<BW_>;                                                                  \
         if (stage > 48 * 1024) cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage); \
-        kf<<<B, 32, stage, s>>>(gcol, grow, nc, bw, st);                                                  \
+        kf<<<B, 32 * GTH_GW, stage, s>>>(gcol, grow, nc, bw, st);                                                  \
         klaunched("k_ldl_gth_staged");                                                                    \
         auto ki = k_gth_inverse<BW_>;                                                                     \
         const size_t ism = stage + sizeof(float) * 4 * BW_ * 33;                                          \

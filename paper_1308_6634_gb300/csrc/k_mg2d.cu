@@ -27,7 +27,7 @@ namespace plsqr {
 
 // Tile extent; threads per block on the finest level (many tiles), on the coarser levels (few
 // tiles: more threads per tile) and in the one-launch coarse end.
-constexpr int MTX = 64, MTY = 32, MNT = 256, CNT = 512, TNT = 1024;
+constexpr int MTX = 64, MTY = 32, MNT = 256, CNT = 1024, TNT = 1024;
 
 // Tile geometry: logical halo H on both axes; in storage the x halo is HX >= H (HX * sizeof(T)
 // a multiple of 16 bytes, the TMA rule for the innermost coordinate), so logical column lx is
