@@ -22,6 +22,7 @@
 // gcol[k][t] = l_{k+t,k}, and grow[i][t] = l_{i,i-t}.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <stdexcept>
 
 #include "kernels.cuh"
@@ -247,6 +248,218 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ g
         }
         __syncwarp();
     }
+}
+
+// Wide bands (3D coarsest grids): the same elimination with a circular window of the bw + 1
+// columns pivot k touches, in shared memory (column j in slot j mod (bw + 1), an odd slot stride
+// so that consecutive rows of different slots fall in different banks), and nt = round32(bw)
+// threads (at most 1024).  Step k: d_k by a block reduction in a fixed order (warp partials to
+// lane 0, then the warp totals in warp order, read by every thread); l_{k+t,k} by thread t-1;
+// then thread t-1 updates row offset t of the columns k + tau, tau = 1..bw - t (its loop ends
+// where its rows end), and the excess of column k + t.  Column k + bw + 1 is fetched into
+// registers during the step and written to the freed slot at its end.  Output as the narrow
+// kernels: gcol[k][0] = 1/d_k, gcol[k][t] = l_{k+t,k}, grow[i][t] = l_{i,i-t}.
+__global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gcol_all, float* __restrict__ grow_all,
+                                                         int nc, int bw, int BWP, GkState* st) {
+    extern __shared__ __align__(16) float win[];
+    __shared__ float sl[1024 + 2];
+    __shared__ float wred[32];
+    const int NT = blockDim.x, NW = NT >> 5;
+    const int S = bw + 1, SW = S | 1;
+    const int inst = blockIdx.x, tid = threadIdx.x, t = tid + 1;
+    if (parked(st[inst])) return;
+    float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    for (int e = tid; e < nc * BWP; e += NT)  // row layout: entries no pivot writes
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
+    for (int e = tid; e < min(S, nc) * S; e += NT) {
+        const int c = e / S, r = e - c * S;
+        win[c * SW + r] = gc[(int64_t)c * BWP + r];
+    }
+    for (int e = tid; e < NT + 2; e += NT) sl[e] = 0.f;
+    __syncthreads();
+    float* const wend = win + S * SW;
+    for (int k = 0; k < nc; ++k) {
+        const int sk = k % S;
+        const float* ck = win + sk * SW;
+        // the next column of the window, fetched while this step runs
+        const bool nxt = k + S < nc;
+        const float pre0 = (nxt && tid < S) ? gc[(int64_t)(k + S) * BWP + tid] : 0.f;
+        const float pre1 = (nxt && tid + NT < S) ? gc[(int64_t)(k + S) * BWP + tid + NT] : 0.f;
+        float part = (t <= bw ? ck[t] : 0.f) + (tid == 0 ? ck[0] : 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if ((tid & 31) == 0) wred[tid >> 5] = part;
+        __syncthreads();
+        float dk = 0.f;
+        for (int w = 0; w < NW; ++w) dk += wred[w];
+        const float rd = 1.0f / dk;
+        const float s_k = ck[0];
+        if (t <= bw) {
+            const float l = ck[t] * rd;
+            sl[t] = l;
+            gc[(int64_t)k * BWP + t] = l;
+            if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
+        }
+        if (tid == 0) gc[(int64_t)k * BWP] = rd;
+        __syncthreads();
+        // row offset t of the columns k + tau, tau = 1 .. min(bw - t, nc - 1 - k)
+        const int last = min(bw - t, nc - 1 - k);
+        float* e = win + (sk + 1 == S ? 0 : sk + 1) * SW + t;
+        const float* lp = sl + 1 + t;
+        const float* ap = ck + 1;
+        for (int tau = 1; tau <= last; ++tau) {
+            *e = fmaf(*lp, *ap, *e);
+            ++lp;
+            ++ap;
+            e += SW;
+            if (e >= wend) e -= S * SW;
+        }
+        if (t <= bw && k + t < nc) {
+            float* es = win + ((k + t) % S) * SW;
+            *es = fmaf(sl[t], s_k, *es);
+        }
+        __syncthreads();
+        if (nxt) {
+            float* dst = win + sk * SW;
+            if (tid < S) dst[tid] = pre0;
+            if (tid + NT < S) dst[tid + NT] = pre1;
+        }
+    }
+}
+
+// X = L^{-T} D^{-1} L^{-1} for wide bands, one warp per column j: forward z_i = delta_ij +
+// sum_t l_{i,i-t} z_{i-t} over the rows i >= j (row layout, consecutive lanes on consecutive t),
+// y_i = z_i / d_i kept in X[i][j]; backward x_i = y_i + sum_t l_{i+t,i} x_{i+t} from the last row
+// to row j (column layout), stored at X[i][j] and X[j][i].  The last bw values of z (x) sit in a
+// ring in shared memory; the rows of the factor are loaded JW rows ahead into registers, the y
+// values of a pass of 32 rows one per lane.  The warp sums go to lane 0 in a fixed order.  All
+// terms are non-negative (l >= 0), as in the narrow kernel.  bw <= 32 * JT.
+constexpr int JT = 8;  // factor entries per lane per row
+constexpr int JW = 4;  // rows in flight
+
+template <int NWARP>
+__global__ void __launch_bounds__(32 * NWARP) k_gth_inverse_wide(const float* __restrict__ gcol_all,
+                                                                 const float* __restrict__ grow_all,
+                                                                 float* __restrict__ X_all, int nc, int bw, int BWP,
+                                                                 GkState* st) {
+    extern __shared__ float ring_all[];
+    const int inst = blockIdx.y;
+    if (parked(st[inst])) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * NWARP + warp;
+    if (j >= nc) return;  // no block-wide barrier below
+    const float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    const float* gr = grow_all + (int64_t)inst * nc * BWP;
+    float* X = X_all + (int64_t)inst * nc * nc;
+    const int R = bw + 1;
+    float* ring = ring_all + warp * R;
+    float fl[JW][JT];  // factor rows in flight (entry t = 1 + lane + 32 q)
+    auto fetch = [&](const float* tab, int row, float (&dst)[JT]) {
+#pragma unroll
+        for (int q = 0; q < JT; ++q) {
+            const int t = 1 + lane + 32 * q;
+            dst[q] = (row >= 0 && row < nc && t <= bw) ? tab[(int64_t)row * BWP + t] : 0.f;
+        }
+    };
+    // ---- forward over rows j, j+1, ... ----
+    for (int e = lane; e < R; e += 32) ring[e] = 0.f;
+#pragma unroll
+    for (int w = 0; w < JW; ++w) fetch(gr, j + w, fl[w]);
+    float dv = (j + lane < nc) ? gc[(int64_t)(j + lane) * BWP] : 0.f;  // 1/d of rows j + lane
+    __syncwarp();
+    int im = j % R;
+    for (int i0 = j; i0 < nc; i0 += JW) {
+#pragma unroll
+        for (int w = 0; w < JW; ++w) {
+            const int i = i0 + w;
+            if (i < nc) {
+                float part = 0.f;
+#pragma unroll
+                for (int q = 0; q < JT; ++q) {
+                    const int t = 1 + lane + 32 * q;
+                    if (t <= i - j && t <= bw) {
+                        const int r = im - t;
+                        part = fmaf(fl[w][q], ring[r < 0 ? r + R : r], part);
+                    }
+                }
+                fetch(gr, i + JW, fl[w]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+                const float d = __shfl_sync(0xffffffffu, dv, (i - j) & 31);
+                if (((i - j) & 31) == 31) dv = (i + 1 + lane < nc) ? gc[(int64_t)(i + 1 + lane) * BWP] : 0.f;
+                __syncwarp();
+                if (lane == 0) {
+                    const float z = (i == j ? 1.f : 0.f) + part;
+                    ring[im] = z;
+                    X[(int64_t)i * nc + j] = z * d;
+                }
+                __syncwarp();
+                im = im + 1 == R ? 0 : im + 1;
+            }
+        }
+    }
+    // ---- backward over rows nc-1, nc-2, ..., j ----
+    for (int e = lane; e < R; e += 32) ring[e] = 0.f;
+#pragma unroll
+    for (int w = 0; w < JW; ++w) fetch(gc, nc - 1 - w, fl[w]);
+    float yv = (nc - 1 - lane >= j) ? X[(int64_t)(nc - 1 - lane) * nc + j] : 0.f;  // y of rows nc-1-lane
+    __syncwarp();
+    im = (nc - 1) % R;
+    for (int i0 = nc - 1; i0 >= j; i0 -= JW) {
+#pragma unroll
+        for (int w = 0; w < JW; ++w) {
+            const int i = i0 - w;
+            if (i >= j) {
+                float part = 0.f;
+#pragma unroll
+                for (int q = 0; q < JT; ++q) {
+                    const int t = 1 + lane + 32 * q;
+                    if (t <= nc - 1 - i && t <= bw) {
+                        const int r = im + t;
+                        part = fmaf(fl[w][q], ring[r >= R ? r - R : r], part);
+                    }
+                }
+                fetch(gc, i - JW, fl[w]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+                const float y = __shfl_sync(0xffffffffu, yv, (nc - 1 - i) & 31);
+                if (((nc - 1 - i) & 31) == 31)
+                    yv = (i - 1 - lane >= j) ? X[(int64_t)(i - 1 - lane) * nc + j] : 0.f;
+                __syncwarp();
+                if (lane == 0) {
+                    const float x = y + part;
+                    ring[im] = x;
+                    X[(int64_t)i * nc + j] = x;
+                    if (i != j) X[(int64_t)j * nc + i] = x;
+                }
+                __syncwarp();
+                im = im == 0 ? R - 1 : im - 1;
+            }
+        }
+    }
+}
+
+bool gth_wide_supported(int bw, int nc) {
+    const int S = bw + 1, SW = S | 1;
+    return bw > 0 && bw <= 32 * JT && (size_t)S * SW * sizeof(float) <= 200 * 1024 && nc > 0;
+}
+
+void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+    if (!gth_wide_supported(bw, nc)) throw std::runtime_error("gth_wide_factor_inverse: bandwidth not supported");
+    kbegin(KC_SETUP, s);
+    const int BWP = gth_stride(bw);
+    const int S = bw + 1, SW = S | 1;
+    const size_t smem = sizeof(float) * (size_t)S * SW;
+    const int nt = std::max(32, ((bw + 31) / 32) * 32);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ldl_gth_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ldl_gth_window<<<B, nt, smem, s>>>(gcol, grow, nc, bw, BWP, st);
+    klaunched("k_ldl_gth_window");
+    constexpr int NW = 4;
+    dim3 grid((unsigned)((nc + NW - 1) / NW), B);
+    k_gth_inverse_wide<NW><<<grid, 32 * NW, sizeof(float) * NW * (bw + 1), s>>>(gcol, grow, X, nc, bw, BWP, st);
+    klaunched("k_gth_inverse_wide");
+    kfinish(s);
 }
 
 int gth_window(int bw) { return bw <= 8 ? 8 : bw <= 16 ? 16 : bw <= 32 ? 32 : 0; }

@@ -115,6 +115,10 @@ bool gth_supported(int bw, int nc);
 template <typename T>
 void gth_assemble(const T* cond, bool is_kappa, float* gcol, Dims d, int bw, int B, cudaStream_t s);
 void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
+// Wide bands: the float L D L^T with a window of bw + 1 columns, and the float inverse with a warp
+// per column.
+bool gth_wide_supported(int bw, int nc);
+void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
 
 // ---- temporally blocked 2D V-cycle (one launch per level and direction) ----
 bool mg2d_supported(int ndim, int nu);

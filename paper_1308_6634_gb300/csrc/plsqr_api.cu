@@ -85,6 +85,7 @@ struct plsqr_ctx {
     float* Xf = nullptr;  // the same rounded to float (single-precision handles)
     // single-precision handles with a coarsest bandwidth <= 32: subtraction-free L D L^T in float
     bool gth = false;
+    bool gthw = false;  // wide band: float L D L^T (windowed) and float inverse
     float* gcol = nullptr;  // [B][nc][stride]: column layout (input conductances, then l and 1/d)
     float* grow = nullptr;  // [B][nc][stride]: row layout of l
     GkState* st = nullptr;
@@ -171,7 +172,8 @@ struct Plan {
     int L, nc, bw;
     int64_t level_N[16];
     size_t bytes;
-    bool gth;
+    bool gth;   // float factor and inverse (bandwidth <= 32)
+    bool gthw;  // float factor and inverse of a wide band
 };
 
 Plan make_plan(const plsqr_config* c, int64_t m) {
@@ -202,9 +204,10 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
     const char* e64 = std::getenv("PLSQR_COARSE64");
     pl.gth = c->precision == PLSQR_FP32 && gth_supported(pl.bw, pl.nc) && !(e64 && e64[0] == '1');
-    if (!pl.gth && (size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 +
-                           pl.bw * 8 >
-                       227 * 1024)
+    pl.gthw = c->precision == PLSQR_FP32 && !pl.gth && gth_wide_supported(pl.bw, pl.nc) && !(e64 && e64[0] == '1');
+    if (!pl.gth && !pl.gthw &&
+        (size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 + pl.bw * 8 >
+            227 * 1024)
         throw InvalidArg("coarsest level too wide for the banded factorisation: add levels");
     const size_t esz = c->precision == PLSQR_FP64 ? 8 : 4;
     const int64_t B = c->max_batch, N = pl.d.N;
@@ -214,7 +217,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += esz * B * (N + m);          // tmp (N), tmpm (m)
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
     for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
-    if (pl.gth) {
+    if (pl.gth || pl.gthw) {
         b += sizeof(float) * B * (size_t)pl.nc * 2 * gth_stride(pl.bw);
         b += sizeof(float) * B * (size_t)pl.nc * pl.nc;
     } else {
@@ -339,6 +342,11 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     if (h->gth) {
         gth_assemble<T>(cc, lc == 0, h->gcol, h->lv[lc].d, h->bw, B, s);
         gth_factor_inverse(h->gcol, h->grow, h->Xf, h->nc, h->bw, B, h->st, s);
+        return;
+    }
+    if (h->gthw) {
+        gth_assemble<T>(cc, lc == 0, h->gcol, h->lv[lc].d, h->bw, B, s);
+        gth_wide_factor_inverse(h->gcol, h->grow, h->Xf, h->nc, h->bw, B, h->st, s);
         return;
     }
     coarse_assemble<T>(cc, lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
@@ -716,7 +724,8 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
             }
         }
         h->gth = pl.gth;
-        if (h->gth) {
+        h->gthw = pl.gthw;
+        if (h->gth || h->gthw) {
             h->gcol = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
             h->grow = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
         } else {

@@ -154,7 +154,8 @@ def test_priorconditioner(prec, shape, levels, nu, cycles):
     assert rel(host(S.apply_M(dev(b, prec))), O.apply_M(kappa, b)) < (1e-13 if prec == "fp64" else 1e-6)
 
 
-@pytest.mark.parametrize("shape", [(32, 32), (24, 16), (8, 8), (2, 3, 4), (4, 4, 2)])
+@pytest.mark.parametrize("shape", [(32, 32), (24, 16), (8, 8), (2, 3, 4), (4, 4, 2), (8, 8, 8), (12, 12, 12),
+                                   (6, 10, 14)])
 def test_single_precision_coarse_solve(shape):
     """Float handles factor the coarsest operator without subtractions (L D L^T carrying the row-sum
     excess).  With one level the priorconditioner is exactly that coarse solve, so it must match the
@@ -169,10 +170,11 @@ def test_single_precision_coarse_solve(shape):
     assert rel(host(S.prec_apply(dev(b, "fp32"))), ref) < 5e-6
 
 
-def test_single_precision_coarse_solve_matches_double_route(monkeypatch):
-    """The float coarse route against the double-precision banded Cholesky route of the same handle
+@pytest.mark.parametrize("shape,levels", [((256, 256), 4), ((48, 48, 48), 3)])
+def test_single_precision_coarse_solve_matches_double_route(shape, levels, monkeypatch):
+    """The float coarse route (bandwidth 32 in 2D; the windowed factor of bandwidth 144 with the
+    double inverse in 3D) against the double-precision banded Cholesky route of the same handle
     type (PLSQR_COARSE64=1) inside a full V-cycle."""
-    shape, levels = (256, 256), 4
     kappa = _kappa_field(shape)
     b = np.random.default_rng(12).standard_normal(shape)
     outs = []
