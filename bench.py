@@ -298,7 +298,7 @@ def main():
     from paper_1308_6634_gb300 import plsqr
     B = args.batch
     S = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles, max_batch=B)
-    seeds = [rank * B + b for b in range(B)]
+    seeds = replica_seeds(rank, B)
     mask = W.inputs(seeds[0])[1]
     S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles, n_bins=W.n_bins)
     if args.kappa_bf16:
@@ -339,10 +339,7 @@ def main():
             torch.distributed.barrier()
     per_step = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     total_ms = float(per_step.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     value = world * B * args.steps / (total_ms / 1e3)
 
     # end to end through the host-buffer API: H2D of g, solve, D2H of f inside the timed region
@@ -448,6 +445,22 @@ def main():
 
 def W_N(W):
     return int(np.prod(W.shape))
+
+
+def replica_seeds(rank, B):
+    """Seeds of the B instances a rank solves: replicas of the workload, disjoint across ranks."""
+    return [rank * B + b for b in range(B)]
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks of the default process group (the timing rule)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_fp64_single(W, plsqr, torch, dev, g32, steps=2):
