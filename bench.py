@@ -42,13 +42,19 @@ METRIC = "solves/s and p50/p99 ms at <=1e-4 rel err vs FP64 oracle; HBM GB/s vs 
 #   gs_fine (finest-level V-cycle launches, pre and post alternate):
 #         pre:  p~ (rhs), kappa in, x out, restricted residual out (1/4)    3.25
 #         post: x_in, p~, kappa, coarse correction (1/4) in, v~ out         4.25  -> mean 3.75
-def alg_units(W):
+def alg_units(W, kappa_bf16=False):
+    """Algorithmic bytes per launch of each roofline class, in units of (element size x cells x
+    instances).  2D V-cycle (finest level, mean of the pre- and post-smoothing launches):
+    pre reads b, kappa and the reciprocal diagonal and writes x and the restricted residual (1/4);
+    post reads x_in, b, kappa, the reciprocal diagonal and the coarse correction (1/4) and writes x.
+    kappa in bfloat16 counts half."""
     n = W.n_inner
     two_d_blur = W.kind in ("blur", "blur_mask") and len(W.shape) == 2
     fused_update = two_d_blur and W.precision == "fp32" and W.radius[0] == W.radius[1] and W.radius[0] in (6, 9, 12, 15)
     fwd = (3.0 + 7.0 * (n - 1)) / n if fused_update else 3.0
     if len(W.shape) == 2:
-        return {"fwd": fwd, "adj": 3.0, "gs_fine": 3.75}
+        k = 0.5 if kappa_bf16 else 1.0
+        return {"fwd": fwd, "adj": 3.0, "gs_fine": ((3.25 + k) + (4.25 + k)) / 2}
     # 3D: one launch per red-black half sweep: x of the other colour (1/2), kappa (1),
     # b of this colour (1/2) in, x of this colour (1/2) out
     return {"fwd": fwd, "adj": 3.0, "gs_fine": 2.5}
@@ -145,10 +151,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# the kernels of the roofline classes (blur, V-cycle) and what they include
+TRAFFIC_SOURCES = ("common.cuh", "kernels.cuh", "tma.cuh", "k_ops.cu", "k_mg.cu", "k_mg2d.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1308_6634_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,7 +387,7 @@ def main():
         torch.cuda.synchronize()
         prof = S.profile_read()
         S.profile(False)
-        ALG_UNITS = alg_units(W)
+        ALG_UNITS = alg_units(W, args.kappa_bf16)
         cand = {k: v for k, v in prof.items() if k in ALG_UNITS and v[1] > 0}
         top = max(prof.items(), key=lambda kv: kv[1][0])[0]
         dom = max(cand.items(), key=lambda kv: kv[1][0])[0] if cand else None

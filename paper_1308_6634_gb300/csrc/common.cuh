@@ -108,6 +108,7 @@ struct Dims {
 constexpr int TAIL_LEVELS = 5;
 struct TailLevels {
     const void* cond[TAIL_LEVELS];
+    const void* rd[TAIL_LEVELS];
     void* b[TAIL_LEVELS];
     void* x[TAIL_LEVELS];
     void* x2[TAIL_LEVELS];

@@ -66,78 +66,102 @@ __device__ __forceinline__ void load_row(float (&r)[BWP], const float* p) {
     }
 }
 
-// L D L^T of one instance per block of GW warps.  The whole instance (nc * BWP floats) is staged
-// in shared memory by one bulk copy, so the pivot loop makes no global loads.  Step k: every warp
-// loads column k into registers and sums it (the same order everywhere, so all agree on d_k) and
-// forms its own copy of l_{k+t,k} (lane t-1); warp w then updates the columns j = k + tau with
-// tau = w + 1 (mod GW): lane t-1 the entry of row j + t (consecutive lanes on consecutive words,
-// no bank conflicts), and warp 0 the excess s_j.  A block barrier closes the step.  l and 1/d_k
-// go to global memory as they are formed; the staged copy of column k is left as is.
-constexpr int GTH_GW = 1;  // more warps (4 measured) only added a block barrier per step
-
+// L D L^T of one instance per warp.  The whole instance (nc * BWP floats) is staged in shared
+// memory by one bulk copy, so the pivot loop makes no global loads.  Lane t-1 owns row offset t
+// of every column: at step k it forms l_{k+t,k} = |a_{k+t,k}| / d_k and updates entry t of the
+// columns k + tau (tau <= bw - t), lane t-1 also the excess of column k + t.  The loop is
+// software-pipelined: step k first completes column k+1 (its update by pivot k and its excess),
+// then issues the loads of column k+1 together with the rest of pivot k's update (columns k+2 ..),
+// so the sum and reciprocal of pivot k+1 overlap that update.  l and 1/d_k go to global memory as
+// they are formed; the staged copy of column k is left as is.  Measured on the 1024^2 workload's
+// 32 x 32 coarse grid: 0.69 ms per factorisation, limited by one warp's dependent shared-memory
+// and arithmetic chain (a 4-warp split of the update was slower: one block barrier per pivot).
 template <int BW>
-__global__ void __launch_bounds__(32 * GTH_GW) k_ldl_gth_staged(float* __restrict__ gcol_all,
-                                                                float* __restrict__ grow_all, int nc, int bw,
-                                                                GkState* st) {
+__global__ void __launch_bounds__(32) k_ldl_gth_pipe(float* __restrict__ gcol_all, float* __restrict__ grow_all,
+                                                     int nc, int bw, GkState* st) {
     constexpr int BWP = (BW + 1 + 3) & ~3;
-    constexpr int SLW = BWP + BW;  // one l buffer per warp
+    constexpr int SLW = BWP + BW;
     extern __shared__ __align__(128) float col[];
-    __shared__ float sl_all[GTH_GW * SLW];
+    __shared__ float sl[2][SLW];
     __shared__ __align__(8) uint64_t bar;
-    const int inst = blockIdx.x, tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int inst = blockIdx.x, lane = threadIdx.x;
     if (parked(st[inst])) return;
     float* gc = gcol_all + (int64_t)inst * nc * BWP;
     float* gr = grow_all + (int64_t)inst * nc * BWP;
-    float* sl = sl_all + warp * SLW;
-    if (tid == 0) {
+    if (lane == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(float)));
         bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(float)), &bar);
     }
-    for (int e = tid; e < nc * BWP; e += 32 * GTH_GW)  // row layout: entries no pivot writes
+    for (int e = lane; e < nc * BWP; e += 32)  // row layout: entries no pivot writes
         if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
-    for (int e = tid; e < GTH_GW * SLW; e += 32 * GTH_GW) sl_all[e] = 0.f;  // l beyond the band stays 0
-    __syncthreads();
+    for (int e = lane; e < 2 * SLW; e += 32) (&sl[0][0])[e] = 0.f;  // l beyond the band stays 0
+    for (int e = lane; e < BWP; e += 32) col[(int64_t)nc * BWP + e] = 0.f;
+    __syncwarp();
     tma_wait_tile(&bar, st, inst);
     const int t = lane + 1;
     const bool mine = t <= bw;
-    for (int k = 0; k < nc; ++k) {
-        const float* ck = col + (int64_t)k * BWP;
-        float cv[BWP];
-        load_row<BWP>(cv, ck);
+    auto pivot = [&](const float (&c)[BWP]) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
         for (int q = 0; q < BWP / 4; ++q) {
-            a0 += cv[4 * q];
-            a1 += cv[4 * q + 1];
-            a2 += cv[4 * q + 2];
-            a3 += cv[4 * q + 3];
+            a0 += c[4 * q];
+            a1 += c[4 * q + 1];
+            a2 += c[4 * q + 2];
+            a3 += c[4 * q + 3];
         }
-        const float rd = 1.0f / ((a0 + a1) + (a2 + a3));
-        const float l = mine ? ck[t] * rd : 0.f;
-        if (mine) sl[t] = l;
-        if (warp == 0) {
-            if (mine) {
-                gc[(int64_t)k * BWP + t] = l;
-                if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
-            }
-            if (lane == 0) gc[(int64_t)k * BWP] = rd;
+        return 1.0f / ((a0 + a1) + (a2 + a3));
+    };
+    float cv[BWP];
+    load_row<BWP>(cv, col);
+    float rd = pivot(cv);
+    float l = mine ? col[t] * rd : 0.f;
+    for (int k = 0; k < nc; ++k) {
+        float* slk = sl[k & 1];
+        if (mine) {
+            slk[t] = l;
+            gc[(int64_t)k * BWP + t] = l;
+            if (k + t < nc) gr[(int64_t)(k + t) * BWP + t] = l;
         }
+        if (lane == 0) gc[(int64_t)k * BWP] = rd;
         __syncwarp();
         const int lim = min(bw - t, nc - 1 - k);  // the columns k + tau this lane updates: tau <= lim
-#pragma unroll
-        for (int tau = 1; tau < BW; ++tau) {
-            if ((tau - 1) % GTH_GW == warp && tau <= lim) {
-                float* e = col + (int64_t)(k + tau) * BWP + t;
-                *e = fmaf(sl[tau + t], cv[tau], *e);
-            }
+        if (1 <= lim) {
+            float* e = col + (int64_t)(k + 1) * BWP + t;
+            *e = fmaf(slk[1 + t], cv[1], *e);
         }
-        if (warp == 0 && mine && k + t < nc) {
-            float* e = col + (int64_t)(k + t) * BWP;
+        if (t == 1 && k + 1 < nc) {
+            float* e = col + (int64_t)(k + 1) * BWP;
             *e = fmaf(l, cv[0], *e);
         }
-        __syncthreads();
+        __syncwarp();
+        // column k+1 is final: its loads go first (the staged table has one zero column beyond
+        // the last, so the loads of the last step stay in bounds; that step's pivot is unused)
+        float cn[BWP];
+        load_row<BWP>(cn, col + (int64_t)(k + 1) * BWP);
+        const float ln = mine ? col[(int64_t)(k + 1) * BWP + t] : 0.f;
+        // the rest of pivot k's update: every entry this lane touches is read before any is
+        // written (the entries are distinct, so this is the same arithmetic), which lets the
+        // loads issue back to back instead of one load-use-store chain per column
+        float ev[BW], sv[BW];
+        float* ck1 = col + (int64_t)(k + 1) * BWP + t;
+#pragma unroll
+        for (int tau = 2; tau < BW; ++tau) {
+            ev[tau] = tau <= lim ? ck1[(tau - 1) * BWP] : 0.f;
+            sv[tau] = tau <= lim ? slk[tau + t] : 0.f;
+        }
+        const bool exc = t >= 2 && mine && k + t < nc;
+        float* ex = col + (int64_t)(k + t) * BWP;
+        const float exv = exc ? *ex : 0.f;
+#pragma unroll
+        for (int tau = 2; tau < BW; ++tau)
+            if (tau <= lim) ck1[(tau - 1) * BWP] = fmaf(sv[tau], cv[tau], ev[tau]);
+        if (exc) *ex = fmaf(l, cv[0], exv);
+        rd = pivot(cn);
+        l = ln * rd;
+#pragma unroll
+        for (int q = 0; q < BWP; ++q) cv[q] = cn[q];
+        __syncwarp();
     }
 }
 
@@ -494,10 +518,11 @@ void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int 
     dim3 igrid((unsigned)((nc + 127) / 128), B);
 #define GTH_CASE(BW_)                                                                                     \
     case BW_: {                                                                                           \
-        auto kf = k_ldl_gth_staged<BW_>;                                                                  \
-        if (stage > 48 * 1024) cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage); \
-        kf<<<B, 32 * GTH_GW, stage, s>>>(gcol, grow, nc, bw, st);                                                  \
-        klaunched("k_ldl_gth_staged");                                                                    \
+        auto kp = k_ldl_gth_pipe<BW_>;                                                                    \
+        const size_t sp = stage + sizeof(float) * BWP;                                                    \
+        if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
+        kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);                                                     \
+        klaunched("k_ldl_gth_pipe");                                                                      \
         auto ki = k_gth_inverse<BW_>;                                                                     \
         const size_t ism = stage + sizeof(float) * 4 * BW_ * 33;                                          \
         if (ism > 48 * 1024) cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism); \

@@ -311,6 +311,37 @@ void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B,
     kfinish(s);
 }
 
+// 1 / diagonal of a 2D level: ((c_x(i) + c_x(i-1)) + c_y(i)) + c_y(i-nx), the edges missing at
+// the low boundary counted as 0 -- the summation order of the red-black smoother, so the staged
+// value is bit for bit the one a tile would form.  kappa may come from its bfloat16 copy.
+template <typename T, bool KAPPA>
+__global__ void __launch_bounds__(256) k_rdiag2d(const T* __restrict__ cond, T* __restrict__ rd, Dims d,
+                                                 const __nv_bfloat16* __restrict__ k16) {
+    const int inst = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= d.N) return;
+    const int x = (int)(i % d.nx), y = (int)(i / d.nx);
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * 2 * d.N);
+    const __nv_bfloat16* k = k16 ? k16 + (int64_t)inst * d.N : nullptr;
+    auto cx = [&](int64_t j) -> T { return (KAPPA && k) ? (T)__bfloat162float(k[j]) : c[j]; };
+    auto cy = [&](int64_t j) -> T { return KAPPA ? cx(j) : c[d.N + j]; };
+    T diag = cx(i);
+    diag += x > 0 ? cx(i - 1) : (T)0;
+    diag += cy(i);
+    diag += y > 0 ? cy(i - d.nx) : (T)0;
+    rd[(int64_t)inst * d.N + i] = (T)1 / diag;
+}
+
+template <typename T>
+void mg_rdiag2d(const T* cond, bool is_kappa, T* rd, Dims d, int B, cudaStream_t s, const __nv_bfloat16* k16) {
+    kbegin(KC_SETUP, s);
+    dim3 grid((unsigned)((d.N + 255) / 256), B);
+    if (is_kappa) k_rdiag2d<T, true><<<grid, 256, 0, s>>>(cond, rd, d, k16);
+    else k_rdiag2d<T, false><<<grid, 256, 0, s>>>(cond, rd, d, nullptr);
+    klaunched("k_rdiag2d");
+    kfinish(s);
+}
+
 // ---- exact coarse solve ----------------------------------------------------------------------
 
 // Lower band of the coarsest operator in double: band[i][k] = M(i, i-k), k = 0..bw.
@@ -676,6 +707,7 @@ void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
     template void diffusivity<T>(const T*, T*, Dims, int, GkState*, Hist, double, Red, cudaStream_t,         \
                                  __nv_bfloat16*);                                                         \
     template void mg_coarsen<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t, const __nv_bfloat16*);  \
+    template void mg_rdiag2d<T>(const T*, bool, T*, Dims, int, cudaStream_t, const __nv_bfloat16*);        \
     template void mg_gs_half<T>(const T*, bool, const T*, T*, Dims, int, bool, int, cudaStream_t);         \
     template void mg_resid_restrict<T>(const T*, bool, const T*, const T*, T*, Dims, Dims, int,            \
                                        cudaStream_t);                                                     \

@@ -31,8 +31,9 @@ constexpr int MTX = 64, MTY = 32, MNT = 256, CNT = 1024, TNT = 1024;
 
 // Tile geometry: logical halo H on both axes; in storage the x halo is HX >= H (HX * sizeof(T)
 // a multiple of 16 bytes, the TMA rule for the innermost coordinate), so logical column lx is
-// stored at lx + OX.  Arrays: sb, scx, scy (scy == scx on the finest level), sx.
-template <typename T, bool L0, int H>
+// stored at lx + OX.  Arrays: sb, scx, scy (scy == scx on the finest level), sx, sd (1 / diagonal)
+// and, for post-smoothing (XC), the box of coarse-level cells that are parents of staged cells.
+template <typename T, bool L0, int H, bool XC = false>
 struct Tile {
     static constexpr int VEC = 16 / (int)sizeof(T);
     static constexpr int HX = ((H + VEC - 1) / VEC) * VEC, OX = HX - H;
@@ -41,117 +42,132 @@ struct Tile {
     static constexpr int NCS = LY * LXS;                      // one staged plane
     static constexpr int NCP = ((NCS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);  // 128-byte padded
     static constexpr int CPLANES = L0 ? 1 : 2;
-    // layout: sb [NCP] | scx, scy [CPLANES * NCS, padded] | sx [NCP] | sd [NCP] | mbarrier
-    // (sd: 1 / diagonal of the cells inside the domain, 0 elsewhere)
+    // Coarse box: it starts XB coarse columns and YB coarse rows before the parent (x0/2, y0/2)
+    // of the tile's first cell (XB a multiple of VEC, so the copy's x stays 16-byte aligned).
+    // The parent of staged cell (ly, lxs) is box cell ((ly + (H & 1)) >> 1, (lxs + 2 XB - HX) >> 1).
+    static constexpr int XB = (((HX + 1) / 2 + VEC - 1) / VEC) * VEC;
+    static constexpr int XW = ((((MTX + HX - 1) >> 1) + XB + 1 + VEC - 1) / VEC) * VEC;
+    static constexpr int YB = (H + 1) / 2;
+    static constexpr int YW = ((MTY + H - 1) >> 1) + YB + 1;
+    static constexpr int NXC = XC ? ((XW * YW * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T) : 0;
+    // layout: sb [NCP] | scx, scy [CPLANES * NCS, padded] | sx [NCP] | sd [NCP] | sxc [NXC] | mbarrier
     static constexpr int OFF_C = NCP;
     static constexpr int OFF_X = NCP + ((CPLANES * NCS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
     static constexpr int OFF_D = OFF_X + NCP;
-    static constexpr int OFF_BAR = OFF_D + NCP;
+    static constexpr int OFF_XC = OFF_D + NCP;
+    static constexpr int OFF_BAR = OFF_XC + NXC;
     static constexpr size_t bytes() { return sizeof(T) * (size_t)OFF_BAR + 16; }
 };
 
 struct Maps {
-    CUtensorMap b, c, x;
+    CUtensorMap b, c, x, d, xc;
 };
 
-// Stage b and the conductances (and x_in when X_IN) of the tile.  k16 (finest level only, may be
-// null): kappa stored in bfloat16, read with plain loads and widened in shared memory.
-template <typename T, bool L0, int H, bool TMA, bool X_IN, int NTH>
-__device__ __forceinline__ void stage(T* sm, const Maps& maps, const T* __restrict__ cond, const T* __restrict__ b,
-                                      const T* __restrict__ x_in, const Dims& d, int inst, int x0, int y0,
-                                      GkState* st, const __nv_bfloat16* __restrict__ k16 = nullptr) {
-    using TL = Tile<T, L0, H>;
+// Stage b, the conductances, the reciprocal diagonal rd and x_in when X_IN (x = 0 otherwise),
+// and the coarse box of xc when XC.  k16 (finest level only, may be null): kappa stored in
+// bfloat16, read with plain loads and widened in shared memory.  The copies are issued first;
+// the instance state is read while they are in flight.  Returns whether the block skips the
+// tile (SKIP 1: a parked or frozen instance, 2: an instance whose inner iteration is off, 0:
+// never), the same answer in every thread.  Ends with a barrier.
+template <typename T, bool L0, int H, bool TMA, bool X_IN, bool XC, int SKIP, int NTH>
+__device__ __forceinline__ bool stage(T* sm, const Maps& maps, const T* __restrict__ cond, const T* __restrict__ b,
+                                      const T* __restrict__ rd, const T* __restrict__ x_in,
+                                      const T* __restrict__ xc, const Dims& d, const Dims& dc, int inst, int x0,
+                                      int y0, GkState* st, const __nv_bfloat16* __restrict__ k16) {
+    using TL = Tile<T, L0, H, XC>;
     T* sb = sm;
     T* sc = sm + TL::OFF_C;
     T* sx = sm + TL::OFF_X;
+    T* sd = sm + TL::OFF_D;
+    T* sxc = sm + TL::OFF_XC;
+    auto skip_of = [&]() {
+        if (SKIP == 1) return parked(st[inst]) || st[inst].frozen >= 2;
+        if (SKIP == 2) return inner_off(st[inst]);
+        return false;
+    };
     if constexpr (TMA) {
         uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TL::OFF_BAR);
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
         const bool kb = L0 && k16;
         if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
             const uint32_t plane = TL::NCS * sizeof(T);
-            mbar_expect_tx(bar, plane * (1 + (kb ? 0 : TL::CPLANES) + (X_IN ? 1 : 0)));
+            mbar_expect_tx(bar, plane * (2 + (kb ? 0 : TL::CPLANES) + (X_IN ? 1 : 0)) +
+                                    (XC ? (uint32_t)(TL::XW * TL::YW * sizeof(T)) : 0u));
             const int gx = x0 - TL::HX, gy = y0 - H;
             tma_load_3d(sb, &maps.b, bar, gx, gy, inst);
+            tma_load_3d(sd, &maps.d, bar, gx, gy, inst);
             if (!kb) tma_load_3d(sc, &maps.c, bar, gx, gy, L0 ? inst : 2 * inst);
             if (X_IN) tma_load_3d(sx, &maps.x, bar, gx, gy, inst);
+            if (XC) tma_load_3d(sxc, &maps.xc, bar, (x0 >> 1) - TL::XB, (y0 >> 1) - TL::YB, inst);
         }
+        const bool skip = skip_of();
+        if (!X_IN)
+            for (int i = threadIdx.x; i < TL::NCS; i += NTH) sx[i] = (T)0;
         if (kb) {  // meanwhile, kappa from bfloat16 (zero outside the domain, like the TMA fill)
             const __nv_bfloat16* k = k16 + (int64_t)inst * d.N;
             for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
                 const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
                 const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
-                sc[i] = (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
+                sc[i] = (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && !skip)
                             ? (T)__bfloat162float(k[(int64_t)gy * d.nx + gx])
                             : (T)0;
             }
         }
+        __syncthreads();  // the barrier's initialisation is visible to every thread
         tma_wait_tile(bar, st, inst);
         __syncthreads();
         if (threadIdx.x == 0) mbar_inval(bar);  // the next tile of this block initialises it again
+        return skip;
     } else {
+        if (skip_of()) return true;
         const int64_t off = (int64_t)inst * d.N;
         const T* c = cond + (L0 ? off : (int64_t)inst * 2 * d.N);
         for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
             const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
             const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
-            T vb = (T)0, vx = (T)0, vy = (T)0, vv = (T)0;
+            T vb = (T)0, vx = (T)0, vy = (T)0, vv = (T)0, vd = (T)0;
             if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
                 const int64_t g = (int64_t)gy * d.nx + gx;
                 vb = b[off + g];
+                vd = rd[off + g];
                 vx = (L0 && k16) ? (T)__bfloat162float(k16[off + g]) : c[g];
                 if (!L0) vy = c[d.N + g];
                 if (X_IN) vv = x_in[off + g];
             }
             sb[i] = vb;
+            sd[i] = vd;
             sc[i] = vx;
             if (!L0) sc[TL::NCS + i] = vy;
-            if (X_IN) sx[i] = vv;
+            sx[i] = vv;
+        }
+        if (XC) {
+            const int64_t offc = (int64_t)inst * dc.N;
+            for (int q = threadIdx.x; q < TL::XW * TL::YW; q += NTH) {
+                const int cy = q / TL::XW, cx = q - cy * TL::XW;
+                const int gy = (y0 >> 1) - TL::YB + cy, gx = (x0 >> 1) - TL::XB + cx;
+                sxc[q] = (gx >= 0 && gx < dc.nx && gy >= 0 && gy < dc.ny) ? xc[offc + (int64_t)gy * dc.nx + gx]
+                                                                          : (T)0;
+            }
         }
         __syncthreads();
-    }
-}
-
-// sd = 1 / (sum of the four conductances around the cell) for the staged cells inside the domain
-// and at least one cell from the staged edge, 0 elsewhere (the summation order of the diagonal is
-// that of the one-half-sweep kernels).
-template <typename T, bool L0, int H, int NTH>
-__device__ __forceinline__ void diag_inverse(T* sm, const Dims& d, int x0, int y0) {
-    using TL = Tile<T, L0, H>;
-    const T* scx = sm + TL::OFF_C;
-    const T* scy = L0 ? scx : scx + TL::NCS;
-    T* sd = sm + TL::OFF_D;
-    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
-        const int ly = i / TL::LXS, lxs = i - ly * TL::LXS;
-        const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
-        T v = (T)0;
-        if (ly >= 1 && lxs >= 1 && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
-            T diag = scx[i];
-            diag += scx[i - 1];
-            diag += scy[i];
-            diag += scy[i - TL::LXS];
-            v = (T)1 / diag;
-        }
-        sd[i] = v;
+        return false;
     }
 }
 
 // One half sweep of `colour` over the logical cells at distance >= lo from the staged edge:
-// x = (b + off) * sd.  Cells outside the domain have b = 0 and sd = 0 and stay 0.
-template <typename T, int LX, int LY, int LXS, int OX, int H, int NTH>
+// x = (b + off) * sd.  Cells outside the domain have b = 0 and sd = 0 and stay 0.  Tiles start
+// at even global coordinates (x0, y0 multiples of the tile extents) and the halo is the same on
+// both axes, so the colour of logical cell (lx, ly), (gx + gy) mod 2, is (lx + ly) mod 2.
+template <typename T, int LX, int LY, int LXS, int OX, int NTH>
 __device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* scx, const T* scy, T* sx, int lo,
-                                          int colour, int x0, int y0) {
+                                          int colour) {
     const int hi = LX - 1 - lo, hiy = LY - 1 - lo;
     const int half = (hi - lo + 2) >> 1;
     const int rows = hiy - lo + 1;
     for (int k = threadIdx.x; k < rows * half; k += NTH) {
         const int ry = k / half, j = k - ry * half;
         const int ly = lo + ry;
-        const int gy = y0 - H + ly;
-        const int gx_lo = x0 - H + lo;
-        const int p = (colour - gy - gx_lo) & 1;  // first lx in [lo, hi] with (gx + gy) % 2 == colour
-        const int lx = lo + p + 2 * j;
+        const int lx = lo + ((colour ^ ly ^ lo) & 1) + 2 * j;  // first lx >= lo of the colour, then every other
         if (lx > hi) continue;
         const int i = ly * LXS + lx + OX;
         T off = scx[i] * sx[i + 1];
@@ -163,11 +179,12 @@ __device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* sc
 }
 
 // Pre-smoothing of one tile from x = 0 (nu red->black sweeps), residual and restriction to bc.
-// Ends with a barrier, so that a block can go on with another tile.
-template <typename T, bool L0, int NU, bool TMA, int NTH>
-__device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b, T* x,
-                                         T* bc, const Dims& d, const Dims& dc, GkState* st, int inst, int x0,
-                                         int y0, const __nv_bfloat16* k16 = nullptr) {
+// Returns false when the block skips the tile (see stage).  Ends with a barrier, so that a block
+// can go on with another tile.
+template <typename T, bool L0, int NU, bool TMA, int SKIP, int NTH>
+__device__ __forceinline__ bool pre_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
+                                         const T* rd, T* x, T* bc, const Dims& d, const Dims& dc, GkState* st,
+                                         int inst, int x0, int y0, const __nv_bfloat16* k16 = nullptr) {
     constexpr int H = 2 * NU + 1;
     using TL = Tile<T, L0, H>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
@@ -177,13 +194,12 @@ __device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps,
     T* scy = L0 ? scx : scx + TL::NCS;
     T* sx = sm + TL::OFF_X;
     const T* sd = sm + TL::OFF_D;
-    for (int i = threadIdx.x; i < TL::NCS; i += NTH) sx[i] = (T)0;
-    stage<T, L0, H, TMA, false, NTH>(sm, maps, cond, b, nullptr, d, inst, x0, y0, st, k16);
-    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
-    __syncthreads();
+    if (stage<T, L0, H, TMA, false, false, SKIP, NTH>(sm, maps, cond, b, rd, nullptr, nullptr, d, dc, inst, x0, y0,
+                                                      st, k16))
+        return false;
 #pragma unroll
     for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, H, NTH>(sb, sd, scx, scy, sx, s + 1, s & 1, x0, y0);
+        half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, s & 1);
         __syncthreads();
     }
     // residual r = b - (diag x - off) on the tile, summed over the 2 x 2 children
@@ -217,28 +233,31 @@ __device__ __forceinline__ void pre_tile(unsigned char* smraw, const Maps& maps,
         if (gx < d.nx && gy < d.ny) x[off + (int64_t)gy * d.nx + gx] = sx[(H + ty) * LXS + H + tx + OX];
     }
     __syncthreads();
+    return true;
 }
 
 template <typename T, bool L0, int NU, bool TMA, int NTH>
 __global__ void __launch_bounds__(NTH) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
-                                                  const T* __restrict__ b, T* __restrict__ x, T* __restrict__ bc,
-                                                  Dims d, Dims dc, GkState* st, const __nv_bfloat16* __restrict__ k16) {
+                                                  const T* __restrict__ b, const T* __restrict__ rd,
+                                                  T* __restrict__ x, T* __restrict__ bc, Dims d, Dims dc, GkState* st,
+                                                  const __nv_bfloat16* __restrict__ k16) {
     extern __shared__ __align__(128) unsigned char smraw[];
     pdl_grid_sync();
-    if (parked(st[blockIdx.z]) || st[blockIdx.z].frozen >= 2) return;
-    pre_tile<T, L0, NU, TMA, NTH>(smraw, maps, cond, b, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX, blockIdx.y * MTY,
-                                  k16);
+    pre_tile<T, L0, NU, TMA, 1, NTH>(smraw, maps, cond, b, rd, x, bc, d, dc, st, blockIdx.z, blockIdx.x * MTX,
+                                     blockIdx.y * MTY, k16);
 }
 
 // One tile of x_out = smooth(x_in + P xc) with nu black->red sweeps (x_in and x_out must differ:
-// blocks read neighbouring tiles of x_in as halo).  Returns this thread's share of x_out . b over
-// the tile when DOT.  Ends with a barrier.
-template <typename T, bool L0, int NU, bool DOT, bool TMA, int NTH>
-__device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
-                                       const T* x_in, T* x_out, const T* xc, const Dims& d, const Dims& dc,
-                                       GkState* st, int inst, int x0, int y0, const __nv_bfloat16* k16 = nullptr) {
+// blocks read neighbouring tiles of x_in as halo).  Returns false when the block skips the tile
+// (see stage); *part is this thread's share of x_out . b over the tile when DOT.  Ends with a
+// barrier.
+template <typename T, bool L0, int NU, bool DOT, bool TMA, int SKIP, int NTH>
+__device__ __forceinline__ bool post_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
+                                          const T* rd, const T* x_in, T* x_out, const T* xc, const Dims& d,
+                                          const Dims& dc, GkState* st, int inst, int x0, int y0, T* part_out,
+                                          const __nv_bfloat16* k16 = nullptr) {
     constexpr int H = 2 * NU;
-    using TL = Tile<T, L0, H>;
+    using TL = Tile<T, L0, H, true>;
     constexpr int LXS = TL::LXS, OX = TL::OX;
     T* sm = reinterpret_cast<T*>(smraw);
     T* sb = sm;
@@ -246,31 +265,19 @@ __device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, c
     T* scy = L0 ? scx : scx + TL::NCS;
     T* sx = sm + TL::OFF_X;
     const T* sd = sm + TL::OFF_D;
-    // P xc for this thread's staged cells (inside the domain), loaded before the tile so that the
-    // loads overlap the staging
-    constexpr int NPT = (TL::NCS + NTH - 1) / NTH;
-    const int64_t offc = (int64_t)inst * dc.N;
-    T xcv[NPT];
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) {
-        const int i = threadIdx.x + q * NTH;
+    const T* sxc = sm + TL::OFF_XC;
+    if (stage<T, L0, H, TMA, true, true, SKIP, NTH>(sm, maps, cond, b, rd, x_in, xc, d, dc, inst, x0, y0, st, k16))
+        return false;
+    // + P xc.  The extents are even (2^(levels-1) divides them), so a cell outside the domain has
+    // its parent outside the coarse grid: it adds the zero fill and stays 0.
+    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
         const int ly = i / LXS, lxs = i - ly * LXS;
-        const int gy = y0 - H + ly, gx = x0 - TL::HX + lxs;
-        xcv[q] = (i < TL::NCS && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny)
-                     ? xc[offc + (int64_t)(gy >> 1) * dc.nx + (gx >> 1)]
-                     : (T)0;
-    }
-    stage<T, L0, H, TMA, true, NTH>(sm, maps, cond, b, x_in, d, inst, x0, y0, st, k16);
-    diag_inverse<T, L0, H, NTH>(sm, d, x0, y0);
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) {  // + P xc (cells outside the domain add 0 and stay 0)
-        const int i = threadIdx.x + q * NTH;
-        if (i < TL::NCS) sx[i] = sx[i] + xcv[q];
+        sx[i] = sx[i] + sxc[((ly + (H & 1)) >> 1) * TL::XW + ((lxs + 2 * TL::XB - TL::HX) >> 1)];
     }
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, H, NTH>(sb, sd, scx, scy, sx, s + 1, 1 - (s & 1), x0, y0);
+        half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, 1 - (s & 1));
         __syncthreads();
     }
     const int64_t off = (int64_t)inst * d.N;
@@ -285,23 +292,25 @@ __device__ __forceinline__ T post_tile(unsigned char* smraw, const Maps& maps, c
         }
     }
     __syncthreads();
-    return part;
+    *part_out = part;
+    return true;
 }
 
 // DOT: also alpha = sqrt(x_out . b) and the rotations (finest level of the last V-cycle:
 // x_out = v~, b = p~).
 template <typename T, bool L0, int NU, bool DOT, bool INIT, bool TMA, int NTH>
 __global__ void __launch_bounds__(NTH) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
-                                                   const T* __restrict__ b, const T* __restrict__ x_in,
-                                                   T* __restrict__ x_out, const T* __restrict__ xc, Dims d, Dims dc,
-                                                   GkState* st, Hist hist, Red red,
-                                                   const __nv_bfloat16* __restrict__ k16) {
+                                                   const T* __restrict__ b, const T* __restrict__ rd,
+                                                   const T* __restrict__ x_in, T* __restrict__ x_out,
+                                                   const T* __restrict__ xc, Dims d, Dims dc, GkState* st, Hist hist,
+                                                   Red red, const __nv_bfloat16* __restrict__ k16) {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int inst = blockIdx.z;
     pdl_grid_sync();
-    if (DOT ? inner_off(st[inst]) : (parked(st[inst]) || st[inst].frozen >= 2)) return;
-    const T part = post_tile<T, L0, NU, DOT, TMA, NTH>(smraw, maps, cond, b, x_in, x_out, xc, d, dc, st, inst,
-                                                 blockIdx.x * MTX, blockIdx.y * MTY, k16);
+    T part;
+    if (!post_tile<T, L0, NU, DOT, TMA, DOT ? 2 : 1, NTH>(smraw, maps, cond, b, rd, x_in, x_out, xc, d, dc, st, inst,
+                                                          blockIdx.x * MTX, blockIdx.y * MTY, &part, k16))
+        return;
     if (DOT) {
         const int nblk = gridDim.x * gridDim.y;
         double tot;
@@ -341,8 +350,9 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
         const Dims d = tl.d[q], dc = tl.d[q + 1];
         const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);
         for (int t = rank; t < nt; t += CS)
-            pre_tile<T, false, NU, TMA, TNT>(smraw, tm.pre[q], (const T*)tl.cond[q], (const T*)tl.b[q], (T*)tl.x[q],
-                                             (T*)tl.b[q + 1], d, dc, st, inst, (t % tx) * MTX, (t / tx) * MTY);
+            pre_tile<T, false, NU, TMA, 0, TNT>(smraw, tm.pre[q], (const T*)tl.cond[q], (const T*)tl.b[q],
+                                             (const T*)tl.rd[q], (T*)tl.x[q], (T*)tl.b[q + 1], d, dc, st, inst,
+                                             (t % tx) * MTX, (t / tx) * MTY);
         tail_phase_barrier();
     }
     {
@@ -367,52 +377,60 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
         const Dims d = tl.d[q], dc = tl.d[q + 1];
         const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);
         for (int t = rank; t < nt; t += CS)
-            post_tile<T, false, NU, false, TMA, TNT>(smraw, tm.post[q], (const T*)tl.cond[q], (const T*)tl.b[q],
-                                                     (const T*)tl.x[q], (T*)tl.x2[q], (const T*)tl.x2[q + 1], d, dc,
-                                                     st, inst, (t % tx) * MTX, (t / tx) * MTY);
+{
+            T unused;
+            post_tile<T, false, NU, false, TMA, 0, TNT>(smraw, tm.post[q], (const T*)tl.cond[q], (const T*)tl.b[q],
+                                                        (const T*)tl.rd[q], (const T*)tl.x[q], (T*)tl.x2[q],
+                                                        (const T*)tl.x2[q + 1], d, dc, st, inst, (t % tx) * MTX,
+                                                        (t / tx) * MTY, &unused);
+        }
         if (q > 0) tail_phase_barrier();
     }
 }
 
 // TMA maps for one launch; false when the layout rules are not met (plain loads instead).
-template <typename T, bool L0, int H>
-static bool make_maps(Maps& m, const T* cond, const T* b, const T* x_in, const Dims& d, int B) {
-    using TL = Tile<T, L0, H>;
+// xc (post-smoothing): the coarse-level iterate, with the coarse dimensions dc.
+template <typename T, bool L0, int H, bool XC>
+static bool make_maps(Maps& m, const T* cond, const T* b, const T* rd, const T* x_in, const T* xc, const Dims& d,
+                      const Dims& dc, int B) {
+    using TL = Tile<T, L0, H, XC>;
     const int esz = (int)sizeof(T);
     bool ok = tma_map_3d(&m.b, b, esz, d.nx, d.ny, B, TL::LXS, TL::LY, 1);
+    ok = ok && tma_map_3d(&m.d, rd, esz, d.nx, d.ny, B, TL::LXS, TL::LY, 1);
     ok = ok && tma_map_3d(&m.c, cond, esz, d.nx, d.ny, (int64_t)B * TL::CPLANES, TL::LXS, TL::LY, TL::CPLANES);
     if (x_in) ok = ok && tma_map_3d(&m.x, x_in, esz, d.nx, d.ny, B, TL::LXS, TL::LY, 1);
+    if (XC) ok = ok && tma_map_3d(&m.xc, xc, esz, dc.nx, dc.ny, B, TL::XW, TL::YW, 1);
     return ok;
 }
 
 template <typename T, bool L0, int NU>
-static void pre_launch(const T* cond, const T* b, T* x, T* bc, Dims d, Dims dc, int B, GkState* st, cudaStream_t s,
-                       const __nv_bfloat16* k16) {
+static void pre_launch(const T* cond, const T* b, const T* rd, T* x, T* bc, Dims d, Dims dc, int B, GkState* st,
+                       cudaStream_t s, const __nv_bfloat16* k16) {
     constexpr int H = 2 * NU + 1;
     const size_t smem = Tile<T, L0, H>::bytes();
     Maps maps;
-    const bool tma = tma_enabled() && make_maps<T, L0, H>(maps, cond, b, nullptr, d, B);
+    const bool tma = tma_enabled() && make_maps<T, L0, H, false>(maps, cond, b, rd, nullptr, nullptr, d, dc, B);
     constexpr int NTH = L0 ? MNT : CNT;
     auto kfn = tma ? k_mg_pre2d<T, L0, NU, true, NTH> : k_mg_pre2d<T, L0, NU, false, NTH>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
-    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, x, bc, d, dc, st, k16);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, rd, x, bc, d, dc, st, k16);
 }
 
 template <typename T, bool L0, int NU, bool DOT, bool INIT>
-static void post_launch(const T* cond, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int B,
-                        GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16) {
+static void post_launch(const T* cond, const T* b, const T* rd, const T* xi, T* x, const T* xc, Dims d, Dims dc,
+                        int B, GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16) {
     constexpr int H = 2 * NU;
-    const size_t smem = Tile<T, L0, H>::bytes();
+    const size_t smem = Tile<T, L0, H, true>::bytes();
     Maps maps;
-    const bool tma = tma_enabled() && make_maps<T, L0, H>(maps, cond, b, xi, d, B);
+    const bool tma = tma_enabled() && make_maps<T, L0, H, true>(maps, cond, b, rd, xi, xc, d, dc, B);
     constexpr int NTH = L0 ? MNT : CNT;
     auto kfn = tma ? k_mg_post2d<T, L0, NU, DOT, INIT, true, NTH> : k_mg_post2d<T, L0, NU, DOT, INIT, false, NTH>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((d.nx + MTX - 1) / MTX, (d.ny + MTY - 1) / MTY, B);
     if (DOT && (int64_t)grid.x * grid.y > red.max_blocks)
         throw std::runtime_error("mg_post2d: too many blocks for the reduction scratch");
-    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, xi, x, xc, d, dc, st, hist, red, k16);
+    launch_k(kfn, grid, dim3(NTH), smem, s, maps, cond, b, rd, xi, x, xc, d, dc, st, hist, red, k16);
 }
 
 bool mg2d_supported(int ndim, int nu) { return ndim == 2 && nu >= 1 && nu <= 3; }
@@ -423,7 +441,7 @@ constexpr int TAIL_CS = 16;  // blocks per cluster (non-portable size; the drive
 // a phase then run in parallel instead of sharing one SM's issue slots).
 template <typename T, int NU>
 static size_t tail_smem(int nc) {
-    return std::max({Tile<T, false, 2 * NU + 1>::bytes(), Tile<T, false, 2 * NU>::bytes(), sizeof(T) * (size_t)nc,
+    return std::max({Tile<T, false, 2 * NU + 1>::bytes(), Tile<T, false, 2 * NU, true>::bytes(), sizeof(T) * (size_t)nc,
                      (size_t)120 * 1024});
 }
 
@@ -505,8 +523,10 @@ static void tail_launch(const TailLevels& tl, const T* X, int nc, int B, GkState
     for (int q = 0; q + 1 < tl.n && tma; ++q) {
         const T* c = (const T*)tl.cond[q];
         const T* b = (const T*)tl.b[q];
-        tma = make_maps<T, false, 2 * NU + 1>(tm.pre[q], c, b, nullptr, tl.d[q], B) &&
-              make_maps<T, false, 2 * NU>(tm.post[q], c, b, (const T*)tl.x[q], tl.d[q], B);
+        const T* rd = (const T*)tl.rd[q];
+        tma = make_maps<T, false, 2 * NU + 1, false>(tm.pre[q], c, b, rd, nullptr, nullptr, tl.d[q], tl.d[q + 1], B) &&
+              make_maps<T, false, 2 * NU, true>(tm.post[q], c, b, rd, (const T*)tl.x[q], (const T*)tl.x2[q + 1],
+                                                tl.d[q], tl.d[q + 1], B);
     }
     cudaLaunchAttribute at[2];
     const cudaLaunchConfig_t cfg = tail_config<T, NU>(B, tail_smem<T, NU>(nc), s, at);
@@ -532,13 +552,13 @@ template void mg2d_tail<float>(const TailLevels&, int, const float*, int, int, G
 template void mg2d_tail<double>(const TailLevels&, int, const double*, int, int, GkState*, cudaStream_t);
 
 template <typename T>
-void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,
-              cudaStream_t s, const __nv_bfloat16* k16) {
+void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc, Dims d, Dims dc, int nu, int B,
+              GkState* st, cudaStream_t s, const __nv_bfloat16* k16) {
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
 #define PRE_CASE(NU_)                                                                   \
     case NU_:                                                                           \
-        if (is_kappa) pre_launch<T, true, NU_>(cond, b, x, bc, d, dc, B, st, s, k16);  \
-        else pre_launch<T, false, NU_>(cond, b, x, bc, d, dc, B, st, s, nullptr);      \
+        if (is_kappa) pre_launch<T, true, NU_>(cond, b, rd, x, bc, d, dc, B, st, s, k16);  \
+        else pre_launch<T, false, NU_>(cond, b, rd, x, bc, d, dc, B, st, s, nullptr);      \
         break;
     switch (nu) {
         PRE_CASE(1)
@@ -552,15 +572,16 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dim
 }
 
 template <typename T>
-void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int nu,
-               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16) {
+void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* xi, T* x, const T* xc, Dims d,
+               Dims dc, int nu, int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s,
+               const __nv_bfloat16* k16) {
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
 #define POST_CASE(NU_)                                                                                           \
     case NU_:                                                                                                    \
-        if (!is_kappa) post_launch<T, false, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, nullptr); \
-        else if (dot == 0) post_launch<T, true, NU_, false, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
-        else if (dot == 1) post_launch<T, true, NU_, true, true>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
-        else post_launch<T, true, NU_, true, false>(cond, b, xi, x, xc, d, dc, B, st, hist, red, s, k16);             \
+        if (!is_kappa) post_launch<T, false, NU_, false, false>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s, nullptr); \
+        else if (dot == 0) post_launch<T, true, NU_, false, false>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
+        else if (dot == 1) post_launch<T, true, NU_, true, true>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s, k16); \
+        else post_launch<T, true, NU_, true, false>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s, k16);             \
         break;
     switch (nu) {
         POST_CASE(1)
@@ -573,13 +594,14 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, cons
     kfinish(s);
 }
 
-template void mg2d_pre<float>(const float*, bool, const float*, float*, float*, Dims, Dims, int, int, GkState*,
-                              cudaStream_t, const __nv_bfloat16*);
-template void mg2d_pre<double>(const double*, bool, const double*, double*, double*, Dims, Dims, int, int, GkState*,
-                               cudaStream_t, const __nv_bfloat16*);
-template void mg2d_post<float>(const float*, bool, const float*, const float*, float*, const float*, Dims, Dims, int,
-                               int, int, GkState*, Hist, Red, cudaStream_t, const __nv_bfloat16*);
-template void mg2d_post<double>(const double*, bool, const double*, const double*, double*, const double*, Dims, Dims,
-                                int, int, int, GkState*, Hist, Red, cudaStream_t, const __nv_bfloat16*);
+template void mg2d_pre<float>(const float*, bool, const float*, const float*, float*, float*, Dims, Dims, int, int,
+                              GkState*, cudaStream_t, const __nv_bfloat16*);
+template void mg2d_pre<double>(const double*, bool, const double*, const double*, double*, double*, Dims, Dims, int,
+                               int, GkState*, cudaStream_t, const __nv_bfloat16*);
+template void mg2d_post<float>(const float*, bool, const float*, const float*, const float*, float*, const float*,
+                               Dims, Dims, int, int, int, GkState*, Hist, Red, cudaStream_t, const __nv_bfloat16*);
+template void mg2d_post<double>(const double*, bool, const double*, const double*, const double*, double*,
+                                const double*, Dims, Dims, int, int, int, GkState*, Hist, Red, cudaStream_t,
+                                const __nv_bfloat16*);
 
 }  // namespace plsqr

@@ -168,11 +168,19 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     pdl_grid_sync();
     const int plane = blockIdx.z;
     const int inst = plane / d.nz;
-    if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * BTX, y0 = blockIdx.y * BTY;
+    if constexpr (TMA) {  // the copy goes first; the instance state is read while it is in flight
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            mbar_expect_tx(&bar, LX * LY * sizeof(float));
+            tma_load_3d(sin, &map_in, &bar, x0 - R, y0 - R, plane);
+        }
+    }
+    const bool skip = EPI != EPI_PLAIN && inner_off(st[inst]);  // the same in every thread
+    if (!TMA && skip) return;
     if (PI)  // made visible by the barrier that follows the tile staging
         for (int k = tid; k < 2 * (2 * R + 1); k += BNT) stap[k] = tapt[(int64_t)inst * 2 * (2 * R + 1) + k];
-    const int x0 = blockIdx.x * BTX, y0 = blockIdx.y * BTY;
     const int64_t plane_off = (int64_t)plane * d.nx * d.ny;
     const int64_t mask_off = (int64_t)(plane - inst * d.nz) * d.nx * d.ny;
     // this thread's outputs: column c, rows srow..srow+7 of the tile; their previous values
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
     for (int o = 0; o < 8; ++o) {
         pv[o] = wv[o] = fv[o] = 0.f;
         const int gy = y0 + srow + o;
-        if (gy < d.ny && ogx < d.nx) {
+        if (gy < d.ny && ogx < d.nx && !skip) {
             const int64_t gi = plane_off + (int64_t)gy * d.nx + ogx;
             if (EPI == EPI_FWD) pv[o] = prev[gi];
             if (EPI == EPI_ADJ) pv[o] = out[gi];
@@ -195,13 +203,9 @@ __global__ void __launch_bounds__(BNT) k_blur2d_rb(const __grid_constant__ CUten
         }
     }
     if constexpr (TMA) {
-        if (tid == 0) mbar_init(&bar, 1);
-        __syncthreads();
-        if (tid == 0) {
-            mbar_expect_tx(&bar, LX * LY * sizeof(float));
-            tma_load_3d(sin, &map_in, &bar, x0 - R, y0 - R, plane);
-        }
+        __syncthreads();  // the barrier's initialisation is visible to every thread
         tma_wait_tile(&bar, st, inst);
+        if (skip) return;
     } else {
         for (int i = tid; i < LY * LX; i += BNT) {
             const int r = i / LX, c = i - r * LX;

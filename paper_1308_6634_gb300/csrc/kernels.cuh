@@ -86,6 +86,11 @@ void diffusivity(const T* f, T* kappa, Dims d, int B, GkState* st, Hist hist, do
 template <typename T>
 void mg_coarsen(const T* cf, bool fine_is_kappa, T* cc, Dims df, Dims dc, int B, cudaStream_t s,
                 const __nv_bfloat16* k16 = nullptr);
+// rd = 1 / diagonal of a 2D level's operator, in the smoother's summation order (once per outer
+// step; the temporally blocked V-cycle kernels stage it)
+template <typename T>
+void mg_rdiag2d(const T* cond, bool is_kappa, T* rd, Dims d, int B, cudaStream_t s,
+                const __nv_bfloat16* k16 = nullptr);
 // kappa widened to bfloat16 storage (round to nearest even)
 void to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
 template <typename T>
@@ -127,14 +132,15 @@ bool mg2d_supported(int ndim, int nu);
 int mg2d_tail_level(const Dims* d, int L, int nu, size_t elem, int nc);
 template <typename T>
 void mg2d_tail(const TailLevels& tl, int nu, const T* X, int nc, int B, GkState* st, cudaStream_t s);
-// x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x)
+// x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x).  rd: 1 / diagonal (mg_rdiag2d)
 template <typename T>
-void mg2d_pre(const T* cond, bool is_kappa, const T* b, T* x, T* bc, Dims d, Dims dc, int nu, int B, GkState* st,
-              cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
+void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc, Dims d, Dims dc, int nu, int B,
+              GkState* st, cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
 // x = nu black->red sweeps from xi + P xc.  dot: 0 none, 1 alpha_1 (init), 2 alpha and rotations
 template <typename T>
-void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* xi, T* x, const T* xc, Dims d, Dims dc, int nu,
-               int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
+void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* xi, T* x, const T* xc, Dims d,
+               Dims dc, int nu, int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s,
+               const __nv_bfloat16* k16 = nullptr);
 
 // ---- Golub-Kahan scalars and updates ----
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);

@@ -51,6 +51,7 @@ struct Level {
     char* b = nullptr;     // [B][N_l]
     char* x = nullptr;     // pre-smoothed iterate (fused path) or the V-cycle result (generic path)
     char* x2 = nullptr;    // V-cycle result of this level (fused path)
+    char* rd = nullptr;    // [B][N_l] 1 / diagonal (2D levels above the coarsest)
 };
 
 }  // namespace
@@ -217,6 +218,8 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += esz * B * (N + m);          // tmp (N), tmpm (m)
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
     for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
+    if (c->ndim == 2)
+        for (int l = 0; l + 1 < pl.L; ++l) b += esz * B * pl.level_N[l];  // reciprocal diagonals
     if (pl.gth || pl.gthw) {
         b += sizeof(float) * B * (size_t)pl.nc * 2 * gth_stride(pl.bw);
         b += sizeof(float) * B * (size_t)pl.nc * pl.nc;
@@ -306,9 +309,9 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
     const bool isk = l == 0;
     T* xpre = l == 0 ? P<T>(h->tmp) : P<T>(Lv.x);
     const Level& C = h->lv[l + 1];
-    mg2d_pre<T>(cond, isk, b, xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s, isk ? K16(h) : nullptr);
+    mg2d_pre<T>(cond, isk, b, P<T>(Lv.rd), xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s, isk ? K16(h) : nullptr);
     vcycle_fused<T>(h, l + 1, P<T>(C.b), P<T>(C.x2), B, 0, s);
-    mg2d_post<T>(cond, isk, b, xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s,
+    mg2d_post<T>(cond, isk, b, P<T>(Lv.rd), xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s,
                  isk ? K16(h) : nullptr);
 }
 
@@ -337,6 +340,10 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     for (int l = 0; l + 1 < h->L; ++l)
         mg_coarsen<T>(l == 0 ? P<T>(h->kappa) : P<T>(h->lv[l].cond), l == 0, P<T>(h->lv[l + 1].cond), h->lv[l].d,
                       h->lv[l + 1].d, B, s, l == 0 ? K16(h) : nullptr);
+    if (use_fused_mg(h))
+        for (int l = 0; l + 1 < h->L; ++l)
+            mg_rdiag2d<T>(l == 0 ? P<T>(h->kappa) : P<T>(h->lv[l].cond), l == 0, P<T>(h->lv[l].rd), h->lv[l].d, B, s,
+                          l == 0 ? K16(h) : nullptr);
     const int lc = h->L - 1;
     const T* cc = lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond);
     if (h->gth) {
@@ -709,6 +716,8 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
             h->lv[l].x = dalloc(h, e * B * Nl);
             h->lv[l].x2 = dalloc(h, e * B * Nl);
         }
+        if (h->d.ndim == 2)
+            for (int l = 0; l + 1 < h->L; ++l) h->lv[l].rd = dalloc(h, e * B * h->lv[l].d.N);
         {
             Dims dl[16];
             for (int l = 0; l < h->L; ++l) dl[l] = h->lv[l].d;
@@ -717,6 +726,7 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
             for (int q = 0; q < h->tail.n; ++q) {
                 const Level& Lv = h->lv[h->tail_lc + q];
                 h->tail.cond[q] = Lv.cond;
+                h->tail.rd[q] = Lv.rd;
                 h->tail.b[q] = Lv.b;
                 h->tail.x[q] = Lv.x;
                 h->tail.x2[q] = Lv.x2;
