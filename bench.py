@@ -152,7 +152,8 @@ class ClockSampler:
 
 
 # the kernels of the roofline classes (blur, V-cycle) and what they include
-TRAFFIC_SOURCES = ("common.cuh", "kernels.cuh", "tma.cuh", "k_ops.cu", "k_mg.cu", "k_mg2d.cu")
+TRAFFIC_SOURCES = ("common.cuh", "kernels.cuh", "tma.cuh", "k_ops.cu", "k_mg.cu", "k_mg2d.cu", "k_mg2d_alt.cu",
+                   "k_mg2d_impl.cuh")
 
 
 def kernel_source_hash():
@@ -441,6 +442,7 @@ def main():
                        "n_inner": W.n_inner, "reg": W.reg, "T": W.T, "tau": W.tau, "levels": W.levels,
                        "sweeps": W.nu, "cycles": W.cycles, "batch": B, "parallelism": f"replicas x{world}",
                        "kappa": "bf16" if args.kappa_bf16 else W.precision,
+                       "tiles": [list(S.tile_shape(l)[1:]) for l in range(W.levels - 1) if S.tile_shape(l)[0] >= 0],
                        "l2": "flushed between steps" if flush is not None else "working set larger than L2"},
             "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
             "gpu_launches": int(launches_per_step * args.steps),

@@ -185,6 +185,26 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
 
+/* ---- V-cycle tile shapes ------------------------------------------------------------------------
+ * The 2D V-cycle (Sec. 4.2 priorconditioner: red-black Gauss-Seidel smoothing, restriction,
+ * prolongation on each level above the coarsest) runs each level as tiles staged in shared memory.
+ * Several tile shapes are compiled in; every shape gives the same result bit for bit, only the
+ * speed differs.  By default the first solve of a handle tunes them (env PLSQR_AUTOTUNE=0: keep
+ * shape 0 everywhere): for each level it times CUDA-graph replays of that level's smoothing
+ * launches with each shape and the handle's full batch, and keeps the fastest; choices are cached
+ * per process for levels of the same size, batch, precision and sweep count.
+ *
+ * plsqr_autotune: tune now (fresh != 0: measure again instead of using the cache).  Uses the
+ *   handle's scratch buffers: not while slots are in use (PLSQR_E_STATE).
+ * plsqr_set_tile_shape: level 0 .. mg_levels-2 takes shape `shape` (0 is the default; level 0 has
+ *   its own list); marks the handle as tuned.  PLSQR_E_INVALID for an unknown level or shape.
+ * plsqr_tile_shape: the shape of a level (-1 and zero extents where the level is not run by the
+ *   tiled 2D kernels: 3D handles, the coarsest level), its tile extents and threads per block.
+ *   Any output pointer may be NULL. */
+int plsqr_autotune(plsqr_handle h, int32_t fresh);
+int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape);
+int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx, int32_t* ty, int32_t* threads);
+
 /* ---- bfloat16 kappa ----------------------------------------------------------------------------
  * on != 0: later solves keep the diffusivity kappa (eq. 1.13) only in bfloat16 (8 significant bits,
  * rounded to nearest even from the single-precision value); the finest level of the V-cycle and

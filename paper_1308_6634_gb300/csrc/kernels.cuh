@@ -132,15 +132,19 @@ bool mg2d_supported(int ndim, int nu);
 int mg2d_tail_level(const Dims* d, int L, int nu, size_t elem, int nc);
 template <typename T>
 void mg2d_tail(const TailLevels& tl, int nu, const T* X, int nc, int B, GkState* st, cudaStream_t s);
-// x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x).  rd: 1 / diagonal (mg_rdiag2d)
+// x = nu red->black sweeps from 0 on M_l x = b; bc = R (b - M_l x).  rd: 1 / diagonal (mg_rdiag2d).
+// shape: the tile shape (mg2d_shape), 0 the default; every shape gives the same result.
 template <typename T>
 void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc, Dims d, Dims dc, int nu, int B,
-              GkState* st, cudaStream_t s, const __nv_bfloat16* k16 = nullptr);
+              GkState* st, cudaStream_t s, const __nv_bfloat16* k16 = nullptr, int shape = 0);
 // x = nu black->red sweeps from xi + P xc.  dot: 0 none, 1 alpha_1 (init), 2 alpha and rotations
 template <typename T>
 void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* xi, T* x, const T* xc, Dims d,
                Dims dc, int nu, int B, int dot, GkState* st, Hist hist, Red red, cudaStream_t s,
-               const __nv_bfloat16* k16 = nullptr);
+               const __nv_bfloat16* k16 = nullptr, int shape = 0);
+// Tile shape `id` of the finest (fine) or the coarser levels: extents and threads per block; false
+// past the last shape.
+bool mg2d_shape(bool fine, int id, int* tx, int* ty, int* nth);
 
 // ---- Golub-Kahan scalars and updates ----
 void set_params(GkState* st, const SolveParams* prm, int B, bool reset_outer, cudaStream_t s);

@@ -23,6 +23,7 @@
 
 #include "../../include/plsqr.h"
 #include "kernels.cuh"
+#include "tma.cuh"
 
 using namespace plsqr;
 
@@ -111,6 +112,8 @@ struct plsqr_ctx {
     __nv_bfloat16* kappa16 = nullptr;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
+    int tile[16] = {};        // tile shape of each 2D V-cycle level (mg2d_shape ids; 0 the default)
+    bool tuned = false;       // tile shapes chosen (autotuned or set)
     TailLevels tail{};
     bool no_fuse_update = false;  // PLSQR_FUSE_UPDATE=0: separate update kernel (comparisons)
     Profiler prof;
@@ -309,10 +312,11 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
     const bool isk = l == 0;
     T* xpre = l == 0 ? P<T>(h->tmp) : P<T>(Lv.x);
     const Level& C = h->lv[l + 1];
-    mg2d_pre<T>(cond, isk, b, P<T>(Lv.rd), xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s, isk ? K16(h) : nullptr);
+    mg2d_pre<T>(cond, isk, b, P<T>(Lv.rd), xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, h->st, s, isk ? K16(h) : nullptr,
+                h->tile[l]);
     vcycle_fused<T>(h, l + 1, P<T>(C.b), P<T>(C.x2), B, 0, s);
     mg2d_post<T>(cond, isk, b, P<T>(Lv.rd), xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, dot, h->st, hist_of(h), h->red, s,
-                 isk ? K16(h) : nullptr);
+                 isk ? K16(h) : nullptr, h->tile[l]);
 }
 
 bool use_fused_mg(const plsqr_ctx* h) { return mg2d_supported(h->d.ndim, h->nu) && h->L > 1 && !h->generic_mg; }
@@ -425,8 +429,131 @@ void ensure_hist(plsqr_ctx* h, int n_outer, int n_inner) {
     }
 }
 
+// ---- tile-shape autotuner ----------------------------------------------------------------------
+//
+// Every tile shape gives the same V-cycle bit for bit, so the choice is free: for each 2D level
+// above the coarsest the tuner captures a CUDA graph of 8 pre/post-smoothing pairs of that level
+// with each shape (the handle's full batch, scratch buffers, a zeroed instance state), replays it,
+// and keeps the fastest.  The kernels do the same work whatever the values they read.  Choices
+// are cached per process by the level's size, the batch, the element size, nu and the kappa
+// storage, so handles of the same layout tune once.
+
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+std::map<std::tuple<int, int, int, int, int, int, int>, int>& tune_cache() {
+    static std::map<std::tuple<int, int, int, int, int, int, int>, int> c;
+    return c;
+}
+
+template <typename T>
+void autotune(plsqr_ctx* h, bool fresh = false) {
+    h->tuned = true;
+    if (!use_fused_mg(h) || !tma_enabled()) return;
+    const int B = h->B;
+    cudaStream_t s = h->stream;
+    Profiler* prev = current_profiler();
+    current_profiler() = nullptr;  // tuning launches are neither profiled nor counted
+    GkState* st0 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        current_profiler() = prev;
+        if (st0) cudaFree(st0);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    try {
+        ck(cudaStreamSynchronize(h->user_stream), "autotune");
+        ck(cudaMalloc(&st0, sizeof(GkState) * B), "cudaMalloc");
+        ck(cudaMemsetAsync(st0, 0, sizeof(GkState) * B, s), "memset");
+        ck(cudaEventCreate(&e0), "cudaEventCreate");
+        ck(cudaEventCreate(&e1), "cudaEventCreate");
+        for (int l = 0; l + 1 < h->L; ++l) {
+            const Level& Lv = h->lv[l];
+            const Level& C = h->lv[l + 1];
+            const bool isk = l == 0;
+            const auto key = std::make_tuple(Lv.d.nx, Lv.d.ny, B, (int)h->esz, h->nu, isk ? 1 : 0, h->kbf16 ? 1 : 0);
+            if (!fresh) {
+                std::lock_guard<std::mutex> lk(tune_mutex());
+                auto it = tune_cache().find(key);
+                if (it != tune_cache().end()) {
+                    h->tile[l] = it->second;
+                    continue;
+                }
+            }
+            const T* cond = isk ? P<T>(h->kappa) : P<T>(Lv.cond);
+            T* b = isk ? P<T>(h->p) : P<T>(Lv.b);
+            T* xpre = isk ? P<T>(h->tmp) : P<T>(Lv.x);
+            T* x = isk ? P<T>(h->v) : P<T>(Lv.x2);
+            const int64_t n = (int64_t)B * Lv.d.N, nc = (int64_t)B * C.d.N;
+            ck(cudaMemsetAsync(b, 0, sizeof(T) * n, s), "memset");
+            ck(cudaMemsetAsync(Lv.rd, 0, sizeof(T) * n, s), "memset");
+            ck(cudaMemsetAsync(C.x2, 0, sizeof(T) * nc, s), "memset");
+            if (!isk) ck(cudaMemsetAsync(Lv.cond, 0, sizeof(T) * 2 * n, s), "memset");
+            int best = 0;
+            float best_ms = 0.f;
+            for (int id = 0;; ++id) {
+                int tx, ty, nth;
+                if (!mg2d_shape(isk, id, &tx, &ty, &nth)) break;
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+                try {
+                    for (int r = 0; r < 8; ++r) {
+                        mg2d_pre<T>(cond, isk, b, P<T>(Lv.rd), xpre, P<T>(C.b), Lv.d, C.d, h->nu, B, st0, s,
+                                    isk ? K16(h) : nullptr, id);
+                        mg2d_post<T>(cond, isk, b, P<T>(Lv.rd), xpre, x, P<T>(C.x2), Lv.d, C.d, h->nu, B, 0, st0,
+                                     hist_of(h), h->red, s, isk ? K16(h) : nullptr, id);
+                    }
+                } catch (...) {
+                    cudaStreamEndCapture(s, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                ck(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+                const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                ck(ie, "cudaGraphInstantiate");
+                float ms = 0.f;
+                cudaError_t e = cudaGraphLaunch(exec, s);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                cudaGraphExecDestroy(exec);
+                ck(e, "autotune");
+                if (id == 0 || ms < best_ms) {
+                    best = id;
+                    best_ms = ms;
+                }
+            }
+            h->tile[l] = best;
+            std::lock_guard<std::mutex> lk(tune_mutex());
+            tune_cache()[key] = best;
+        }
+        ck(cudaStreamSynchronize(s), "autotune");
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+bool autotune_enabled() {
+    const char* e = std::getenv("PLSQR_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+template <typename T>
+void maybe_autotune(plsqr_ctx* h) {
+    if (!h->tuned && autotune_enabled()) autotune<T>(h);
+}
+
 template <typename T>
 void run_outer_steps(plsqr_ctx* h, int B, int n_outer, int n_inner) {
+    maybe_autotune<T>(h);
     cudaStream_t s = h->stream;
     if (!h->use_graph || h->prof.enabled) {
         for (int k = 0; k < n_outer; ++k) outer_step<T>(h, B, n_inner, s);
@@ -887,6 +1014,49 @@ int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on) {
 }
 
 // ---- stopping rules ----------------------------------------------------------------------------
+
+int plsqr_autotune(plsqr_handle h, int32_t fresh) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (h->serving) throw std::logic_error("tile shapes cannot change while slots are in use");
+        by_type(h, [&](auto tv) {
+            using T = decltype(tv);
+            autotune<T>(h, fresh != 0);
+        });
+        clear_graphs(h);  // captured with the previous shapes
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (h->serving) throw std::logic_error("tile shapes cannot change while slots are in use");
+        if (level < 0 || level >= h->L - 1) throw InvalidArg("level must be in 0..mg_levels-2");
+        int tx, ty, nth;
+        if (shape < 0 || !mg2d_shape(level == 0, shape, &tx, &ty, &nth)) throw InvalidArg("no such tile shape");
+        h->tile[level] = shape;
+        h->tuned = true;
+        clear_graphs(h);
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx, int32_t* ty, int32_t* threads) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (level < 0 || level >= 16) throw InvalidArg("bad level");
+        const bool fused = use_fused_mg(h) && level < h->L - 1;
+        const int id = fused ? h->tile[level] : -1;
+        int v[3] = {0, 0, 0};
+        if (fused) mg2d_shape(level == 0, id, &v[0], &v[1], &v[2]);
+        if (shape) *shape = id;
+        if (tx) *tx = v[0];
+        if (ty) *ty = v[1];
+        if (threads) *threads = v[2];
+        return PLSQR_OK;
+    });
+}
 
 int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, double r_rel) {
     if (!h) return PLSQR_E_INVALID;

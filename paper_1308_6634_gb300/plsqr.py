@@ -82,6 +82,9 @@ def lib():
         "plsqr_query": ([vp], C.c_int),
         "plsqr_slot_progress": ([vp, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "plsqr_slot_finish": ([vp, i32, vp, C.POINTER(Stats)], C.c_int),
+        "plsqr_autotune": ([vp, i32], C.c_int),
+        "plsqr_set_tile_shape": ([vp, i32, i32], C.c_int),
+        "plsqr_tile_shape": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -95,7 +98,8 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
-            "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish"]
+            "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
+            "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
 
@@ -309,6 +313,20 @@ class Solver:
     def set_kappa_bf16(self, on=True):
         """Keep kappa in bfloat16 for later solves (2D single precision, temporally blocked V-cycle)."""
         _check(self.h, lib().plsqr_set_kappa_bf16(self.h, 1 if on else 0))
+
+    # ---- V-cycle tile shapes ----
+    def autotune(self, fresh=False):
+        """Time every compiled tile shape on each 2D V-cycle level and keep the fastest."""
+        _check(self.h, lib().plsqr_autotune(self.h, 1 if fresh else 0))
+
+    def set_tile_shape(self, level, shape):
+        _check(self.h, lib().plsqr_set_tile_shape(self.h, int(level), int(shape)))
+
+    def tile_shape(self, level):
+        """(shape id, tile x, tile y, threads) of a level; id -1 where the tiled 2D kernels do not run."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(self.h, lib().plsqr_tile_shape(self.h, int(level), *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     # ---- slots (continuous batching) ----
     def slot_start(self, slot, g, reg, T, tau, n_outer, n_inner, sigma=None):
