@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <stdexcept>
 
 #include "kernels.cuh"
@@ -163,6 +164,136 @@ __global__ void __launch_bounds__(32) k_ldl_gth_pipe(float* __restrict__ gcol_al
         for (int q = 0; q < BWP; ++q) cv[q] = cn[q];
         __syncwarp();
     }
+}
+
+// The same factorisation by four warps with look-ahead.  In step k warp 0 runs only the chain
+// of pivots: it completes column k+1 (its update by pivot k and its excess), sums it and forms
+// 1/d_{k+1} and l_{.,k+1}; meanwhile warps 1-3 apply pivot k to columns k+2 .. k+BW-1 (warp w
+// the columns k + tau with tau = w + 1 (mod 3)) and warp 1 updates the excesses of columns
+// k+2 .. k+bw.  A block barrier closes the step.  The l of consecutive pivots go to alternate
+// shared buffers.  Every entry sees the operations of k_ldl_gth_pipe in the same order: the
+// results are bit for bit the same.
+constexpr int GTH_BULK = 3;  // warps applying the bulk of each pivot
+
+template <int BW, int W>
+__device__ __forceinline__ void gth_bulk(float* col, const float* slk, const float (&cv)[(BW + 1 + 3) & ~3],
+                                         int k, int t, int lim) {
+    constexpr int BWP = (BW + 1 + 3) & ~3;
+    constexpr int NT = (BW - 1 - (W + 1) + GTH_BULK) / GTH_BULK;  // columns of this warp: tau = W+1, W+4, ..
+    float ev[NT > 0 ? NT : 1], sv[NT > 0 ? NT : 1];
+    float* ck = col + (int64_t)k * BWP + t;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+        const int tau = W + 1 + GTH_BULK * q;
+        ev[q] = tau <= lim ? ck[tau * BWP] : 0.f;
+        sv[q] = tau <= lim ? slk[tau + t] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+        const int tau = W + 1 + GTH_BULK * q;
+        if (tau <= lim) ck[tau * BWP] = fmaf(sv[q], cv[tau], ev[q]);
+    }
+}
+
+template <int BW>
+__global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __restrict__ gcol_all,
+                                                                        float* __restrict__ grow_all, int nc,
+                                                                        int bw, GkState* st) {
+    constexpr int BWP = (BW + 1 + 3) & ~3;
+    constexpr int SLW = BWP + BW;
+    constexpr int NTH = 32 * (1 + GTH_BULK);
+    extern __shared__ __align__(128) float col[];
+    __shared__ float sl[2][SLW];
+    __shared__ __align__(8) uint64_t bar;
+    const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (parked(st[inst])) return;
+    float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(float)));
+        bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(float)), &bar);
+    }
+    for (int e = tid; e < nc * BWP; e += NTH)  // row layout: entries no pivot writes
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
+    for (int e = tid; e < 2 * SLW; e += NTH) (&sl[0][0])[e] = 0.f;  // l beyond the band stays 0
+    for (int e = tid; e < BWP; e += NTH) col[(int64_t)nc * BWP + e] = 0.f;
+    __syncthreads();
+    tma_wait_tile(&bar, st, inst);
+    const int t = lane + 1;
+    const bool mine = t <= bw;
+    auto pivot = [&](const float (&c)[BWP]) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int q = 0; q < BWP / 4; ++q) {
+            a0 += c[4 * q];
+            a1 += c[4 * q + 1];
+            a2 += c[4 * q + 2];
+            a3 += c[4 * q + 3];
+        }
+        return 1.0f / ((a0 + a1) + (a2 + a3));
+    };
+    // pivot 0
+    if (warp == 0) {
+        float c0[BWP];
+        load_row<BWP>(c0, col);
+        const float rd = pivot(c0);
+        const float l = mine ? col[t] * rd : 0.f;
+        if (mine) {
+            sl[0][t] = l;
+            gc[t] = l;
+            if (t < nc) gr[(int64_t)t * BWP + t] = l;
+        }
+        if (lane == 0) gc[0] = rd;
+    }
+    __syncthreads();
+    for (int k = 0; k < nc; ++k) {
+        const float* slk = sl[k & 1];
+        const int lim = min(bw - t, nc - 1 - k);  // the columns k + tau lane t-1 updates: tau <= lim
+        float cv[BWP];
+        load_row<BWP>(cv, col + (int64_t)k * BWP);  // column k is final
+        if (warp == 0) {
+            if (1 <= lim) {
+                float* e = col + (int64_t)(k + 1) * BWP + t;
+                *e = fmaf(slk[1 + t], cv[1], *e);
+            }
+            if (t == 1 && k + 1 < nc) {
+                float* e = col + (int64_t)(k + 1) * BWP;
+                *e = fmaf(slk[1], cv[0], *e);
+            }
+            __syncwarp();
+            if (k + 1 < nc) {
+                float* sln = sl[(k + 1) & 1];
+                float cn[BWP];
+                load_row<BWP>(cn, col + (int64_t)(k + 1) * BWP);
+                const float rd = pivot(cn);
+                const float l = mine ? col[(int64_t)(k + 1) * BWP + t] * rd : 0.f;
+                if (mine) {
+                    sln[t] = l;
+                    gc[(int64_t)(k + 1) * BWP + t] = l;
+                    if (k + 1 + t < nc) gr[(int64_t)(k + 1 + t) * BWP + t] = l;
+                }
+                if (lane == 0) gc[(int64_t)(k + 1) * BWP] = rd;
+            }
+        } else if (warp == 1) {
+            gth_bulk<BW, 1>(col, slk, cv, k, t, lim);
+            if (t >= 2 && mine && k + t < nc) {
+                float* e = col + (int64_t)(k + t) * BWP;
+                *e = fmaf(slk[t], cv[0], *e);
+            }
+        } else if (warp == 2) {
+            gth_bulk<BW, 2>(col, slk, cv, k, t, lim);
+        } else {
+            gth_bulk<BW, 3>(col, slk, cv, k, t, lim);
+        }
+        __syncthreads();
+    }
+}
+
+// PLSQR_GTH_WARPS=1: the one-warp factorisation (comparisons)
+bool gth_split_enabled() {
+    const char* e = std::getenv("PLSQR_GTH_WARPS");
+    return !(e && e[0] == '1');
 }
 
 // X = L^{-T} D^{-1} L^{-1}, one thread per column j (BW = window >= bw, a power of two).
@@ -518,11 +649,18 @@ void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int 
     dim3 igrid((unsigned)((nc + 127) / 128), B);
 #define GTH_CASE(BW_)                                                                                     \
     case BW_: {                                                                                           \
-        auto kp = k_ldl_gth_pipe<BW_>;                                                                    \
         const size_t sp = stage + sizeof(float) * BWP;                                                    \
-        if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
-        kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);                                                     \
-        klaunched("k_ldl_gth_pipe");                                                                      \
+        if (gth_split_enabled()) {                                                                        \
+            auto kq = k_ldl_gth_split<BW_>;                                                               \
+            if (sp > 48 * 1024) cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
+            kq<<<B, 32 * (1 + GTH_BULK), sp, s>>>(gcol, grow, nc, bw, st);                               \
+            klaunched("k_ldl_gth_split");                                                                 \
+        } else {                                                                                          \
+            auto kp = k_ldl_gth_pipe<BW_>;                                                                \
+            if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
+            kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);                                                 \
+            klaunched("k_ldl_gth_pipe");                                                                  \
+        }                                                                                                 \
         auto ki = k_gth_inverse<BW_>;                                                                     \
         const size_t ism = stage + sizeof(float) * 4 * BW_ * 33;                                          \
         if (ism > 48 * 1024) cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism); \

@@ -186,6 +186,22 @@ def test_single_precision_coarse_solve_matches_double_route(shape, levels, monke
     assert rel(outs[0], outs[1]) < 2e-6
 
 
+@pytest.mark.parametrize("shape,levels", [((256, 256), 4), ((64, 64), 3), ((8, 8), 1), ((16, 24), 1)])
+def test_four_warp_float_factor_matches_one_warp(shape, levels, monkeypatch):
+    """The float L D L^T split over four warps (look-ahead: one warp runs the pivot chain, three
+    apply the previous pivot) does the same operations on every entry in the same order as the
+    one-warp kernel (PLSQR_GTH_WARPS=1): the V-cycles agree bit for bit."""
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(14).standard_normal(shape)
+    outs = []
+    for warps in ("4", "1"):
+        monkeypatch.setenv("PLSQR_GTH_WARPS", warps)
+        S = _P().Solver(shape, "fp32", levels=levels)
+        S.prec_setup(dev(kappa, "fp32"))
+        outs.append(host(S.prec_apply(dev(b, "fp32"))))
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nu", [1, 2, 3])
 def test_fused_vcycle_matches_one_launch_per_half_sweep(prec, nu, monkeypatch):
