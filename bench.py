@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-fp64-single", action="store_true")
     ap.add_argument("--kappa-bf16", action="store_true", help="keep kappa in bfloat16 (2D single precision)")
+    ap.add_argument("--tiles", default=None,
+                    help="V-cycle tile shape id per level (comma-separated) instead of the autotuner's choice")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="serving: device-memory budget")
@@ -153,7 +155,7 @@ class ClockSampler:
 
 # the kernels of the roofline classes (blur, V-cycle) and what they include
 TRAFFIC_SOURCES = ("common.cuh", "kernels.cuh", "tma.cuh", "k_ops.cu", "k_mg.cu", "k_mg2d.cu", "k_mg2d_alt.cu",
-                   "k_mg2d_impl.cuh")
+                   "k_mg2d_alt2.cu", "k_mg2d_impl.cuh")
 
 
 def kernel_source_hash():
@@ -314,6 +316,9 @@ def main():
     S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles, n_bins=W.n_bins)
     if args.kappa_bf16:
         S.set_kappa_bf16(True)
+    if args.tiles:
+        for lv, sid in enumerate(int(x) for x in args.tiles.split(",")):
+            S.set_tile_shape(lv, sid)
     gs = make_inputs(W, S, seeds, torch, dev)
     fs = [torch.empty(W.shape, dtype=S.dtype, device=dev) for _ in range(B)]
     regs, Ts, taus = [W.reg] * B, [W.T] * B, [W.tau] * B

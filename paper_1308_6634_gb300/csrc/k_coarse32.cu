@@ -67,6 +67,21 @@ __device__ __forceinline__ void load_row(float (&r)[BWP], const float* p) {
     }
 }
 
+// d_k = s_k + sum_i |a_ik| of a staged column (excess first), in a fixed order: four partial sums
+// over every fourth entry.
+template <int BWP>
+__device__ __forceinline__ float pivot_sum(const float (&c)[BWP]) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int q = 0; q < BWP / 4; ++q) {
+        a0 += c[4 * q];
+        a1 += c[4 * q + 1];
+        a2 += c[4 * q + 2];
+        a3 += c[4 * q + 3];
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
 // L D L^T of one instance per warp.  The whole instance (nc * BWP floats) is staged in shared
 // memory by one bulk copy, so the pivot loop makes no global loads.  Lane t-1 owns row offset t
 // of every column: at step k it forms l_{k+t,k} = |a_{k+t,k}| / d_k and updates entry t of the
@@ -222,22 +237,11 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __
     tma_wait_tile(&bar, st, inst);
     const int t = lane + 1;
     const bool mine = t <= bw;
-    auto pivot = [&](const float (&c)[BWP]) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int q = 0; q < BWP / 4; ++q) {
-            a0 += c[4 * q];
-            a1 += c[4 * q + 1];
-            a2 += c[4 * q + 2];
-            a3 += c[4 * q + 3];
-        }
-        return 1.0f / ((a0 + a1) + (a2 + a3));
-    };
-    // pivot 0
-    if (warp == 0) {
-        float c0[BWP];
-        load_row<BWP>(c0, col);
-        const float rd = pivot(c0);
+    // warp 0 keeps the column of the current pivot in registers from the step that formed it
+    float cw[BWP];
+    if (warp == 0) {  // pivot 0
+        load_row<BWP>(cw, col);
+        const float rd = __frcp_rn(pivot_sum(cw));
         const float l = mine ? col[t] * rd : 0.f;
         if (mine) {
             sl[0][t] = l;
@@ -250,24 +254,24 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __
     for (int k = 0; k < nc; ++k) {
         const float* slk = sl[k & 1];
         const int lim = min(bw - t, nc - 1 - k);  // the columns k + tau lane t-1 updates: tau <= lim
-        float cv[BWP];
-        load_row<BWP>(cv, col + (int64_t)k * BWP);  // column k is final
         if (warp == 0) {
+            // pivot k's update of column k+1 and its excess; the lane's own entry stays in a register
+            float* e1 = col + (int64_t)(k + 1) * BWP + t;
+            float own = mine ? *e1 : 0.f;  // rows t > bw are outside the column (and the table)
             if (1 <= lim) {
-                float* e = col + (int64_t)(k + 1) * BWP + t;
-                *e = fmaf(slk[1 + t], cv[1], *e);
+                own = fmaf(slk[1 + t], cw[1], own);
+                *e1 = own;
             }
             if (t == 1 && k + 1 < nc) {
                 float* e = col + (int64_t)(k + 1) * BWP;
-                *e = fmaf(slk[1], cv[0], *e);
+                *e = fmaf(slk[1], cw[0], *e);
             }
             __syncwarp();
             if (k + 1 < nc) {
                 float* sln = sl[(k + 1) & 1];
-                float cn[BWP];
-                load_row<BWP>(cn, col + (int64_t)(k + 1) * BWP);
-                const float rd = pivot(cn);
-                const float l = mine ? col[(int64_t)(k + 1) * BWP + t] * rd : 0.f;
+                load_row<BWP>(cw, col + (int64_t)(k + 1) * BWP);
+                const float rd = __frcp_rn(pivot_sum(cw));
+                const float l = mine ? own * rd : 0.f;
                 if (mine) {
                     sln[t] = l;
                     gc[(int64_t)(k + 1) * BWP + t] = l;
@@ -275,16 +279,20 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __
                 }
                 if (lane == 0) gc[(int64_t)(k + 1) * BWP] = rd;
             }
-        } else if (warp == 1) {
-            gth_bulk<BW, 1>(col, slk, cv, k, t, lim);
-            if (t >= 2 && mine && k + t < nc) {
-                float* e = col + (int64_t)(k + t) * BWP;
-                *e = fmaf(slk[t], cv[0], *e);
-            }
-        } else if (warp == 2) {
-            gth_bulk<BW, 2>(col, slk, cv, k, t, lim);
         } else {
-            gth_bulk<BW, 3>(col, slk, cv, k, t, lim);
+            float cv[BWP];
+            load_row<BWP>(cv, col + (int64_t)k * BWP);  // column k is final
+            if (warp == 1) {
+                gth_bulk<BW, 1>(col, slk, cv, k, t, lim);
+                if (t >= 2 && mine && k + t < nc) {
+                    float* e = col + (int64_t)(k + t) * BWP;
+                    *e = fmaf(slk[t], cv[0], *e);
+                }
+            } else if (warp == 2) {
+                gth_bulk<BW, 2>(col, slk, cv, k, t, lim);
+            } else {
+                gth_bulk<BW, 3>(col, slk, cv, k, t, lim);
+            }
         }
         __syncthreads();
     }

@@ -1,6 +1,6 @@
 // k_mg2d.cu -- the 2D V-cycle launches: the default tile shapes (with plain-load fallbacks), the
-// dispatch over the shapes the autotuner picks (k_mg2d_alt.cu compiles the others), and the opt-in
-// one-launch coarse end.
+// dispatch over the shapes the autotuner picks (k_mg2d_alt.cu and k_mg2d_alt2.cu compile the
+// others), and the opt-in one-launch coarse end.
 #include "k_mg2d_impl.cuh"
 
 namespace plsqr {
@@ -9,7 +9,8 @@ PLSQR_MG2D_SHAPE_DECL(, float, true, F0, true)
 PLSQR_MG2D_SHAPE_DECL(, double, true, F0, true)
 PLSQR_MG2D_SHAPE_DECL(, float, false, C0, true)
 PLSQR_MG2D_SHAPE_DECL(, double, false, C0, true)
-PLSQR_MG2D_ALT_SHAPES(extern)
+PLSQR_MG2D_ALT_FINE(extern)
+PLSQR_MG2D_ALT_COARSE(extern)
 
 struct TailMaps {
     Maps pre[TAIL_LEVELS - 1], post[TAIL_LEVELS - 1];
@@ -206,6 +207,7 @@ bool mg2d_shape(bool fine, int id, int* tx, int* ty, int* nth) {
         switch (id) {
             case 0: v[0] = F0::TX, v[1] = F0::TY, v[2] = F0::NTH; break;
             case 1: v[0] = F1::TX, v[1] = F1::TY, v[2] = F1::NTH; break;
+            case 2: v[0] = F2::TX, v[1] = F2::TY, v[2] = F2::NTH; break;
             default: return false;
         }
     } else {
@@ -215,6 +217,7 @@ bool mg2d_shape(bool fine, int id, int* tx, int* ty, int* nth) {
             case 2: v[0] = C2::TX, v[1] = C2::TY, v[2] = C2::NTH; break;
             case 3: v[0] = C3::TX, v[1] = C3::TY, v[2] = C3::NTH; break;
             case 4: v[0] = C4::TX, v[1] = C4::TY, v[2] = C4::NTH; break;
+            case 5: v[0] = C5::TX, v[1] = C5::TY, v[2] = C5::NTH; break;
             default: return false;
         }
     }
@@ -229,6 +232,7 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc
     bool done = false;
     if (is_kappa) {
         if (shape == 1) done = pre_shape<T, true, F1, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
+        if (shape == 2) done = pre_shape<T, true, F2, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (!done) pre_shape<T, true, F0, true>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
     } else {
         switch (shape) {
@@ -236,6 +240,7 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc
             case 2: done = pre_shape<T, false, C2, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, nullptr); break;
             case 3: done = pre_shape<T, false, C3, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, nullptr); break;
             case 4: done = pre_shape<T, false, C4, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, nullptr); break;
+            case 5: done = pre_shape<T, false, C5, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, nullptr); break;
             default: break;
         }
         if (!done) pre_shape<T, false, C0, true>(cond, b, rd, x, bc, d, dc, nu, B, st, s, nullptr);
@@ -253,6 +258,8 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* x
     if (is_kappa) {
         if (shape == 1)
             done = post_shape<T, true, F1, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
+        if (shape == 2)
+            done = post_shape<T, true, F2, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
         if (!done) post_shape<T, true, F0, true>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
     } else {
         switch (shape) {
@@ -264,6 +271,7 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* x
             POST_ALT(2, C2)
             POST_ALT(3, C3)
             POST_ALT(4, C4)
+            POST_ALT(5, C5)
 #undef POST_ALT
             default: break;
         }

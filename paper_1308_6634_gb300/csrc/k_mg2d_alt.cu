@@ -1,9 +1,9 @@
-// k_mg2d_alt.cu -- the V-cycle tile shapes that the autotuner can choose instead of the defaults
-// (TMA staging only), compiled apart from k_mg2d.cu so that the two build in parallel.
+// k_mg2d_alt.cu -- the finest-level V-cycle tile shapes that the autotuner can choose instead of the
+// default (TMA staging only), compiled apart from k_mg2d.cu so that the units build in parallel.
 #include "k_mg2d_impl.cuh"
 
 namespace plsqr {
 
-PLSQR_MG2D_ALT_SHAPES()
+PLSQR_MG2D_ALT_FINE()
 
 }  // namespace plsqr

@@ -36,17 +36,19 @@ struct Shape {
     static constexpr int TX = TX_, TY = TY_, NTH = NTH_;
     static_assert(TX % 8 == 0 && TY % 2 == 0, "tiles start at even coordinates, x on 16-byte boundaries of xc");
 };
-// The shapes compiled in.  Level 0 (many tiles): F0 (default), F1.  Coarser levels (few tiles,
-// so more threads per tile or smaller tiles spread over more SMs): C0 (default) .. C4.  The
+// The shapes compiled in.  Level 0 (many tiles): F0 (default) .. F2.  Coarser levels (few tiles,
+// so more threads per tile or smaller tiles spread over more SMs): C0 (default) .. C5.  The
 // defaults also have plain-load variants; the others need TMA staging.  Every shape gives bit for
 // bit the same V-cycle (the same arithmetic per cell in the same order), only the schedule differs.
 using F0 = Shape<64, 32, 256>;
 using F1 = Shape<32, 32, 256>;
+using F2 = Shape<32, 16, 256>;
 using C0 = Shape<64, 32, 1024>;
 using C1 = Shape<32, 16, 512>;
 using C2 = Shape<32, 16, 256>;
 using C3 = Shape<16, 16, 256>;
 using C4 = Shape<16, 16, 128>;
+using C5 = Shape<16, 8, 128>;
 using TailShape = Shape<64, 32, 1024>;  // the one-launch coarse end
 constexpr int TNT = TailShape::NTH;
 
@@ -443,10 +445,13 @@ bool post_shape(const T* cond, const T* b, const T* rd, const T* xi, T* x, const
                                                   Dims, int, int, int, GkState*, Hist, Red, cudaStream_t,       \
                                                   const __nv_bfloat16*);
 
-// the shapes of k_mg2d_alt.cu (TMA staging only)
-#define PLSQR_MG2D_ALT_SHAPES(EXT)                          \
+// the shapes of k_mg2d_alt.cu (level 0) and k_mg2d_alt2.cu (coarser levels), TMA staging only
+#define PLSQR_MG2D_ALT_FINE(EXT)                            \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F1, false)      \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F1, false)     \
+    PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F2, false)      \
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F2, false)
+#define PLSQR_MG2D_ALT_COARSE(EXT)                          \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C1, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C1, false)    \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C2, false)     \
@@ -454,6 +459,8 @@ bool post_shape(const T* cond, const T* b, const T* rd, const T* xi, T* x, const
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C3, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C3, false)    \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C4, false)     \
-    PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C4, false)
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C4, false)    \
+    PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C5, false)     \
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C5, false)
 
 }  // namespace plsqr

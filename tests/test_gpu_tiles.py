@@ -38,8 +38,8 @@ def _kappa_field(shape, seed=5):
     f = synth.phantom_rects_disks(max(shape), 8, 5, seed)[: shape[0], : shape[1]] + 0.01 * rng.standard_normal(shape)
     return O.diffusivity(f, "pm_log", 0.05)[0]
 
-N_COARSE = 5  # shapes 0..4 of the coarser levels
-N_FINE = 2    # shapes 0..1 of the finest level
+N_COARSE = 6  # shapes 0..5 of the coarser levels
+N_FINE = 3    # shapes 0..2 of the finest level
 
 
 @pytest.mark.parametrize("shape,levels,prec", [((1024, 1024), 6, "fp32"), ((136, 200), 4, "fp32"),
