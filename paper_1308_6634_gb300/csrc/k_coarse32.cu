@@ -415,21 +415,28 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ g
 
 // Wide bands (3D coarsest grids): the same elimination with a circular window of the bw + 1
 // columns pivot k touches, in shared memory (column j in slot j mod (bw + 1), an odd slot stride
-// so that consecutive rows of different slots fall in different banks), and nt = round32(bw)
-// threads (at most 1024).  Step k: d_k by a block reduction in a fixed order (warp partials to
-// lane 0, then the warp totals in warp order, read by every thread); l_{k+t,k} by thread t-1;
-// then thread t-1 updates row offset t of the columns k + tau, tau = 1..bw - t (its loop ends
-// where its rows end), and the excess of column k + t.  Column k + bw + 1 is fetched into
-// registers during the step and written to the freed slot at its end.  Output as the narrow
-// kernels: gcol[k][0] = 1/d_k, gcol[k][t] = l_{k+t,k}, grow[i][t] = l_{i,i-t}.
+// so that consecutive rows of different slots fall in different banks).  The block has NQ groups
+// of NT0 = round32(bw) threads (NQ * NT0 <= 1024).  Step k: d_k by a block reduction in a fixed
+// order (warp partials to lane 0, then the warp totals in warp order, read by every thread; the
+// warps of groups 1.. add zeros); l_{k+t,k} by thread t-1 of group 0; then thread t-1 of group g
+// updates row offset t of the columns k + tau, tau = g+1, g+1+NQ, .. <= bw - t (its rows end
+// there), GTH_WCH columns at a time with their loads issued before the stores; group 0 also
+// updates the excess of column k + t.  Every entry receives one update per pivot, as in the
+// narrow kernels.  Column k + bw + 1 is fetched into registers during the step and written to the
+// freed slot at its end.  Output as the narrow kernels: gcol[k][0] = 1/d_k, gcol[k][t] = l_{k+t,k},
+// grow[i][t] = l_{i,i-t}.
+constexpr int GTH_WQ = 4;   // thread groups splitting each pivot's columns
+constexpr int GTH_WCH = 4;  // columns per batch of loads
+
 __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gcol_all, float* __restrict__ grow_all,
                                                          int nc, int bw, int BWP, GkState* st) {
     extern __shared__ __align__(16) float win[];
     __shared__ float sl[1024 + 2];
     __shared__ float wred[32];
     const int NT = blockDim.x, NW = NT >> 5;
+    const int NT0 = max(32, ((bw + 31) / 32) * 32), NQ = NT / NT0;
     const int S = bw + 1, SW = S | 1;
-    const int inst = blockIdx.x, tid = threadIdx.x, t = tid + 1;
+    const int inst = blockIdx.x, tid = threadIdx.x, g = tid / NT0, t = tid - g * NT0 + 1;
     if (parked(st[inst])) return;
     float* gc = gcol_all + (int64_t)inst * nc * BWP;
     float* gr = grow_all + (int64_t)inst * nc * BWP;
@@ -439,9 +446,8 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gco
         const int c = e / S, r = e - c * S;
         win[c * SW + r] = gc[(int64_t)c * BWP + r];
     }
-    for (int e = tid; e < NT + 2; e += NT) sl[e] = 0.f;
+    for (int e = tid; e < 1024 + 2; e += NT) sl[e] = 0.f;
     __syncthreads();
-    float* const wend = win + S * SW;
     for (int k = 0; k < nc; ++k) {
         const int sk = k % S;
         const float* ck = win + sk * SW;
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gco
         const bool nxt = k + S < nc;
         const float pre0 = (nxt && tid < S) ? gc[(int64_t)(k + S) * BWP + tid] : 0.f;
         const float pre1 = (nxt && tid + NT < S) ? gc[(int64_t)(k + S) * BWP + tid + NT] : 0.f;
-        float part = (t <= bw ? ck[t] : 0.f) + (tid == 0 ? ck[0] : 0.f);
+        float part = (g == 0 && t <= bw ? ck[t] : 0.f) + (tid == 0 ? ck[0] : 0.f);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
         if ((tid & 31) == 0) wred[tid >> 5] = part;
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gco
         for (int w = 0; w < NW; ++w) dk += wred[w];
         const float rd = 1.0f / dk;
         const float s_k = ck[0];
-        if (t <= bw) {
+        if (g == 0 && t <= bw) {
             const float l = ck[t] * rd;
             sl[t] = l;
             gc[(int64_t)k * BWP + t] = l;
@@ -466,19 +472,33 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gco
         }
         if (tid == 0) gc[(int64_t)k * BWP] = rd;
         __syncthreads();
-        // row offset t of the columns k + tau, tau = 1 .. min(bw - t, nc - 1 - k)
+        // row offset t of the columns k + tau, tau = g+1, g+1+NQ, .. <= min(bw - t, nc - 1 - k)
         const int last = min(bw - t, nc - 1 - k);
-        float* e = win + (sk + 1 == S ? 0 : sk + 1) * SW + t;
-        const float* lp = sl + 1 + t;
-        const float* ap = ck + 1;
-        for (int tau = 1; tau <= last; ++tau) {
-            *e = fmaf(*lp, *ap, *e);
-            ++lp;
-            ++ap;
-            e += SW;
-            if (e >= wend) e -= S * SW;
+        int tau = g + 1;
+        int slot = sk + tau;
+        if (slot >= S) slot -= S;
+        for (; tau + (GTH_WCH - 1) * NQ <= last; tau += GTH_WCH * NQ) {
+            float* ep[GTH_WCH];
+            float ev[GTH_WCH], lv[GTH_WCH], av[GTH_WCH];
+#pragma unroll
+            for (int c = 0; c < GTH_WCH; ++c) {
+                ep[c] = win + slot * SW + t;
+                ev[c] = *ep[c];
+                lv[c] = sl[tau + c * NQ + t];
+                av[c] = ck[tau + c * NQ];
+                slot += NQ;
+                if (slot >= S) slot -= S;
+            }
+#pragma unroll
+            for (int c = 0; c < GTH_WCH; ++c) *ep[c] = fmaf(lv[c], av[c], ev[c]);
         }
-        if (t <= bw && k + t < nc) {
+        for (; tau <= last; tau += NQ) {
+            float* e = win + slot * SW + t;
+            *e = fmaf(sl[tau + t], ck[tau], *e);
+            slot += NQ;
+            if (slot >= S) slot -= S;
+        }
+        if (g == 0 && t <= bw && k + t < nc) {
             float* es = win + ((k + t) % S) * SW;
             *es = fmaf(sl[t], s_k, *es);
         }
@@ -614,7 +634,8 @@ void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw,
     const int BWP = gth_stride(bw);
     const int S = bw + 1, SW = S | 1;
     const size_t smem = sizeof(float) * (size_t)S * SW;
-    const int nt = std::max(32, ((bw + 31) / 32) * 32);
+    const int nt0 = std::max(32, ((bw + 31) / 32) * 32);
+    const int nt = nt0 * std::max(1, std::min(GTH_WQ, 1024 / nt0));
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ldl_gth_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ldl_gth_window<<<B, nt, smem, s>>>(gcol, grow, nc, bw, BWP, st);
     klaunched("k_ldl_gth_window");
