@@ -141,7 +141,8 @@ def _kappa_field(shape, seed=5):
 @pytest.mark.parametrize("shape,levels,nu,cycles", [((96, 160), 4, 2, 1), ((64, 64), 3, 2, 2),
                                                     ((32, 48), 1, 2, 1), ((48, 80), 3, 1, 1),
                                                     ((40, 72), 3, 3, 1), ((136, 200), 4, 2, 1),
-                                                    ((16, 24, 32), 3, 2, 1), ((24, 24, 24), 4, 1, 1)])
+                                                    ((16, 24, 32), 3, 2, 1), ((24, 24, 24), 4, 1, 1),
+                                                    ((40, 24, 56), 3, 3, 1), ((32, 32, 32), 3, 2, 2)])
 def test_priorconditioner(prec, shape, levels, nu, cycles):
     kappa = _kappa_field(shape)
     rng = np.random.default_rng(6)
