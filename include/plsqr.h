@@ -185,6 +185,27 @@ int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
 
+/* ---- several damping parameters from one bidiagonalisation (Sec. 3.3) ---------------------------
+ * The Golub-Kahan bidiagonalisation inside MLSQR does not depend on tau (the Krylov spaces are
+ * shift invariant), so with its Lanczos vectors V_k stored, the projected problem (3.6)
+ *     min_y || [B_k ; sqrt(tau) I] y - beta_1 e_1 ||
+ * gives the MLSQR iterate f_k(tau) = V_k y(tau) for any number of values of tau.
+ *
+ * plsqr_mlsqr_multi_tau: one MLSQR run of n_inner steps from f = 0 with the current hierarchy
+ *   (plsqr_prec_setup), storing the normalised vectors v~_1 .. v~_n_inner on the device
+ *   (n_inner * N elements, allocated for the call and freed before it returns), then for each of
+ *   the n_tau <= 32 values taus[t] >= 0: f_out[t] (device, N values) = V y(taus[t]), all of them in
+ *   one pass over the stored vectors.  rbar_hist (host, n_tau x n_inner, may be NULL): ||rbar_i||
+ *   for each tau.  *iters_done (may be NULL): completed steps.  Returns PLSQR_E_BREAKDOWN (with the
+ *   iterates of the completed steps) if the bidiagonalisation stopped early, PLSQR_E_NOMEM if the
+ *   vectors do not fit, PLSQR_E_STATE while slots are in use.  Synchronises.
+ * plsqr_projected_solve: its host part, which needs no GPU: y (k values) and ||rbar_i|| (k values,
+ *   may be NULL) of (3.6) from alpha[0..k] = alpha_1 .. alpha_{k+1} and beta[0..k] = beta_1 ..
+ *   beta_{k+1}, by the rotations of Algorithm 2 (steps 8-20) applied to coefficient vectors. */
+int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_t n_tau, const double* taus,
+                          void* const* f_out, double* rbar_hist, int32_t* iters_done);
+int plsqr_projected_solve(int32_t k, const double* alpha, const double* beta, double tau, double* y, double* rbar);
+
 /* ---- V-cycle tile shapes ------------------------------------------------------------------------
  * The 2D V-cycle (Sec. 4.2 priorconditioner: red-black Gauss-Seidel smoothing, restriction,
  * prolongation on each level above the coarsest) runs each level as tiles staged in shared memory.

@@ -7,6 +7,8 @@
 // that eliminates sqrt(tau) I (eq. 3.6), and records ||rbar_i||.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <stdexcept>
 #include <string>
 
@@ -333,11 +335,69 @@ void fill_nan(double* p, int64_t n, cudaStream_t s) {
     kfinish(s);
 }
 
+// ---- stored Lanczos vectors (reuse for several damping parameters, Sec. 3.3) -------------------
+
+// V_j = v~ / alpha (the normalised basis vector the update of step 7 / 20 uses) and the current
+// alpha, beta of the bidiagonalisation (one instance).
+template <typename T>
+__global__ void __launch_bounds__(256) k_store_basis(const T* __restrict__ v, T* __restrict__ Vj, int64_t N,
+                                                     const GkState* st, double* ab, int store_v) {
+    const GkState& s = st[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ab[0] = s.alpha;
+        ab[1] = s.beta;
+    }
+    if (!store_v) return;
+    const T c = (T)s.c_upd_v;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) Vj[i] = v[i] * c;
+}
+
+template <typename T>
+void gk_store_basis(const T* v, T* Vj, int64_t N, const GkState* st, double* ab, bool store_v, cudaStream_t s) {
+    kbegin(KC_GK, s);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4096));
+    k_store_basis<T><<<blocks, 256, 0, s>>>(v, Vj, N, st, ab, store_v ? 1 : 0);
+    klaunched("k_store_basis");
+    kfinish(s);
+}
+
+// outs[t] = sum_j coef[t][j] V_j for the n_tau <= MT_MAX coefficient rows, one pass over V.
+template <typename T>
+__global__ void __launch_bounds__(256) k_combine_basis(const T* __restrict__ V, int k, int64_t N,
+                                                       const double* __restrict__ coef, int n_tau, OutPtrs<T> outs) {
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+        T acc[MT_MAX];
+#pragma unroll
+        for (int t = 0; t < MT_MAX; ++t) acc[t] = (T)0;
+        for (int j = 0; j < k; ++j) {
+            const T vj = V[(int64_t)j * N + i];
+#pragma unroll
+            for (int t = 0; t < MT_MAX; ++t)
+                if (t < n_tau) acc[t] = fma((T)coef[t * k + j], vj, acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < MT_MAX; ++t)
+            if (t < n_tau) outs.p[t][i] = acc[t];
+    }
+}
+
+template <typename T>
+void combine_basis(const T* V, int k, int64_t N, const double* coef, int n_tau, const OutPtrs<T>& outs,
+                   cudaStream_t s) {
+    kbegin(KC_GK, s);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4096));
+    k_combine_basis<T><<<blocks, 256, 0, s>>>(V, k, N, coef, n_tau, outs);
+    klaunched("k_combine_basis");
+    kfinish(s);
+}
+
 #define PLSQR_INST_LSQR(T)                                                                                   \
     template void gk_init_norm<T>(const T*, int64_t, int, GkState*, Red, cudaStream_t);                       \
     template void gk_dot_rotate<T>(const T*, const T*, int64_t, int, bool, GkState*, Hist, Red, cudaStream_t); \
     template void gk_update<T>(T*, T*, const T*, int64_t, int, bool, const GkState*, cudaStream_t);           \
-    template void resid_norm<T>(const T*, const T*, int64_t, int, GkState*, Hist, Red, cudaStream_t);
+    template void resid_norm<T>(const T*, const T*, int64_t, int, GkState*, Hist, Red, cudaStream_t);         \
+    template void gk_store_basis<T>(const T*, T*, int64_t, const GkState*, double*, bool, cudaStream_t);     \
+    template void combine_basis<T>(const T*, int, int64_t, const double*, int, const OutPtrs<T>&, cudaStream_t);
 
 PLSQR_INST_LSQR(float)
 PLSQR_INST_LSQR(double)

@@ -157,6 +157,19 @@ void gk_dot_rotate(const T* v, const T* p, int64_t N, int B, bool init, GkState*
                    cudaStream_t s);
 template <typename T>
 void gk_update(T* f, T* w, const T* v, int64_t N, int B, bool init, const GkState* st, cudaStream_t s);
+// Stored Lanczos vectors (one instance): V_j = v~ / alpha and ab = (alpha, beta) now; store_v
+// false records the scalars only.
+template <typename T>
+void gk_store_basis(const T* v, T* Vj, int64_t N, const GkState* st, double* ab, bool store_v, cudaStream_t s);
+constexpr int MT_MAX = 32;  // damping parameters per combination pass
+template <typename T>
+struct OutPtrs {
+    T* p[MT_MAX];
+};
+// outs[t] = sum_{j < k} coef[t * k + j] V_j, t < n_tau (coef on the device)
+template <typename T>
+void combine_basis(const T* V, int k, int64_t N, const double* coef, int n_tau, const OutPtrs<T>& outs,
+                   cudaStream_t s);
 template <typename T>
 void resid_norm(const T* g, const T* Af, int64_t m, int B, GkState* st, Hist hist, Red red, cudaStream_t s);
 void fill_nan(double* p, int64_t n, cudaStream_t s);

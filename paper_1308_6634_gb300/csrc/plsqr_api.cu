@@ -114,6 +114,10 @@ struct plsqr_ctx {
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
     int tile[16] = {};        // tile shape of each 2D V-cycle level (mg2d_shape ids; 0 the default)
     bool tuned = false;       // tile shapes chosen (autotuned or set)
+    // stored Lanczos vectors of the running inner solve (plsqr_mlsqr_multi_tau): V_j, (alpha, beta)
+    char* basis = nullptr;
+    double* basis_ab = nullptr;
+    int basis_n = 0;
     TailLevels tail{};
     bool no_fuse_update = false;  // PLSQR_FUSE_UPDATE=0: separate update kernel (comparisons)
     Profiler prof;
@@ -378,6 +382,7 @@ void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
     op_apply<T>(h->od, true, EPI_ADJ_INIT, g, p, nullptr, tmp, B, h->st, h->red, s);  // step 3
     if (!prec_apply<T>(h, p, v, B, s, 1))                                           // step 4
         gk_dot_rotate<T>(v, p, N, B, true, h->st, hs, h->red, s);                   // steps 5-6
+    if (h->basis) gk_store_basis<T>(v, P<T>(h->basis), N, h->st, h->basis_ab, h->basis_n > 0, s);
     gk_update<T>(f, w, v, N, B, true, h->st, s);                                    // step 7
     bool pending = false;  // update (steps 19-20) of the previous iteration not yet applied
     for (int i = 1; i <= n_inner; ++i) {
@@ -391,6 +396,9 @@ void mlsqr_seq(plsqr_ctx* h, int B, int n_inner, cudaStream_t s) {
         op_apply<T>(h->od, true, EPI_ADJ, u, p, p, tmp, B, h->st, h->red, s);                // step 11
         if (!prec_apply<T>(h, p, v, B, s, 2))                                                // step 12
             gk_dot_rotate<T>(v, p, N, B, false, h->st, hs, h->red, s);                       // 13-17
+        if (h->basis)
+            gk_store_basis<T>(v, P<T>(h->basis) + (int64_t)std::min(i, h->basis_n - 1) * N, N, h->st,
+                              h->basis_ab + 2 * i, i < h->basis_n, s);
         pending = true;
     }
     if (pending) gk_update<T>(f, w, v, N, B, false, h->st, s);                               // 19-20
@@ -1399,6 +1407,126 @@ int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void
         if (rbar_hist) std::memcpy(rbar_hist, h->h_stage, sizeof(double) * n_inner);
         if (iters_done) *iters_done = h->st_host[0].iter;
         return h->st_host[0].status != 0 ? PLSQR_E_BREAKDOWN : PLSQR_OK;
+    });
+}
+
+int plsqr_projected_solve(int32_t k, const double* alpha, const double* beta, double tau, double* y,
+                          double* rbar) {
+    if (k < 1 || !alpha || !beta || !y || !(tau >= 0.0)) return PLSQR_E_INVALID;
+    // Algorithm 2 steps 8-20 on coefficient vectors in the basis V (x = sum_j y_j V_j, w likewise):
+    // the damping rotation (eq. 3.6) and the plane rotation of each step, as in the device code.
+    std::vector<double> w((size_t)k + 1, 0.0);
+    for (int j = 0; j < k; ++j) y[j] = 0.0;
+    w[0] = 1.0;  // w~_1 = v~_1
+    double phibar = beta[0], rhobar = alpha[0], res2 = 0.0;
+    const double sq = std::sqrt(tau);
+    for (int i = 0; i < k; ++i) {
+        double rhohat = rhobar, psi = 0.0;
+        if (tau > 0.0) {
+            rhohat = std::sqrt(rhobar * rhobar + tau);
+            const double c1 = rhobar / rhohat, s1 = sq / rhohat;
+            psi = s1 * phibar;
+            phibar = c1 * phibar;
+        }
+        const double b = beta[i + 1], a = alpha[i + 1];
+        const double rho = std::sqrt(rhohat * rhohat + b * b);
+        if (!(rho > 0.0) || !std::isfinite(rho)) return PLSQR_E_BREAKDOWN;
+        const double c = rhohat / rho, sn = b / rho;
+        const double theta = sn * a;
+        rhobar = -c * a;
+        const double phi = c * phibar;
+        phibar = sn * phibar;
+        res2 += psi * psi;
+        for (int j = 0; j <= i; ++j) y[j] += (phi / rho) * w[j];   // step 19
+        for (int j = 0; j <= i; ++j) w[j] *= -(theta / rho);       // step 20
+        w[i + 1] = 1.0;
+        if (rbar) rbar[i] = std::sqrt(phibar * phibar + res2);
+    }
+    return PLSQR_OK;
+}
+
+int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_t n_tau, const double* taus,
+                          void* const* f_out, double* rbar_hist, int32_t* iters_done) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!g || !f_out || !taus) throw InvalidArg("NULL pointer");
+        if (n_tau < 1 || n_tau > MT_MAX) throw InvalidArg("n_tau must be in 1..32");
+        for (int t = 0; t < n_tau; ++t) {
+            if (!(taus[t] >= 0.0) || !std::isfinite(taus[t])) throw InvalidArg("tau must be finite and >= 0");
+            if (!f_out[t]) throw InvalidArg("NULL pointer");
+        }
+        if (h->serving) throw std::logic_error("not while slots are in use");
+        int32_t reg = 0;
+        double T = 1.0, tau0 = 0.0;
+        validate_solve(h, 1, &reg, &T, &tau0, 1, n_inner);
+        cudaStream_t s = h->user_stream;
+        const int64_t N = h->d.N;
+        char* V = nullptr;
+        double *ab = nullptr, *coef = nullptr;
+        int k = 0;
+        auto release = [&]() {
+            h->basis = nullptr;
+            h->basis_ab = nullptr;
+            h->basis_n = 0;
+            if (V) cudaFree(V);
+            if (ab) cudaFree(ab);
+            if (coef) cudaFree(coef);
+        };
+        try {
+            ck(cudaMalloc((void**)&V, h->esz * (size_t)n_inner * N), "cudaMalloc (stored Lanczos vectors)");
+            ck(cudaMalloc((void**)&ab, sizeof(double) * 2 * (size_t)(n_inner + 1)), "cudaMalloc");
+            ck(cudaMalloc((void**)&coef, sizeof(double) * (size_t)n_tau * n_inner), "cudaMalloc");
+            ck(cudaMemsetAsync(ab, 0, sizeof(double) * 2 * (size_t)(n_inner + 1), s), "memset");
+            h->basis = V;
+            h->basis_ab = ab;
+            h->basis_n = n_inner;
+            // the bidiagonalisation does not depend on tau (Sec. 3.3): one run, undamped
+            ensure_hist(h, 1, n_inner);
+            ck(cudaMemcpyAsync(h->g, g, h->esz * h->m, cudaMemcpyDeviceToDevice, s), "g");
+            h->prm_host[0].reg = reg;
+            h->prm_host[0].T = T;
+            h->prm_host[0].tau = 0.0;
+            ck(cudaMemcpyAsync(h->prm_dev, h->prm_host, sizeof(SolveParams), cudaMemcpyHostToDevice, s), "params");
+            set_params(h->st, h->prm_dev, 1, true, s);
+            by_type(h, [&](auto tv) {
+                using TT = decltype(tv);
+                mlsqr_seq<TT>(h, 1, n_inner, s);
+            });
+            std::vector<double> abh(2 * (size_t)(n_inner + 1));
+            ck(cudaMemcpyAsync(abh.data(), ab, sizeof(double) * abh.size(), cudaMemcpyDeviceToHost, s), "scalars");
+            ck(cudaMemcpyAsync(h->st_host, h->st, sizeof(GkState), cudaMemcpyDeviceToHost, s), "state");
+            ck(cudaStreamSynchronize(s), "sync");
+            k = std::min<int>(n_inner, h->st_host[0].iter);
+            if (iters_done) *iters_done = k;
+            if (k < 1) throw std::runtime_error("the bidiagonalisation broke down at its first step");
+            std::vector<double> alpha((size_t)k + 1), beta((size_t)k + 1);
+            for (int j = 0; j <= k; ++j) {
+                alpha[j] = abh[2 * j];
+                beta[j] = abh[2 * j + 1];
+            }
+            std::vector<double> ch((size_t)n_tau * k), rb((size_t)k);
+            for (int t = 0; t < n_tau; ++t) {
+                if (plsqr_projected_solve(k, alpha.data(), beta.data(), taus[t], ch.data() + (size_t)t * k, rb.data()) !=
+                    PLSQR_OK)
+                    throw std::runtime_error("projected problem broke down");
+                if (rbar_hist)
+                    for (int i = 0; i < n_inner; ++i) rbar_hist[(size_t)t * n_inner + i] = i < k ? rb[i] : NAN;
+            }
+            ck(cudaMemcpyAsync(coef, ch.data(), sizeof(double) * ch.size(), cudaMemcpyHostToDevice, s), "coef");
+            by_type(h, [&](auto tv) {
+                using TT = decltype(tv);
+                OutPtrs<TT> outs{};
+                for (int t = 0; t < n_tau; ++t) outs.p[t] = (TT*)f_out[t];
+                combine_basis<TT>(P<TT>(V), k, N, coef, n_tau, outs, s);
+            });
+            ck(cudaStreamSynchronize(s), "sync");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            release();
+            throw;
+        }
+        release();
+        return k < n_inner ? PLSQR_E_BREAKDOWN : PLSQR_OK;
     });
 }
 

@@ -83,6 +83,9 @@ def lib():
         "plsqr_slot_progress": ([vp, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "plsqr_slot_finish": ([vp, i32, vp, C.POINTER(Stats)], C.c_int),
         "plsqr_autotune": ([vp, i32], C.c_int),
+        "plsqr_mlsqr_multi_tau": ([vp, vp, i32, i32, C.POINTER(d), C.POINTER(vp), C.POINTER(d), C.POINTER(i32)],
+                                  C.c_int),
+        "plsqr_projected_solve": ([i32, C.POINTER(d), C.POINTER(d), d, C.POINTER(d), C.POINTER(d)], C.c_int),
         "plsqr_set_tile_shape": ([vp, i32, i32], C.c_int),
         "plsqr_tile_shape": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
     }
@@ -99,9 +102,28 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
-            "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape"]
+            "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_mlsqr_multi_tau",
+            "plsqr_projected_solve"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
+
+
+def projected_solve(alpha, beta, tau):
+    """Host solve of the projected problem (3.6): (y, rbar history) from alpha_1..alpha_{k+1} and
+    beta_1..beta_{k+1} (both of length k + 1).  Needs no GPU."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    k = len(alpha) - 1
+    if k < 1 or len(beta) != k + 1:
+        raise ValueError("alpha and beta need k + 1 >= 2 values each")
+    y = np.empty(k)
+    rb = np.empty(k)
+    P = C.POINTER(C.c_double)
+    rc = lib().plsqr_projected_solve(k, alpha.ctypes.data_as(P), beta.ctypes.data_as(P), float(tau),
+                                     y.ctypes.data_as(P), rb.ctypes.data_as(P))
+    if rc != OK:
+        raise PlsqrError(rc, "projected problem broke down")
+    return y, rb
 
 
 def _check(h, rc):
@@ -313,6 +335,20 @@ class Solver:
     def set_kappa_bf16(self, on=True):
         """Keep kappa in bfloat16 for later solves (2D single precision, temporally blocked V-cycle)."""
         _check(self.h, lib().plsqr_set_kappa_bf16(self.h, 1 if on else 0))
+
+    def mlsqr_multi_tau(self, g, taus, n_inner):
+        """One MLSQR bidiagonalisation from f = 0 with the current hierarchy, its Lanczos vectors
+        stored; returns ([f(tau) for tau in taus], rbar histories (len(taus) x n_inner), steps done)."""
+        torch = _torch()
+        taus = [float(t) for t in taus]
+        fs = [torch.empty(self.shape, dtype=self.dtype, device=g.device) for _ in taus]
+        ta = (C.c_double * len(taus))(*taus)
+        fp = (C.c_void_p * len(taus))(*[_dptr(f, self.dtype, self.N) for f in fs])
+        hist = (C.c_double * (len(taus) * n_inner))()
+        done = C.c_int32(0)
+        _check(self.h, lib().plsqr_mlsqr_multi_tau(self.h, _dptr(g, self.dtype, self.m), int(n_inner), len(taus), ta,
+                                                   fp, hist, C.byref(done)))
+        return fs, np.array(hist[:], dtype=np.float64).reshape(len(taus), n_inner), done.value
 
     # ---- V-cycle tile shapes ----
     def autotune(self, fresh=False):

@@ -452,3 +452,42 @@ def test_breakdown_and_invalid_arguments():
         P.Solver((100, 100), "fp32", levels=4)
     with pytest.raises(P.PlsqrError):
         S.set_operator("joseph", n_angles=0, n_bins=10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_multi_tau_from_one_bidiagonalisation(prec):
+    """Sec. 3.3: the Lanczos vectors do not depend on tau, so one bidiagonalisation with its vectors
+    stored gives the MLSQR iterate for every tau through the projected problem (3.6).  Each result
+    must match the oracle's MLSQR run with that tau (as closely as one MLSQR run does) and the
+    library's own MLSQR run with that tau (the same basis: only the last combination differs)."""
+    taus = [0.0, 5e-3, 0.1, 1.0]
+    n = 5  # the short horizon of test_mlsqr_short_horizon, before single-precision rounding chaos
+    W = synth.Workload("t", "blur", (96, 160), prec, "tv", 1e-2, 0.0, 1, n, levels=4, nu=2, cycles=1,
+                       sigma=(2.0, 2.0), radius=(6, 6), phantom=dict(type="rects_disks", rects=6, disks=4))
+    op, g, _ = _problem(W)
+    kappa = _kappa_field(W.shape, 7)
+    S = _solver_for(W, op, None)
+    S.prec_setup(dev(kappa, prec))
+    fs, hists, done = S.mlsqr_multi_tau(dev(g, prec), taus, n)
+    assert done == n
+    mg = O.Multigrid(kappa, W.levels, W.nu, W.cycles)
+    for tau, f, hist in zip(taus, fs, hists):
+        f_ref, h_ref, st = O.mlsqr(op, g, tau, n, prec=mg)
+        f_own, h_own, rc = S.mlsqr(dev(g, prec), tau, n)
+        assert st == 0 and rc == 0
+        if prec == "fp64":
+            assert rel(host(f), f_ref) < 1e-9 and rel(hist, h_ref) < 1e-12, tau
+            assert rel(host(f), host(f_own)) < 1e-12 and rel(hist, h_own) < 1e-13, tau
+        else:
+            assert rel(host(f), f_ref) < 1e-3 and rel(hist, h_ref) < 1e-5, tau
+            assert rel(host(f), host(f_own)) < 1e-5 and rel(hist, h_own) < 1e-12, tau
+
+
+def test_multi_tau_invalid_arguments():
+    S = _P().Solver((32, 32), "fp32", levels=2)
+    S.set_operator("blur", sigma=(1.0, 1.0), radius=(3, 3))
+    S.prec_setup(dev(np.ones((32, 32)), "fp32"))
+    g = dev(np.random.default_rng(1).standard_normal((32, 32)), "fp32")
+    for taus in ([-1.0], [float("nan")], [0.0] * 33):
+        with pytest.raises(RuntimeError):
+            S.mlsqr_multi_tau(g, taus, 3)
