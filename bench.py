@@ -443,12 +443,17 @@ def main():
             bytes_per_launch = ALG_UNITS[dom] * esz * W_N(W) * B
             achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
             total_prof = sum(v[0] for v in prof.values())
+            by_class = {}
+            for k2, (ms2, cnt2) in cand.items():  # every class with algorithmic bytes, same arithmetic
+                a2 = ALG_UNITS[k2] * esz * W_N(W) * B / (ms2 / cnt2 / 1e3) / 1e9
+                by_class[k2] = {"achieved_gbs": round(a2, 1), "frac": round(a2 / peak, 4),
+                                "avg_launch_us": round(1e3 * ms2 / cnt2, 2)}
             roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                         "traffic": ncu_traffic(dom, W.name), "alg_bytes_per_launch": bytes_per_launch,
                         "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
                         "share_of_eager_device_time": ms / total_prof, "largest_class": top,
-                        "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+                        "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}, "by_class": by_class}
 
     # the plain form beside it: the same workload with the same kernels instantiated in double,
     # one instance per call, no CUDA graph

@@ -33,21 +33,21 @@ namespace plsqr {
 
 // Column j of the strictly lower triangle of M_c is the conductances of cell j's edges in the
 // +x, +y (+z) directions; an edge to the ghost cell beyond the high boundary adds to s_j instead.
-template <typename T, bool KAPPA>
-__global__ void __launch_bounds__(256) k_gth_assemble(const T* __restrict__ cond, float* __restrict__ gcol, Dims d,
+template <typename T, typename V, bool KAPPA>
+__global__ void __launch_bounds__(256) k_gth_assemble(const T* __restrict__ cond, V* __restrict__ gcol, Dims d,
                                                       int BWP) {
     const int inst = blockIdx.y;
     const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (j >= d.N) return;
-    float* col = gcol + ((int64_t)inst * d.N + j) * BWP;
-    for (int t = 0; t < BWP; ++t) col[t] = 0.f;
+    V* col = gcol + ((int64_t)inst * d.N + j) * BWP;
+    for (int t = 0; t < BWP; ++t) col[t] = (V)0;
     const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
     const int co[3] = {(int)(j % d.nx), (int)((j / d.nx) % d.ny), (int)(j / ((int64_t)d.nx * d.ny))};
     const int n[3] = {d.nx, d.ny, d.nz};
     const int strd[3] = {1, d.nx, d.nx * d.ny};
-    float s = 0.f;
+    V s = (V)0;
     for (int dd = 0; dd < d.ndim; ++dd) {
-        const float ce = (float)(KAPPA ? c[j] : c[(int64_t)dd * d.N + j]);
+        const V ce = (V)(KAPPA ? c[j] : c[(int64_t)dd * d.N + j]);
         if (co[dd] + 1 < n[dd]) col[strd[dd]] = ce;
         else s += ce;
     }
@@ -67,11 +67,26 @@ __device__ __forceinline__ void load_row(float (&r)[BWP], const float* p) {
     }
 }
 
+template <int BWP>
+__device__ __forceinline__ void load_row(double (&r)[BWP], const double* p) {
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int q = 0; q < BWP / 2; ++q) {
+        const double2 v = p2[q];
+        r[2 * q] = v.x;
+        r[2 * q + 1] = v.y;
+    }
+}
+
+// correctly rounded reciprocal (the value of 1 / x)
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // d_k = s_k + sum_i |a_ik| of a staged column (excess first), in a fixed order: four partial sums
 // over every fourth entry.
-template <int BWP>
-__device__ __forceinline__ float pivot_sum(const float (&c)[BWP]) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+template <typename V, int BWP>
+__device__ __forceinline__ V pivot_sum(const V (&c)[BWP]) {
+    V a0 = (V)0, a1 = (V)0, a2 = (V)0, a3 = (V)0;
 #pragma unroll
     for (int q = 0; q < BWP / 4; ++q) {
         a0 += c[4 * q];
@@ -190,59 +205,60 @@ __global__ void __launch_bounds__(32) k_ldl_gth_pipe(float* __restrict__ gcol_al
 // results are bit for bit the same.
 constexpr int GTH_BULK = 3;  // warps applying the bulk of each pivot
 
-template <int BW, int W>
-__device__ __forceinline__ void gth_bulk(float* col, const float* slk, const float (&cv)[(BW + 1 + 3) & ~3],
+template <typename V, int BW, int W>
+__device__ __forceinline__ void gth_bulk(V* col, const V* slk, const V (&cv)[(BW + 1 + 3) & ~3],
                                          int k, int t, int lim) {
     constexpr int BWP = (BW + 1 + 3) & ~3;
     constexpr int NT = (BW - 1 - (W + 1) + GTH_BULK) / GTH_BULK;  // columns of this warp: tau = W+1, W+4, ..
-    float ev[NT > 0 ? NT : 1], sv[NT > 0 ? NT : 1];
-    float* ck = col + (int64_t)k * BWP + t;
+    V ev[NT > 0 ? NT : 1], sv[NT > 0 ? NT : 1];
+    V* ck = col + (int64_t)k * BWP + t;
 #pragma unroll
     for (int q = 0; q < NT; ++q) {
         const int tau = W + 1 + GTH_BULK * q;
-        ev[q] = tau <= lim ? ck[tau * BWP] : 0.f;
-        sv[q] = tau <= lim ? slk[tau + t] : 0.f;
+        ev[q] = tau <= lim ? ck[tau * BWP] : (V)0;
+        sv[q] = tau <= lim ? slk[tau + t] : (V)0;
     }
 #pragma unroll
     for (int q = 0; q < NT; ++q) {
         const int tau = W + 1 + GTH_BULK * q;
-        if (tau <= lim) ck[tau * BWP] = fmaf(sv[q], cv[tau], ev[q]);
+        if (tau <= lim) ck[tau * BWP] = fma(sv[q], cv[tau], ev[q]);
     }
 }
 
-template <int BW>
-__global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __restrict__ gcol_all,
-                                                                        float* __restrict__ grow_all, int nc,
+template <typename V, int BW>
+__global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(V* __restrict__ gcol_all,
+                                                                        V* __restrict__ grow_all, int nc,
                                                                         int bw, GkState* st) {
     constexpr int BWP = (BW + 1 + 3) & ~3;
     constexpr int SLW = BWP + BW;
     constexpr int NTH = 32 * (1 + GTH_BULK);
-    extern __shared__ __align__(128) float col[];
-    __shared__ float sl[2][SLW];
+    extern __shared__ __align__(128) unsigned char colraw[];
+    V* col = reinterpret_cast<V*>(colraw);
+    __shared__ V sl[2][SLW];
     __shared__ __align__(8) uint64_t bar;
     const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (parked(st[inst])) return;
-    float* gc = gcol_all + (int64_t)inst * nc * BWP;
-    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    V* gc = gcol_all + (int64_t)inst * nc * BWP;
+    V* gr = grow_all + (int64_t)inst * nc * BWP;
     if (tid == 0) {
         mbar_init(&bar, 1);
-        mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(float)));
-        bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(float)), &bar);
+        mbar_expect_tx(&bar, (uint32_t)(nc * BWP * sizeof(V)));
+        bulk_load(col, gc, (uint32_t)(nc * BWP * sizeof(V)), &bar);
     }
     for (int e = tid; e < nc * BWP; e += NTH)  // row layout: entries no pivot writes
-        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
-    for (int e = tid; e < 2 * SLW; e += NTH) (&sl[0][0])[e] = 0.f;  // l beyond the band stays 0
-    for (int e = tid; e < BWP; e += NTH) col[(int64_t)nc * BWP + e] = 0.f;
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = (V)0;
+    for (int e = tid; e < 2 * SLW; e += NTH) (&sl[0][0])[e] = (V)0;  // l beyond the band stays 0
+    for (int e = tid; e < BWP; e += NTH) col[(int64_t)nc * BWP + e] = (V)0;
     __syncthreads();
     tma_wait_tile(&bar, st, inst);
     const int t = lane + 1;
     const bool mine = t <= bw;
     // warp 0 keeps the column of the current pivot in registers from the step that formed it
-    float cw[BWP];
+    V cw[BWP];
     if (warp == 0) {  // pivot 0
         load_row<BWP>(cw, col);
-        const float rd = __frcp_rn(pivot_sum(cw));
-        const float l = mine ? col[t] * rd : 0.f;
+        const V rd = rcp_rn(pivot_sum<V, BWP>(cw));
+        const V l = mine ? col[t] * rd : (V)0;
         if (mine) {
             sl[0][t] = l;
             gc[t] = l;
@@ -252,26 +268,26 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __
     }
     __syncthreads();
     for (int k = 0; k < nc; ++k) {
-        const float* slk = sl[k & 1];
+        const V* slk = sl[k & 1];
         const int lim = min(bw - t, nc - 1 - k);  // the columns k + tau lane t-1 updates: tau <= lim
         if (warp == 0) {
             // pivot k's update of column k+1 and its excess; the lane's own entry stays in a register
-            float* e1 = col + (int64_t)(k + 1) * BWP + t;
-            float own = mine ? *e1 : 0.f;  // rows t > bw are outside the column (and the table)
+            V* e1 = col + (int64_t)(k + 1) * BWP + t;
+            V own = mine ? *e1 : (V)0;  // rows t > bw are outside the column (and the table)
             if (1 <= lim) {
-                own = fmaf(slk[1 + t], cw[1], own);
+                own = fma(slk[1 + t], cw[1], own);
                 *e1 = own;
             }
             if (t == 1 && k + 1 < nc) {
-                float* e = col + (int64_t)(k + 1) * BWP;
-                *e = fmaf(slk[1], cw[0], *e);
+                V* e = col + (int64_t)(k + 1) * BWP;
+                *e = fma(slk[1], cw[0], *e);
             }
             __syncwarp();
             if (k + 1 < nc) {
-                float* sln = sl[(k + 1) & 1];
+                V* sln = sl[(k + 1) & 1];
                 load_row<BWP>(cw, col + (int64_t)(k + 1) * BWP);
-                const float rd = __frcp_rn(pivot_sum(cw));
-                const float l = mine ? own * rd : 0.f;
+                const V rd = rcp_rn(pivot_sum<V, BWP>(cw));
+                const V l = mine ? own * rd : (V)0;
                 if (mine) {
                     sln[t] = l;
                     gc[(int64_t)(k + 1) * BWP + t] = l;
@@ -280,18 +296,18 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(float* __
                 if (lane == 0) gc[(int64_t)(k + 1) * BWP] = rd;
             }
         } else {
-            float cv[BWP];
+            V cv[BWP];
             load_row<BWP>(cv, col + (int64_t)k * BWP);  // column k is final
             if (warp == 1) {
-                gth_bulk<BW, 1>(col, slk, cv, k, t, lim);
+                gth_bulk<V, BW, 1>(col, slk, cv, k, t, lim);
                 if (t >= 2 && mine && k + t < nc) {
-                    float* e = col + (int64_t)(k + t) * BWP;
-                    *e = fmaf(slk[t], cv[0], *e);
+                    V* e = col + (int64_t)(k + t) * BWP;
+                    *e = fma(slk[t], cv[0], *e);
                 }
             } else if (warp == 2) {
-                gth_bulk<BW, 2>(col, slk, cv, k, t, lim);
+                gth_bulk<V, BW, 2>(col, slk, cv, k, t, lim);
             } else {
-                gth_bulk<BW, 3>(col, slk, cv, k, t, lim);
+                gth_bulk<V, BW, 3>(col, slk, cv, k, t, lim);
             }
         }
         __syncthreads();
@@ -310,23 +326,24 @@ bool gth_split_enabled() {
 // in X[k][j].  Backward from the last row to row j: x_i = y_i + (pending), then the rows above
 // receive l_{i,i-t} x_i.  x_i (i >= j) is stored at X[i][j] and X[j][i].  The factor tables are
 // staged in shared memory for each pass.
-template <int BW>
-__global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ gcol_all,
-                                                     const float* __restrict__ grow_all, float* __restrict__ X_all,
+template <typename V, int BW>
+__global__ void __launch_bounds__(128) k_gth_inverse(const V* __restrict__ gcol_all,
+                                                     const V* __restrict__ grow_all, V* __restrict__ X_all,
                                                      int nc, GkState* st) {
     constexpr int BWP = (BW + 1 + 3) & ~3;
-    extern __shared__ __align__(128) float tab[];
+    extern __shared__ __align__(128) unsigned char tabraw[];
+    V* tab = reinterpret_cast<V*>(tabraw);
     const int inst = blockIdx.y;
     if (parked(st[inst])) return;
     const int jb = blockIdx.x * 128;
     const int j = jb + threadIdx.x;
     const int j0 = jb + (threadIdx.x & ~31);
-    const float* gc = gcol_all + (int64_t)inst * nc * BWP;
-    const float* gr = grow_all + (int64_t)inst * nc * BWP;
-    float* X = X_all + (int64_t)inst * nc * nc;
+    const V* gc = gcol_all + (int64_t)inst * nc * BWP;
+    const V* gr = grow_all + (int64_t)inst * nc * BWP;
+    V* X = X_all + (int64_t)inst * nc * nc;
     const bool live = j < nc;
     __shared__ __align__(8) uint64_t bar[2];
-    const uint32_t bytes = (uint32_t)((nc - jb) * BWP * sizeof(float));
+    const uint32_t bytes = (uint32_t)((nc - jb) * BWP * sizeof(V));
     // ---- forward ----
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -336,22 +353,22 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ g
     }
     __syncthreads();
     tma_wait_tile(&bar[0], st, inst);
-    float pend[BW];
+    V pend[BW];
 #pragma unroll
-    for (int u = 0; u < BW; ++u) pend[u] = 0.f;
+    for (int u = 0; u < BW; ++u) pend[u] = (V)0;
     if (j0 < nc) {
         for (int base = j0; base < nc; base += BW) {
 #pragma unroll
             for (int u = 0; u < BW; ++u) {
                 const int k = base + u;
                 if (k < nc) {
-                    float row[BWP];
+                    V row[BWP];
                     load_row<BWP>(row, tab + (int64_t)(k - jb) * BWP);
-                    const float z = pend[u] + (k == j ? 1.f : 0.f);
-                    pend[u] = 0.f;
+                    const V z = pend[u] + (k == j ? (V)1 : (V)0);
+                    pend[u] = (V)0;
                     if (live && k >= j) X[(int64_t)k * nc + j] = z * row[0];
 #pragma unroll
-                    for (int t = 1; t <= BW; ++t) pend[(u + t) & (BW - 1)] = fmaf(row[t], z, pend[(u + t) & (BW - 1)]);
+                    for (int t = 1; t <= BW; ++t) pend[(u + t) & (BW - 1)] = fma(row[t], z, pend[(u + t) & (BW - 1)]);
                 }
             }
         }
@@ -364,41 +381,41 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const float* __restrict__ g
     }
     tma_wait_tile(&bar[1], st, inst);
 #pragma unroll
-    for (int u = 0; u < BW; ++u) pend[u] = 0.f;
+    for (int u = 0; u < BW; ++u) pend[u] = (V)0;
     if (j0 >= nc) return;
     // y values of the next chunk are loaded one chunk ahead (they were written by this thread)
-    float ynx[BW];
+    V ynx[BW];
     const int top = nc - 1;
 #pragma unroll
     for (int v = 0; v < BW; ++v) {
         const int i = top - v;
-        ynx[v] = (live && i >= j) ? X[(int64_t)i * nc + j] : 0.f;
+        ynx[v] = (live && i >= j) ? X[(int64_t)i * nc + j] : (V)0;
     }
     // the warp's chunk of x (BW rows x 32 columns) goes through shared memory so that the mirror
     // entries X[j][i] are written along rows
-    float (*tile)[33] = reinterpret_cast<float (*)[33]>(tab + (size_t)nc * BWP) + (threadIdx.x >> 5) * BW;
+    V (*tile)[33] = reinterpret_cast<V (*)[33]>(tab + (size_t)nc * BWP) + (threadIdx.x >> 5) * BW;
     const int lane = threadIdx.x & 31;
     for (int base = top; base >= j0; base -= BW) {
-        float ycur[BW];
+        V ycur[BW];
 #pragma unroll
         for (int v = 0; v < BW; ++v) ycur[v] = ynx[v];
 #pragma unroll
         for (int v = 0; v < BW; ++v) {
             const int i = base - BW - v;
-            ynx[v] = (live && i >= j && i >= j0) ? X[(int64_t)i * nc + j] : 0.f;
+            ynx[v] = (live && i >= j && i >= j0) ? X[(int64_t)i * nc + j] : (V)0;
         }
 #pragma unroll
         for (int v = 0; v < BW; ++v) {
             const int i = base - v;
             if (i >= j0) {
-                float row[BWP];
+                V row[BWP];
                 load_row<BWP>(row, tab + (int64_t)(i - jb) * BWP);
-                const float x = ycur[v] + pend[v];
-                pend[v] = 0.f;
+                const V x = ycur[v] + pend[v];
+                pend[v] = (V)0;
                 tile[v][lane] = x;
                 if (live && i >= j) X[(int64_t)i * nc + j] = x;
 #pragma unroll
-                for (int t = 1; t <= BW; ++t) pend[(v + t) & (BW - 1)] = fmaf(row[t], x, pend[(v + t) & (BW - 1)]);
+                for (int t = 1; t <= BW; ++t) pend[(v + t) & (BW - 1)] = fma(row[t], x, pend[(v + t) & (BW - 1)]);
             }
         }
         __syncwarp();
@@ -653,60 +670,71 @@ int gth_stride(int bw) {
     return ((w ? w : bw) + 1 + 3) & ~3;
 }
 
-bool gth_supported(int bw, int nc) {
-    const int BWP = gth_stride(bw);
-    return gth_window(bw) != 0 && (size_t)nc * BWP * sizeof(float) + sizeof(float) * 4 * 32 * 33 <= 220 * 1024;
+bool gth_supported(int bw, int nc, size_t esz) {
+    const int BWP = gth_stride(bw), W = gth_window(bw);
+    if (W == 0 || (esz == 8 && W > 16)) return false;  // double: windows 8 and 16 (register budget)
+    return (size_t)nc * BWP * esz + esz * 4 * W * 33 <= 220 * 1024;
 }
 
-template <typename T>
-void gth_assemble(const T* cond, bool is_kappa, float* gcol, Dims d, int bw, int B, cudaStream_t s) {
+template <typename T, typename V>
+void gth_assemble(const T* cond, bool is_kappa, V* gcol, Dims d, int bw, int B, cudaStream_t s) {
     kbegin(KC_SETUP, s);
     const int BWP = gth_stride(bw);
     dim3 grid((unsigned)((d.N + 255) / 256), B);
-    if (is_kappa) k_gth_assemble<T, true><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
-    else k_gth_assemble<T, false><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
+    if (is_kappa) k_gth_assemble<T, V, true><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
+    else k_gth_assemble<T, V, false><<<grid, 256, 0, s>>>(cond, gcol, d, BWP);
     klaunched("k_gth_assemble");
     kfinish(s);
 }
 
-void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
-    if (!gth_supported(bw, nc)) throw std::runtime_error("gth_factor_inverse: bandwidth or size not supported");
-    kbegin(KC_SETUP, s);
+template <typename V, int BW>
+static void gth_launch(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
     const int BWP = gth_stride(bw);
-    const size_t stage = sizeof(float) * (size_t)nc * BWP;
-    const int W = gth_window(bw);
+    const size_t stage = sizeof(V) * (size_t)nc * BWP;
+    const size_t sp = stage + sizeof(V) * BWP;
+    bool done = false;
+    if constexpr (sizeof(V) == 4) {
+        if (!gth_split_enabled()) {
+            auto kp = k_ldl_gth_pipe<BW>;
+            if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
+            kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);
+            klaunched("k_ldl_gth_pipe");
+            done = true;
+        }
+    }
+    if (!done) {
+        auto kq = k_ldl_gth_split<V, BW>;
+        if (sp > 48 * 1024) cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
+        kq<<<B, 32 * (1 + GTH_BULK), sp, s>>>(gcol, grow, nc, bw, st);
+        klaunched("k_ldl_gth_split");
+    }
+    auto ki = k_gth_inverse<V, BW>;
+    const size_t ism = stage + sizeof(V) * 4 * BW * 33;
+    if (ism > 48 * 1024) cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
     dim3 igrid((unsigned)((nc + 127) / 128), B);
-#define GTH_CASE(BW_)                                                                                     \
-    case BW_: {                                                                                           \
-        const size_t sp = stage + sizeof(float) * BWP;                                                    \
-        if (gth_split_enabled()) {                                                                        \
-            auto kq = k_ldl_gth_split<BW_>;                                                               \
-            if (sp > 48 * 1024) cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
-            kq<<<B, 32 * (1 + GTH_BULK), sp, s>>>(gcol, grow, nc, bw, st);                               \
-            klaunched("k_ldl_gth_split");                                                                 \
-        } else {                                                                                          \
-            auto kp = k_ldl_gth_pipe<BW_>;                                                                \
-            if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
-            kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);                                                 \
-            klaunched("k_ldl_gth_pipe");                                                                  \
-        }                                                                                                 \
-        auto ki = k_gth_inverse<BW_>;                                                                     \
-        const size_t ism = stage + sizeof(float) * 4 * BW_ * 33;                                          \
-        if (ism > 48 * 1024) cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism); \
-        ki<<<igrid, 128, ism, s>>>(gcol, grow, X, nc, st);                                                \
-        klaunched("k_gth_inverse");                                                                       \
-        break;                                                                                            \
+    ki<<<igrid, 128, ism, s>>>(gcol, grow, X, nc, st);
+    klaunched("k_gth_inverse");
+}
+
+template <typename V>
+void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+    if (!gth_supported(bw, nc, sizeof(V)))
+        throw std::runtime_error("gth_factor_inverse: bandwidth or size not supported");
+    kbegin(KC_SETUP, s);
+    switch (gth_window(bw)) {
+        case 8: gth_launch<V, 8>(gcol, grow, X, nc, bw, B, st, s); break;
+        case 16: gth_launch<V, 16>(gcol, grow, X, nc, bw, B, st, s); break;
+        case 32:
+            if constexpr (sizeof(V) == 4) gth_launch<V, 32>(gcol, grow, X, nc, bw, B, st, s);
+            break;
     }
-    switch (W) {
-        GTH_CASE(8)
-        GTH_CASE(16)
-        GTH_CASE(32)
-    }
-#undef GTH_CASE
     kfinish(s);
 }
 
-template void gth_assemble<float>(const float*, bool, float*, Dims, int, int, cudaStream_t);
-template void gth_assemble<double>(const double*, bool, float*, Dims, int, int, cudaStream_t);
+template void gth_assemble<float, float>(const float*, bool, float*, Dims, int, int, cudaStream_t);
+template void gth_assemble<double, float>(const double*, bool, float*, Dims, int, int, cudaStream_t);
+template void gth_assemble<double, double>(const double*, bool, double*, Dims, int, int, cudaStream_t);
+template void gth_factor_inverse<float>(float*, float*, float*, int, int, int, GkState*, cudaStream_t);
+template void gth_factor_inverse<double>(double*, double*, double*, int, int, int, GkState*, cudaStream_t);
 
 }  // namespace plsqr

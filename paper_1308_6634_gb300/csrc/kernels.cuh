@@ -114,12 +114,14 @@ void coarse_inverse(const double* band, const double* rdiag, double* X, int nc, 
 template <typename T>
 void coarse_symv(const T* X, const T* b, T* x, int nc, int B, const GkState* st, cudaStream_t s);
 void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s);
-// Single-precision subtraction-free coarse factorisation and inverse (bandwidth <= 32).
+// Subtraction-free coarse factorisation and inverse in float (bandwidth <= 32) or double
+// (bandwidth <= 16): V is the type of the tables and of X.
 int gth_stride(int bw);
-bool gth_supported(int bw, int nc);
-template <typename T>
-void gth_assemble(const T* cond, bool is_kappa, float* gcol, Dims d, int bw, int B, cudaStream_t s);
-void gth_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
+bool gth_supported(int bw, int nc, size_t esz);
+template <typename T, typename V>
+void gth_assemble(const T* cond, bool is_kappa, V* gcol, Dims d, int bw, int B, cudaStream_t s);
+template <typename V>
+void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
 // Wide bands: the float L D L^T with a window of bw + 1 columns, and the float inverse with a warp
 // per column.
 bool gth_wide_supported(int bw, int nc);

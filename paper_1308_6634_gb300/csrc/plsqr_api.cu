@@ -88,8 +88,9 @@ struct plsqr_ctx {
     // single-precision handles with a coarsest bandwidth <= 32: subtraction-free L D L^T in float
     bool gth = false;
     bool gthw = false;  // wide band: float L D L^T (windowed) and float inverse
-    float* gcol = nullptr;  // [B][nc][stride]: column layout (input conductances, then l and 1/d)
-    float* grow = nullptr;  // [B][nc][stride]: row layout of l
+    char* gcol = nullptr;  // [B][nc][stride] (float, or double for FP64 handles): column layout
+                           // (input conductances, then l and 1/d)
+    char* grow = nullptr;  // [B][nc][stride]: row layout of l
     GkState* st = nullptr;
     SolveParams* prm_dev = nullptr;
     SolveParams* prm_host = nullptr;  // pinned
@@ -211,7 +212,8 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     pl.bw = c->ndim == 3 ? dc.nx * dc.ny : dc.nx;
     if (pl.nc > 16384) throw InvalidArg("coarsest level has more than 16384 cells: add levels");
     const char* e64 = std::getenv("PLSQR_COARSE64");
-    pl.gth = c->precision == PLSQR_FP32 && gth_supported(pl.bw, pl.nc) && !(e64 && e64[0] == '1');
+    const size_t vsz = c->precision == PLSQR_FP64 ? 8 : 4;  // the GTH tables in the handle's type
+    pl.gth = gth_supported(pl.bw, pl.nc, vsz) && !(e64 && e64[0] == '1');
     pl.gthw = c->precision == PLSQR_FP32 && !pl.gth && gth_wide_supported(pl.bw, pl.nc) && !(e64 && e64[0] == '1');
     if (!pl.gth && !pl.gthw &&
         (size_t)(pl.bw + 4) * (pl.bw + 1) * sizeof(double) + (size_t)pl.bw * (pl.bw + 1) * 2 + pl.bw * 8 >
@@ -228,8 +230,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     if (c->ndim == 2)
         for (int l = 0; l + 1 < pl.L; ++l) b += esz * B * pl.level_N[l];  // reciprocal diagonals
     if (pl.gth || pl.gthw) {
-        b += sizeof(float) * B * (size_t)pl.nc * 2 * gth_stride(pl.bw);
-        b += sizeof(float) * B * (size_t)pl.nc * pl.nc;
+        b += (pl.gth ? vsz : sizeof(float)) * B * (size_t)pl.nc * (2 * gth_stride(pl.bw) + pl.nc);
     } else {
         b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
         b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
@@ -354,14 +355,15 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
                           l == 0 ? K16(h) : nullptr);
     const int lc = h->L - 1;
     const T* cc = lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond);
-    if (h->gth) {
-        gth_assemble<T>(cc, lc == 0, h->gcol, h->lv[lc].d, h->bw, B, s);
-        gth_factor_inverse(h->gcol, h->grow, h->Xf, h->nc, h->bw, B, h->st, s);
+    if (h->gth) {  // tables and inverse in the handle's type
+        gth_assemble<T, T>(cc, lc == 0, P<T>(h->gcol), h->lv[lc].d, h->bw, B, s);
+        gth_factor_inverse<T>(P<T>(h->gcol), P<T>(h->grow), const_cast<T*>(coarse_inverse_of<T>(h)), h->nc, h->bw,
+                              B, h->st, s);
         return;
     }
     if (h->gthw) {
-        gth_assemble<T>(cc, lc == 0, h->gcol, h->lv[lc].d, h->bw, B, s);
-        gth_wide_factor_inverse(h->gcol, h->grow, h->Xf, h->nc, h->bw, B, h->st, s);
+        gth_assemble<T, float>(cc, lc == 0, P<float>(h->gcol), h->lv[lc].d, h->bw, B, s);
+        gth_wide_factor_inverse(P<float>(h->gcol), P<float>(h->grow), h->Xf, h->nc, h->bw, B, h->st, s);
         return;
     }
     coarse_assemble<T>(cc, lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
@@ -870,9 +872,11 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         }
         h->gth = pl.gth;
         h->gthw = pl.gthw;
-        if (h->gth || h->gthw) {
-            h->gcol = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
-            h->grow = (float*)dalloc(h, sizeof(float) * B * (size_t)h->nc * gth_stride(h->bw));
+        if (h->gth || h->gthw) {  // tables in the handle's type (the wide route: float only)
+            const size_t vsz = h->gth ? h->esz : sizeof(float);
+            h->gcol = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
+            h->grow = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
+            if (h->fp64) h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
         } else {
             h->band = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * (h->bw + 1));
             h->rdiag = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc);

@@ -187,6 +187,23 @@ def test_single_precision_coarse_solve_matches_double_route(shape, levels, monke
     assert rel(outs[0], outs[1]) < 2e-6
 
 
+@pytest.mark.parametrize("shape,levels", [((64, 64), 3), ((128, 96), 4), ((8, 16), 1), ((12, 12), 1)])
+def test_double_subtraction_free_coarse_solve_matches_cholesky_route(shape, levels, monkeypatch):
+    """FP64 handles with a coarsest bandwidth <= 16 factor the coarsest operator by the
+    subtraction-free L D L^T in double; the V-cycle must match the banded-Cholesky route of the same
+    handle type (PLSQR_COARSE64=1) to double rounding, and the oracle's dense Cholesky solve."""
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(15).standard_normal(shape)
+    outs = []
+    for route in ("0", "1"):
+        monkeypatch.setenv("PLSQR_COARSE64", route)
+        S = _P().Solver(shape, "fp64", levels=levels)
+        S.prec_setup(dev(kappa, "fp64"))
+        outs.append(host(S.prec_apply(dev(b, "fp64"))))
+    assert rel(outs[0], outs[1]) < 1e-12
+    assert rel(outs[0], O.Multigrid(kappa, levels, 2, 1).apply(b)) < 1e-11
+
+
 @pytest.mark.parametrize("shape,levels", [((256, 256), 4), ((64, 64), 3), ((8, 8), 1), ((16, 24), 1)])
 def test_four_warp_float_factor_matches_one_warp(shape, levels, monkeypatch):
     """The float L D L^T split over four warps (look-ahead: one warp runs the pivot chain, three
