@@ -267,7 +267,10 @@ int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, 
  * plsqr_step: enqueues one outer step for every running slot that has not reached its target
  *   (the others are skipped) and returns without waiting.
  * plsqr_query: 1 while the last enqueued slot operation runs, 0 when done, < 0 on a CUDA error.
- * plsqr_slot_progress: outer steps done by `slot` and whether it is running (host-side counts).
+ * plsqr_slot_progress: outer steps done by `slot` (host-side count) and *active: 0 empty, 1
+ *   running, 2 stopped early by the outer rule of plsqr_set_stopping (R fell by less than r_rel:
+ *   its f is final; reported once the step that stopped it is done).  Stopping parameters set for
+ *   an index before plsqr_slot_start apply to the request started there.
  * plsqr_slot_finish: copies the slot's f (device, N values) to f_out, fills stats (histories of
  *   the steps done, R of the final f), empties the slot; waits for the handle's stream.
  *   Returns PLSQR_E_BREAKDOWN when the slot broke down (f holds its last complete iterate). */

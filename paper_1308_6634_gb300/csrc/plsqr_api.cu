@@ -105,6 +105,7 @@ struct plsqr_ctx {
     std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     // slots (continuous batching): host bookkeeping, per-slot blur taps
     bool serving = false;
+    bool st_after_step = false;  // st_host holds the states copied after the last plsqr_step
     std::vector<int> slot_active, slot_outer, slot_target;
     float* taps_inst = nullptr;       // device [B][2][2R+1]
     float* taps_inst_host = nullptr;  // pinned staging, same shape
@@ -1160,6 +1161,8 @@ int plsqr_slot_start(plsqr_handle h, int32_t slot, const void* g, int32_t reg, d
         const size_t mb = h->esz * h->m, nb = h->esz * h->d.N;
         ck(cudaMemcpyAsync(h->g + slot * mb, g, mb, cudaMemcpyDeviceToDevice, s), "copy g");
         ck(cudaMemsetAsync(h->f + slot * nb, 0, nb, s), "f0");
+        ck(cudaEventSynchronize(h->ev_out), "cudaEventSynchronize");  // no copy of the states in flight
+        h->st_host[slot].status = ST_OK;
         h->prm_host[slot].reg = reg;
         h->prm_host[slot].T = T;
         h->prm_host[slot].tau = tau;
@@ -1198,6 +1201,9 @@ int plsqr_step(plsqr_handle h) {
         for (int b = 0; b < h->B; ++b)
             if (h->slot_active[b] && h->slot_outer[b] < h->slot_target[b]) ++h->slot_outer[b];
         h->last_launches = h->prof.launches - launches0;
+        // the instance states after the step, read by plsqr_slot_progress once the step is done
+        ck(cudaMemcpyAsync(h->st_host, h->st, sizeof(GkState) * h->B, cudaMemcpyDeviceToHost, s), "state");
+        h->st_after_step = true;
         ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
         return PLSQR_OK;
     });
@@ -1218,8 +1224,15 @@ int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32
     if (!h) return PLSQR_E_INVALID;
     if (slot < 0 || slot >= h->B) return fail(h, PLSQR_E_INVALID, "slot out of range");
     const bool on = h->serving && h->slot_active[slot];
+    int act = on ? 1 : 0;
+    // stopped early by the outer rule (Algorithm 3 step 5): visible once the last step is done
+    if (on && h->st_after_step) {
+        const cudaError_t q = cudaEventQuery(h->ev_out);
+        if (q == cudaSuccess && h->st_host[slot].status == ST_CONVERGED) act = 2;
+        if (q == cudaErrorNotReady) cudaGetLastError();  // not ready is not an error
+    }
     if (outer_done) *outer_done = on ? h->slot_outer[slot] : 0;
-    if (active) *active = on ? 1 : 0;
+    if (active) *active = act;
     return PLSQR_OK;
 }
 

@@ -380,9 +380,10 @@ class Solver:
         return rc == 1
 
     def slot_progress(self, slot):
+        """(outer steps done, state): state 0 empty, 1 running, 2 stopped early by the outer rule."""
         done, act = C.c_int32(0), C.c_int32(0)
         _check(self.h, lib().plsqr_slot_progress(self.h, int(slot), C.byref(done), C.byref(act)))
-        return done.value, bool(act.value)
+        return done.value, act.value
 
     def slot_finish(self, slot, n_outer, n_inner, f_out=None):
         """Returns (f, info) for a slot that ran n_outer steps of n_inner iterations."""

@@ -45,6 +45,11 @@ class Request:
     t_arrival: float = 0.0  # seconds after the stream starts
     sigma: float = 0.0      # blur
     n_angles: int = 0       # tomography
+    # stopping rules (0: off): S4 with eta * delta per inner solve, the outer stop when R falls by
+    # less than r_rel; a request stopped by the outer rule leaves its slot early
+    eta: float = 0.0
+    delta: float = 0.0
+    r_rel: float = 0.0
     # filled by the engine
     t_admit: float = math.nan
     t_done: float = math.nan
@@ -165,8 +170,8 @@ class Bucket:
             return 0
         done = 0
         for slot, (req, _) in list(self.running.items()):
-            k, _ = S.slot_progress(slot)
-            if k >= req.n_outer:
+            k, state = S.slot_progress(slot)
+            if k >= req.n_outer or state == 2:
                 f, info = S.slot_finish(slot, req.n_outer, req.n_inner)
                 req.t_done = now_fn()
                 req.status = info["status"]
@@ -178,6 +183,7 @@ class Bucket:
         while free and self.queue:
             req, g = self.queue.popleft()
             slot = free.pop(0)
+            S.set_stopping(req.eta, req.delta, req.r_rel, index=slot)
             S.slot_start(slot, g, req.reg, req.T, req.tau, req.n_outer, req.n_inner,
                          sigma=(req.sigma, req.sigma) if req.kind == "blur" else None)
             req.t_admit = now_fn()

@@ -150,3 +150,45 @@ def test_admission_waits_for_memory():
     eng.run(reqs, data)
     assert all(np.isfinite(r.t_done) for r in reqs)
     assert len(eng.buckets) == 1
+
+
+def test_outer_stop_frees_the_slot_early_with_the_solo_result():
+    """A request carrying the outer stopping rule (Algorithm 3 step 5: R fell by less than r_rel)
+    is reported stopped (state 2) once the step that stopped it is done, leaves its slot before its
+    n_outer steps, and its f and histories are those of plsqr_solve alone with the same rule."""
+    from paper_1308_6634_gb300 import plsqr, serving
+    n, sigma, R, n_outer, n_inner, r_rel = 96, 4.0, 12, 12, 8, 0.05
+    g = _deblur_data(n, sigma, R, 5)
+    S1 = plsqr.Solver((n, n), "fp32", levels=3, max_batch=1)
+    S1.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    S1.set_stopping(r_rel=r_rel)
+    f1, info1 = S1.solve(g, "pm_log", 5e-2, 1e-3, n_outer, n_inner)
+    rows = int(np.sum(np.isfinite(info1["rbar_hist"][:, 0])))
+    assert 2 <= rows < n_outer  # the rule stopped the solve early
+    # the slot API: the slot reports the stop and its result is the solo one
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=4)
+    S.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    S.set_stopping(r_rel=r_rel, index=1)
+    S.slot_start(1, g, "pm_log", 5e-2, 1e-3, n_outer, n_inner)
+    steps = 0
+    while True:
+        S.step()
+        steps += 1
+        torch.cuda.synchronize()
+        k, state = S.slot_progress(1)
+        if state == 2 or k >= n_outer:
+            break
+    assert state == 2 and steps < n_outer
+    f2, info2 = S.slot_finish(1, n_outer, n_inner)
+    torch.cuda.synchronize()
+    assert torch.equal(f1, f2)
+    assert np.array_equal(info1["rbar_hist"][:rows], info2["rbar_hist"][:rows])
+    # the engine frees the slot early and keeps the result
+    req = serving.Request(rid=0, kind="blur", n=n, reg="pm_log", T=5e-2, tau=1e-3, n_outer=n_outer,
+                          n_inner=n_inner, seed=5, sigma=sigma, r_rel=r_rel)
+    eng = serving.Engine(keep_results=True, slots_for_size={n: 4})
+    eng.run([req], {0: g}, realtime=False)
+    f3, _ = eng.results()[0]
+    b = next(iter(eng.buckets.values()))
+    assert b.steps < n_outer
+    assert torch.equal(f1, f3)
