@@ -206,6 +206,14 @@ int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_
                           void* const* f_out, double* rbar_hist, int32_t* iters_done);
 int plsqr_projected_solve(int32_t k, const double* alpha, const double* beta, double tau, double* y, double* rbar);
 
+/* ---- self-test of the bounded waits ------------------------------------------------------------
+ * Every wait of a kernel on its TMA copies is bounded: when it runs out the kernel records
+ * PLSQR_E_TIMEOUT (status 5) in the instance state, waits once more (bounded) and returns.
+ * plsqr_selftest_wait runs that wait on a barrier that completes (complete != 0: *status_out = 0)
+ * or that announces bytes no copy will bring (complete = 0: *status_out = 5 after 2 x 65536
+ * polls).  No copy is issued and nothing faults or hangs.  Needs a GPU; synchronises. */
+int plsqr_selftest_wait(int32_t complete, int32_t* status_out);
+
 /* ---- V-cycle tile shapes ------------------------------------------------------------------------
  * The 2D V-cycle (Sec. 4.2 priorconditioner: red-black Gauss-Seidel smoothing, restriction,
  * prolongation on each level above the coarsest) runs each level as tiles staged in shared memory.

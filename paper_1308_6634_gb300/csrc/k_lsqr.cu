@@ -335,6 +335,29 @@ void fill_nan(double* p, int64_t n, cudaStream_t s) {
     kfinish(s);
 }
 
+// ---- self-test of the bounded wait ------------------------------------------------------------
+
+// The wait of the TMA staging (tma_wait_tile) on an mbarrier that either completes (one plain
+// arrival) or never does (an arrival that announces 16 bytes no copy will bring): the second case
+// runs out after `limit` polls, twice, and records ST_TIMEOUT in the state.  No copy is ever issued.
+__global__ void k_selftest_wait(GkState* st, int complete, uint32_t limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        if (complete) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+        else mbar_expect_tx(&bar, 16);
+    }
+    __syncthreads();
+    tma_wait_tile(&bar, st, 0, limit);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&bar);
+}
+
+void selftest_wait(GkState* st, bool complete, uint32_t limit, cudaStream_t s) {
+    k_selftest_wait<<<1, 32, 0, s>>>(st, complete ? 1 : 0, limit);
+    klaunched("k_selftest_wait");
+}
+
 // ---- stored Lanczos vectors (reuse for several damping parameters, Sec. 3.3) -------------------
 
 // V_j = v~ / alpha (the normalised basis vector the update of step 7 / 20 uses) and the current

@@ -164,6 +164,9 @@ void gk_update(T* f, T* w, const T* v, int64_t N, int B, bool init, const GkStat
 template <typename T>
 void gk_store_basis(const T* v, T* Vj, int64_t N, const GkState* st, double* ab, bool store_v, cudaStream_t s);
 constexpr int MT_MAX = 32;  // damping parameters per combination pass
+// The bounded wait of the TMA staging on a barrier that completes, or never does (complete false:
+// ST_TIMEOUT in st[0] after 2 x limit polls).  Issues no copy.
+void selftest_wait(GkState* st, bool complete, uint32_t limit, cudaStream_t s);
 template <typename T>
 struct OutPtrs {
     T* p[MT_MAX];

@@ -42,7 +42,10 @@ struct NoMem : std::runtime_error {
 };
 
 void ck(cudaError_t e, const char* what) {
-    if (e == cudaErrorMemoryAllocation) throw NoMem(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // reported through the return code: do not leave it for the caller's next CUDA call
+        throw NoMem(std::string(what) + ": " + cudaGetErrorString(e));
+    }
     if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -1425,6 +1428,27 @@ int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void
         if (iters_done) *iters_done = h->st_host[0].iter;
         return h->st_host[0].status != 0 ? PLSQR_E_BREAKDOWN : PLSQR_OK;
     });
+}
+
+int plsqr_selftest_wait(int32_t complete, int32_t* status_out) {
+    if (!status_out) return PLSQR_E_INVALID;
+    GkState* st = nullptr;
+    if (cudaMalloc(&st, sizeof(GkState)) != cudaSuccess) {
+        cudaGetLastError();
+        return PLSQR_E_NOMEM;
+    }
+    int rc = PLSQR_OK;
+    try {
+        ck(cudaMemset(st, 0, sizeof(GkState)), "memset");
+        selftest_wait(st, complete != 0, 1u << 16, nullptr);
+        GkState h{};
+        ck(cudaMemcpy(&h, st, sizeof(GkState), cudaMemcpyDeviceToHost), "state");
+        *status_out = h.status;
+    } catch (const std::exception&) {
+        rc = PLSQR_E_CUDA;
+    }
+    cudaFree(st);
+    return rc;
 }
 
 int plsqr_projected_solve(int32_t k, const double* alpha, const double* beta, double tau, double* y,

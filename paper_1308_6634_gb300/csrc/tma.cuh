@@ -71,20 +71,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TMA_WAIT_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = TMA_WAIT_LIMIT) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
 
 // All threads: wait for the tile; on timeout flag the instance and wait once more.
-__device__ __forceinline__ void tma_wait_tile(uint64_t* bar, GkState* st, int inst) {
-    if (!mbar_wait_bounded(bar, 0)) {
+__device__ __forceinline__ void tma_wait_tile(uint64_t* bar, GkState* st, int inst, uint32_t limit = TMA_WAIT_LIMIT) {
+    if (!mbar_wait_bounded(bar, 0, limit)) {
         if (threadIdx.x == 0 && st) {
             st[inst].status = ST_TIMEOUT;
             st[inst].status_any = ST_TIMEOUT;
         }
-        mbar_wait_bounded(bar, 0);
+        mbar_wait_bounded(bar, 0, limit);
     }
 }
 

@@ -86,6 +86,7 @@ def lib():
         "plsqr_mlsqr_multi_tau": ([vp, vp, i32, i32, C.POINTER(d), C.POINTER(vp), C.POINTER(d), C.POINTER(i32)],
                                   C.c_int),
         "plsqr_projected_solve": ([i32, C.POINTER(d), C.POINTER(d), d, C.POINTER(d), C.POINTER(d)], C.c_int),
+        "plsqr_selftest_wait": ([i32, C.POINTER(i32)], C.c_int),
         "plsqr_set_tile_shape": ([vp, i32, i32], C.c_int),
         "plsqr_tile_shape": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
     }
@@ -103,9 +104,19 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
             "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_mlsqr_multi_tau",
-            "plsqr_projected_solve"]
+            "plsqr_projected_solve", "plsqr_selftest_wait"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
+
+
+def selftest_wait(complete):
+    """The bounded TMA wait on a barrier that completes (returns 0) or never does (returns the
+    timeout status 5); see plsqr_selftest_wait."""
+    st = C.c_int32(-1)
+    rc = lib().plsqr_selftest_wait(1 if complete else 0, C.byref(st))
+    if rc != OK:
+        raise PlsqrError(rc, "selftest_wait failed")
+    return st.value
 
 
 def projected_solve(alpha, beta, tau):
