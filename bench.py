@@ -17,6 +17,7 @@ first MLSQR residual estimates against the oracle's).
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -184,12 +185,19 @@ TRAFFIC_SOURCES = ("common.cuh", "tma.cuh", "k_ops.cu", "k_mg.cu", "k_mg2d.cu", 
                    "k_mg2d_impl.cuh")
 
 
+def _code_only(text):
+    """Source text without comments and blank lines (the hash follows the code, not the prose)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1308_6634_gb300", "csrc")
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -106,7 +106,8 @@ __device__ __forceinline__ V pivot_sum(const V (&c)[BWP]) {
 // so the sum and reciprocal of pivot k+1 overlap that update.  l and 1/d_k go to global memory as
 // they are formed; the staged copy of column k is left as is.  Measured on the 1024^2 workload's
 // 32 x 32 coarse grid: 0.69 ms per factorisation, limited by one warp's dependent shared-memory
-// and arithmetic chain (a 4-warp split of the update was slower: one block barrier per pivot).
+// and arithmetic chain.  k_ldl_gth_split below (four warps, the pivot chain on one of them) takes
+// 0.29 ms and is the default; this kernel remains for comparisons (PLSQR_GTH_WARPS=1).
 template <int BW>
 __global__ void __launch_bounds__(32) k_ldl_gth_pipe(float* __restrict__ gcol_all, float* __restrict__ grow_all,
                                                      int nc, int bw, GkState* st) {

@@ -1,6 +1,6 @@
 // k_mg2d_impl.cuh -- temporally blocked V-cycle kernels for 2D grids (Sec. 4.2 priorconditioner),
-// templated on the tile shape; k_mg2d.cu and k_mg2d_alt.cu instantiate them for the shapes the
-// autotuner chooses from.
+// templated on the tile shape; k_mg2d.cu, k_mg2d_alt.cu and k_mg2d_alt2.cu instantiate them for
+// the shapes the autotuner chooses from.
 //
 // A block owns a TX x TY tile of one level and stages the tile plus a halo of the right-hand
 // side, the edge conductances and (post-smoothing) the iterate in shared memory, with TMA tile
