@@ -201,7 +201,9 @@ int64_t plsqr_last_launches(plsqr_handle h);
  *   vectors do not fit, PLSQR_E_STATE while slots are in use.  Synchronises.
  * plsqr_projected_solve: its host part, which needs no GPU: y (k values) and ||rbar_i|| (k values,
  *   may be NULL) of (3.6) from alpha[0..k] = alpha_1 .. alpha_{k+1} and beta[0..k] = beta_1 ..
- *   beta_{k+1}, by the rotations of Algorithm 2 (steps 8-20) applied to coefficient vectors. */
+ *   beta_{k+1}, by the rotations of Algorithm 2 (steps 8-20) applied to coefficient vectors.
+ *   PLSQR_E_INVALID for k < 1, NULL arrays or tau < 0; PLSQR_E_BREAKDOWN if a rotation is
+ *   undefined (rho = 0 or not finite). */
 int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_t n_tau, const double* taus,
                           void* const* f_out, double* rbar_hist, int32_t* iters_done);
 int plsqr_projected_solve(int32_t k, const double* alpha, const double* beta, double tau, double* y, double* rbar);

@@ -1539,7 +1539,14 @@ int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_
             ck(cudaStreamSynchronize(s), "sync");
             k = std::min<int>(n_inner, h->st_host[0].iter);
             if (iters_done) *iters_done = k;
-            if (k < 1) throw std::runtime_error("the bidiagonalisation broke down at its first step");
+            if (k < 1) {  // broke down before its first step: every f(tau) is the starting point 0
+                for (int t = 0; t < n_tau; ++t) ck(cudaMemsetAsync(f_out[t], 0, h->esz * N, s), "memset");
+                if (rbar_hist)
+                    for (int i = 0; i < n_tau * n_inner; ++i) rbar_hist[i] = NAN;
+                ck(cudaStreamSynchronize(s), "sync");
+                release();
+                return PLSQR_E_BREAKDOWN;
+            }
             std::vector<double> alpha((size_t)k + 1), beta((size_t)k + 1);
             for (int j = 0; j <= k; ++j) {
                 alpha[j] = abh[2 * j];

@@ -508,3 +508,11 @@ def test_multi_tau_invalid_arguments():
     for taus in ([-1.0], [float("nan")], [0.0] * 33):
         with pytest.raises(RuntimeError):
             S.mlsqr_multi_tau(g, taus, 3)
+
+
+def test_multi_tau_zero_data_breaks_down_at_the_start():
+    S = _P().Solver((32, 32), "fp64", levels=2)
+    S.set_operator("blur", sigma=(1.0, 1.0), radius=(3, 3))
+    S.prec_setup(dev(np.ones((32, 32)), "fp64"))
+    fs, hists, done = S.mlsqr_multi_tau(dev(np.zeros((32, 32)), "fp64"), [0.0, 0.1], 4)
+    assert done == 0 and all(float(f.abs().max()) == 0.0 for f in fs) and np.all(np.isnan(hists))
