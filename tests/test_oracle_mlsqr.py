@@ -138,3 +138,29 @@ def test_priorconditioning_reaches_discrepancy_sooner():
 
     kp, ku = first_below(mg), first_below(None)
     assert kp < ku
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_iterates_of_every_tau_lie_in_one_krylov_space(levels):
+    """Sec. 2.1 / 3.3: K_k(P A^T A, P A^T g) does not depend on tau (shift invariance), so the k-th
+    MLSQR iterate of every damping parameter lies in that one space.  The space is built here by
+    dense products, independently of the oracle's bidiagonalisation; projecting each iterate on it
+    leaves rounding only, while the iterates themselves differ between the values of tau."""
+    op, g, kappa = _problem()
+    shape = op.shape
+    mg = O.Multigrid(kappa, levels=levels, nu=2, cycles=1)
+    P = _dense(mg.apply, shape)
+    A = _dense(op.A, shape)
+    k = 4
+    K = [P @ (A.T @ g.ravel())]
+    for _ in range(k - 1):
+        K.append(P @ (A.T @ (A @ K[-1])))
+    Q, _ = np.linalg.qr(np.stack(K, 1))
+    fs = []
+    for tau in (0.0, 1e-3, 0.05, 1.0):
+        f, _, st = O.mlsqr(op, g, tau, k, prec=mg)
+        assert st == 0
+        v = f.ravel()
+        assert np.linalg.norm(v - Q @ (Q.T @ v)) <= 1e-8 * np.linalg.norm(v), tau
+        fs.append(v)
+    assert np.linalg.norm(fs[-1] - fs[0]) > 1e-2 * np.linalg.norm(fs[0])  # the damping does change the iterate
