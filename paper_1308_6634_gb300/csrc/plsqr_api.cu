@@ -144,6 +144,9 @@ char* dalloc(plsqr_ctx* h, size_t bytes) {
     if (bytes == 0) bytes = 16;
     ck(cudaMalloc(&p, bytes), "cudaMalloc");
     h->allocs.push_back(p);
+    // zeroed once, so that no kernel (the tile-shape timing before the first plsqr_prec_setup
+    // included) ever reads uninitialised memory
+    ck(cudaMemset(p, 0, bytes), "cudaMemset");
     return (char*)p;
 }
 
@@ -500,11 +503,12 @@ void autotune(plsqr_ctx* h, bool fresh = false) {
             T* b = isk ? P<T>(h->p) : P<T>(Lv.b);
             T* xpre = isk ? P<T>(h->tmp) : P<T>(Lv.x);
             T* x = isk ? P<T>(h->v) : P<T>(Lv.x2);
+            // the kernels read the hierarchy (kappa / conductances, 1/diagonal) as it is, so a tuning
+            // between plsqr_prec_setup and plsqr_prec_apply leaves it intact; they write only V-cycle
+            // scratch (the level's iterates and the coarse right-hand side), zeroed with its inputs
             const int64_t n = (int64_t)B * Lv.d.N, nc = (int64_t)B * C.d.N;
             ck(cudaMemsetAsync(b, 0, sizeof(T) * n, s), "memset");
-            ck(cudaMemsetAsync(Lv.rd, 0, sizeof(T) * n, s), "memset");
             ck(cudaMemsetAsync(C.x2, 0, sizeof(T) * nc, s), "memset");
-            if (!isk) ck(cudaMemsetAsync(Lv.cond, 0, sizeof(T) * 2 * n, s), "memset");
             int best = 0;
             float best_ms = 0.f;
             for (int id = 0;; ++id) {

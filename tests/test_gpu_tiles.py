@@ -95,3 +95,18 @@ def test_autotuned_solve_equals_default_shapes(monkeypatch):
     assert all(s[0] == 0 for s in shapes[1])
     for l, (sid, tx, ty, nth) in enumerate(shapes[0]):
         assert 0 <= sid < (N_FINE if l == 0 else N_COARSE) and tx > 0 and ty > 0 and nth > 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_explicit_autotune_keeps_the_hierarchy(prec):
+    """plsqr_autotune between plsqr_prec_setup and plsqr_prec_apply times the kernels on the
+    handle's buffers; the hierarchy it reads must come out unchanged."""
+    shape, levels = (256, 256), 4
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(22).standard_normal(shape)
+    S = _P().Solver(shape, prec, levels=levels)
+    S.prec_setup(dev(kappa, prec))
+    ref = host(S.prec_apply(dev(b, prec)))
+    S.autotune(fresh=True)
+    got = host(S.prec_apply(dev(b, prec)))
+    assert np.array_equal(got, ref)
