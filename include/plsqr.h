@@ -223,12 +223,16 @@ int plsqr_selftest_wait(int32_t complete, int32_t* status_out);
  * speed differs.  By default the first solve of a handle tunes them (env PLSQR_AUTOTUNE=0: keep
  * shape 0 everywhere): for each level it times CUDA-graph replays of that level's smoothing
  * launches with each shape and the handle's full batch, and keeps the fastest; choices are cached
- * per process for levels of the same size, batch, precision and sweep count.
+ * per process for levels of the same size, batch, precision, sweep count and kappa storage.  The
+ * timing reads the level's hierarchy as it stands and writes only V-cycle scratch, so tuning
+ * between plsqr_prec_setup and plsqr_prec_apply leaves the priorconditioner unchanged.
  *
  * plsqr_autotune: tune now (fresh != 0: measure again instead of using the cache).  Uses the
  *   handle's scratch buffers: not while slots are in use (PLSQR_E_STATE).
  * plsqr_set_tile_shape: level 0 .. mg_levels-2 takes shape `shape` (0 is the default; level 0 has
- *   its own list); marks the handle as tuned.  PLSQR_E_INVALID for an unknown level or shape.
+ *   its own list); marks the handle as tuned, and keeps the shapes when plsqr_set_kappa_bf16 later
+ *   changes the kappa storage (which otherwise makes the next solve tune again).  PLSQR_E_INVALID
+ *   for an unknown level or shape.
  * plsqr_tile_shape: the shape of a level (-1 and zero extents where the level is not run by the
  *   tiled 2D kernels: 3D handles, the coarsest level), its tile extents and threads per block.
  *   Any output pointer may be NULL. */

@@ -119,6 +119,7 @@ struct plsqr_ctx {
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
     int tile[16] = {};        // tile shape of each 2D V-cycle level (mg2d_shape ids; 0 the default)
     bool tuned = false;       // tile shapes chosen (autotuned or set)
+    bool tiles_set = false;   // chosen by plsqr_set_tile_shape: kept when the kappa storage changes
     // stored Lanczos vectors of the running inner solve (plsqr_mlsqr_multi_tau): V_j, (alpha, beta)
     char* basis = nullptr;
     double* basis_ab = nullptr;
@@ -1027,13 +1028,16 @@ int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on) {
         if (on && (h->fp64 || h->d.ndim != 2 || !use_fused_mg(h)))
             throw InvalidArg("bfloat16 kappa needs a 2D single-precision handle with the temporally blocked V-cycle");
         if (on && !h->kappa16) h->kappa16 = (__nv_bfloat16*)dalloc(h, sizeof(__nv_bfloat16) * h->B * h->d.N);
-        if ((on != 0) != h->kbf16) clear_graphs(h);
+        if ((on != 0) != h->kbf16) {
+            clear_graphs(h);
+            if (!h->tiles_set) h->tuned = false;  // the finest level's timing depends on the kappa storage
+        }
         h->kbf16 = on != 0;
         return PLSQR_OK;
     });
 }
 
-// ---- stopping rules ----------------------------------------------------------------------------
+// ---- tile shapes of the 2D V-cycle --------------------------------------------------------------
 
 int plsqr_autotune(plsqr_handle h, int32_t fresh) {
     if (!h) return PLSQR_E_INVALID;
@@ -1043,6 +1047,7 @@ int plsqr_autotune(plsqr_handle h, int32_t fresh) {
             using T = decltype(tv);
             autotune<T>(h, fresh != 0);
         });
+        h->tiles_set = false;
         clear_graphs(h);  // captured with the previous shapes
         return PLSQR_OK;
     });
@@ -1057,6 +1062,7 @@ int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape) {
         if (shape < 0 || !mg2d_shape(level == 0, shape, &tx, &ty, &nth)) throw InvalidArg("no such tile shape");
         h->tile[level] = shape;
         h->tuned = true;
+        h->tiles_set = true;
         clear_graphs(h);
         return PLSQR_OK;
     });
@@ -1077,6 +1083,8 @@ int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx,
         return PLSQR_OK;
     });
 }
+
+// ---- stopping rules ----------------------------------------------------------------------------
 
 int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, double r_rel) {
     if (!h) return PLSQR_E_INVALID;

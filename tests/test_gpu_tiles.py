@@ -110,3 +110,18 @@ def test_explicit_autotune_keeps_the_hierarchy(prec):
     S.autotune(fresh=True)
     got = host(S.prec_apply(dev(b, prec)))
     assert np.array_equal(got, ref)
+
+
+def test_explicit_shapes_survive_a_kappa_storage_change():
+    """Shapes set by plsqr_set_tile_shape are kept when the kappa storage changes; the solve
+    with bfloat16 kappa then runs with them instead of tuning again."""
+    from paper_1308_6634_gb300 import synth
+    n = 128
+    g = synth.phantom_rects_disks(n, 6, 4, 2)
+    S = _P().Solver((n, n), "fp32", levels=3)
+    S.set_operator("blur", sigma=(2.0, 2.0), radius=(6, 6))
+    S.set_tile_shape(0, 2)
+    S.set_tile_shape(1, 5)
+    S.set_kappa_bf16(True)
+    S.solve(dev(g, "fp32"), "tv", 1e-2, 1e-3, 2, 4)
+    assert S.tile_shape(0)[0] == 2 and S.tile_shape(1)[0] == 5
