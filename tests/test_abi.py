@@ -44,3 +44,17 @@ def test_workspace_bytes_and_invalid_configs_without_gpu():
     assert plsqr.plsqr_workspace_bytes(bad) == -1
     too_coarse = plsqr.make_config((512, 512), "fp32", levels=1)
     assert plsqr.plsqr_workspace_bytes(too_coarse) == -1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every entry of the binding raises; nothing falls back to the
+    oracle or to any other CPU path."""
+    from paper_1308_6634_gb300 import plsqr
+    monkeypatch.setattr(plsqr, "_lib", None)
+    monkeypatch.setattr(plsqr, "LIB_PATH", str(tmp_path / "libplsqr.so"))
+    with pytest.raises(ImportError):
+        plsqr.lib()
+    with pytest.raises(ImportError):
+        plsqr.plsqr_workspace_bytes(plsqr.make_config((64, 64), "fp32", levels=3))
+    with pytest.raises(ImportError):
+        plsqr.projected_solve([1.0, 0.5, 0.2], [1.0, 0.3, 0.1], 0.0)
