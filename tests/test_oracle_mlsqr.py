@@ -164,3 +164,34 @@ def test_iterates_of_every_tau_lie_in_one_krylov_space(levels):
         assert np.linalg.norm(v - Q @ (Q.T @ v)) <= 1e-8 * np.linalg.norm(v), tau
         fs.append(v)
     assert np.linalg.norm(fs[-1] - fs[0]) > 1e-2 * np.linalg.norm(fs[0])  # the damping does change the iterate
+
+
+def _cg_damped_normal_equations(A, g, tau, k):
+    """k steps of textbook CG (Hestenes-Stiefel) on (A^T A + tau I) f = A^T g from f = 0."""
+    b = A.T @ g
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    for _ in range(k):
+        q = A.T @ (A @ p) + tau * p
+        a = rr / float(p @ q)
+        x = x + a * p
+        r = r - a * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.05])
+def test_plain_lsqr_equals_cg_on_the_normal_equations(tau):
+    """Sec. 3: LSQR is CG on the (damped) normal equations, carried out on the bidiagonal form;
+    with P = I the iterates of MLSQR are those of CG on (A^T A + tau I) f = A^T g."""
+    op, g, _ = _problem()
+    A = _dense(op.A, op.shape)
+    for k in [1, 2, 3, 5, 7]:
+        f, _, st = O.mlsqr(op, g, tau, k, prec=None)
+        ref = _cg_damped_normal_equations(A, g.ravel(), tau, k)
+        assert st == 0
+        assert np.linalg.norm(f.ravel() - ref) <= 1e-9 * np.linalg.norm(ref), k

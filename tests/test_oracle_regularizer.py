@@ -101,3 +101,36 @@ def test_diffusivity_ghost_and_floor():
     # TV, f = 0 everywhere: kappa = 1/T and R = N T
     k, R = O.diffusivity(np.zeros((5, 6)), "tv", 0.01)
     assert np.all(k == 100.0) and R == pytest.approx(30 * 0.01)
+
+
+def _laplacian_stencil(x):
+    """sum over axes of D^T D x written cell by cell: for each axis, (x - x_low) where a lower
+    neighbour exists, plus (x - x_high) with x_high = 0 beyond the high end."""
+    out = np.zeros_like(x)
+    for idx in np.ndindex(*x.shape):
+        v = 0.0
+        for ax in range(x.ndim):
+            lo, hi = list(idx), list(idx)
+            lo[ax] -= 1
+            hi[ax] += 1
+            if lo[ax] >= 0:
+                v += x[idx] - x[tuple(lo)]
+            v += x[idx] - (x[tuple(hi)] if hi[ax] < x.shape[ax] else 0.0)
+        out[idx] = v
+    return out
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (3, 4, 5)])
+@pytest.mark.parametrize("reg", REGS)
+def test_first_priorconditioner_is_the_laplacian(shape, reg):
+    """Sec. 4.3: Algorithm 3 starts from f = 0, where every gradient vanishes, so kappa is the
+    constant kappa(0) (1, or 1/T for smoothed TV) and the first M_f is kappa(0) times the
+    discrete Laplacian; R(0) = N r(0)."""
+    T = 0.2
+    kappa, R = O.diffusivity(np.zeros(shape), reg, T)
+    k0 = 1.0 / T if reg == "tv" else 1.0
+    assert np.all(kappa == k0)
+    assert R == pytest.approx(np.prod(shape) * O.r_of(reg, T, 0.0), rel=1e-14, abs=0.0)
+    x = np.random.default_rng(3).standard_normal(shape)
+    lap = _laplacian_stencil(x)
+    assert np.abs(O.apply_M(kappa, x) - k0 * lap).max() <= 1e-13 * np.abs(lap).max() * k0

@@ -77,3 +77,32 @@ def test_lagged_diffusivity_fixed_point():
     scale = np.linalg.norm(A.T @ g.ravel())
     assert res[2] < res[1] < res[0]
     assert res[2] < 1e-6 * scale
+
+
+@pytest.mark.parametrize("reg,tau", [("tv", 0.0), ("tv", 1e-3), ("pm_log", 0.0), ("pm_log", 1e-3)])
+def test_regulariser_rises_then_saturates_and_the_level_drops(reg, tau):
+    """The qualitative behaviour of Sec. 4.3 (Fig. 4.3): within an outer step R(f_i) rises with
+    the inner iterations and levels off; over the first outer steps the level it reaches drops
+    (not at every step: with tau > 0 the second TV level here lies 0.1% above the first, the
+    fourth 1.8% below it).  A fixed point that never updates kappa would repeat the first level."""
+    shape = (32, 32)
+    rng = np.random.default_rng(31)
+    f0 = np.zeros(shape)
+    f0[6:20, 5:16] = 1.0
+    f0[15:28, 12:27] = 0.5
+    yy, xx = np.mgrid[:32, :32]
+    f0[(yy - 9) ** 2 + (xx - 24) ** 2 < 25] = 0.8
+    op = O.Operator("blur", shape, sigma=(1.5, 1.5), radius=(5, 5))
+    Af = op.A(f0)
+    g = Af + 0.01 * np.linalg.norm(Af) / np.sqrt(Af.size) * rng.standard_normal(shape)
+    T, n = 0.05, 20
+    # inner iterates of the first outer step: MLSQR restarts from 0, so the run of i iterations
+    # ends at f_i
+    mg = O.Multigrid(O.diffusivity(np.zeros(shape), reg, T)[0], 3, 2, 1)
+    Rs = np.array([O.diffusivity(O.mlsqr(op, g, tau, i, prec=mg)[0], reg, T)[1] for i in range(1, n + 1)])
+    inc = np.diff(Rs)
+    assert Rs[-1] > Rs[0]
+    assert inc[-5:].mean() < 0.25 * inc[:5].mean()
+    out = O.solve(op, g, reg, T, tau, n_outer=4, n_inner=n, levels=3)
+    assert out["R_hist"][1] == pytest.approx(Rs[-1], rel=1e-12)
+    assert out["R_hist"][4] < 0.995 * out["R_hist"][1]
