@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
 
 bool mg2d_supported(int ndim, int nu) { return ndim == 2 && nu >= 1 && nu <= 3; }
 
-constexpr int TAIL_CS = 16;  // blocks per cluster (non-portable size; the driver is asked first)
+constexpr int TAIL_CS = 16;  // blocks per cluster (non-portable size; cudaOccupancyMaxActiveClusters is asked first)
 
 // At least 120 KB per block, so that the blocks of a cluster land on different SMs (the tiles of
 // a phase then run in parallel instead of sharing one SM's issue slots).
