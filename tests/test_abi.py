@@ -58,3 +58,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         plsqr.plsqr_workspace_bytes(plsqr.make_config((64, 64), "fp32", levels=3))
     with pytest.raises(ImportError):
         plsqr.projected_solve([1.0, 0.5, 0.2], [1.0, 0.3, 0.1], 0.0)
+
+
+def test_boundary_from_plain_c():
+    """tests/c/abi_from_c.c includes the header as C99 (-pedantic -Werror), links the library and
+    runs its host-only entry points: the workspace size and the projected solve of (3.6) with
+    k = 1 against its closed form."""
+    from paper_1308_6634_gb300 import build
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    out_dir = os.path.join(ROOT, "tests", "c", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "abi_from_c")
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c", "abi_from_c.c"), "-L", libdir, "-lplsqr", f"-Wl,-rpath,{libdir}", "-lm",
+           "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    p = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0 and p.stdout.strip().endswith("ok"), p.stdout + p.stderr
