@@ -184,6 +184,15 @@ int plsqr_profile(plsqr_handle h, int32_t enable);
 int plsqr_profile_read(plsqr_handle h, double* ms, int64_t* counts, int32_t n);
 /* Number of kernel launches the last solve executed (graph replays included), or -1. */
 int64_t plsqr_last_launches(plsqr_handle h);
+/* Guard bands (a debugging aid for out-of-bounds writes; compute-sanitizer stands in where it
+ * is available).  With the environment variable PLSQR_GUARD=1 when plsqr_create runs, every
+ * workspace allocation of the handle gets 256 bytes of the pattern 0xA5 on each side of the
+ * region the library uses (the regions stay 256-byte aligned; results are unchanged).  This call
+ * synchronises both streams and reads the bands back: *n_checked (may be NULL) = allocations with
+ * bands (0 when the handle was created without them), *n_bad (may be NULL) = allocations with a
+ * changed band.  Allocations made for the duration of one call (plsqr_mlsqr_multi_tau's stored
+ * vectors) and the caller's buffers are not covered. */
+int plsqr_check_guards(plsqr_handle h, int64_t* n_checked, int64_t* n_bad);
 
 /* ---- several damping parameters from one bidiagonalisation (Sec. 3.3) ---------------------------
  * The Golub-Kahan bidiagonalisation inside MLSQR does not depend on tau (the Krylov spaces are

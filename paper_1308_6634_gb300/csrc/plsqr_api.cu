@@ -8,6 +8,7 @@
 // (batch count, n_inner, history shape) and replayed n_outer times; the outer step index
 // lives in device memory, so every replay writes its own history row.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -30,6 +31,26 @@ using namespace plsqr;
 namespace {
 
 const double kPi = 3.14159265358979323846;
+
+// An NVTX range for the scope (host side: it marks when the work is enqueued, and a profiler
+// relates it to the launches made inside).  With no tool attached the calls return at once.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    Range(const char* name, int64_t payload) {
+        nvtxEventAttributes_t a;
+        std::memset(&a, 0, sizeof a);
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        a.payloadType = NVTX_PAYLOAD_TYPE_INT64;
+        a.payload.llValue = payload;
+        nvtxRangePushEx(&a);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct CudaError : std::runtime_error {
     using std::runtime_error::runtime_error;
@@ -57,6 +78,16 @@ struct Level {
     char* x2 = nullptr;    // V-cycle result of this level (fused path)
     char* rd = nullptr;    // [B][N_l] 1 / diagonal (2D levels above the coarsest)
 };
+
+// One workspace allocation.  With guard bands, kGuard bytes of kGuardByte sit on each side of
+// the region the library uses; a write past either end of the region changes them.
+struct Alloc {
+    char* base;    // returned by cudaMalloc, freed with cudaFree
+    char* user;    // the region the library uses: base, or base + kGuard
+    size_t bytes;  // size of that region
+};
+constexpr size_t kGuard = 256;  // keeps the region 256-byte aligned
+constexpr unsigned char kGuardByte = 0xA5;
 
 }  // namespace
 
@@ -129,7 +160,8 @@ struct plsqr_ctx {
     Profiler prof;
     int64_t last_launches = 0;
     bool use_graph = true;
-    std::vector<void*> allocs;
+    std::vector<Alloc> allocs;
+    bool guard = false;  // PLSQR_GUARD=1 at create: guard bands around every workspace allocation
     std::string err;
 };
 
@@ -143,19 +175,25 @@ __nv_bfloat16* K16(plsqr_ctx* h) { return h->kbf16 ? h->kappa16 : nullptr; }
 char* dalloc(plsqr_ctx* h, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
-    ck(cudaMalloc(&p, bytes), "cudaMalloc");
-    h->allocs.push_back(p);
+    const size_t g = h->guard ? kGuard : 0;
+    ck(cudaMalloc(&p, bytes + 2 * g), "cudaMalloc");
+    char* base = (char*)p;
+    h->allocs.push_back(Alloc{base, base + g, bytes});
+    if (g) {
+        ck(cudaMemset(base, kGuardByte, g), "cudaMemset");
+        ck(cudaMemset(base + g + bytes, kGuardByte, g), "cudaMemset");
+    }
     // zeroed once, so that no kernel (the tile-shape timing before the first plsqr_prec_setup
     // included) ever reads uninitialised memory
-    ck(cudaMemset(p, 0, bytes), "cudaMemset");
-    return (char*)p;
+    ck(cudaMemset(base + g, 0, bytes), "cudaMemset");
+    return base + g;
 }
 
 void dfree(plsqr_ctx* h, void* p) {
     if (!p) return;
     for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
-        if (*it == p) {
-            cudaFree(p);
+        if (it->user == p) {
+            cudaFree(it->base);
             h->allocs.erase(it);
             return;
         }
@@ -469,6 +507,7 @@ template <typename T>
 void autotune(plsqr_ctx* h, bool fresh = false) {
     h->tuned = true;
     if (!use_fused_mg(h) || !tma_enabled()) return;
+    Range range("plsqr_autotune");
     const int B = h->B;
     cudaStream_t s = h->stream;
     Profiler* prev = current_profiler();
@@ -575,7 +614,10 @@ void run_outer_steps(plsqr_ctx* h, int B, int n_outer, int n_inner) {
     maybe_autotune<T>(h);
     cudaStream_t s = h->stream;
     if (!h->use_graph || h->prof.enabled) {
-        for (int k = 0; k < n_outer; ++k) outer_step<T>(h, B, n_inner, s);
+        for (int k = 0; k < n_outer; ++k) {
+            Range r("outer step", k + 1);
+            outer_step<T>(h, B, n_inner, s);
+        }
         return;
     }
     auto key = std::make_tuple(B, n_inner, h->h_outer, h->h_inner);
@@ -583,6 +625,7 @@ void run_outer_steps(plsqr_ctx* h, int B, int n_outer, int n_inner) {
     cudaGraphExec_t exec = nullptr;
     int64_t per_replay = 0;
     if (it == h->graphs.end()) {
+        Range r("capture outer step");
         const int64_t before = h->prof.launches;
         cudaGraph_t graph = nullptr;
         ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
@@ -604,7 +647,10 @@ void run_outer_steps(plsqr_ctx* h, int B, int n_outer, int n_inner) {
         exec = it->second.first;
         per_replay = it->second.second;
     }
-    for (int k = 0; k < n_outer; ++k) ck(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+    for (int k = 0; k < n_outer; ++k) {
+        Range r("outer step", k + 1);
+        ck(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+    }
     h->prof.launches += per_replay * n_outer;
 }
 
@@ -623,6 +669,7 @@ void validate_solve(plsqr_ctx* h, int count, const int32_t* reg, const double* T
 template <typename T>
 int solve_impl(plsqr_ctx* h, int count, const void* const* g, bool g_host, const int32_t* reg, const double* Tp,
                const double* tau, int n_outer, int n_inner, void* const* f_out, bool f_host, plsqr_stats* stats) {
+    Range range("plsqr_solve");
     validate_solve(h, count, reg, Tp, tau, n_outer, n_inner);
     ensure_hist(h, n_outer, n_inner);
     cudaStream_t s = h->stream;
@@ -715,7 +762,7 @@ void destroy_ctx(plsqr_ctx* h) {
     if (!h) return;
     clear_graphs(h);
     h->prof.release();
-    for (void* p : h->allocs) cudaFree(p);
+    for (const Alloc& a : h->allocs) cudaFree(a.base);
     h->allocs.clear();
     if (h->prm_host) cudaFreeHost(h->prm_host);
     if (h->st_host) cudaFreeHost(h->st_host);
@@ -836,6 +883,8 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         h->generic_mg = em && em[0] == '1';
         const char* eu = std::getenv("PLSQR_FUSE_UPDATE");
         h->no_fuse_update = eu && eu[0] == '0';
+        const char* egd = std::getenv("PLSQR_GUARD");
+        h->guard = egd && egd[0] == '1';
         ck(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
         ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "cudaEventCreate");
@@ -1204,6 +1253,7 @@ int plsqr_step(plsqr_handle h) {
         for (int b = 0; b < h->B; ++b)
             if (h->slot_active[b] && h->slot_outer[b] < h->slot_target[b]) ++n;
         if (n == 0) return PLSQR_OK;
+        Range range("plsqr_step");
         cudaStream_t s = h->stream;
         const int64_t launches0 = h->prof.launches;
         // a slot that has reached its target is parked (skipped) until it is finished
@@ -1375,6 +1425,7 @@ int plsqr_prec_setup(plsqr_handle h, const void* kappa) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
         if (!kappa) throw InvalidArg("NULL pointer");
+        Range range("plsqr_prec_setup");
         cudaStream_t s = h->user_stream;
         ck(cudaMemcpyAsync(h->kappa, kappa, h->esz * h->d.N, cudaMemcpyDeviceToDevice, s), "kappa");
         if (h->kbf16) to_bf16(P<float>(h->kappa), h->kappa16, h->d.N, s);
@@ -1414,6 +1465,7 @@ int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void
                 int32_t* iters_done) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        Range range("plsqr_mlsqr");
         int32_t reg = 0;
         double T = 1.0;
         validate_solve(h, 1, &reg, &T, &tau, 1, n_inner);
@@ -1509,6 +1561,7 @@ int plsqr_mlsqr_multi_tau(plsqr_handle h, const void* g, int32_t n_inner, int32_
             if (!f_out[t]) throw InvalidArg("NULL pointer");
         }
         if (h->serving) throw std::logic_error("not while slots are in use");
+        Range range("plsqr_mlsqr_multi_tau");
         int32_t reg = 0;
         double T = 1.0, tau0 = 0.0;
         validate_solve(h, 1, &reg, &T, &tau0, 1, n_inner);
@@ -1601,6 +1654,30 @@ int plsqr_profile(plsqr_handle h, int32_t enable) {
             h->prof.count[c] = 0;
         }
         h->prof.enabled = enable != 0;
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_check_guards(plsqr_handle h, int64_t* n_checked, int64_t* n_bad) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "sync");
+        ck(cudaStreamSynchronize(h->user_stream), "sync");
+        int64_t checked = 0, bad = 0;
+        std::vector<unsigned char> band(2 * kGuard);
+        for (const Alloc& a : h->allocs) {
+            if (a.user == a.base) continue;
+            ck(cudaMemcpy(band.data(), a.base, kGuard, cudaMemcpyDeviceToHost), "guard band");
+            ck(cudaMemcpy(band.data() + kGuard, a.user + a.bytes, kGuard, cudaMemcpyDeviceToHost), "guard band");
+            ++checked;
+            for (unsigned char c : band)
+                if (c != kGuardByte) {
+                    ++bad;
+                    break;
+                }
+        }
+        if (n_checked) *n_checked = checked;
+        if (n_bad) *n_bad = bad;
         return PLSQR_OK;
     });
 }

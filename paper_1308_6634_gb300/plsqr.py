@@ -74,6 +74,7 @@ def lib():
         "plsqr_profile": ([vp, i32], C.c_int),
         "plsqr_profile_read": ([vp, vp, vp, i32], C.c_int),
         "plsqr_last_launches": ([vp], i64),
+        "plsqr_check_guards": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "plsqr_blur_noalloc": ([i32, C.POINTER(i64), i32, C.POINTER(d), C.POINTER(i32), vp, vp, vp], C.c_int),
         "plsqr_set_stopping": ([vp, i32, d, d, d], C.c_int),
         "plsqr_set_kappa_bf16": ([vp, i32], C.c_int),
@@ -101,7 +102,7 @@ def lib():
 EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_host", "plsqr_solve_batch",
             "plsqr_destroy", "plsqr_last_error", "plsqr_workspace_bytes", "plsqr_apply_A", "plsqr_apply_At",
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
-            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_blur_noalloc",
+            "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_check_guards", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
             "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_mlsqr_multi_tau",
             "plsqr_projected_solve", "plsqr_selftest_wait"]
@@ -337,6 +338,13 @@ class Solver:
 
     def last_launches(self):
         return int(lib().plsqr_last_launches(self.h))
+
+    def check_guards(self):
+        """(allocations with guard bands, allocations whose bands changed); bands exist when
+        PLSQR_GUARD=1 was set as the handle was created."""
+        checked, bad = C.c_int64(0), C.c_int64(0)
+        _check(self.h, lib().plsqr_check_guards(self.h, C.byref(checked), C.byref(bad)))
+        return checked.value, bad.value
 
     def set_stopping(self, eta=0.0, delta=0.0, r_rel=0.0, index=-1):
         """S4 with eta * delta (0: off) and the outer stop on a relative R decrease below r_rel
