@@ -245,6 +245,19 @@ int plsqr_selftest_wait(int32_t complete, int32_t* status_out);
  * plsqr_tile_shape: the shape of a level (-1 and zero extents where the level is not run by the
  *   tiled 2D kernels: 3D handles, the coarsest level), its tile extents and threads per block.
  *   Any output pointer may be NULL. */
+/* The autotuner's choices are kept per process; these two calls move them between processes
+ * (no GPU needed).  Text format, one entry per line, eight decimal integers:
+ *     nx ny batch element_size sweeps finest kappa_bf16 shape
+ * (the level's extents, the handle's max_batch, 4 or 8 bytes, nu, 1 for level 0 else 0, 1 when
+ * kappa is kept in bfloat16, the shape id).  A later first solve of a handle whose level matches
+ * an entry uses that shape without timing (plsqr_autotune with fresh != 0 still measures).
+ * plsqr_tune_cache_export: writes the entries to buf (at most cap - 1 characters and a NUL; buf may
+ *   be NULL with cap 0) and returns the full text length without the NUL.
+ * plsqr_tune_cache_import: merges the entries of a NUL-terminated text (blank lines skipped) and
+ *   returns how many it read; -PLSQR_E_INVALID, with nothing merged, for a malformed line or an
+ *   unknown shape. */
+int64_t plsqr_tune_cache_export(char* buf, int64_t cap);
+int32_t plsqr_tune_cache_import(const char* text);
 int plsqr_autotune(plsqr_handle h, int32_t fresh);
 int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape);
 int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx, int32_t* ty, int32_t* threads);

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1100,6 +1101,53 @@ int plsqr_autotune(plsqr_handle h, int32_t fresh) {
         clear_graphs(h);  // captured with the previous shapes
         return PLSQR_OK;
     });
+}
+
+// The process-wide choices of the autotuner as text, one entry per line:
+// "nx ny batch element_size sweeps finest kappa_bf16 shape".
+int64_t plsqr_tune_cache_export(char* buf, int64_t cap) {
+    std::string text;
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        for (const auto& kv : tune_cache()) {
+            const auto& k = kv.first;
+            char line[160];
+            std::snprintf(line, sizeof line, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k),
+                          std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k), kv.second);
+            text += line;
+        }
+    }
+    if (buf && cap > 0) {
+        const size_t n = std::min<size_t>(text.size(), (size_t)cap - 1);
+        std::memcpy(buf, text.data(), n);
+        buf[n] = '\0';
+    }
+    return (int64_t)text.size();
+}
+
+int32_t plsqr_tune_cache_import(const char* text) {
+    if (!text) return -PLSQR_E_INVALID;
+    std::vector<std::pair<std::tuple<int, int, int, int, int, int, int>, int>> entries;
+    const char* p = text;
+    while (*p) {
+        const char* e = std::strchr(p, '\n');
+        const std::string line(p, e ? (size_t)(e - p) : std::strlen(p));
+        p = e ? e + 1 : p + line.size();
+        if (line.find_first_not_of(" \t\r") == std::string::npos) continue;  // blank line
+        int v[8];
+        char extra = 0;
+        if (std::sscanf(line.c_str(), "%d %d %d %d %d %d %d %d %c", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                        &v[7], &extra) != 8)
+            return -PLSQR_E_INVALID;
+        int tx, ty, nth;
+        const bool sizes_ok = v[0] > 0 && v[1] > 0 && v[2] >= 1 && v[2] <= 4096 && (v[3] == 4 || v[3] == 8) &&
+                              v[4] >= 1 && v[4] <= 3 && (v[5] == 0 || v[5] == 1) && (v[6] == 0 || v[6] == 1);
+        if (!sizes_ok || v[7] < 0 || !mg2d_shape(v[5] == 1, v[7], &tx, &ty, &nth)) return -PLSQR_E_INVALID;
+        entries.emplace_back(std::make_tuple(v[0], v[1], v[2], v[3], v[4], v[5], v[6]), v[7]);
+    }
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    for (const auto& kv : entries) tune_cache()[kv.first] = kv.second;
+    return (int32_t)entries.size();
 }
 
 int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape) {

@@ -6,6 +6,7 @@ functions keep the C names (plsqr_create, plsqr_solve, ...); ``Solver`` wraps a 
 If the library is missing this module raises instead of falling back to anything else.
 """
 import ctypes as C
+import json
 import os
 
 import numpy as np
@@ -90,6 +91,8 @@ def lib():
         "plsqr_selftest_wait": ([i32, C.POINTER(i32)], C.c_int),
         "plsqr_set_tile_shape": ([vp, i32, i32], C.c_int),
         "plsqr_tile_shape": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "plsqr_tune_cache_export": ([C.c_char_p, i64], i64),
+        "plsqr_tune_cache_import": ([C.c_char_p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -104,7 +107,8 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_check_guards", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
-            "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_mlsqr_multi_tau",
+            "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_tune_cache_export",
+            "plsqr_tune_cache_import", "plsqr_mlsqr_multi_tau",
             "plsqr_projected_solve", "plsqr_selftest_wait"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
@@ -118,6 +122,50 @@ def selftest_wait(complete):
     if rc != OK:
         raise PlsqrError(rc, "selftest_wait failed")
     return st.value
+
+
+TUNE_FIELDS = ("nx", "ny", "batch", "element_size", "sweeps", "finest", "kappa_bf16", "shape")
+
+
+def tune_cache_export():
+    """The autotuner's process-wide tile-shape choices as text (plsqr_tune_cache_export)."""
+    n = lib().plsqr_tune_cache_export(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib().plsqr_tune_cache_export(buf, n + 1)
+    return buf.value.decode()
+
+
+def tune_cache_import(text):
+    """Merge tile-shape choices (plsqr_tune_cache_import's text format); returns the entry count."""
+    rc = lib().plsqr_tune_cache_import(text.encode())
+    if rc < 0:
+        raise PlsqrError(-rc, "malformed tile-shape cache text (nothing merged)")
+    return rc
+
+
+def tune_cache_json():
+    """The choices as JSON: {"format": 1, "entries": [{nx, ny, batch, ..., shape}, ...]}."""
+    entries = [dict(zip(TUNE_FIELDS, (int(v) for v in ln.split())))
+               for ln in tune_cache_export().splitlines() if ln.strip()]
+    return json.dumps({"format": 1, "entries": entries}, indent=1)
+
+
+def tune_cache_load_json(text):
+    d = json.loads(text)
+    if d.get("format") != 1:
+        raise ValueError("unknown tile-shape cache format")
+    lines = "".join(" ".join(str(int(e[k])) for k in TUNE_FIELDS) + "\n" for e in d["entries"])
+    return tune_cache_import(lines)
+
+
+def save_tune_cache(path):
+    with open(path, "w") as fh:
+        fh.write(tune_cache_json())
+
+
+def load_tune_cache(path):
+    with open(path) as fh:
+        return tune_cache_load_json(fh.read())
 
 
 def projected_solve(alpha, beta, tau):
