@@ -17,6 +17,7 @@ a V-cycle down to at most 16 cells per axis, and ceil(n sqrt 2) (made odd) detec
 """
 import collections
 import math
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -198,7 +199,10 @@ class Bucket:
 class Engine:
     """Admission by a device-memory budget; one bucket (handle, stream, slots) per operator class."""
 
-    def __init__(self, hbm_budget_bytes=40 << 30, slots_for_size=None, keep_results=False):
+    def __init__(self, hbm_budget_bytes=40 << 30, slots_for_size=None, keep_results=False, tune_cache=None):
+        """tune_cache: a JSON file of tile-shape choices (plsqr.save_tune_cache).  If it exists it
+        is loaded, so that the first step of each bucket skips the timing; save_tune_cache()
+        writes the choices back."""
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
@@ -207,6 +211,13 @@ class Engine:
         self.bytes_used = 0
         self.keep_results = keep_results
         self.refused = 0
+        self.tune_cache = tune_cache
+        if tune_cache and os.path.exists(tune_cache):
+            plsqr.load_tune_cache(tune_cache)
+
+    def save_tune_cache(self):
+        if self.tune_cache:
+            plsqr.save_tune_cache(self.tune_cache)
 
     def slots_of(self, n):
         return self.slots_for_size.get(n, 4)

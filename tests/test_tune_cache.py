@@ -53,3 +53,24 @@ def test_malformed_text_is_refused_whole(bad):
     with pytest.raises(P.PlsqrError):
         P.tune_cache_import("780 64 1 4 2 0 0 1\n" + bad + "\n")
     assert _entries(P) == before
+
+
+def test_serving_engine_loads_and_saves_the_cache():
+    """The engine loads a cache file at start and writes the process's choices back (the file
+    lives in a git-ignored folder of the test tree)."""
+    import os
+    P = _P()
+    from paper_1308_6634_gb300 import serving
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, "tune_cache.json")
+    with open(path, "w") as fh:
+        fh.write(json.dumps({"format": 1, "entries": [dict(nx=781, ny=128, batch=16, element_size=4, sweeps=2,
+                                                             finest=1, kappa_bf16=0, shape=1)]}))
+    eng = serving.Engine(tune_cache=path)
+    assert (781, 128, 16, 4, 2, 1, 0, 1) in _entries(P)
+    os.remove(path)
+    eng.save_tune_cache()
+    saved = json.load(open(path))
+    assert dict(nx=781, ny=128, batch=16, element_size=4, sweeps=2, finest=1, kappa_bf16=0, shape=1) in saved["entries"]
+    os.remove(path)
