@@ -291,7 +291,10 @@ int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, 
  * steps.  Each slot's arithmetic is that of plsqr_solve on a one-instance handle with the same
  * operator: the instances of a launch never mix, so a request gives the same result alone and in
  * any mix.  The first plsqr_slot_start puts the handle in slot mode, where plsqr_solve*,
- * plsqr_solve_batch and plsqr_set_operator return PLSQR_E_STATE.
+ * plsqr_solve_batch, plsqr_set_operator and the single-operation entry points (plsqr_apply_A,
+ * plsqr_apply_At, plsqr_diffusivity, plsqr_prec_setup, plsqr_prec_apply, plsqr_apply_M,
+ * plsqr_mlsqr, plsqr_mlsqr_multi_tau: they would use the slots' state and scratch vectors) return
+ * PLSQR_E_STATE.
  *
  * plsqr_slot_start: copies g (device, m values) into `slot` (0 <= slot < max_batch, not busy),
  *   sets f = 0, the slot's r, T, tau and target n_outer.  n_inner must equal, and n_outer must

@@ -479,7 +479,6 @@ void ensure_hist(plsqr_ctx* h, int n_outer, int n_inner) {
     size_t need = (size_t)B * h->h_outer * h->h_inner + (size_t)B * (h->h_outer + 1) + (size_t)B * h->h_outer;
     if (need > h->h_stage_n) {
         if (h->h_stage) cudaFreeHost(h->h_stage);
-    if (h->taps_inst_host) cudaFreeHost(h->taps_inst_host);
         h->h_stage = nullptr;
         ck(cudaMallocHost((void**)&h->h_stage, need * sizeof(double)), "cudaMallocHost");
         h->h_stage_n = need;
@@ -1417,9 +1416,18 @@ int64_t plsqr_workspace_bytes(const plsqr_config* cfg, const plsqr_operator* op)
     }
 }
 
+namespace {
+// The single-operation entry points run on instance 0's state and the handle's scratch vectors,
+// which the slots of continuous batching own.
+void refuse_in_slot_mode(const plsqr_ctx* h) {
+    if (h->serving) throw std::logic_error("the handle is in slot mode");
+}
+}  // namespace
+
 int plsqr_apply_A(plsqr_handle h, const void* x, void* y) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!h->op_set) throw std::logic_error("set_operator first");
         if (!x || !y) throw InvalidArg("NULL pointer");
         by_type(h, [&](auto tv) {
@@ -1434,6 +1442,7 @@ int plsqr_apply_A(plsqr_handle h, const void* x, void* y) {
 int plsqr_apply_At(plsqr_handle h, const void* y, void* x) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!h->op_set) throw std::logic_error("set_operator first");
         if (!x || !y) throw InvalidArg("NULL pointer");
         by_type(h, [&](auto tv) {
@@ -1448,6 +1457,7 @@ int plsqr_apply_At(plsqr_handle h, const void* y, void* x) {
 int plsqr_diffusivity(plsqr_handle h, const void* f, int32_t reg, double T, void* kappa_out, double* R_out) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!f || !kappa_out) throw InvalidArg("NULL pointer");
         if (reg < 0 || reg > 3) throw InvalidArg("bad regulariser");
         if (!(T > 0.0) || !std::isfinite(T)) throw InvalidArg("T must be positive and finite");
@@ -1472,6 +1482,7 @@ int plsqr_diffusivity(plsqr_handle h, const void* f, int32_t reg, double T, void
 int plsqr_prec_setup(plsqr_handle h, const void* kappa) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!kappa) throw InvalidArg("NULL pointer");
         Range range("plsqr_prec_setup");
         cudaStream_t s = h->user_stream;
@@ -1488,6 +1499,7 @@ int plsqr_prec_setup(plsqr_handle h, const void* kappa) {
 int plsqr_prec_apply(plsqr_handle h, const void* b, void* x) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!b || !x) throw InvalidArg("NULL pointer");
         by_type(h, [&](auto tv) {
             using T = decltype(tv);
@@ -1500,6 +1512,7 @@ int plsqr_prec_apply(plsqr_handle h, const void* b, void* x) {
 int plsqr_apply_M(plsqr_handle h, const void* x, void* y) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         if (!x || !y) throw InvalidArg("NULL pointer");
         by_type(h, [&](auto tv) {
             using T = decltype(tv);
@@ -1513,6 +1526,7 @@ int plsqr_mlsqr(plsqr_handle h, const void* g, double tau, int32_t n_inner, void
                 int32_t* iters_done) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
+        refuse_in_slot_mode(h);
         Range range("plsqr_mlsqr");
         int32_t reg = 0;
         double T = 1.0;

@@ -101,6 +101,13 @@ def test_slot_api_errors():
     with pytest.raises(plsqr.PlsqrError) as e:
         S.solve(g, "tv", 1e-2, 0.0, 2, 4)                     # slot mode
     assert e.value.code == plsqr.E_STATE
+    # the single-operation entry points would use the slots' state and scratch vectors
+    for call in (lambda: S.apply_A(g), lambda: S.apply_At(g), lambda: S.diffusivity(g, "tv", 1e-2),
+                 lambda: S.prec_setup(g), lambda: S.prec_apply(g), lambda: S.apply_M(g),
+                 lambda: S.mlsqr(g, 0.0, 3)):
+        with pytest.raises(plsqr.PlsqrError) as e:
+            call()
+        assert e.value.code == plsqr.E_STATE
     S.step()
     S.step()
     S.step()  # the slot has reached its target: nothing left to run
@@ -192,3 +199,29 @@ def test_outer_stop_frees_the_slot_early_with_the_solo_result():
     b = next(iter(eng.buckets.values()))
     assert b.steps < n_outer
     assert torch.equal(f1, f3)
+
+
+def test_slot_history_regrowth_keeps_per_slot_taps():
+    """A slot started on an idle handle with a longer history than before regrows the shared
+    history storage; the per-slot blur taps (pinned host staging) stay valid through it, and the
+    second request still equals its one-instance solve."""
+    from paper_1308_6634_gb300 import plsqr
+    n, sigma, R = 96, 4.0, 12
+    g = _deblur_data(n, sigma, R, 5)
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=2)
+    S.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    S.slot_start(0, g, "tv", 1e-2, 1e-3, 1, 4, sigma=(sigma, sigma))
+    S.step()
+    S.slot_finish(0, 1, 4)
+    S.slot_start(1, g, "pm_log", 5e-2, 1e-3, 3, 8, sigma=(sigma, sigma))   # longer history: regrown
+    for _ in range(3):
+        S.step()
+    f2, info2 = S.slot_finish(1, 3, 8)
+    S1 = plsqr.Solver((n, n), "fp32", levels=3, max_batch=1)
+    S1.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    f1, info1 = S1.solve(g, "pm_log", 5e-2, 1e-3, 3, 8)
+    torch.cuda.synchronize()
+    assert info2["status"] == 0
+    assert torch.equal(f1, f2)
+    assert np.array_equal(info1["rbar_hist"], info2["rbar_hist"])
+    S.close()
