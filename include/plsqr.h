@@ -266,8 +266,9 @@ int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx,
  * on != 0: later solves keep the diffusivity kappa (eq. 1.13) only in bfloat16 (8 significant bits,
  * rounded to nearest even from the single-precision value); the finest level of the V-cycle and
  * the first coarsening read it and widen it to float.  Everything else is unchanged, so P is the
- * V-cycle of the rounded kappa.  Needs a 2D PLSQR_FP32 handle with mg_levels >= 2 and 1..3
- * sweeps; otherwise PLSQR_E_INVALID.  plsqr_prec_setup rounds the kappa it is given.  on = 0
+ * V-cycle of the rounded kappa.  Needs a 2D PLSQR_FP32 handle with mg_levels >= 2, 1..3 sweeps
+ * and mg_cycles = 1 (further cycles would form b - M x from a float kappa that is not kept);
+ * otherwise PLSQR_E_INVALID.  plsqr_prec_setup rounds the kappa it is given.  on = 0
  * returns to float kappa (the default). */
 int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on);
 

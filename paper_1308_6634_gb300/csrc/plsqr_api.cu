@@ -1074,8 +1074,11 @@ int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const
 int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
-        if (on && (h->fp64 || h->d.ndim != 2 || !use_fused_mg(h)))
-            throw InvalidArg("bfloat16 kappa needs a 2D single-precision handle with the temporally blocked V-cycle");
+        // several V-cycles per application form b - M x with the float kappa, which bfloat16
+        // storage does not keep
+        if (on && (h->fp64 || h->d.ndim != 2 || !use_fused_mg(h) || h->cycles != 1))
+            throw InvalidArg("bfloat16 kappa needs a 2D single-precision handle with the temporally blocked V-cycle "
+                             "and one V-cycle per application");
         if (on && !h->kappa16) h->kappa16 = (__nv_bfloat16*)dalloc(h, sizeof(__nv_bfloat16) * h->B * h->d.N);
         if ((on != 0) != h->kbf16) {
             clear_graphs(h);

@@ -96,8 +96,9 @@ def test_first_outer_step_equals_float_kappa():
 
 def test_bf16_kappa_rejected_where_not_built():
     from paper_1308_6634_gb300 import plsqr
-    for shape, prec, levels in [((16, 16, 16), "fp32", 2), ((64, 64), "fp64", 3), ((64, 64), "fp32", 1)]:
-        S = plsqr.Solver(shape, prec, levels=levels)
+    for shape, prec, levels, cycles in [((16, 16, 16), "fp32", 2, 1), ((64, 64), "fp64", 3, 1),
+                                        ((64, 64), "fp32", 1, 1), ((64, 64), "fp32", 3, 2)]:
+        S = plsqr.Solver(shape, prec, levels=levels, cycles=cycles)
         with pytest.raises(plsqr.PlsqrError) as e:
             S.set_kappa_bf16(True)
         assert e.value.code == plsqr.E_INVALID
