@@ -312,7 +312,8 @@ int plsqr_set_stopping(plsqr_handle h, int32_t index, double eta, double delta, 
  *   its f is final; reported once the step that stopped it is done).  Stopping parameters set for
  *   an index before plsqr_slot_start apply to the request started there.
  * plsqr_slot_finish: copies the slot's f (device, N values) to f_out, fills stats (histories of
- *   the steps done, R of the final f), empties the slot; waits for the handle's stream.
+ *   the steps done, R of the final f; its arrays must hold the n_outer x n_inner, n_outer + 1 and
+ *   n_outer values of the slot's plsqr_slot_start), empties the slot; waits for the handle's stream.
  *   Returns PLSQR_E_BREAKDOWN when the slot broke down (f holds its last complete iterate). */
 int plsqr_slot_start(plsqr_handle h, int32_t slot, const void* g, int32_t r, double T, double tau,
                      int32_t n_outer, int32_t n_inner, const double* sigma);

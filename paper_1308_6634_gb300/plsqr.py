@@ -288,6 +288,7 @@ class Solver:
         self.h = plsqr_create(self.config, stream if stream is not None else _current_stream())
         self.data_shape = self.shape
         self._mask = None
+        self._slot_shape = {}  # slot -> (n_outer, n_inner) given at slot_start
 
     def close(self):
         if getattr(self, "h", None):
@@ -436,6 +437,7 @@ class Solver:
         sg = None if sigma is None else (C.c_double * 2)(*[float(x) for x in sigma])
         _check(self.h, lib().plsqr_slot_start(self.h, int(slot), _dptr(g, self.dtype, self.m), REG[reg], float(T),
                                               float(tau), int(n_outer), int(n_inner), sg))
+        self._slot_shape[int(slot)] = (int(n_outer), int(n_inner))
 
     def step(self):
         _check(self.h, lib().plsqr_step(self.h))
@@ -453,13 +455,18 @@ class Solver:
         return done.value, act.value
 
     def slot_finish(self, slot, n_outer, n_inner, f_out=None):
-        """Returns (f, info) for a slot that ran n_outer steps of n_inner iterations."""
+        """Returns (f, info) for a slot started for n_outer steps of n_inner iterations (the
+        history arrays are sized by the values given at slot_start, which must match)."""
         torch = _torch()
+        shape = self._slot_shape.get(int(slot))
+        if shape is not None and shape != (int(n_outer), int(n_inner)):
+            raise ValueError(f"slot {slot} was started for {shape[0]} x {shape[1]} iterations")
         if f_out is None:
             f_out = torch.empty(self.shape, dtype=self.dtype, device=torch.device("cuda", torch.cuda.current_device()))
-        st, info = self._stats(n_outer, n_inner)
+        st, info = self._stats(*(shape or (n_outer, n_inner)))
         rc = _check(self.h, lib().plsqr_slot_finish(self.h, int(slot), _dptr(f_out, self.dtype, self.N),
                                                     C.byref(st)))
+        self._slot_shape.pop(int(slot), None)
         info["status"] = rc
         return f_out, info
 
