@@ -37,10 +37,30 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 static const double PI = 3.14159265358979323846;
+
+/* Allocation that stops the test process with a message instead of returning NULL. */
+static void* xmalloc(size_t bytes) {
+    void* p = malloc(bytes ? bytes : 1);
+    if (!p) {
+        fprintf(stderr, "oracle: out of host memory (%zu bytes)\n", bytes);
+        abort();
+    }
+    return p;
+}
+
+static void* xcalloc(size_t n, size_t size) {
+    void* p = calloc(n ? n : 1, size ? size : 1);
+    if (!p) {
+        fprintf(stderr, "oracle: out of host memory (%zu x %zu bytes)\n", n, size);
+        abort();
+    }
+    return p;
+}
 
 /* ------------------------------------------------------------------------------------ */
 /* grid helpers                                                                          */
@@ -224,7 +244,7 @@ static void coarsen(const level_t* F, level_t* C) {
     for (int d = 0; d < 3; ++d) C->G.n[d] = (d < F->G.ndim) ? F->G.n[d] / 2 : 1;
     int64_t NC = grid_size(&C->G);
     for (int d = 0; d < F->G.ndim; ++d) {
-        C->c[d] = (double*)calloc((size_t)NC, sizeof(double));
+        C->c[d] = (double*)xcalloc((size_t)NC, sizeof(double));
         for (int64_t I = 0; I < NC; ++I) {
             int64_t cc[3];
             grid_coords(&C->G, I, cc);
@@ -348,7 +368,7 @@ void* oracle_mg_create(int ndim, const int64_t* n, const double* kappa, int leve
     if (levels < 1 || levels > 16 || ndim < 1 || ndim > 3) return NULL;
     for (int d = 0; d < ndim; ++d)
         if (n[d] % ((int64_t)1 << (levels - 1)) != 0) return NULL;
-    mg_t* mg = (mg_t*)calloc(1, sizeof(mg_t));
+    mg_t* mg = (mg_t*)xcalloc(1, sizeof(mg_t));
     mg->levels = levels;
     mg->nu = nu;
     mg->cycles = cycles;
@@ -357,23 +377,23 @@ void* oracle_mg_create(int ndim, const int64_t* n, const double* kappa, int leve
     for (int d = 0; d < 3; ++d) L0->G.n[d] = d < ndim ? n[d] : 1;
     int64_t N = grid_size(&L0->G);
     for (int d = 0; d < ndim; ++d) {
-        L0->c[d] = (double*)malloc((size_t)N * sizeof(double));
+        L0->c[d] = (double*)xmalloc((size_t)N * sizeof(double));
         memcpy(L0->c[d], kappa, (size_t)N * sizeof(double));
     }
     for (int l = 1; l < levels; ++l) coarsen(&mg->lv[l - 1], &mg->lv[l]);
     for (int l = 0; l < levels; ++l) {
         int64_t Nl = grid_size(&mg->lv[l].G);
-        for (int k = 0; k < 3; ++k) mg->work[l][k] = (double*)calloc((size_t)Nl, sizeof(double));
+        for (int k = 0; k < 3; ++k) mg->work[l][k] = (double*)xcalloc((size_t)Nl, sizeof(double));
     }
-    mg->tmp_r = (double*)calloc((size_t)N, sizeof(double));
-    mg->tmp_e = (double*)calloc((size_t)N, sizeof(double));
+    mg->tmp_r = (double*)xcalloc((size_t)N, sizeof(double));
+    mg->tmp_e = (double*)xcalloc((size_t)N, sizeof(double));
     /* dense coarsest operator, assembled column by column from the stencil */
     level_t* LC = &mg->lv[levels - 1];
     int64_t nc = grid_size(&LC->G);
     mg->nc = nc;
-    mg->chol = (double*)calloc((size_t)(nc * nc), sizeof(double));
-    double* e = (double*)calloc((size_t)nc, sizeof(double));
-    double* col = (double*)calloc((size_t)nc, sizeof(double));
+    mg->chol = (double*)xcalloc((size_t)(nc * nc), sizeof(double));
+    double* e = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* col = (double*)xcalloc((size_t)nc, sizeof(double));
     for (int64_t j = 0; j < nc; ++j) {
         e[j] = 1.0;
         level_apply(LC, e, col);
@@ -482,11 +502,11 @@ static void conv_axis(const grid_t* G, int d, const double* w, int R, const doub
 static void blur(const op_t* op, const double* x, double* y) {
     grid_t G = {op->ndim, {op->n[0], op->ndim > 1 ? op->n[1] : 1, op->ndim > 2 ? op->n[2] : 1}};
     int64_t N = grid_size(&G);
-    double* t = (double*)malloc((size_t)N * sizeof(double));
+    double* t = (double*)xmalloc((size_t)N * sizeof(double));
     memcpy(t, x, (size_t)N * sizeof(double));
     for (int d = 0; d < op->ndim; ++d) {
         int R = op->radius[d];
-        double* w = (double*)malloc((size_t)(2 * R + 1) * sizeof(double));
+        double* w = (double*)xmalloc((size_t)(2 * R + 1) * sizeof(double));
         oracle_blur_taps(op->sigma[d], R, w);
         conv_axis(&G, d, w, R, t, y);
         memcpy(t, y, (size_t)N * sizeof(double));
@@ -583,7 +603,7 @@ void oracle_apply_At(const op_t* op, const double* y, double* x) {
     switch (op->kind) {
         case OP_BLUR: blur(op, y, x); break;
         case OP_BLUR_MASK: {
-            double* t = (double*)malloc((size_t)N * sizeof(double));
+            double* t = (double*)xmalloc((size_t)N * sizeof(double));
             for (int64_t i = 0; i < N; ++i) t[i] = op->mask[i] ? y[i] : 0.0;
             blur(op, t, x);
             free(t);
@@ -623,12 +643,12 @@ static int mlsqr_impl(const op_t* op, void* prec, double tau, int n_inner, const
                       double* rbar_hist, int* status, double eta_delta) {
     mg_t* mg = (mg_t*)prec;
     int64_t N = op_unknowns(op), m = oracle_op_data_len(op);
-    double* u = (double*)malloc((size_t)m * sizeof(double));
-    double* Av = (double*)malloc((size_t)m * sizeof(double));
-    double* p = (double*)malloc((size_t)N * sizeof(double));
-    double* Atu = (double*)malloc((size_t)N * sizeof(double));
-    double* v = (double*)malloc((size_t)N * sizeof(double));
-    double* w = (double*)malloc((size_t)N * sizeof(double));
+    double* u = (double*)xmalloc((size_t)m * sizeof(double));
+    double* Av = (double*)xmalloc((size_t)m * sizeof(double));
+    double* p = (double*)xmalloc((size_t)N * sizeof(double));
+    double* Atu = (double*)xmalloc((size_t)N * sizeof(double));
+    double* v = (double*)xmalloc((size_t)N * sizeof(double));
+    double* w = (double*)xmalloc((size_t)N * sizeof(double));
     int done = 0;
     *status = 0;
     for (int64_t i = 0; i < N; ++i) f[i] = 0.0;
@@ -708,8 +728,8 @@ int oracle_solve_stop(const op_t* op, int reg, double T, double tau, double kflo
                       int cycles, int n_outer, int n_inner, double eta_delta, double r_rel, const double* g,
                       double* f, double* rbar_hist, double* R_hist, double* resid_hist, int* outer_done) {
     int64_t N = op_unknowns(op), m = oracle_op_data_len(op);
-    double* kappa = (double*)malloc((size_t)N * sizeof(double));
-    double* Af = (double*)malloc((size_t)m * sizeof(double));
+    double* kappa = (double*)xmalloc((size_t)N * sizeof(double));
+    double* Af = (double*)xmalloc((size_t)m * sizeof(double));
     int ret = 0, k = 1, stopped = 0;
     double R_prev = 0.0;
     for (int64_t i = 0; i < N; ++i) f[i] = 0.0;
@@ -744,8 +764,8 @@ int oracle_solve(const op_t* op, int reg, double T, double tau, double kfloor, i
                  int nu, int cycles, int n_outer, int n_inner, const double* g, double* f,
                  double* rbar_hist, double* R_hist, double* resid_hist) {
     int64_t N = op_unknowns(op), m = oracle_op_data_len(op);
-    double* kappa = (double*)malloc((size_t)N * sizeof(double));
-    double* Af = (double*)malloc((size_t)m * sizeof(double));
+    double* kappa = (double*)xmalloc((size_t)N * sizeof(double));
+    double* Af = (double*)xmalloc((size_t)m * sizeof(double));
     int ret = 0;
     for (int64_t i = 0; i < N; ++i) f[i] = 0.0;
     for (int k = 1; k <= n_outer; ++k) {
