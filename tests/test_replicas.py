@@ -91,3 +91,45 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["value"] > 0 and d["unit"] == "solves/s"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _rank_leaves(rank, world, port, q):
+    """Rank 1 leaves between steps (before the timing reduction); rank 0 must get an error from
+    its next collective within the process group's timeout instead of waiting for ever."""
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    dist.barrier()
+    if rank == 1:
+        os._exit(0)  # no destroy_process_group: the peer simply goes away
+    try:
+        bench.max_over_ranks(1.0, world, torch.device("cpu"))
+        q.put((0, "no error"))
+    except Exception as e:  # gloo reports the closed connection or the timeout
+        q.put((0, "error: " + type(e).__name__))
+
+
+@pytest.mark.timeout(180)
+def test_a_rank_that_leaves_is_detected_by_the_next_collective():
+    import torch.multiprocessing as mp
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_leaves, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    try:
+        rank, msg = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert rank == 0 and msg.startswith("error"), msg
+    assert procs[1].exitcode == 0
