@@ -323,26 +323,30 @@ int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32
 int plsqr_slot_finish(plsqr_handle h, int32_t slot, void* f_out, plsqr_stats* stats);
 
 /* ---- blur without device allocation ---------------------------------------------------------
- * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * The paper has no counterpart to this entry point.  It is for callers that cannot allocate
  * device memory: a serving process that hands all device memory to its own pool and admits work
- * by a memory budget, code that runs while a stream is being captured into a CUDA graph, and
- * latency-critical loops where cudaMalloc's implicit device synchronisation would stall other
- * streams.
+ * against that budget (an allocation behind its back could fail or push it over), and
+ * latency-critical loops where cudaMalloc / cudaFree would synchronise the device and stall the
+ * other streams.
  *
  * y = B x, the separable Gaussian blur of one image (ndim 2) or volume (ndim 3) with zero
  * boundary and taps exp(-k^2/(2 sigma_d^2)) normalised to unit sum, |k| <= radius[d] -- the same
  * operator and kernels as plsqr_apply_A with PLSQR_OP_BLUR.  n: nx, ny(, nz); sigma, radius:
  * per axis (x first), sigma > 0, 0 <= radius <= 32; precision: PLSQR_FP32 (float arrays) or
- * PLSQR_FP64 (double arrays); x, y: device pointers, N values each, distinct; stream: a
+ * PLSQR_FP64 (double arrays); x, y: device pointers, N values each, not overlapping; stream: a
  * cudaStream_t (NULL = default stream).  No handle, and no cudaMalloc / cudaFree or other
  * allocating call: the taps and the intermediate volume of the 3D blur live in a file-scope
  * device array of 8 MiB that every GPU loading the library holds until exit.  N * element size
- * must not exceed 8 MiB - 2 KiB (2,096,640 floats, 1,048,320 doubles); larger grids, bad sizes
- * or NULL pointers return PLSQR_E_INVALID before anything is enqueued.  The first call on a device
- * looks up the array's device address (make it before any stream capture).  All calls share the
+ * must not exceed 8 MiB - 2 KiB (2,096,640 floats, 1,048,320 doubles); in 3D, nz <= 65535 and
+ * ny <= 524,280 (launch limits).  Larger grids, bad sizes, overlapping x and y or NULL pointers
+ * return PLSQR_E_INVALID before anything is enqueued.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).  All calls share the
  * array, which keeps the last call's contents: calls that overlap on the GPU (other streams,
- * other threads) race on it.  The work is enqueued on `stream`; the call does not synchronise
- * (except that copying the taps from the caller's stack may wait for the host-side staging). */
+ * other threads) race on it.  The taps are computed on the host and handed to a kernel by value
+ * (no copy from host memory).  The work is enqueued on `stream` and the call does not
+ * synchronise.  The staging waits inside the kernels are bounded; should one run out (a copy
+ * that never completed), the kernel goes on, y is unspecified, and this entry point has no
+ * status to report it with. */
 int plsqr_blur_noalloc(int32_t ndim, const int64_t* n, int32_t precision, const double* sigma,
                        const int32_t* radius, const void* x, void* y, void* stream);
 

@@ -749,7 +749,7 @@ static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const
     dim3 grid((d.nx + BTX - 1) / BTX, (d.ny + BTY - 1) / BTY, d.nz * B);
     if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * d.nz > red.max_blocks)
         throw std::runtime_error("blur2d: too many blocks for the reduction scratch");
-    CUtensorMap map;
+    CUtensorMap map{};
     bool tma = false;
     if constexpr (R % 4 == 0 && !MI) {
         tma = tma_enabled() &&

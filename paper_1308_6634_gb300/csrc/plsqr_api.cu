@@ -827,7 +827,24 @@ void by_type(plsqr_ctx* h, F&& fn) {
 // device address is looked up once per device (the host-side name is only a stand-in).
 constexpr size_t kNoallocTapsBytes = 2048;
 constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;
+constexpr int kNoallocMaxRadius = 32;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// The taps of plsqr_blur_noalloc travel as a kernel parameter (by value), so the call holds no
+// pointer to host memory.  w[d][0 .. len[d]) are written at dst + off[d] as double (esz 8) or float.
+struct NoallocTaps {
+    double w[3][2 * kNoallocMaxRadius + 1];
+    int32_t off[3], len[3];
+    int32_t ndim, esz;
+};
+
+__global__ void k_noalloc_taps(const NoallocTaps t, unsigned char* dst) {
+    for (int d = 0; d < t.ndim; ++d)
+        for (int k = threadIdx.x; k < t.len[d]; k += blockDim.x) {
+            if (t.esz == 8) reinterpret_cast<double*>(dst + t.off[d])[k] = t.w[d][k];
+            else reinterpret_cast<float*>(dst + t.off[d])[k] = (float)t.w[d][k];
+        }
+}
 
 namespace {
 
@@ -1769,10 +1786,16 @@ int plsqr_blur_noalloc(int32_t ndim, const int64_t* n, int32_t precision, const 
     int64_t N = 1;
     for (int d = 0; d < ndim; ++d) {
         if (n[d] < 1 || n[d] > (1 << 20)) return PLSQR_E_INVALID;
-        if (!(sigma[d] > 0.0) || radius[d] < 0 || radius[d] > 32) return PLSQR_E_INVALID;
+        if (!(sigma[d] > 0.0) || radius[d] < 0 || radius[d] > kNoallocMaxRadius) return PLSQR_E_INVALID;
         N *= n[d];
     }
     if ((size_t)N * esz > kNoallocScratchBytes - kNoallocTapsBytes) return PLSQR_E_INVALID;  // beyond the maximum
+    // the launch shapes of both passes (grid.y and grid.z are limited to 65535)
+    if (ndim == 3 && (n[2] > 65535 || (n[1] + 7) / 8 > 65535)) return PLSQR_E_INVALID;
+    // x and y must not overlap
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+    const uintptr_t bytes = (uintptr_t)N * esz;
+    if (xa < ya + bytes && ya < xa + bytes) return PLSQR_E_INVALID;
     int err = PLSQR_OK;
     unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(&err));
     if (!scratch) return err;
@@ -1782,28 +1805,29 @@ int plsqr_blur_noalloc(int32_t ndim, const int64_t* n, int32_t precision, const 
         od.kind = OPK_BLUR;
         od.d = make_dims(ndim, n[0], n[1], ndim == 3 ? n[2] : 1);
         od.m = od.d.N;
-        // taps of every axis, in the element type, packed into the first 2 KiB of the scratch
-        double taps_bytes[kNoallocTapsBytes / sizeof(double)];
-        unsigned char* tb = reinterpret_cast<unsigned char*>(taps_bytes);
-        size_t off = 0;
+        // taps of every axis: computed here, passed by value to a kernel that writes them, in the
+        // element type, into the first 2 KiB of the scratch (no host-memory copy)
+        NoallocTaps tp{};
+        tp.ndim = ndim;
+        tp.esz = (int32_t)esz;
+        int32_t off = 0;
         for (int d = 0; d < ndim; ++d) {
             const int R = radius[d];
             double sum = 0.0;
             for (int k = -R; k <= R; ++k) sum += std::exp(-(double)(k * k) / (2.0 * sigma[d] * sigma[d]));
             od.R[d] = R;
             od.taps[d] = scratch + off;
+            tp.off[d] = off;
+            tp.len[d] = 2 * R + 1;
             for (int k = -R; k <= R; ++k) {
                 const double w = std::exp(-(double)(k * k) / (2.0 * sigma[d] * sigma[d])) / sum;
                 od.taps_host[d][k + R] = w;
-                if (esz == 8) std::memcpy(tb + off + (k + R) * 8, &w, 8);
-                else {
-                    const float wf = (float)w;
-                    std::memcpy(tb + off + (k + R) * 4, &wf, 4);
-                }
+                tp.w[d][k + R] = w;
             }
-            off += ((2 * R + 1) * esz + 15) & ~(size_t)15;
+            off += (int32_t)(((2 * R + 1) * esz + 15) & ~(size_t)15);
         }
-        ck(cudaMemcpyAsync(scratch, taps_bytes, off, cudaMemcpyHostToDevice, s), "taps");
+        k_noalloc_taps<<<1, 64, 0, s>>>(tp, scratch);
+        klaunched("k_noalloc_taps");
         Red red{};
         if (esz == 8)
             op_apply<double>(od, false, EPI_PLAIN, (const double*)x, (double*)y, nullptr,

@@ -252,8 +252,12 @@ def plsqr_blur_noalloc(x, sigma, radius, y=None, stream=None):
     """y = B x for a contiguous float32/float64 CUDA tensor of shape (ny, nx) or (nz, ny, nx),
     without any device allocation inside the library (sigma, radius in x, y(, z) order)."""
     torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.dtype not in (torch.float32, torch.float64):
+        raise TypeError(f"plsqr_blur_noalloc: x must be a float32 or float64 tensor, got {getattr(x, 'dtype', x)}")
     if y is None:
         y = torch.empty_like(x)
+    if not isinstance(y, torch.Tensor) or y.dtype != x.dtype:
+        raise TypeError(f"plsqr_blur_noalloc: y must have x's dtype {x.dtype}")
     prec = PREC["fp64"] if x.dtype == torch.float64 else PREC["fp32"]
     nd = x.dim()
     dims = list(reversed(x.shape)) + [1] * (3 - nd)

@@ -76,3 +76,17 @@ def test_boundary_from_plain_c():
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     p = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert p.returncode == 0 and p.stdout.strip().endswith("ok"), p.stdout + p.stderr
+
+
+def test_noalloc_binding_refuses_other_dtypes_before_the_library():
+    """plsqr_blur_noalloc takes float32 or float64 arrays only: a half-precision tensor (2-byte
+    elements, where the kernels would read and write 4 or 8 bytes per value) and a y of another
+    dtype than x are refused by the binding before any library call."""
+    torch = pytest.importorskip("torch")
+    from paper_1308_6634_gb300 import plsqr
+    for dt in (torch.float16, torch.bfloat16, torch.int32):
+        with pytest.raises(TypeError):
+            plsqr.plsqr_blur_noalloc(torch.zeros((8, 8), dtype=dt), (1.0, 1.0), (2, 2))
+    with pytest.raises(TypeError):
+        plsqr.plsqr_blur_noalloc(torch.zeros((8, 8), dtype=torch.float32), (1.0, 1.0), (2, 2),
+                                 y=torch.zeros((8, 8), dtype=torch.float16))

@@ -56,3 +56,20 @@ def test_noalloc_blur_rejects_grids_beyond_the_scratch():
     with pytest.raises(plsqr.PlsqrError) as e:
         plsqr.plsqr_blur_noalloc(x, (2.0, 2.0, 2.0), (6, 6, 6))
     assert e.value.code == plsqr.E_INVALID
+
+
+def test_noalloc_blur_rejects_launch_limits_and_overlapping_buffers():
+    """Sizes whose launch would be invalid, and x overlapping y, are refused before anything is
+    enqueued (the call returns PLSQR_E_INVALID and the stream stays usable)."""
+    from paper_1308_6634_gb300 import plsqr
+    x = torch.zeros((1, 1 << 20, 1), dtype=torch.float32, device="cuda")  # ny = 2^20: z-pass grid.y > 65535
+    with pytest.raises(plsqr.PlsqrError) as e:
+        plsqr.plsqr_blur_noalloc(x, (2.0, 2.0, 2.0), (6, 6, 6))
+    assert e.value.code == plsqr.E_INVALID
+    buf = torch.zeros(2 * 64 * 64, dtype=torch.float32, device="cuda")
+    a, b = buf[: 64 * 64].view(64, 64), buf[64 * 32: 64 * 96].view(64, 64)
+    for y in (a, b):
+        with pytest.raises(plsqr.PlsqrError) as e:
+            plsqr.plsqr_blur_noalloc(a, (2.0, 2.0), (6, 6), y=y)
+        assert e.value.code == plsqr.E_INVALID
+    torch.cuda.synchronize()
