@@ -8,12 +8,17 @@ Perona-Malik log regulariser T = 5e-2, tau = 1e-3, 15 x 50 iterations, 6-level V
 (independent instances per rank, no collective on the data path; weak scaling).
 
 JSON line keys beyond the base contract: p50_ms/p99_ms (per-step latency), roofline of the
-dominant kernel class (eager profiling pass with CUDA events on the launch stream),
-cpu_baseline (the FP64 CPU oracle on a bounded sample, extrapolated), e2e (host buffers, copies
-inside the timed region), clocks (nvidia-smi sampled during the timed region), accuracy (the
-first MLSQR residual estimates against the oracle's).
+dominant kernel class (eager profiling pass with CUDA events on the launch stream), e2e (host
+buffers, copies inside the timed region), clocks (nvidia-smi sampled during the timed region),
+fp64_single (the plain double-precision single-instance form), workloads (the 192^3 inpainting,
+512^2 tomography x1 and x32 and the serving stream, each with its own value, p50/p99, roofline
+and clocks), and the oracle leg: cpu_baseline (the FP64 CPU oracle timed on one whole outer step
+of the workload, on one core and on all cores at once; a solve is n_outer such steps) and
+accuracy (the GPU results of the whole n_outer x n_inner solve against a whole oracle solve of
+the same data, beside the oracle's own spread under a 1e-16 perturbation of g).
 
---impl reference times the FP64 CPU oracle itself on the same workload and metric.
+--impl reference times the FP64 CPU oracle itself on the same workload and metric: each step
+is one outer step of the workload on every host core at once.
 """
 import argparse
 import hashlib
@@ -70,9 +75,9 @@ def joseph_samples(n, n_angles, n_bins, spacing=1.0):
 
 def alg_units(W, kappa_bf16=False):
     """Algorithmic bytes per launch of each roofline class, in units of (element size x cells x
-    instances).  2D V-cycle (finest level, mean of the pre- and post-smoothing launches):
-    pre reads b, kappa and the reciprocal diagonal and writes x and the restricted residual (1/4);
-    post reads x_in, b, kappa, the reciprocal diagonal and the coarse correction (1/4) and writes x.
+    instances): the minimum reads and writes of one pass.  2D V-cycle, finest level (mean of the
+    pre- and post-smoothing launches): pre reads b and kappa and writes x and the restricted
+    residual (1/4); post reads x_in, b, kappa and the coarse correction (1/4) and writes x.
     kappa in bfloat16 counts half."""
     n = W.n_inner
     two_d_blur = W.kind in ("blur", "blur_mask") and len(W.shape) == 2
@@ -80,10 +85,17 @@ def alg_units(W, kappa_bf16=False):
     fwd = (3.0 + 7.0 * (n - 1)) / n if fused_update else 3.0
     if len(W.shape) == 2:
         k = 0.5 if kappa_bf16 else 1.0
-        return {"fwd": fwd, "adj": 3.0, "gs_fine": ((3.25 + k) + (4.25 + k)) / 2}
+        return {"fwd": fwd, "adj": 3.0, "gs_fine": ((2.25 + k) + (3.25 + k)) / 2}
     # 3D: one launch per red-black half sweep: x of the other colour (1/2), kappa (1),
     # b of this colour (1/2) in, x of this colour (1/2) out
     return {"fwd": fwd, "adj": 3.0, "gs_fine": 2.5}
+
+
+def beyond_alg_units(W):
+    """Bytes per launch that a class moves beyond its algorithmic ones, same units: the 2D
+    V-cycle kernels also read the reciprocal diagonal of the level (formed once per outer step,
+    a trade of one plane of reads for the division of every sweep)."""
+    return {"gs_fine": 1.0} if len(W.shape) == 2 else {}
 
 
 def parse():
@@ -104,6 +116,11 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="serving: device-memory budget")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (192^3 inpainting, 512^2 tomography x1 and x32, serving)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the whole-solve accuracy against the oracle")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle processes at once for the all-cores figures (0: every usable core, at most 32)")
     return ap.parse_args()
 
 
@@ -230,76 +247,225 @@ def make_inputs(W, S, seeds, torch, dev):
     return gs
 
 
-def cpu_baseline(W, budget_s=20.0):
-    """The FP64 CPU oracle on a bounded sample: one outer step with i1 and i2 inner
-    iterations; the difference gives the cost of one iteration, the rest the per-outer-step
-    cost (diffusivity, hierarchy, coarse factorisation, initialisation); both extrapolated
-    to the full n_outer x n_inner solve."""
+# ---- the oracle leg (cpu_baseline, accuracy, --impl reference) ------------------------------
+# Everything that runs the oracle runs in spawned worker processes; the GPU side only receives
+# arrays and timings from them.
+
+_ORACLE_CACHE = {}
+_BARRIER = None
+
+
+def _worker_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_problem(name, seed=0):
+    """(oracle operator, data g, mask) of workload `name`, seed `seed`, built once per process."""
+    key = (name, seed)
+    if key not in _ORACLE_CACHE:
+        import oracle as O
+        from paper_1308_6634_gb300 import synth
+        W = synth.WORKLOADS[name]
+        f, mask, z = W.inputs(seed)
+        op = O.Operator(W.kind, W.shape, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
+                        n_bins=W.n_bins)
+        _ORACLE_CACHE[key] = (op, synth.add_noise(op.A(f), W.noise, z), mask)
+    return _ORACLE_CACHE[key]
+
+
+def _oracle_job(task):
+    """Worker: ("data", name) -> (g, mask); ("full", name, eps, k) -> a whole oracle solve of the
+    data perturbed by eps (Algorithm 3, n_outer x n_inner); ("sample", name) -> seconds of one outer
+    step (n_outer = 1, the workload's n_inner); ("prepare", name) builds the problem untimed."""
     import oracle as O
     from paper_1308_6634_gb300 import synth
-    f, mask, z = W.inputs(0)
-    op = O.Operator(W.kind, W.shape, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
-                    n_bins=W.n_bins)
-    g = synth.add_noise(op.A(f), W.noise, z)
-    i1, i2 = 2, 6
-    t0 = time.perf_counter()
-    r1 = O.solve(op, g, W.reg, W.T, W.tau, 1, i1, W.levels, W.nu, W.cycles)
-    t1 = time.perf_counter()
-    r2 = O.solve(op, g, W.reg, W.T, W.tau, 1, i2, W.levels, W.nu, W.cycles)
-    t2 = time.perf_counter()
-    per_iter = max((t2 - t1) - (t1 - t0), 1e-9) / (i2 - i1)
-    per_outer = max((t1 - t0) - i1 * per_iter, 0.0)
-    t_solve = W.n_outer * (per_outer + W.n_inner * per_iter)
-    return dict(value=1.0 / t_solve, t_solve=t_solve, per_iter=per_iter, per_outer=per_outer,
-                sample_s=t2 - t0, rbar=r2["rbar_hist"][0], g=g, mask=mask, i2=i2,
-                sample=f"oracle: 1 outer step x {i1} and x {i2} inner iterations on seed 0 ({t2 - t0:.1f} s), "
-                f"extrapolated to {W.n_outer} x {W.n_inner}")
+    kind, name = task[0], task[1]
+    W = synth.WORKLOADS[name]
+    op, g, mask = _oracle_problem(name)
+    if kind == "prepare":
+        if _BARRIER is not None:
+            _BARRIER.wait(timeout=600)  # one task per process
+        return os.getpid()
+    if kind == "data":
+        return g, mask
+    if kind == "full":
+        eps, k = task[2], task[3]
+        gp = g if eps == 0 else g * (1.0 + eps * np.random.default_rng(4242 + k).standard_normal(g.shape))
+        t0 = time.perf_counter()
+        r = O.solve(op, gp, W.reg, W.T, W.tau, W.n_outer, W.n_inner, W.levels, W.nu, W.cycles)
+        r["seconds"] = time.perf_counter() - t0
+        return r
+    if kind == "sample":
+        if _BARRIER is not None:
+            _BARRIER.wait(timeout=600)  # all processes start together, one sample each
+        t0 = time.perf_counter()
+        O.solve(op, g, W.reg, W.T, W.tau, 1, W.n_inner, W.levels, W.nu, W.cycles)
+        return time.perf_counter() - t0
+    raise ValueError(kind)
+
+
+def usable_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_procs(requested):
+    return max(1, requested if requested > 0 else min(usable_cores(), 32))
+
+
+class OracleTimer:
+    """P spawned oracle processes that time one outer step of workload W each, all at once: one
+    such step is 1/n_outer of a solve (every outer step does the same work: the diffusivity, the
+    hierarchy and coarse factorisation, and n_inner MLSQR iterations)."""
+
+    def __init__(self, W, procs):
+        import multiprocessing as mp
+        self.W, self.procs = W, procs
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(procs, initializer=_worker_init, initargs=(ctx.Barrier(procs),))
+        pids = self.pool.map(_oracle_job, [("prepare", W.name)] * procs, chunksize=1)
+        self.distinct = len(set(pids))
+
+    def step(self):
+        """Wall seconds of one step (P outer steps at once) and the per-process seconds."""
+        t0 = time.perf_counter()
+        each = self.pool.map(_oracle_job, [("sample", self.W.name)] * self.procs, chunksize=1)
+        return time.perf_counter() - t0, each
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(W, procs):
+    """The oracle as it stands, timed on the host cores: one outer step of the workload on one
+    core, then on `procs` cores at once (independent instances)."""
+    one = OracleTimer(W, 1)
+    t1, _ = one.step()
+    one.close()
+    allc = OracleTimer(W, procs)
+    tp, each = allc.step()
+    allc.close()
+    sample = (f"oracle (plain FP64 C, one thread per process): one whole outer step ({W.n_inner} MLSQR "
+              f"iterations with the diffusivity, hierarchy and coarse factorisation) of {W.name} seed 0, i.e. "
+              f"1/{W.n_outer} of a solve; every outer step does the same work")
+    return {"value": procs / W.n_outer / tp, "unit": "solves/s", "cores": procs, "kind": "oracle",
+            "sample": sample + f", on {procs} processes at once ({tp:.1f} s wall, slowest process "
+                               f"{max(each):.1f} s)",
+            "nproc": os.cpu_count(), "usable_cores": usable_cores(),
+            "single_core": {"value": 1.0 / W.n_outer / t1, "unit": "solves/s", "cores": 1,
+                            "outer_step_s": t1, "sample": sample + f" ({t1:.1f} s)"}}
+
+
+class AccuracyLeg:
+    """Whole oracle solves of the workload (seed 0), started in spawned processes before the GPU is
+    touched: the unperturbed solve and two with g perturbed by one part in 1e16 (the oracle's own
+    spread at this horizon).  The GPU solves the same data afterwards."""
+
+    def __init__(self, W, n_perturbed=2):
+        import multiprocessing as mp
+        self.W = W
+        self.pool = mp.get_context("spawn").Pool(n_perturbed + 2)
+        self.data = self.pool.apply_async(_oracle_job, (("data", W.name),))
+        self.full = [self.pool.apply_async(_oracle_job, (("full", W.name, 0.0, 0),))] + \
+                    [self.pool.apply_async(_oracle_job, (("full", W.name, 1e-16, k),)) for k in range(n_perturbed)]
+
+    def finish(self, gpu_runs, timeout=1800):
+        """gpu_runs(g, mask) -> {label: (f, info)} of the GPU forms on the oracle's data."""
+        g, mask = self.data.get(timeout=timeout)
+        gpu = gpu_runs(g, mask)
+        res = [r.get(timeout=timeout) for r in self.full]
+        self.pool.close()
+        self.pool.join()
+        ref, pert = res[0], res[1:]
+        relf = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+        out = {"horizon": f"{self.W.n_outer} x {self.W.n_inner} (whole solve)",
+               "oracle_seconds": ref["seconds"],
+               "oracle_spread_f": [relf(r["f"], ref["f"]) for r in pert],
+               "oracle_spread_R": [relf(r["R_hist"], ref["R_hist"]) for r in pert],
+               "oracle_spread_resid": [relf(r["resid_hist"], ref["resid_hist"]) for r in pert]}
+        for label, (f, info) in gpu.items():
+            out[label] = {"f_rel_err": relf(f, ref["f"]),
+                          "R_hist_rel_err": relf(info["R_hist"], ref["R_hist"]),
+                          "resid_hist_rel_err": relf(info["resid_hist"], ref["resid_hist"]),
+                          "rbar_first5_rel_err": relf(info["rbar_hist"][0][:5], ref["rbar_hist"][0][:5]),
+                          "status": int(info["status"])}
+        out["note"] = ("relative L2 errors against a whole FP64 oracle solve of the same data; the oracle's own "
+                       "result moves by oracle_spread_f when g is perturbed by 1e-16 (rounding chaos of the "
+                       "Krylov iteration on this ill-posed problem), so agreement below that spread is not "
+                       "expected from any implementation that rounds differently; the first five residual "
+                       "estimates precede the chaos")
+        return out
 
 
 def run_reference(args, W):
+    """The oracle as the reference arm: each step is one outer step of the workload on every usable
+    host core at once (independent instances), i.e. procs / n_outer solves."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    procs = oracle_procs(args.cpu_procs)
+    timer = OracleTimer(W, procs)
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state
-    vals = []
+        timer.step()
+    walls, slowest = [], []
     t0 = time.perf_counter()
-    info = None
     for _ in range(args.steps):
-        info = cpu_baseline(W)
-        vals.append(info["t_solve"])
+        w, each = timer.step()
+        walls.append(w)
+        slowest.append(max(each))
     wall = time.perf_counter() - t0
-    t_solve = float(np.mean(vals))
+    timer.close()
+    step_s = float(np.mean(walls))
+    value = procs / W.n_outer / step_s
+    sample = (f"oracle (plain FP64 C, one thread per process): one whole outer step of {W.name} seed 0 "
+              f"(1/{W.n_outer} of a solve) on each of {procs} processes at once, per step")
     line = {
-        "impl": "reference", "metric": METRIC, "value": 1.0 / t_solve, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve, "higher_is_better": True,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W.name, "shape": list(W.shape), "n_outer": W.n_outer, "n_inner": W.n_inner,
-                   "batch": 1, "parallelism": "replicas"},
-        "cpu_baseline": {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": info["sample"]},
-        "e2e": {"value": 1.0 / t_solve, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": wall,
+        "config": config_of(W, 1, world, args.kappa_bf16),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": procs, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count(), "usable_cores": usable_cores(),
+                         "distinct_processes": timer.distinct},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": 1e3 * float(np.percentile(walls, 50)), "p99_ms": 1e3 * float(np.percentile(walls, 99)),
+        "slowest_process_s": float(np.mean(slowest)), "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
+def flushes_l2(W, B):
+    """The GPU arm flushes L2 between timed steps when the solve's working set (about ten vectors
+    per instance) is smaller than L2; otherwise the inputs are larger than L2."""
+    esz = 4 if W.precision == "fp32" else 8
+    return B * W_N(W) * esz * 10 < L2_BYTES
+
+
+def config_of(W, B, world, kappa_bf16):
+    """The workload's configuration (the same dictionary in both arms; `l2` describes the timing of
+    the GPU arm)."""
+    return {"workload": W.name, "shape": list(W.shape), "operator": W.kind, "n_outer": W.n_outer,
+            "n_inner": W.n_inner, "reg": W.reg, "T": W.T, "tau": W.tau, "levels": W.levels, "sweeps": W.nu,
+            "cycles": W.cycles, "batch": B, "parallelism": f"replicas x{world}",
+            "kappa": "bf16" if kappa_bf16 else W.precision,
+            "l2": "flushed between steps" if flushes_l2(W, B) else "working set larger than L2"}
+
+
+def serving_stream(count, rate, budget_gb, warmup, rank, torch, dev):
     """The serving stream: Poisson arrivals of deblurring and tomography requests of mixed sizes
-    served by the continuous-batching engine; value = completed solves / (last completion - first
-    arrival); per-request latency percentiles over --requests requests."""
-    import torch
+    served by the continuous-batching engine; solves/s = completed solves / (last completion - first
+    arrival); per-request latency percentiles over `count` requests."""
     from paper_1308_6634_gb300 import serving
-    rank, world, local = dist_env()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    count = args.requests
-    reqs = serving.make_stream(count, rate=args.rate, seed=rank)
+    reqs = serving.make_stream(count, rate=rate, seed=rank)
     data = {r.rid: serving.make_data(r, torch, dev)[0] for r in reqs}
-    warm = serving.make_stream(max(8, args.warmup * 4), rate=1000.0, seed=10_000 + rank)
+    warm = serving.make_stream(max(8, warmup * 4), rate=1000.0, seed=10_000 + rank)
     wdata = {r.rid: serving.make_data(r, torch, dev)[0] for r in warm}
-    eng = serving.Engine(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)))
+    eng = serving.Engine(hbm_budget_bytes=int(budget_gb * (1 << 30)))
     eng.run(warm, wdata, realtime=False)  # creates and warms buckets (graph capture)
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
@@ -308,21 +474,164 @@ def run_serving(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     sm = serving.summarize(reqs)
+    out = {"value": sm["solves_per_s"], "unit": "solves/s", "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"],
+           "config": {"workload": f"serve_stream_{count}_poisson{rate:g}", "sizes": list(serving.SIZES),
+                      "size_p": list(serving.SIZE_P), "angles": list(serving.ANGLES), "n_outer": 10, "n_inner": 30,
+                      "hbm_budget_gb": budget_gb},
+           "serving": sm, "buckets": len(eng.buckets), "bucket_bytes": eng.bytes_used,
+           "admission_refusals": eng.refused, "clocks": clk.summary(), "wall_s": wall,
+           "warmup_requests": len(warm)}
+    del eng
+    torch.cuda.synchronize()
+    return out
+
+
+def run_serving(args):
+    import torch
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sv = serving_stream(args.requests, args.rate, args.hbm_budget_gb, args.warmup, rank, torch, dev)
     if rank == 0:
         line = {
-            "metric": "solves/s and p50/p99 ms (serving stream)", "value": sm["solves_per_s"] * world,
-            "unit": "solves/s", "n_gpus": world, "steps": count, "warmup": len(warm),
-            "ms_per_step": 1e3 * wall / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serve_stream_{count}_poisson{args.rate:g}", "sizes": list(serving.SIZES),
-                       "size_p": list(serving.SIZE_P), "angles": list(serving.ANGLES), "n_outer": 10,
-                       "n_inner": 30, "parallelism": f"replicas x{world}", "hbm_budget_gb": args.hbm_budget_gb},
-            "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "serving": sm,
-            "buckets": len(eng.buckets), "bucket_bytes": eng.bytes_used, "admission_refusals": eng.refused,
-            "clocks": clk.summary(), "wall_s": wall,
+            "metric": "solves/s and p50/p99 ms (serving stream)", "value": sv["value"] * world,
+            "unit": "solves/s", "n_gpus": world, "steps": args.requests, "warmup": sv["warmup_requests"],
+            "ms_per_step": 1e3 * sv["wall_s"] / args.requests, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(sv["config"], parallelism=f"replicas x{world}"),
+            "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "serving": sv["serving"], "buckets": sv["buckets"],
+            "bucket_bytes": sv["bucket_bytes"], "admission_refusals": sv["admission_refusals"],
+            "clocks": sv["clocks"], "wall_s": sv["wall_s"],
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+def roofline_of(W, B, prof, kappa_bf16=False):
+    """Roofline of the dominant kernel class from an eager profile (per class: ms, launches)."""
+    esz = 4 if W.precision == "fp32" else 8
+    ALG_UNITS = alg_units(W, kappa_bf16)
+    extra = beyond_alg_units(W)
+    cand = {k: v for k, v in prof.items() if k in ALG_UNITS and v[1] > 0}
+    top = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    total_prof = sum(v[0] for v in prof.values())
+    classes_ms = {k: round(v[0], 3) for k, v in prof.items()}
+    if W.kind == "joseph" and "fwd" in prof and prof["fwd"][1] > 0:
+        # the projector is bound by its gathers and instruction issue, not by bytes: FP32 FMA ceiling
+        ms, cnt = prof["fwd"]
+        samples = joseph_samples(W.shape[0], W.n_angles, W.n_bins) * B
+        achieved = 4.0 * samples / (ms / cnt / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "fwd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "traffic": None, "alg_flop_per_launch": 4.0 * samples, "samples_per_launch": samples,
+                "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
+                "share_of_eager_device_time": ms / total_prof, "largest_class": top, "classes_ms": classes_ms}
+    if not cand:
+        return None
+    dom = max(cand.items(), key=lambda kv: kv[1][0])[0]
+    peak, src = measured_peaks()
+    ms, cnt = prof[dom]
+    bytes_per_launch = ALG_UNITS[dom] * esz * W_N(W) * B
+    achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
+    by_class = {}
+    for k2, (ms2, cnt2) in cand.items():  # every class with algorithmic bytes, same arithmetic
+        a2 = ALG_UNITS[k2] * esz * W_N(W) * B / (ms2 / cnt2 / 1e3) / 1e9
+        by_class[k2] = {"achieved_gbs": round(a2, 1), "frac": round(a2 / peak, 4),
+                        "avg_launch_us": round(1e3 * ms2 / cnt2, 2)}
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": ncu_traffic(dom, W.name), "alg_bytes_per_launch": bytes_per_launch,
+            "beyond_alg_bytes_per_launch": extra.get(dom, 0.0) * esz * W_N(W) * B,
+            "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
+            "share_of_eager_device_time": ms / total_prof, "largest_class": top,
+            "classes_ms": classes_ms, "by_class": by_class}
+
+
+class GpuRun:
+    """One workload on the GPU: a handle with B instances, device data of B seeds, and the timing."""
+
+    def __init__(self, W, B, torch, dev, plsqr, seeds, kappa_bf16=False, tiles=None):
+        self.W, self.B, self.torch, self.dev = W, B, torch, dev
+        self.S = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles, max_batch=B)
+        mask = W.inputs(seeds[0])[1]
+        self.S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles,
+                            n_bins=W.n_bins)
+        if kappa_bf16:
+            self.S.set_kappa_bf16(True)
+        if tiles:
+            for lv, sid in enumerate(int(x) for x in tiles.split(",")):
+                self.S.set_tile_shape(lv, sid)
+        self.kappa_bf16 = kappa_bf16
+        self.gs = make_inputs(W, self.S, seeds, torch, dev)
+        self.fs = [torch.empty(W.shape, dtype=self.S.dtype, device=dev) for _ in range(B)]
+        self.esz = 4 if W.precision == "fp32" else 8
+        self.flush = (torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+                      if flushes_l2(W, B) else None)
+
+    def step(self, stats=False):
+        W, B, S = self.W, self.B, self.S
+        if B == 1:
+            return S.solve(self.gs[0], W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=self.fs[0], stats=stats)
+        return S.solve_batch(self.gs, [W.reg] * B, [W.T] * B, [W.tau] * B, W.n_outer, W.n_inner, f_outs=self.fs,
+                             stats=stats)
+
+    def time(self, steps, warmup, world=1):
+        torch = self.torch
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        self.step(stats=True)
+        self.launches_per_step = self.S.last_launches()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        with ClockSampler(self.dev.index) as clk:
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            for k in range(steps):
+                if self.flush is not None:
+                    self.flush.zero_()
+                starts[k].record()
+                self.step()
+                ends[k].record()
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+        self.per_step = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+        self.clocks = clk.summary()
+        return float(self.per_step.sum())
+
+    def profile(self):
+        self.S.profile(True)
+        self.step()
+        self.torch.cuda.synchronize()
+        prof = self.S.profile_read()
+        self.S.profile(False)
+        return roofline_of(self.W, self.B, prof, self.kappa_bf16)
+
+    def tiles(self):
+        return [list(self.S.tile_shape(l)[1:]) for l in range(self.W.levels - 1) if self.S.tile_shape(l)[0] >= 0]
+
+    def summary(self, steps):
+        total_ms = float(self.per_step.sum())
+        return {"value": self.B * steps / (total_ms / 1e3), "unit": "solves/s", "ms_per_step": total_ms / steps,
+                "p50_ms": float(np.percentile(self.per_step, 50)), "p99_ms": float(np.percentile(self.per_step, 99)),
+                "steps": steps, "gpu_launches_per_step": int(self.launches_per_step),
+                "config": config_of(self.W, self.B, 1, self.kappa_bf16),
+                "tiles": self.tiles(), "clocks": self.clocks}
+
+    def close(self):
+        self.S.close()
+        del self.gs, self.fs, self.flush
+        self.torch.cuda.synchronize()
+
+
+# Other workloads measured by the default run beside the headline one: (key, workload, batch, steps,
+# warm-up steps)
+EXTRAS = (("inpaint192_fp32", "inpaint192_fp32", 1, 3, 2),
+          ("tomo512_fp32", "tomo512_fp32", 1, 3, 2),
+          ("tomo512_fp32_x32", "tomo512_fp32", 32, 1, 1))
 
 
 def main():
@@ -334,8 +643,12 @@ def main():
     if args.impl == "reference":
         return run_reference(args, W)
 
-    import torch
     rank, world, local = dist_env()
+    oracle_leg = rank == 0 and world == 1 and not args.no_cpu_baseline
+    # the whole-solve oracle runs start before the GPU is touched (spawned processes)
+    acc_leg = AccuracyLeg(W) if oracle_leg and not args.no_accuracy else None
+
+    import torch
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -344,57 +657,17 @@ def main():
     torch.cuda.set_device(dev)
     from paper_1308_6634_gb300 import plsqr
     B = args.batch
-    S = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles, max_batch=B)
-    seeds = replica_seeds(rank, B)
-    mask = W.inputs(seeds[0])[1]
-    S.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=mask, n_angles=W.n_angles, n_bins=W.n_bins)
-    if args.kappa_bf16:
-        S.set_kappa_bf16(True)
-    if args.tiles:
-        for lv, sid in enumerate(int(x) for x in args.tiles.split(",")):
-            S.set_tile_shape(lv, sid)
-    gs = make_inputs(W, S, seeds, torch, dev)
-    fs = [torch.empty(W.shape, dtype=S.dtype, device=dev) for _ in range(B)]
-    regs, Ts, taus = [W.reg] * B, [W.T] * B, [W.tau] * B
-
-    def step(stats=False):
-        if B == 1:
-            return S.solve(gs[0], W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=fs[0], stats=stats)
-        return S.solve_batch(gs, regs, Ts, taus, W.n_outer, W.n_inner, f_outs=fs, stats=stats)
-
-    esz = 4 if W.precision == "fp32" else 8
-    working_set = B * int(np.prod(W.shape)) * esz * 10
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if working_set < L2_BYTES else None
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    _, info = step(stats=True)
-    launches_per_step = S.last_launches()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(dev.index) as clk:
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            if flush is not None:
-                flush.zero_()
-            starts[k].record()
-            step()
-            ends[k].record()
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-    per_step = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    total_ms = float(per_step.sum())
+    run = GpuRun(W, B, torch, dev, plsqr, replica_seeds(rank, B), args.kappa_bf16, args.tiles)
+    total_ms = run.time(args.steps, args.warmup, world)
     total_ms = max_over_ranks(total_ms, world, dev)
     value = world * B * args.steps / (total_ms / 1e3)
+    per_step, clocks = run.per_step, run.clocks
+    esz = run.esz
 
     # end to end through the host-buffer API: H2D of g, solve, D2H of f inside the timed region
     e2e = None
     if not args.no_e2e:
+        S, gs, fs = run.S, run.gs, run.fs
         pin_g = [torch.empty(g.shape, dtype=g.dtype, pin_memory=True) for g in gs]
         for pg, g in zip(pin_g, gs):
             pg.copy_(g)
@@ -409,7 +682,7 @@ def main():
                 S.solve_host(pin_g[0].numpy(), W.reg, W.T, W.tau, W.n_outer, W.n_inner, f_out=pin_f[0].numpy())
             else:
                 dg = [pg.to(dev, non_blocking=True) for pg in pin_g]
-                S.solve_batch(dg, regs, Ts, taus, W.n_outer, W.n_inner, f_outs=fs, stats=False)
+                S.solve_batch(dg, [W.reg] * B, [W.T] * B, [W.tau] * B, W.n_outer, W.n_inner, f_outs=fs, stats=False)
                 for pf, f in zip(pin_f, fs):
                     pf.copy_(f, non_blocking=True)
                 torch.cuda.synchronize()
@@ -420,75 +693,40 @@ def main():
                "h2d_bytes_per_step": int(B * gs[0].numel() * esz), "d2h_bytes_per_step": int(B * W_N(W) * esz)}
 
     # roofline of the dominant kernel class: eager profiling pass, CUDA events on the launch stream
-    roofline = None
-    if not args.no_profile:
-        S.profile(True)
-        step()
-        torch.cuda.synchronize()
-        prof = S.profile_read()
-        S.profile(False)
-        ALG_UNITS = alg_units(W, args.kappa_bf16)
-        cand = {k: v for k, v in prof.items() if k in ALG_UNITS and v[1] > 0}
-        top = max(prof.items(), key=lambda kv: kv[1][0])[0]
-        dom = max(cand.items(), key=lambda kv: kv[1][0])[0] if cand else None
-        peak, src = measured_peaks()
-        if W.kind == "joseph" and "fwd" in prof and prof["fwd"][1] > 0:
-            # the projector is bound by its gathers and instruction issue, not by bytes: FP32 FMA ceiling
-            ms, cnt = prof["fwd"]
-            samples = joseph_samples(W.shape[0], W.n_angles, W.n_bins) * B
-            achieved = 4.0 * samples / (ms / cnt / 1e3) / 1e12
-            total_prof = sum(v[0] for v in prof.values())
-            roofline = {"bound": "alu", "kernel": "fwd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                        "traffic": None, "alg_flop_per_launch": 4.0 * samples, "samples_per_launch": samples,
-                        "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
-                        "share_of_eager_device_time": ms / total_prof, "largest_class": top,
-                        "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}}
-            dom = None
-        if dom is not None:
-            ms, cnt = prof[dom]
-            bytes_per_launch = ALG_UNITS[dom] * esz * W_N(W) * B
-            achieved = bytes_per_launch / (ms / cnt / 1e3) / 1e9
-            total_prof = sum(v[0] for v in prof.values())
-            by_class = {}
-            for k2, (ms2, cnt2) in cand.items():  # every class with algorithmic bytes, same arithmetic
-                a2 = ALG_UNITS[k2] * esz * W_N(W) * B / (ms2 / cnt2 / 1e3) / 1e9
-                by_class[k2] = {"achieved_gbs": round(a2, 1), "frac": round(a2 / peak, 4),
-                                "avg_launch_us": round(1e3 * ms2 / cnt2, 2)}
-            roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
-                        "traffic": ncu_traffic(dom, W.name), "alg_bytes_per_launch": bytes_per_launch,
-                        "avg_launch_us": 1e3 * ms / cnt, "launches_timed": cnt,
-                        "share_of_eager_device_time": ms / total_prof, "largest_class": top,
-                        "classes_ms": {k: round(v[0], 3) for k, v in prof.items()}, "by_class": by_class}
+    roofline = None if args.no_profile else run.profile()
 
     # the plain form beside it: the same workload with the same kernels instantiated in double,
     # one instance per call, no CUDA graph
-    fp64_single = None
+    fp64_single, S64 = None, None
     if rank == 0 and world == 1 and not args.no_fp64_single and W.precision == "fp32":
-        fp64_single = time_fp64_single(W, plsqr, torch, dev, gs[0])
+        fp64_single, S64 = time_fp64_single(W, plsqr, torch, dev, run.gs[0])
 
-    cpu = None
-    acc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(W)
-        cpu = {"value": cb["value"], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]}
-        # accuracy on the oracle's own data g: the same first outer step on the GPU
-        ref = cb["rbar"]
-        S1 = plsqr.Solver(W.shape, W.precision, levels=W.levels, sweeps=W.nu, cycles=W.cycles)
-        S1.set_operator(W.kind, sigma=W.sigma, radius=W.radius, mask=cb["mask"], n_angles=W.n_angles,
-                        n_bins=W.n_bins)
-        if args.kappa_bf16:
-            S1.set_kappa_bf16(True)
-        _, inf1 = S1.solve(torch.as_tensor(cb["g"], dtype=S1.dtype, device=dev), W.reg, W.T, W.tau, 1, cb["i2"])
-        got = inf1["rbar_hist"][0]
-        acc = {"rbar_rel_err_first4": float(np.linalg.norm(got[:4] - ref[:4]) / np.linalg.norm(ref[:4])),
-               "rbar_rel_err_per_iter": [float(abs(a - b) / abs(b)) for a, b in zip(got, ref)],
-               "note": "||rbar_i|| of the first outer step on the oracle's data against the oracle's; rounding "
-                       "chaos sets in after a few iterations (tomography: from the fifth), so later entries "
-                       "measure the problem's sensitivity; long-horizon parity is tested against the oracle's "
-                       "rounding envelope (tests/)"}
+    # the other workloads (single GPU only: the headline's timed work stays the one multi-GPU job)
+    workloads = None
+    if rank == 0 and world == 1 and not args.no_extras and W.name == "deblur1024_fp32":
+        workloads = {}
+        for key, wname, b, st, wu in EXTRAS:
+            r2 = GpuRun(synth.WORKLOADS[wname], b, torch, dev, plsqr, replica_seeds(0, b))
+            r2.time(st, wu)
+            workloads[key] = dict(r2.summary(st), roofline=r2.profile())
+            r2.close()
+        workloads["serve_2000_poisson200"] = serving_stream(2000, 200.0, args.hbm_budget_gb, 3, 0, torch, dev)
+
+    accuracy = None
+    if acc_leg is not None:
+        def gpu_runs(g, mask):
+            out = {}
+            gd = torch.as_tensor(g, dtype=run.S.dtype, device=dev)
+            f, info = run.S.solve(gd, W.reg, W.T, W.tau, W.n_outer, W.n_inner)
+            out["gpu"] = (f.double().cpu().numpy(), info)
+            if S64 is not None:
+                f64, info64 = S64.solve(torch.as_tensor(g, dtype=torch.float64, device=dev), W.reg, W.T, W.tau,
+                                        W.n_outer, W.n_inner)
+                out["gpu_fp64_single"] = (f64.cpu().numpy(), info64)
+            return out
+        accuracy = acc_leg.finish(gpu_runs)
+
+    cpu = cpu_baseline(W, oracle_procs(args.cpu_procs)) if oracle_leg else None
 
     if rank == 0:
         line = {
@@ -496,16 +734,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if W.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": W.name, "shape": list(W.shape), "operator": W.kind, "n_outer": W.n_outer,
-                       "n_inner": W.n_inner, "reg": W.reg, "T": W.T, "tau": W.tau, "levels": W.levels,
-                       "sweeps": W.nu, "cycles": W.cycles, "batch": B, "parallelism": f"replicas x{world}",
-                       "kappa": "bf16" if args.kappa_bf16 else W.precision,
-                       "tiles": [list(S.tile_shape(l)[1:]) for l in range(W.levels - 1) if S.tile_shape(l)[0] >= 0],
-                       "l2": "flushed between steps" if flush is not None else "working set larger than L2"},
+            "config": config_of(W, B, world, args.kappa_bf16),
+            "tiles": run.tiles(),
             "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
-            "gpu_launches": int(launches_per_step * args.steps),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "accuracy": acc,
-            "fp64_single": fp64_single,
+            "gpu_launches": int(run.launches_per_step * args.steps),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "accuracy": accuracy,
+            "fp64_single": fp64_single, "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -559,8 +793,9 @@ def time_fp64_single(W, plsqr, torch, dev, g32, steps=2):
                      n_bins=W.n_bins)
     f32, _ = S32.solve(g32, W.reg, W.T, W.tau, W.n_outer, W.n_inner)
     diff = float(torch.linalg.vector_norm(f32.double() - f) / torch.linalg.vector_norm(f))
+    S32.close()
     return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_solve": ms, "batch": 1, "graph": False,
-            "dtype": "f64", "steps": steps, "rel_diff_fp32_vs_fp64_f": diff}
+            "dtype": "f64", "steps": steps, "rel_diff_fp32_vs_fp64_f": diff}, S
 
 
 if __name__ == "__main__":

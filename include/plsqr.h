@@ -43,7 +43,7 @@ typedef enum {
     PLSQR_E_NOMEM = 2,     /* device allocation failed */
     PLSQR_E_CUDA = 3,      /* a CUDA call failed */
     PLSQR_E_BREAKDOWN = 4, /* Golub-Kahan breakdown in some inner solve */
-    PLSQR_E_TIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    PLSQR_E_TIMEOUT = 5,   /* a bounded device wait gave up (TMA staging, grid barrier) */
     PLSQR_E_STATE = 6      /* call out of order (e.g. solve before set_operator) */
 } plsqr_status;
 
@@ -261,6 +261,20 @@ int32_t plsqr_tune_cache_import(const char* text);
 int plsqr_autotune(plsqr_handle h, int32_t fresh);
 int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape);
 int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx, int32_t* ty, int32_t* threads);
+/* plsqr_mg_schedule (Sec. 4.2, schedule only): how the handle runs one 2D V-cycle.  *coop = 1: the
+ *   levels from *first_level down (every coarser level, the coarse solve and, from level 0, alpha)
+ *   in one cooperative launch of at most *max_blocks blocks (0: every block that can be resident),
+ *   all resident at once and separated by bounded grid-wide barriers between the phases; the
+ *   levels above first_level keep their two launches.  *coop = 0: two launches per level and one
+ *   for the coarse solve (*first_level = -1).  -1: not decided yet: the autotuner times the
+ *   per-level launches and the cooperative launch from every level with three block caps at the
+ *   first solve and keeps the fastest (every schedule gives the same V-cycle bit for bit).  0 for
+ *   3D handles, sweeps other than 2, coarse levels too large to stage, or PLSQR_MG_COOP=0 at
+ *   create; PLSQR_MG_COOP=1 at create selects the cooperative launch from level
+ *   PLSQR_MG_COOP_LEVEL (default 0) wherever it is supported.  first_level and max_blocks may be
+ *   NULL.  A grid barrier that runs out records status 5 in every instance's state; the solve then
+ *   returns PLSQR_E_TIMEOUT. */
+int plsqr_mg_schedule(plsqr_handle h, int32_t* coop, int32_t* first_level, int32_t* max_blocks);
 
 /* ---- bfloat16 kappa ----------------------------------------------------------------------------
  * on != 0: later solves keep the diffusivity kappa (eq. 1.13) only in bfloat16 (8 significant bits,

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libplsqr.so")
-SOURCES = ["k_ops.cu", "k_mg.cu", "k_mg2d.cu", "k_mg2d_alt.cu", "k_mg2d_alt2.cu", "k_coarse32.cu", "k_lsqr.cu", "plsqr_api.cu"]
+SOURCES = ["k_ops.cu", "k_mg.cu", "k_mg2d.cu", "k_mg2d_alt.cu", "k_mg2d_alt2.cu", "k_coarse32.cu", "k_lsqr.cu", "k_mg2d_coop.cu", "plsqr_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -127,6 +127,35 @@ void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* 
 bool gth_wide_supported(int bw, int nc);
 void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
 
+// ---- the whole 2D V-cycle in one cooperative launch ----
+constexpr int COOP_LEVELS = 8;
+// Per-level buffers of one V-cycle application: level 0 holds the right-hand side b (p~ or a
+// residual), the pre-smoothed iterate x and the result x2; levels >= 1 the restricted residual b,
+// the pre-smoothed x and the post-smoothed x2; the last level is the coarsest (x2 = X b).
+struct CoopLevels {
+    const void* cond[COOP_LEVELS];  // level 0: kappa; levels >= 1: conductances [B][2][N_l]
+    const void* rd[COOP_LEVELS];    // 1 / diagonal of the smoothed levels
+    void* b[COOP_LEVELS];
+    void* x[COOP_LEVELS];
+    void* x2[COOP_LEVELS];
+    Dims d[COOP_LEVELS];
+    int L;
+};
+// The grid barrier's counters (zero between launches) and the abort flag, in device memory.
+struct CoopSync {
+    unsigned* arrive;
+    unsigned* depart;
+    int* abort;
+};
+// Whether the cooperative V-cycle can run for this level count and coarsest size (nu = 2).
+bool mg2d_coop_supported(int nu, size_t elem, int L, int nc);
+// Levels lc .. L-1 of one V-cycle in one launch: x2[lc] = the V-cycle of level lc applied to b[lc]
+// (lc = 0: the whole V-cycle, x2[0] = P b[0]; dot as in mg2d_post: 0 none, 1 alpha_1, 2 alpha and
+// the rotations, finest level only).  cap: at most this many blocks (0: as many as are resident).
+template <typename T>
+void mg2d_vcycle_coop(const CoopLevels& cl, int lc, int cap, int nu, const T* X, int nc, int B, int dot,
+                      GkState* st, Hist hist, Red red, CoopSync sy, const __nv_bfloat16* k16, cudaStream_t s);
+
 // ---- temporally blocked 2D V-cycle (one launch per level and direction) ----
 bool mg2d_supported(int ndim, int nu);
 // First level from which the coarse end of a 2D V-cycle (levels.. L-1) runs as one cluster launch

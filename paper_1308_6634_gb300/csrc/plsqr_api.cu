@@ -11,6 +11,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -149,6 +150,13 @@ struct plsqr_ctx {
     __nv_bfloat16* kappa16 = nullptr;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
+    // the whole 2D V-cycle in one cooperative launch: -1 undecided (the autotuner times both
+    // schedules), 0 per-level launches, 1 cooperative; PLSQR_MG_COOP=0/1 fixes it
+    int coop = -1;
+    int coop_lc = 0;                // first level of the cooperative launch (the levels above: per-level)
+    int coop_cap = 0;               // at most this many blocks (0: every resident block)
+    bool coop_ok = false;           // supported for this handle (2D, nu = 2, TMA, levels, coarse size)
+    unsigned* coop_sync = nullptr;  // grid barrier counters and abort flag (zero between launches)
     int tile[16] = {};        // tile shape of each 2D V-cycle level (mg2d_shape ids; 0 the default)
     bool tuned = false;       // tile shapes chosen (autotuned or set)
     bool tiles_set = false;   // chosen by plsqr_set_tile_shape: kept when the kappa storage changes
@@ -347,6 +355,29 @@ void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
     }
 }
 
+// Levels lc..L-1 of a V-cycle in one cooperative launch: x = the level-lc V-cycle applied to b (the
+// hierarchy and scratch of vcycle_fused; level lc > 0 takes b = lv[lc].b, x = lv[lc].x2).
+template <typename T>
+void vcycle_coop(plsqr_ctx* h, int lc, const T* b, T* x, int B, int dot, cudaStream_t s) {
+    CoopLevels cl{};
+    cl.L = h->L;
+    for (int l = 0; l < h->L; ++l) {
+        const Level& Lv = h->lv[l];
+        cl.d[l] = Lv.d;
+        cl.cond[l] = l == 0 ? (const void*)h->kappa : (const void*)Lv.cond;
+        cl.rd[l] = Lv.rd;
+        cl.b[l] = l == lc ? (void*)b : (void*)Lv.b;
+        cl.x[l] = l == 0 ? (void*)h->tmp : (void*)Lv.x;
+        cl.x2[l] = l == lc ? (void*)x : (void*)Lv.x2;
+    }
+    CoopSync sy;
+    sy.arrive = h->coop_sync;
+    sy.depart = h->coop_sync + 1;
+    sy.abort = reinterpret_cast<int*>(h->coop_sync + 2);
+    mg2d_vcycle_coop<T>(cl, lc, h->coop_cap, h->nu, coarse_inverse_of<T>(h), h->nc, B, dot, h->st, hist_of(h),
+                        h->red, sy, lc == 0 ? K16(h) : nullptr, s);
+}
+
 // Temporally blocked V-cycle (2D): one pre and one post launch per level.  dot (finest level
 // only): 0 none, 1 alpha_1, 2 alpha and the rotations fused into the last post launch.
 template <typename T>
@@ -354,6 +385,10 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
     const Level& Lv = h->lv[l];
     if (l == h->L - 1) {
         coarse_symv<T>(coarse_inverse_of<T>(h), b, x, h->nc, B, h->st, s);
+        return;
+    }
+    if (h->coop == 1 && l == h->coop_lc) {  // levels l..L-1 in one cooperative launch
+        vcycle_coop<T>(h, l, b, x, B, dot, s);
         return;
     }
     if (l == h->tail_lc) {  // levels l..L-1 in one cluster launch (x is lv[l].x2 here)
@@ -373,17 +408,23 @@ void vcycle_fused(plsqr_ctx* h, int l, const T* b, T* x, int B, int dot, cudaStr
 
 bool use_fused_mg(const plsqr_ctx* h) { return mg2d_supported(h->d.ndim, h->nu) && h->L > 1 && !h->generic_mg; }
 
+// One V-cycle on level 0 with the handle's schedule (dot: see vcycle_fused).
+template <typename T>
+void vcycle_2d(plsqr_ctx* h, const T* b, T* x, int B, int dot, cudaStream_t s) {
+    vcycle_fused<T>(h, 0, b, x, B, dot, s);
+}
+
 // x = P b: `cycles` V-cycles from zero, x <- x + V(b - M x).  Returns true when alpha and the
 // rotations were fused into the last launch (dot: 1 init, 2 iteration; 0 = not requested).
 template <typename T>
 bool prec_apply(plsqr_ctx* h, const T* b, T* x, int B, cudaStream_t s, int dot = 0) {
     const bool fused = use_fused_mg(h);
     const bool fuse_dot = fused && dot != 0 && h->cycles == 1;
-    if (fused) vcycle_fused<T>(h, 0, b, x, B, fuse_dot ? dot : 0, s);
+    if (fused) vcycle_2d<T>(h, b, x, B, fuse_dot ? dot : 0, s);
     else vcycle<T>(h, 0, b, x, B, s);
     for (int c = 1; c < h->cycles; ++c) {
         mg_apply_level<T>(P<T>(h->kappa), true, x, b, P<T>(h->r0), h->d, B, s);
-        if (fused) vcycle_fused<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, 0, s);
+        if (fused) vcycle_2d<T>(h, P<T>(h->r0), P<T>(h->e0), B, 0, s);
         else vcycle<T>(h, 0, P<T>(h->r0), P<T>(h->e0), B, s);
         mg_axpy<T>(x, P<T>(h->e0), (int64_t)B * h->d.N, s);
     }
@@ -503,6 +544,96 @@ std::map<std::tuple<int, int, int, int, int, int, int>, int>& tune_cache() {
     return c;
 }
 
+bool coop_forced() {
+    const char* e = std::getenv("PLSQR_MG_COOP");
+    return e && (e[0] == '0' || e[0] == '1');
+}
+
+std::map<std::tuple<int, int, int, int, int, int>, std::array<int, 3>>& schedule_cache() {
+    static std::map<std::tuple<int, int, int, int, int, int>, std::array<int, 3>> c;
+    return c;
+}
+
+// Per-level launches or one cooperative launch for the whole V-cycle: a CUDA graph of 8 V-cycles
+// of each, with the handle's batch and tile shapes, replayed and timed; the faster one is kept
+// (cached per process by grid, batch, element size, levels and kappa storage).  Both give the same
+// V-cycle bit for bit.  st0: a zeroed state for the timing (the handle's own is left alone).
+template <typename T>
+void choose_schedule(plsqr_ctx* h, GkState* st0, cudaEvent_t e0, cudaEvent_t e1, bool fresh) {
+    const int B = h->B;
+    cudaStream_t s = h->stream;
+    const auto key = std::make_tuple(h->d.nx, h->d.ny, B, (int)h->esz, h->L, h->kbf16 ? 1 : 0);
+    if (!fresh) {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        auto it = schedule_cache().find(key);
+        if (it != schedule_cache().end()) {
+            h->coop = it->second[0];
+            h->coop_lc = it->second[1];
+            h->coop_cap = it->second[2];
+            return;
+        }
+    }
+    int dev = 0, sms = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    // candidates: per-level launches, and the cooperative launch from each level with three caps
+    std::vector<std::array<int, 3>> cand{{0, 0, 0}};
+    for (int lc = 0; lc + 1 < h->L; ++lc)
+        for (int cap : {sms, 2 * sms, 0}) cand.push_back({1, lc, cap});
+    GkState* keep = h->st;
+    h->st = st0;
+    std::vector<float> ms(cand.size(), 0.f);
+    try {
+        ck(cudaMemsetAsync(h->p, 0, h->esz * B * h->d.N, s), "memset");
+        for (size_t c = 0; c < cand.size(); ++c) {
+            h->coop = cand[c][0];
+            h->coop_lc = cand[c][1];
+            h->coop_cap = cand[c][2];
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+            try {
+                for (int r = 0; r < 8; ++r) vcycle_2d<T>(h, P<T>(h->p), P<T>(h->v), B, 0, s);
+            } catch (...) {
+                cudaStreamEndCapture(s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            ck(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            ck(ie, "cudaGraphInstantiate");
+            cudaError_t e = cudaGraphLaunch(exec, s);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[c], e0, e1);
+            cudaGraphExecDestroy(exec);
+            ck(e, "autotune schedule");
+        }
+    } catch (...) {
+        h->st = keep;
+        h->coop = 0;
+        throw;
+    }
+    h->st = keep;
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (ms[c] < ms[best]) best = c;
+    const char* lg = std::getenv("PLSQR_TUNE_LOG");
+    if (lg && lg[0] == '1')
+        for (size_t c = 0; c < cand.size(); ++c)
+            std::fprintf(stderr, "plsqr schedule %dx%d batch %d: coop %d first level %d cap %d: %.2f us per V-cycle%s\n",
+                         h->d.nx, h->d.ny, B, cand[c][0], cand[c][1], cand[c][2], 1e3f * ms[c] / 24.f,
+                         c == best ? " (chosen)" : "");
+    h->coop = cand[best][0];
+    h->coop_lc = cand[best][1];
+    h->coop_cap = cand[best][2];
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    schedule_cache()[key] = cand[best];
+}
+
 template <typename T>
 void autotune(plsqr_ctx* h, bool fresh = false) {
     h->tuned = true;
@@ -591,6 +722,7 @@ void autotune(plsqr_ctx* h, bool fresh = false) {
             std::lock_guard<std::mutex> lk(tune_mutex());
             tune_cache()[key] = best;
         }
+        if (h->coop_ok && h->coop < 0) choose_schedule<T>(h, st0, e0, e1, fresh);
         ck(cudaStreamSynchronize(s), "autotune");
     } catch (...) {
         cleanup();
@@ -718,7 +850,7 @@ int solve_impl(plsqr_ctx* h, int count, const void* const* g, bool g_host, const
         ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");
         for (int b = 0; b < count; ++b) {
             int sb = h->st_host[b].status_any;
-            if (sb != 0) ret = PLSQR_E_BREAKDOWN;
+            if (sb != 0 && ret == PLSQR_OK) ret = sb == PLSQR_E_TIMEOUT ? PLSQR_E_TIMEOUT : PLSQR_E_BREAKDOWN;
             if (!stats) continue;
             plsqr_stats& S = stats[b];
             S.status = sb;
@@ -930,11 +1062,31 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         }
         if (h->d.ndim == 2)
             for (int l = 0; l + 1 < h->L; ++l) h->lv[l].rd = dalloc(h, e * B * h->lv[l].d.N);
+        h->coop_sync = (unsigned*)dalloc(h, 4 * sizeof(unsigned));
+        {
+            const char* ec = std::getenv("PLSQR_MG_COOP");
+            // every level must be a TMA layout (rows of 16-byte multiples; the coarsest is staged
+            // as the coarse-correction box of the level above it)
+            bool rows16 = true;
+            for (int l = 0; l < h->L; ++l) rows16 = rows16 && ((size_t)h->lv[l].d.nx * e) % 16 == 0;
+            h->coop_ok = !h->generic_mg && h->d.ndim == 2 && h->L >= 2 && rows16 && tma_enabled() &&
+                         mg2d_coop_supported(h->nu, h->esz, h->L, h->nc) && !(ec && ec[0] == '0');
+            if (!h->coop_ok) h->coop = 0;
+            else if (ec && ec[0] == '1') {
+                h->coop = 1;
+                const char* el = std::getenv("PLSQR_MG_COOP_LEVEL");
+                h->coop_lc = el ? std::max(0, std::min(h->L - 2, std::atoi(el))) : 0;
+            }
+        }
         {
             Dims dl[16];
             for (int l = 0; l < h->L; ++l) dl[l] = h->lv[l].d;
             h->tail_lc = h->generic_mg ? h->L : mg2d_tail_level(dl, h->L, h->nu, h->esz, h->nc);
             h->tail.n = h->tail_lc < h->L ? h->L - h->tail_lc : 0;
+            if (h->tail_lc < h->L) {  // the opt-in cluster tail and the cooperative V-cycle exclude each other
+                h->coop_ok = false;
+                h->coop = 0;
+            }
             for (int q = 0; q < h->tail.n; ++q) {
                 const Level& Lv = h->lv[h->tail_lc + q];
                 h->tail.cond[q] = Lv.cond;
@@ -1100,6 +1252,7 @@ int plsqr_set_kappa_bf16(plsqr_handle h, int32_t on) {
         if ((on != 0) != h->kbf16) {
             clear_graphs(h);
             if (!h->tiles_set) h->tuned = false;  // the finest level's timing depends on the kappa storage
+            if (h->coop_ok && !coop_forced()) h->coop = -1;
         }
         h->kbf16 = on != 0;
         return PLSQR_OK;
@@ -1112,6 +1265,7 @@ int plsqr_autotune(plsqr_handle h, int32_t fresh) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {
         if (h->serving) throw std::logic_error("tile shapes cannot change while slots are in use");
+        if (h->coop_ok && !coop_forced()) h->coop = -1;  // timed again
         by_type(h, [&](auto tv) {
             using T = decltype(tv);
             autotune<T>(h, fresh != 0);
@@ -1198,6 +1352,14 @@ int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx,
         if (threads) *threads = v[2];
         return PLSQR_OK;
     });
+}
+
+int plsqr_mg_schedule(plsqr_handle h, int32_t* coop, int32_t* first_level, int32_t* max_blocks) {
+    if (!h || !coop) return PLSQR_E_INVALID;
+    *coop = h->coop_ok ? h->coop : 0;
+    if (first_level) *first_level = *coop == 1 ? h->coop_lc : -1;
+    if (max_blocks) *max_blocks = *coop == 1 ? h->coop_cap : 0;
+    return PLSQR_OK;
 }
 
 // ---- stopping rules ----------------------------------------------------------------------------

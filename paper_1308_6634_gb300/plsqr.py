@@ -93,6 +93,7 @@ def lib():
         "plsqr_tile_shape": ([vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "plsqr_tune_cache_export": ([C.c_char_p, i64], i64),
         "plsqr_tune_cache_import": ([C.c_char_p], i32),
+        "plsqr_mg_schedule": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -108,7 +109,7 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_check_guards", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
             "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_tune_cache_export",
-            "plsqr_tune_cache_import", "plsqr_mlsqr_multi_tau",
+            "plsqr_tune_cache_import", "plsqr_mg_schedule", "plsqr_mlsqr_multi_tau",
             "plsqr_projected_solve", "plsqr_selftest_wait"]
 
 KCLASS = ["fwd", "adj", "op_plain", "gs_fine", "mg_other", "coarse", "gk", "setup"]
@@ -435,6 +436,14 @@ class Solver:
         v = [C.c_int32() for _ in range(4)]
         _check(self.h, lib().plsqr_tile_shape(self.h, int(level), *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def mg_schedule(self, detail=False):
+        """1: the 2D V-cycle runs (from some level down) as one cooperative launch; 0: per-level
+        launches; -1: not chosen yet.  detail=True: (that, first level, block cap)
+        (plsqr_mg_schedule)."""
+        v = [C.c_int32() for _ in range(3)]
+        _check(self.h, lib().plsqr_mg_schedule(self.h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v) if detail else v[0].value
 
     # ---- slots (continuous batching) ----
     def slot_start(self, slot, g, reg, T, tau, n_outer, n_inner, sigma=None):
