@@ -628,8 +628,11 @@ class GpuRun:
 
 
 # Other workloads measured by the default run beside the headline one: (key, workload, batch, steps,
-# warm-up steps)
-EXTRAS = (("inpaint192_fp32", "inpaint192_fp32", 1, 3, 2),
+# warm-up steps).  The batched 1024^2 forms are the throughput form of the headline workload (B
+# independent instances per launch).
+EXTRAS = (("deblur1024_fp32_x8", "deblur1024_fp32", 8, 2, 1),
+          ("deblur1024_fp32_x32", "deblur1024_fp32", 32, 1, 1),
+          ("inpaint192_fp32", "inpaint192_fp32", 1, 3, 2),
           ("tomo512_fp32", "tomo512_fp32", 1, 3, 2),
           ("tomo512_fp32_x32", "tomo512_fp32", 32, 1, 1))
 
@@ -711,6 +714,8 @@ def main():
             workloads[key] = dict(r2.summary(st), roofline=r2.profile())
             r2.close()
         workloads["serve_2000_poisson200"] = serving_stream(2000, 200.0, args.hbm_budget_gb, 3, 0, torch, dev)
+        # the same mix at an arrival rate inside the engine's capacity: latency without a growing queue
+        workloads["serve_800_poisson40"] = serving_stream(800, 40.0, args.hbm_budget_gb, 3, 0, torch, dev)
 
     accuracy = None
     if acc_leg is not None:

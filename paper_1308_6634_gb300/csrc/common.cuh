@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace plsqr {
 
 constexpr int ST_IDLE = 7;       // an empty slot of a serving handle: kernels skip the instance
@@ -126,6 +128,41 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// One row of the coarsest level's exact solve, (X b)_row = sum_c X[row][c] b[c], by one warp: lane l
+// takes the 16-byte groups l, l + 32, ... of the row (four floats or two doubles each; all of a
+// row's loads are independent, so they are in flight together), multiplies them with the same
+// group of b (16-byte aligned in shared memory) in column order within the group, and the warp
+// sums the lanes (butterfly).  The rows of X are 16-byte aligned when nc is a multiple of 4;
+// otherwise a plain strided loop.  Every schedule calls this function, so they agree bit for bit.
+template <typename T>
+__device__ __forceinline__ T coarse_row_dot(const T* __restrict__ Xr, const T* sb, int nc, int lane) {
+    constexpr int V = 16 / (int)sizeof(T);
+    T acc = (T)0;
+    if (nc % 4 == 0) {
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        const V4* X4 = reinterpret_cast<const V4*>(Xr);
+        const V4* B4 = reinterpret_cast<const V4*>(sb);
+        const int ng = nc / V;
+#pragma unroll 8
+        for (int g = lane; g < ng; g += 32) {
+            const V4 q = __ldg(X4 + g);
+            const V4 bq = B4[g];
+            if constexpr (sizeof(T) == 4) {
+                acc = fma(q.x, bq.x, acc);
+                acc = fma(q.y, bq.y, acc);
+                acc = fma(q.z, bq.z, acc);
+                acc = fma(q.w, bq.w, acc);
+            } else {
+                acc = fma(q.x, bq.x, acc);
+                acc = fma(q.y, bq.y, acc);
+            }
+        }
+    } else {
+        for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sb[c], acc);
+    }
+    return warp_sum_t<T>(acc);
+}
+
 // Sum over the block; the result is valid in thread 0.  Fixed reduction tree.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */) {
@@ -164,6 +201,37 @@ __device__ __forceinline__ bool reduce_last(double v, const Red& rd, int inst, i
     double s = 0.0;
     for (int i = threadIdx.x; i < nblk; i += NT) s += __ldcg(&rd.partials[(int64_t)inst * rd.max_blocks + i]);
     double tot = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) {
+        rd.counters[inst] = 0u;
+        *total = tot;
+        return true;
+    }
+    return false;
+}
+
+// Every block of instance `inst` calls this after its threads wrote (and fenced) their partial sums
+// at fixed positions of rd.partials[inst][0 .. nparts); returns true in thread 0 of the last of the
+// nblk blocks, with the sum of the nparts partials in *total: each thread sums the positions
+// t, t + NT, ... in order, then a fixed tree.  The positions, not the blocks, fix the order, so the
+// result does not depend on how the work was split into blocks.
+template <int NT>
+__device__ __forceinline__ bool sum_partials_last(const Red& rd, int inst, int nblk, int nparts, double* total) {
+    __shared__ double sh[NT / 32];
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&rd.counters[inst], 1u);
+        is_last = (prev == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    const double* p = rd.partials + (int64_t)inst * rd.max_blocks;
+    double s = 0.0;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < nparts; i += NT) s += __ldcg(p + i);
+    const double tot = block_sum<NT>(s, sh);
     if (threadIdx.x == 0) {
         rd.counters[inst] = 0u;
         *total = tot;

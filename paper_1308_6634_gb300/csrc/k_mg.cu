@@ -662,10 +662,7 @@ __global__ void __launch_bounds__(256) k_coarse_symv(const T* __restrict__ X_all
     __syncthreads();
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= nc) return;
-    const T* Xr = X_all + (int64_t)inst * nc * nc + (int64_t)row * nc;
-    T acc = (T)0;
-    for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sb[c], acc);
-    acc = warp_sum_t<T>(acc);
+    const T acc = coarse_row_dot<T>(X_all + (int64_t)inst * nc * nc + (int64_t)row * nc, sb, nc, lane);
     if (lane == 0) x_all[(int64_t)inst * nc + row] = acc;
 }
 

@@ -3,6 +3,9 @@
 // others), and the opt-in one-launch coarse end.
 #include "k_mg2d_impl.cuh"
 
+#include <mutex>
+#include <set>
+
 namespace plsqr {
 
 PLSQR_MG2D_SHAPE_DECL(, float, true, F0, true)
@@ -58,10 +61,7 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
         const int per = (nc + CS - 1) / CS, r0 = rank * per, r1 = min(nc, r0 + per);
         const int lane = threadIdx.x & 31;
         for (int row = r0 + (threadIdx.x >> 5); row < r1; row += TNT / 32) {
-            const T* Xr = X + (int64_t)inst * nc * nc + (int64_t)row * nc;
-            T acc = (T)0;
-            for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sbv[c], acc);
-            acc = warp_sum_t<T>(acc);
+            const T acc = coarse_row_dot<T>(X + (int64_t)inst * nc * nc + (int64_t)row * nc, sbv, nc, lane);
             if (lane == 0) xL[row] = acc;
         }
         __syncthreads();
@@ -72,17 +72,26 @@ __global__ void __launch_bounds__(TNT) k_mg_tail2d(const __grid_constant__ TailL
         constexpr int MTX = TailShape::TX, MTY = TailShape::TY;
         const int tx = (d.nx + MTX - 1) / MTX, nt = tx * ((d.ny + MTY - 1) / MTY);
         for (int t = rank; t < nt; t += CS) {
-            T unused;
             post_tile<T, false, NU, false, TMA, 0, TailShape>(smraw, tm.post[q], (const T*)tl.cond[q],
                                                               (const T*)tl.b[q], (const T*)tl.rd[q], (const T*)tl.x[q],
                                                               (T*)tl.x2[q], (const T*)tl.x2[q + 1], d, dc, st, inst,
-                                                              (t % tx) * MTX, (t / tx) * MTY, &unused);
+                                                              (t % tx) * MTX, (t / tx) * MTY, nullptr, 0);
         }
         if (q > 0) tail_phase_barrier();
     }
 }
 
 bool mg2d_supported(int ndim, int nu) { return ndim == 2 && nu >= 1 && nu <= 3; }
+
+void max_carveout_set(const void* kfn) {
+    static std::mutex mu;
+    static std::set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(kfn)) return;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        cudaGetLastError();
+    done.insert(kfn);
+}
 
 constexpr int TAIL_CS = 16;  // blocks per cluster (non-portable size; cudaOccupancyMaxActiveClusters is asked first)
 
@@ -208,6 +217,7 @@ bool mg2d_shape(bool fine, int id, int* tx, int* ty, int* nth) {
             case 0: v[0] = F0::TX, v[1] = F0::TY, v[2] = F0::NTH; break;
             case 1: v[0] = F1::TX, v[1] = F1::TY, v[2] = F1::NTH; break;
             case 2: v[0] = F2::TX, v[1] = F2::TY, v[2] = F2::NTH; break;
+            case 3: v[0] = F3::TX, v[1] = F3::TY, v[2] = F3::NTH; break;
             default: return false;
         }
     } else {
@@ -233,6 +243,7 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc
     if (is_kappa) {
         if (shape == 1) done = pre_shape<T, true, F1, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (shape == 2) done = pre_shape<T, true, F2, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
+        if (shape == 3) done = pre_shape<T, true, F3, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (!done) pre_shape<T, true, F0, true>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
     } else {
         switch (shape) {
@@ -260,6 +271,8 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* x
             done = post_shape<T, true, F1, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
         if (shape == 2)
             done = post_shape<T, true, F2, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
+        if (shape == 3)
+            done = post_shape<T, true, F3, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
         if (!done) post_shape<T, true, F0, true>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
     } else {
         switch (shape) {

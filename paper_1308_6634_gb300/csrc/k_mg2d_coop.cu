@@ -131,10 +131,7 @@ __global__ void __launch_bounds__(SF::NTH) k_vcycle_coop(const __grid_constant__
             for (int i = threadIdx.x; i < nc; i += NTH) sbv[i] = b[i];
             __syncthreads();
             for (int row = grp * 8 + w; row < min(nc, grp * 8 + 8); row += NTH / 32) {
-                const T* Xr = X + (int64_t)inst * nc * nc + (int64_t)row * nc;
-                T acc = (T)0;
-                for (int c = lane; c < nc; c += 32) acc = fma(Xr[c], sbv[c], acc);
-                acc = warp_sum_t<T>(acc);
+                const T acc = coarse_row_dot<T>(X + (int64_t)inst * nc * nc + (int64_t)row * nc, sbv, nc, lane);
                 if (lane == 0) ((T*)cl.x2[L - 1])[(int64_t)inst * nc + row] = acc;
             }
         }
@@ -149,11 +146,10 @@ __global__ void __launch_bounds__(SF::NTH) k_vcycle_coop(const __grid_constant__
         const int tx = (d.nx + SC::TX - 1) / SC::TX, nt = tx * ((d.ny + SC::TY - 1) / SC::TY);
         for (int u = blockIdx.x; u < nt * B; u += gridDim.x) {
             const int inst = u / nt, t = u - inst * nt;
-            T unused;
             post_tile<T, false, NU, false, true, 1, SC>(smraw, cm.post[l], (const T*)cl.cond[l], (const T*)cl.b[l],
                                                         (const T*)cl.rd[l], (const T*)cl.x[l], (T*)cl.x2[l],
                                                         (const T*)cl.x2[l + 1], d, dc, st, inst, (t % tx) * SC::TX,
-                                                        (t / tx) * SC::TY, &unused);
+                                                        (t / tx) * SC::TY, nullptr, 0);
         }
         if (l == lc) break;  // the last phase of a launch that starts below the finest level
         if (!coop_barrier(sy, ++phase, st, B)) {
@@ -166,15 +162,16 @@ __global__ void __launch_bounds__(SF::NTH) k_vcycle_coop(const __grid_constant__
         const int tx = (d.nx + SF::TX - 1) / SF::TX, nt = tx * ((d.ny + SF::TY - 1) / SF::TY);
         for (int u = blockIdx.x; u < nt * B; u += gridDim.x) {
             const int inst = u / nt, t = u - inst * nt;
-            T part;
+            const int nseg = (d.nx + 31) / 32;
             if (!post_tile<T, true, NU, DOTM != 0, true, DOTM != 0 ? 2 : 1, SF>(
                     smraw, cm.post[0], (const T*)cl.cond[0], (const T*)cl.b[0], (const T*)cl.rd[0],
                     (const T*)cl.x[0], (T*)cl.x2[0], (const T*)cl.x2[1], d, dc, st, inst, (t % tx) * SF::TX,
-                    (t / tx) * SF::TY, &part, k16))
+                    (t / tx) * SF::TY, DOTM != 0 ? red.partials + (int64_t)inst * red.max_blocks : nullptr, nseg,
+                    k16))
                 continue;
             if (DOTM != 0) {
                 double tot;
-                if (reduce_last<NTH>((double)part, red, inst, t, nt, &tot))
+                if (sum_partials_last<NTH>(red, inst, nt, ((d.ny + 15) / 16) * nseg, &tot))
                     finalize_alpha<DOTM == 1>(st[inst], tot, hist, inst);
             }
         }
@@ -262,10 +259,8 @@ static void coop_launch(const CoopLevels& cl, int lc, int cap, const T* X, int n
     if (!ok) throw std::runtime_error("vcycle_coop: tensor maps unavailable for this layout");
     const int blocks = coop_blocks<T, NU, DOTM>(cl, lc, cap, nc, B);
     if (blocks <= 0) throw std::runtime_error("vcycle_coop: no resident blocks");
-    if (DOTM != 0 &&
-        (int64_t)((cl.d[0].nx + CoopF::TX - 1) / CoopF::TX) * ((cl.d[0].ny + CoopF::TY - 1) / CoopF::TY) >
-            red.max_blocks)
-        throw std::runtime_error("vcycle_coop: too many tiles for the reduction scratch");
+    if (DOTM != 0 && (int64_t)((cl.d[0].ny + 15) / 16) * ((cl.d[0].nx + 31) / 32) > red.max_blocks)
+        throw std::runtime_error("vcycle_coop: too many segments for the reduction scratch");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(CoopF::NTH);

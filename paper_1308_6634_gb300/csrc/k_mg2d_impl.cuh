@@ -31,18 +31,22 @@ namespace plsqr {
 
 // Tile extents (TX, TY; even, TX a multiple of 8) and threads per block.  The finest level has
 // many tiles; the coarser levels have few, so they take more threads per tile.
-template <int TX_, int TY_, int NTH_>
+// MINB_: blocks per SM the finest-level float kernels are compiled for (register budget): the
+// 32 x 32 post-smoothing tile then fits 8 blocks per SM (one wave for the 1024 tiles of a 1024^2
+// level; 37 registers allowed only 6).
+template <int TX_, int TY_, int NTH_, int MINB_ = 1>
 struct Shape {
-    static constexpr int TX = TX_, TY = TY_, NTH = NTH_;
+    static constexpr int TX = TX_, TY = TY_, NTH = NTH_, MINB = MINB_;
     static_assert(TX % 8 == 0 && TY % 2 == 0, "tiles start at even coordinates, x on 16-byte boundaries of xc");
 };
-// The shapes compiled in.  Level 0 (many tiles): F0 (default) .. F2.  Coarser levels (few tiles,
+// The shapes compiled in.  Level 0 (many tiles): F0 (default) .. F3.  Coarser levels (few tiles,
 // so more threads per tile or smaller tiles spread over more SMs): C0 (default) .. C5.  The
 // defaults also have plain-load variants; the others need TMA staging.  Every shape gives bit for
 // bit the same V-cycle (the same arithmetic per cell in the same order), only the schedule differs.
 using F0 = Shape<64, 32, 256>;
-using F1 = Shape<32, 32, 256>;
+using F1 = Shape<32, 32, 256, 7>;
 using F2 = Shape<32, 16, 256>;
+using F3 = Shape<64, 32, 512>;
 using C0 = Shape<64, 32, 1024>;
 using C1 = Shape<32, 16, 512>;
 using C2 = Shape<32, 16, 256>;
@@ -178,6 +182,33 @@ __device__ __forceinline__ bool stage(T* sm, const Maps& maps, const T* __restri
     }
 }
 
+// The Gauss-Seidel update of one cell, x = (b + sum_nb c_nb x_nb) / diag with the reciprocal
+// diagonal rd, in a fixed order of operations (every schedule and storage layout uses it, so they
+// agree bit for bit): cE, cW are the conductances of the east / west edges (kappa of the cell and
+// of its west neighbour on the finest level), cN, cS those of the north / south edges.
+template <typename T>
+__device__ __forceinline__ T gs_update(T b, T rd, T cE, T cW, T cN, T cS, T xE, T xW, T xN, T xS) {
+    T off = cE * xE;
+    off = fma(cW, xW, off);
+    off = fma(cN, xN, off);
+    off = fma(cS, xS, off);
+    return (b + off) * rd;
+}
+
+// r = b - (diag x - off) of one cell, the residual the restriction sums (the same fixed order).
+template <typename T>
+__device__ __forceinline__ T gs_residual(T b, T x, T cE, T cW, T cN, T cS, T xE, T xW, T xN, T xS) {
+    T diag = cE;
+    diag += cW;
+    diag += cN;
+    diag += cS;
+    T off = cE * xE;
+    off = fma(cW, xW, off);
+    off = fma(cN, xN, off);
+    off = fma(cS, xS, off);
+    return b - fma(diag, x, -off);
+}
+
 // One half sweep of `colour` over the logical cells at distance >= lo from the staged edge:
 // x = (b + off) * sd.  Cells outside the domain have b = 0 and sd = 0 and stay 0.  Tiles start
 // at even global coordinates (x0, y0 multiples of the tile extents) and the halo is the same on
@@ -194,11 +225,8 @@ __device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* sc
         const int lx = lo + ((colour ^ ly ^ lo) & 1) + 2 * j;  // first lx >= lo of the colour, then every other
         if (lx > hi) continue;
         const int i = ly * LXS + lx + OX;
-        T off = scx[i] * sx[i + 1];
-        off += scx[i - 1] * sx[i - 1];
-        off += scy[i] * sx[i + LXS];
-        off += scy[i - LXS] * sx[i - LXS];
-        sx[i] = (sb[i] + off) * sd[i];
+        sx[i] = gs_update(sb[i], sd[i], scx[i], scx[i - 1], scy[i], scy[i - LXS], sx[i + 1], sx[i - 1],
+                          sx[i + LXS], sx[i - LXS]);
     }
 }
 
@@ -221,47 +249,42 @@ __device__ __forceinline__ bool pre_tile(unsigned char* smraw, const Maps& maps,
     if (stage<T, L0, H, TMA, false, false, SKIP, S>(sm, maps, cond, b, rd, nullptr, nullptr, d, dc, inst, x0, y0,
                                                       st, k16))
         return false;
-#pragma unroll
-    for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, s & 1);
-        __syncthreads();
-    }
-    // residual r = b - (diag x - off) on the tile, summed over the 2 x 2 children
     const int64_t offc = (int64_t)inst * dc.N;
-    for (int k = threadIdx.x; k < (MTX / 2) * (MTY / 2); k += NTH) {
-        const int cy = k / (MTX / 2), cx = k - cy * (MTX / 2);
-        const int X = (x0 >> 1) + cx, Y = (y0 >> 1) + cy;
-        if (X >= dc.nx || Y >= dc.ny) continue;
-        T sum = (T)0;
-#pragma unroll
-        for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-            for (int ox = 0; ox < 2; ++ox) {
-                const int i = (H + 2 * cy + oy) * LXS + (H + 2 * cx + ox) + OX;
-                T diag = scx[i];
-                diag += scx[i - 1];
-                diag += scy[i];
-                diag += scy[i - LXS];
-                T off = scx[i] * sx[i + 1];
-                off += scx[i - 1] * sx[i - 1];
-                off += scy[i] * sx[i + LXS];
-                off += scy[i - LXS] * sx[i - LXS];
-                sum += sb[i] - (diag * sx[i] - off);
-            }
-        bc[offc + (int64_t)Y * dc.nx + X] = sum;
-    }
     const int64_t off = (int64_t)inst * d.N;
-    for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
-        const int ty = k / MTX, tx = k - ty * MTX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx < d.nx && gy < d.ny) x[off + (int64_t)gy * d.nx + gx] = sx[(H + ty) * LXS + H + tx + OX];
+    {
+#pragma unroll
+        for (int s = 0; s < 2 * NU; ++s) {
+            half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, s & 1);
+            __syncthreads();
+        }
+        // residual r = b - (diag x - off) on the tile, summed over the 2 x 2 children
+        for (int k = threadIdx.x; k < (MTX / 2) * (MTY / 2); k += NTH) {
+            const int cy = k / (MTX / 2), cx = k - cy * (MTX / 2);
+            const int X = (x0 >> 1) + cx, Y = (y0 >> 1) + cy;
+            if (X >= dc.nx || Y >= dc.ny) continue;
+            T sum = (T)0;
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+                for (int ox = 0; ox < 2; ++ox) {
+                    const int i = (H + 2 * cy + oy) * LXS + (H + 2 * cx + ox) + OX;
+                    sum += gs_residual(sb[i], sx[i], scx[i], scx[i - 1], scy[i], scy[i - LXS], sx[i + 1], sx[i - 1],
+                                       sx[i + LXS], sx[i - LXS]);
+                }
+            bc[offc + (int64_t)Y * dc.nx + X] = sum;
+        }
+        for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
+            const int ty = k / MTX, tx = k - ty * MTX;
+            const int gx = x0 + tx, gy = y0 + ty;
+            if (gx < d.nx && gy < d.ny) x[off + (int64_t)gy * d.nx + gx] = sx[(H + ty) * LXS + H + tx + OX];
+        }
     }
     __syncthreads();
     return true;
 }
 
 template <typename T, bool L0, int NU, bool TMA, class S>
-__global__ void __launch_bounds__(S::NTH) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
+__global__ void __launch_bounds__(S::NTH, (sizeof(T) == 4 && L0) ? S::MINB : 1) k_mg_pre2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
                                                   const T* __restrict__ b, const T* __restrict__ rd,
                                                   T* __restrict__ x, T* __restrict__ bc, Dims d, Dims dc, GkState* st,
                                                   const __nv_bfloat16* __restrict__ k16) {
@@ -273,13 +296,19 @@ __global__ void __launch_bounds__(S::NTH) k_mg_pre2d(const __grid_constant__ Map
 
 // One tile of x_out = smooth(x_in + P xc) with nu black->red sweeps (x_in and x_out must differ:
 // blocks read neighbouring tiles of x_in as halo).  Returns false when the block skips the tile
-// (see stage); *part is this thread's share of x_out . b over the tile when DOT.  Ends with a
-// barrier.
+// (see stage).  DOT: also the partial sums of x_out . b over 32 x 16 segments of the grid (32
+// columns, 16 rows, anchored at multiples of 32 and 16), written to segp[(y / 16) * nseg + x / 32]
+// (nseg = ceil(nx / 32)): each row of a segment by one warp (the 32 products summed in T by a
+// butterfly), then its 16 row sums in double in row order.  The segments do not depend on the
+// tile shape, so alpha (their sum, see sum_partials_last) is the same whatever shape the
+// autotuner picks.  Ends with a barrier.
 template <typename T, bool L0, int NU, bool DOT, bool TMA, int SKIP, class S>
 __device__ __forceinline__ bool post_tile(unsigned char* smraw, const Maps& maps, const T* cond, const T* b,
                                           const T* rd, const T* x_in, T* x_out, const T* xc, const Dims& d,
-                                          const Dims& dc, GkState* st, int inst, int x0, int y0, T* part_out,
-                                          const __nv_bfloat16* k16 = nullptr) {
+                                          const Dims& dc, GkState* st, int inst, int x0, int y0, double* segp,
+                                          int nseg, const __nv_bfloat16* k16 = nullptr) {
+    static_assert(!DOT || (S::TX % 32 == 0 && S::TY % 16 == 0), "tiles hold whole 32 x 16 segments");
+    __shared__ double srow[DOT ? S::TY * (S::TX / 32) : 1];  // row sums of the tile's segments
     constexpr int H = 2 * NU;
     using TL = Tile<T, L0, H, S, true>;
     constexpr int LXS = TL::LXS, OX = TL::OX, NTH = S::NTH, MTX = S::TX, MTY = S::TY;
@@ -292,38 +321,60 @@ __device__ __forceinline__ bool post_tile(unsigned char* smraw, const Maps& maps
     const T* sxc = sm + TL::OFF_XC;
     if (stage<T, L0, H, TMA, true, true, SKIP, S>(sm, maps, cond, b, rd, x_in, xc, d, dc, inst, x0, y0, st, k16))
         return false;
-    // + P xc.  The extents are even (2^(levels-1) divides them), so a cell outside the domain has
-    // its parent outside the coarse grid: it adds the zero fill and stays 0.
-    for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
-        const int ly = i / LXS, lxs = i - ly * LXS;
-        sx[i] = sx[i] + sxc[((ly + (H & 1)) >> 1) * TL::XW + ((lxs + 2 * TL::XB - TL::HX) >> 1)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < 2 * NU; ++s) {
-        half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, 1 - (s & 1));
-        __syncthreads();
-    }
     const int64_t off = (int64_t)inst * d.N;
-    T part = (T)0;
-    for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
-        const int ty = k / MTX, tx = k - ty * MTX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx < d.nx && gy < d.ny) {
-            const int i = (H + ty) * LXS + H + tx + OX;
-            x_out[off + (int64_t)gy * d.nx + gx] = sx[i];
-            if (DOT) part = fma(sx[i], sb[i], part);
+    {
+        // + P xc.  The extents are even (2^(levels-1) divides them), so a cell outside the domain
+        // has its parent outside the coarse grid: it adds the zero fill and stays 0.
+        for (int i = threadIdx.x; i < TL::NCS; i += NTH) {
+            const int ly = i / LXS, lxs = i - ly * LXS;
+            sx[i] = sx[i] + sxc[((ly + (H & 1)) >> 1) * TL::XW + ((lxs + 2 * TL::XB - TL::HX) >> 1)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 2 * NU; ++s) {
+            half_sweep<T, TL::LX, TL::LY, LXS, OX, NTH>(sb, sd, scx, scy, sx, s + 1, 1 - (s & 1));
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < MTX * MTY; k += NTH) {
+            const int ty = k / MTX, tx = k - ty * MTX;
+            const int gx = x0 + tx, gy = y0 + ty;
+            T prod = (T)0;
+            if (gx < d.nx && gy < d.ny) {
+                const int i = (H + ty) * LXS + H + tx + OX;
+                x_out[off + (int64_t)gy * d.nx + gx] = sx[i];
+                if (DOT) prod = sx[i] * sb[i];
+            }
+            if (DOT) {  // the warp's 32 lanes are one 32-column row of a segment (TX is a multiple of 32)
+                const T v = warp_sum_t<T>(prod);  // in T: a butterfly in double would load the FP64 pipe
+                if ((threadIdx.x & 31) == 0) srow[ty * (MTX / 32) + (tx >> 5)] = (double)v;
+            }
+        }
+        if (DOT) {
+            __syncthreads();
+            // one thread per segment of the tile: its 16 row sums in row order (rows beyond ny and
+            // columns beyond nx added 0; segments wholly outside the grid do not exist)
+            constexpr int NSX = MTX / 32, NSY = MTY / 16;
+            if (threadIdx.x < NSX * NSY) {
+                const int sy = threadIdx.x / NSX, sx_ = threadIdx.x - sy * NSX;
+                const int gx0 = x0 + 32 * sx_, gy0 = y0 + 16 * sy;
+                if (gx0 < d.nx && gy0 < d.ny) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v += srow[(16 * sy + r) * NSX + sx_];
+                    segp[(int64_t)(gy0 >> 4) * nseg + (gx0 >> 5)] = v;
+                    __threadfence();
+                }
+            }
         }
     }
     __syncthreads();
-    *part_out = part;
     return true;
 }
 
 // DOT: also alpha = sqrt(x_out . b) and the rotations (finest level of the last V-cycle:
 // x_out = v~, b = p~).
 template <typename T, bool L0, int NU, bool DOT, bool INIT, bool TMA, class S>
-__global__ void __launch_bounds__(S::NTH) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
+__global__ void __launch_bounds__(S::NTH, (sizeof(T) == 4 && L0) ? S::MINB : 1) k_mg_post2d(const __grid_constant__ Maps maps, const T* __restrict__ cond,
                                                    const T* __restrict__ b, const T* __restrict__ rd,
                                                    const T* __restrict__ x_in, T* __restrict__ x_out,
                                                    const T* __restrict__ xc, Dims d, Dims dc, GkState* st, Hist hist,
@@ -331,16 +382,25 @@ __global__ void __launch_bounds__(S::NTH) k_mg_post2d(const __grid_constant__ Ma
     extern __shared__ __align__(128) unsigned char smraw[];
     const int inst = blockIdx.z;
     pdl_grid_sync();
-    T part;
+    const int nseg = (d.nx + 31) / 32;
     if (!post_tile<T, L0, NU, DOT, TMA, DOT ? 2 : 1, S>(smraw, maps, cond, b, rd, x_in, x_out, xc, d, dc, st, inst,
-                                                        blockIdx.x * S::TX, blockIdx.y * S::TY, &part, k16))
+                                                        blockIdx.x * S::TX, blockIdx.y * S::TY,
+                                                        DOT ? red.partials + (int64_t)inst * red.max_blocks : nullptr,
+                                                        nseg, k16))
         return;
     if (DOT) {
-        const int nblk = gridDim.x * gridDim.y;
         double tot;
-        if (reduce_last<S::NTH>((double)part, red, inst, blockIdx.x + gridDim.x * blockIdx.y, nblk, &tot))
+        if (sum_partials_last<S::NTH>(red, inst, gridDim.x * gridDim.y, ((d.ny + 15) / 16) * nseg, &tot))
             finalize_alpha<INIT>(st[inst], tot, hist, inst);
     }
+}
+
+// Ask for the largest shared-memory carveout (all of the unified L1 / shared storage an SM can give
+// to shared memory), so that the occupancy is set by the blocks' needs and not by the driver's
+// default split; once per kernel.
+template <typename K>
+void max_carveout(K kfn) {
+    max_carveout_set(reinterpret_cast<const void*>(kfn));
 }
 
 // TMA maps for one launch; false when the layout rules are not met (plain loads instead).
@@ -372,6 +432,7 @@ bool pre_launch(const T* cond, const T* b, const T* rd, T* x, T* bc, Dims d, Dim
     if constexpr (PLAIN)
         if (!tma) kfn = k_mg_pre2d<T, L0, NU, false, S>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    max_carveout(kfn);
     dim3 grid((d.nx + S::TX - 1) / S::TX, (d.ny + S::TY - 1) / S::TY, B);
     launch_k(kfn, grid, dim3(S::NTH), smem, s, maps, cond, b, rd, x, bc, d, dc, st, k16);
     return true;
@@ -389,9 +450,10 @@ bool post_launch(const T* cond, const T* b, const T* rd, const T* xi, T* x, cons
     if constexpr (PLAIN)
         if (!tma) kfn = k_mg_post2d<T, L0, NU, DOT, INIT, false, S>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    max_carveout(kfn);
     dim3 grid((d.nx + S::TX - 1) / S::TX, (d.ny + S::TY - 1) / S::TY, B);
-    if (DOT && (int64_t)grid.x * grid.y > red.max_blocks)
-        throw std::runtime_error("mg_post2d: too many blocks for the reduction scratch");
+    if (DOT && (int64_t)((d.ny + 15) / 16) * ((d.nx + 31) / 32) > red.max_blocks)
+        throw std::runtime_error("mg_post2d: too many segments for the reduction scratch");
     launch_k(kfn, grid, dim3(S::NTH), smem, s, maps, cond, b, rd, xi, x, xc, d, dc, st, hist, red, k16);
     return true;
 }
@@ -450,7 +512,9 @@ bool post_shape(const T* cond, const T* b, const T* rd, const T* xi, T* x, const
     PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F1, false)      \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F1, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F2, false)      \
-    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F2, false)
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F2, false)     \
+    PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F3, false)      \
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F3, false)
 #define PLSQR_MG2D_ALT_COARSE(EXT)                          \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C1, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C1, false)    \

@@ -342,6 +342,61 @@ __global__ void __launch_bounds__(256) k_blur_z(const T* __restrict__ in, T* out
     }
 }
 
+// Register-blocked z pass for float with the z radius R known at compile time (the 3D workloads'
+// 9, 12, 15): a thread owns one (x, y) column and ZR consecutive z outputs, loads the ZR + 2R
+// input values of its column straight from memory into registers (coalesced across the 32 x
+// lanes; all loads independent, so they are in flight together), and forms every output from
+// them with the taps as FMA operands from the constant bank -- no shared memory and no reload of a
+// value per tap.  The taps are summed in the order of k_blur_z, so the result is the same.
+constexpr int ZR = 16;
+
+template <int R>
+struct TapsZ {
+    float w[2 * R + 1];
+};
+
+template <int R, int EPI, bool MASK_OUT>
+__global__ void __launch_bounds__(256) k_blur_z_rb(const float* __restrict__ in, float* out, const float* prev,
+                                                   const uint8_t* __restrict__ mask, Dims d, const TapsZ<R> wz,
+                                                   GkState* st, Red red) {
+    pdl_grid_sync();
+    const int nzt = (d.nz + ZR - 1) / ZR;
+    const int inst = blockIdx.z / nzt, zt = blockIdx.z - inst * nzt;
+    const bool skip = EPI != EPI_PLAIN && inner_off(st[inst]);  // the same in every thread of the block
+    const int gx = blockIdx.x * 32 + (threadIdx.x & 31), gy = blockIdx.y * 8 + (threadIdx.x >> 5), z0 = zt * ZR;
+    const bool inxy = gx < d.nx && gy < d.ny && !skip;
+    const int64_t plane = (int64_t)d.nx * d.ny;
+    const int64_t col = (int64_t)inst * d.N + (int64_t)gy * d.nx + gx;
+    float win[ZR + 2 * R];
+#pragma unroll
+    for (int k = 0; k < ZR + 2 * R; ++k) {
+        const int gz = z0 - R + k;
+        win[k] = (inxy && gz >= 0 && gz < d.nz) ? __ldg(in + col + gz * plane) : 0.f;
+    }
+    float ca = 1.f, cp = 0.f;
+    if (EPI != EPI_PLAIN && !skip) epi_coefs<float, EPI>(st[inst], ca, cp);
+    float part = 0.f;
+#pragma unroll
+    for (int o = 0; o < ZR; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wz.w[k], win[o + k], acc);
+        const int gz = z0 + o;
+        if (inxy && gz < d.nz) {
+            const int64_t oo = (int64_t)gz * plane + (int64_t)gy * d.nx + gx;
+            if (MASK_OUT) acc = mask[oo] ? acc : 0.f;
+            const float v = epi_store<float, EPI>(acc, ca, cp, out, prev, (int64_t)inst * d.N + oo);
+            if (EPI == EPI_FWD) part = fmaf(v, v, part);
+        }
+    }
+    if (EPI == EPI_FWD && !skip) {
+        const int nblk = gridDim.x * gridDim.y * nzt;
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt);
+        double tot;
+        if (reduce_last<256>((double)part, red, inst, blk, nblk, &tot)) finalize_beta(st[inst], tot);
+    }
+}
+
 // A = I (denoising): the epilogue alone.
 template <typename T, int EPI>
 __global__ void __launch_bounds__(256) k_identity(const T* __restrict__ in, T* out, const T* prev, int64_t n,
@@ -757,12 +812,14 @@ static void launch_blur2d_rb(const OpDev& op, const float* in, float* out, const
         if (tma) {
             if constexpr (!MI && !MO) {
                 if (op.tapt) {
+                    max_carveout_set((const void*)k_blur2d_rb<R, EPI, MI, MO, true, UPD, true>);
                     launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD, true>, grid, dim3(BNT), 0, s, map, in, out, prev,
                              (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, op.tapt);
                     klaunched("k_blur2d_rb");
                     return;
                 }
             }
+            max_carveout_set((const void*)k_blur2d_rb<R, EPI, MI, MO, true, UPD, false>);
             launch_k(k_blur2d_rb<R, EPI, MI, MO, true, UPD, false>, grid, dim3(BNT), 0, s, map, in, out, prev,
                      (const uint8_t*)op.mask, d, wx, wy, st, red, fu, wu, (const float*)nullptr);
         }
@@ -810,11 +867,35 @@ static void launch_blur2d(const OpDev& op, const T* in, T* out, const T* prev, i
     klaunched("k_blur2d");
 }
 
+template <int R, int EPI, bool MO>
+static void launch_blur_z_rb(const OpDev& op, const float* in, float* out, const float* prev, int B, GkState* st,
+                             Red red, cudaStream_t s) {
+    const Dims& d = op.d;
+    TapsZ<R> wz;
+    for (int k = 0; k <= 2 * R; ++k) wz.w[k] = (float)op.taps_host[2][k];
+    const int nzt = (d.nz + ZR - 1) / ZR;
+    dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, nzt * B);
+    if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * nzt > red.max_blocks)
+        throw std::runtime_error("blur_z: too many blocks for the reduction scratch");
+    launch_k(k_blur_z_rb<R, EPI, MO>, grid, dim3(256), 0, s, in, out, prev, (const uint8_t*)op.mask, d, wz, st, red);
+    klaunched("k_blur_z_rb");
+}
+
 template <typename T, int EPI, bool MO>
 static void launch_blur_z(const OpDev& op, const T* in, T* out, const T* prev, int B, GkState* st, Red red,
                           cudaStream_t s) {
     const Dims& d = op.d;
     const int Rz = op.R[2];
+    if constexpr (std::is_same<T, float>::value) {
+        if (!op.generic_blur) {
+            switch (Rz) {
+                case 9: launch_blur_z_rb<9, EPI, MO>(op, in, out, prev, B, st, red, s); return;
+                case 12: launch_blur_z_rb<12, EPI, MO>(op, in, out, prev, B, st, red, s); return;
+                case 15: launch_blur_z_rb<15, EPI, MO>(op, in, out, prev, B, st, red, s); return;
+                default: break;
+            }
+        }
+    }
     const int nw = 2 * Rz + 1;
     size_t smem = sizeof(T) * ((size_t)((nw + 1) & ~1) + (size_t)(ZTZ + 2 * Rz) * 256);
     auto kfn = k_blur_z<T, EPI, MO>;

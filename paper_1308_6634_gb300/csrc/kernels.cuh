@@ -12,6 +12,10 @@ namespace plsqr {
 // Programmatic dependent launches are used unless PLSQR_PDL=0.
 bool pdl_enabled();
 
+// The largest shared-memory carveout for a kernel (once per kernel), so that its occupancy is set
+// by its blocks' needs and not by the driver's default split of L1 and shared memory.
+void max_carveout_set(const void* kfn);
+
 // Launch a kernel that begins with pdl_grid_sync(), with the programmatic-serialization attribute
 // so that its launch overlaps the tail of the previous kernel in the stream.
 template <typename... KArgs, typename... Args>

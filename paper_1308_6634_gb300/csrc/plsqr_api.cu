@@ -291,7 +291,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
         b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
     }
     b += (sizeof(GkState) + sizeof(SolveParams) + sizeof(unsigned)) * B;
-    b += sizeof(double) * B * 8192;
+    b += sizeof(double) * B * std::max<int64_t>(8192, (int64_t)((pl.d.ny + 15) / 16) * ((pl.d.nx + 31) / 32));
     pl.bytes = b;
     return pl;
 }
@@ -713,6 +713,10 @@ void autotune(plsqr_ctx* h, bool fresh = false) {
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 cudaGraphExecDestroy(exec);
                 ck(e, "autotune");
+                const char* lg = std::getenv("PLSQR_TUNE_LOG");
+                if (lg && lg[0] == '1')
+                    std::fprintf(stderr, "plsqr tiles level %d (%dx%d) batch %d: shape %d (%dx%d/%d): %.2f us per pre+post\n",
+                                 l, Lv.d.nx, Lv.d.ny, B, id, tx, ty, nth, 1e3f * ms / 24.f);
                 if (id == 0 || ms < best_ms) {
                     best = id;
                     best_ms = ms;
@@ -1116,7 +1120,9 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         ck(cudaMallocHost((void**)&h->prm_host, sizeof(SolveParams) * B), "cudaMallocHost");
         std::memset(h->prm_host, 0, sizeof(SolveParams) * B);  // stopping rules off
         ck(cudaMallocHost((void**)&h->st_host, sizeof(GkState) * B), "cudaMallocHost");
-        h->red.max_blocks = 8192;
+        // per-block partials, and the 32 x 16 segments of the 2D V-cycle's alpha
+        h->red.max_blocks =
+            (int32_t)std::max<int64_t>(8192, (int64_t)((h->d.ny + 15) / 16) * ((h->d.nx + 31) / 32));
         h->red.partials = (double*)dalloc(h, sizeof(double) * B * h->red.max_blocks);
         h->red.counters = (unsigned*)dalloc(h, sizeof(unsigned) * B);
         ck(cudaMemset(h->red.counters, 0, sizeof(unsigned) * B), "memset");
