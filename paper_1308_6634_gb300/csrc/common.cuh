@@ -244,43 +244,67 @@ __device__ __forceinline__ bool good_pos(double x, double ref) {
     return isfinite(x) && x > 1e-30 * ref;
 }
 
+// 1 / sqrt(x) in double for x > 0, by the Newton-Raphson iteration for the inverse square root,
+// y <- y (3/2 - (x/2) y^2), from the single-precision estimate rsqrtf (relative error ~1e-7; the
+// iteration converges quadratically, so two steps reach double rounding).  GB300's double pipe is
+// narrow and its square root and division run long dependent chains; this takes seven dependent
+// double operations.  Outside the single-precision normal range it defers to rsqrt; a
+// non-positive or non-finite x gives NaN, which callers turn into a breakdown.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    if (!(x > 0.0) || !isfinite(x)) return nan("");
+    if (!(x > 1.2e-38 && x < 3.0e38)) return rsqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double h = 0.5 * x;
+    y = y * fma(-h, y * y, 1.5);
+    y = y * fma(-h, y * y, 1.5);
+    return y;
+}
+
 // alpha_{i+1} = sqrt(v~ . p~) (Algorithm 2 steps 5 / 13) from the reduced dot product, then
 // (INIT = false) the orthogonal transformation: the Paige-Saunders damping rotation that
 // eliminates sqrt(tau) I (eq. 3.6) and Algorithm 1 steps 10-16, the coefficients of the
-// pending update (steps 19-20) and ||rbar_i||.  Runs on one thread.
+// pending update (steps 19-20) and ||rbar_i||.  Runs on one thread, on a copy of the state in
+// registers; each rotation takes one inverse square root (c = a / r, s = b / r, r = (a^2 + b^2) / r
+// with 1 / r = rsqrt_nr(a^2 + b^2)) instead of a square root and divisions.
 template <bool INIT>
-__device__ __forceinline__ void finalize_alpha(GkState& s, double tot, const Hist& hist, int inst) {
-    const double an = sqrt(tot);
+__device__ __forceinline__ void finalize_alpha(GkState& sg, double tot, const Hist& hist, int inst) {
+    GkState s = sg;
+    const double ian = tot > 0.0 ? rsqrt_nr(tot) : 0.0;  // 1 / alpha
+    const double an = tot * ian;
     if (!good_pos(an, s.beta1)) {
-        s.status = ST_BREAKDOWN;
-        s.status_any = ST_BREAKDOWN;
+        sg.status = ST_BREAKDOWN;
+        sg.status_any = ST_BREAKDOWN;
         return;
     }
     if (INIT) {  // step 7: rhobar_1 = alpha_1, w~_1 = v~_1
         s.alpha = an;
         s.rhobar = an;
-        s.c_upd_v = 1.0 / an;
-        s.c_fwd_a = 1.0 / an;
+        s.c_upd_v = ian;
+        s.c_fwd_a = ian;
         s.c_fwd_p = an / s.beta;
+        sg = s;
         return;
     }
     double rhohat = s.rhobar, psi = 0.0;
     if (s.tau > 0.0) {
-        rhohat = sqrt(s.rhobar * s.rhobar + s.tau);
-        const double c1 = s.rhobar / rhohat, s1 = s.sqrt_tau / rhohat;
+        const double q = s.rhobar * s.rhobar + s.tau;
+        const double ir = rsqrt_nr(q);
+        rhohat = q * ir;
+        const double c1 = s.rhobar * ir, s1 = s.sqrt_tau * ir;
         psi = s1 * s.phibar;
         s.phibar = c1 * s.phibar;
     }
     const double beta = s.beta_new;
-    const double rho = sqrt(rhohat * rhohat + beta * beta);
-    const double c = rhohat / rho, sn = beta / rho;
+    const double q2 = rhohat * rhohat + beta * beta;
+    const double irho = rsqrt_nr(q2);  // 1 / rho
+    const double c = rhohat * irho, sn = beta * irho;
     const double theta = sn * an;
     s.rhobar = -c * an;
     const double phi = c * s.phibar;
     s.phibar = sn * s.phibar;
     s.res2 += psi * psi;
-    s.cf = phi / rho;
-    s.cw = theta / rho;
+    s.cf = phi * irho;
+    s.cw = theta * irho;
     if (s.frozen) {
         // S4 held after the previous iteration: its update was the last one; this iteration's
         // is void and the remaining iterations of the inner solve are skipped
@@ -288,16 +312,18 @@ __device__ __forceinline__ void finalize_alpha(GkState& s, double tot, const His
         s.frozen = 2;
     } else {
         s.iter += 1;
-        const double rb = sqrt(s.phibar * s.phibar + s.res2);
+        const double rq = s.phibar * s.phibar + s.res2;
+        const double rb = rq > 0.0 ? rq * rsqrt_nr(rq) : 0.0;
         if (hist.rbar && s.outer < hist.n_outer && s.iter <= hist.n_inner)
             hist.rbar[((int64_t)inst * hist.n_outer + s.outer) * hist.n_inner + (s.iter - 1)] = rb;
         if (s.eta_delta > 0.0 && rb <= s.eta_delta) s.frozen = 1;  // S4 (Sec. 3.4)
     }
     s.alpha = an;
     s.beta = beta;
-    s.c_upd_v = 1.0 / an;
-    s.c_fwd_a = 1.0 / an;
-    s.c_fwd_p = an / beta;
+    s.c_upd_v = ian;
+    s.c_fwd_a = ian;
+    s.c_fwd_p = an * s.c_adj_a;  // alpha_{i+1} / beta_{i+1}; c_adj_a = 1 / beta_{i+1} (finalize_beta)
+    sg = s;
 }
 
 }  // namespace plsqr

@@ -375,19 +375,6 @@ void coarse_assemble(const T* cond, bool is_kappa, double* band, Dims d, int bw,
     kfinish(s);
 }
 
-// 1/sqrt(a) for a > 0 in double: single-precision seed, then two Newton-Raphson steps for
-// the reciprocal square root, r <- r (3/2 - a r^2 / 2) (each step squares the relative error:
-// ~2e-7 -> ~1e-13 -> rounding level).  Six dependent multiply-adds instead of a division and
-// a square root on the critical path of the factorisation.  Non-positive or non-finite a
-// gives NaN, which propagates into the inverse and surfaces as a breakdown.
-__device__ __forceinline__ double rsqrt_nr(double a) {
-    if (!(a > 0.0) || !isfinite(a)) return nan("");
-    double r = (double)rsqrtf((float)a);
-    r = r * fma(-0.5 * a * r, r, 1.5);
-    r = r * fma(-0.5 * a * r, r, 1.5);
-    return r;
-}
-
 // In-place banded Cholesky M = L L^T, one block per instance.  The rows that column j touches
 // live in a sliding window of bw+4 rows in shared memory.  Column j:
 //  phase 1: the factors f_i = L(i,j)/a_j of the column (one per row), scaling of column j-1 by

@@ -219,8 +219,26 @@ __device__ __forceinline__ void half_sweep(const T* sb, const T* sd, const T* sc
     const int hi = LX - 1 - lo, hiy = LY - 1 - lo;
     const int half = (hi - lo + 2) >> 1;
     const int rows = hiy - lo + 1;
-    for (int k = threadIdx.x; k < rows * half; k += NTH) {
-        const int ry = k / half, j = k - ry * half;
+    // A thread keeps one column slot j of the colour and walks down the rows, rpp rows per step
+    // (every row gets all of its cells: the first rpp * half threads cover rpp whole rows), so the
+    // index advances by a constant instead of being divided out of a flat counter per cell.
+    const int rpp = NTH / half;
+    const int t = threadIdx.x;
+    if (rpp == 0 || t >= rpp * half) {
+        if (rpp == 0)  // rows longer than the block: the flat loop
+            for (int k = t; k < rows * half; k += NTH) {
+                const int ry = k / half, j = k - ry * half;
+                const int ly = lo + ry;
+                const int lx = lo + ((colour ^ ly ^ lo) & 1) + 2 * j;
+                if (lx > hi) continue;
+                const int i = ly * LXS + lx + OX;
+                sx[i] = gs_update(sb[i], sd[i], scx[i], scx[i - 1], scy[i], scy[i - LXS], sx[i + 1], sx[i - 1],
+                                  sx[i + LXS], sx[i - LXS]);
+            }
+        return;
+    }
+    const int j = t % half;
+    for (int ry = t / half; ry < rows; ry += rpp) {
         const int ly = lo + ry;
         const int lx = lo + ((colour ^ ly ^ lo) & 1) + 2 * j;  // first lx >= lo of the colour, then every other
         if (lx > hi) continue;

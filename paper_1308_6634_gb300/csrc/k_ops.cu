@@ -57,16 +57,18 @@ __device__ __forceinline__ T epi_store(T acc, T ca, T cp, T* out, const T* prev,
 }
 
 // Finalise beta_{i+1} = ||u|| (Algorithm 2 step 10) in the last block.
+// (1 / beta by the inverse square root of common.cuh; 1 / alpha is c_fwd_a.)
 __device__ __forceinline__ void finalize_beta(GkState& s, double tot) {
-    double bn = sqrt(tot);
+    const double ib = tot > 0.0 ? rsqrt_nr(tot) : 0.0;
+    const double bn = tot * ib;
     if (!good_pos(bn, s.beta1)) {
         s.status = ST_BREAKDOWN;
         s.status_any = ST_BREAKDOWN;
         return;
     }
     s.beta_new = bn;
-    s.c_adj_a = 1.0 / bn;
-    s.c_adj_p = bn / s.alpha;
+    s.c_adj_a = ib;
+    s.c_adj_p = bn * s.c_fwd_a;
 }
 
 constexpr int BTX = 64, BTY = 32, BNT = 256;
