@@ -315,6 +315,20 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(V* __rest
     }
 }
 
+// The inverse by one warp per column for double tables and batches up to 16; PLSQR_GTH_INV=thread
+// or =warp forces one (comparisons).  Measured at batch 1 on the GB300: with double tables (16-wide
+// band, 256 cells) the thread-per-column kernel runs its band of multiply-adds on the narrow
+// double pipe and the warp kernel takes the setup of the 64^2 workload from 7.2 to 4.6 ms per
+// solve; with float tables (32-wide band, 1024 cells) the warp kernel issues about ten
+// instructions per row and column against under two for the thread kernel, and loses (272
+// against 227 us).
+bool gth_inverse_by_warp(int B, size_t esz) {
+    const char* e = std::getenv("PLSQR_GTH_INV");
+    if (e && e[0] == 't') return false;
+    if (e && e[0] == 'w') return true;
+    return esz == 8 && B <= 16;
+}
+
 // PLSQR_GTH_WARPS=1: the one-warp factorisation (comparisons)
 bool gth_split_enabled() {
     const char* e = std::getenv("PLSQR_GTH_WARPS");
@@ -428,6 +442,109 @@ __global__ void __launch_bounds__(128) k_gth_inverse(const V* __restrict__ gcol_
             }
         }
         __syncwarp();
+    }
+}
+
+// The same inverse with one warp per column j, for small batches.  k_gth_inverse gives each
+// column to one thread, whose chain of 2 nc rows (each a band of BW multiply-adds on one thread)
+// sets the time of the whole launch at batch 1.  Here the BW pending sums of the column live one
+// per lane: lane L keeps the pending sum of the row of residue L (mod 32), so that a row costs
+// one shuffle of its finished entry from the lane that owns it and one multiply-add per lane, and
+// a lane whose row is finished starts on the row 32 further on.  Forward: z_k = (pending of row k)
+// (+1 at k = j), y_k = z_k / d_k stored at X[k][j], then z_{k+t} += l_{k+t,k} z_k.  Backward:
+// x_i = y_i + (pending of row i), then x_{i-t} += l_{i,i-t} x_i.  Every entry of X sees the
+// operations of k_gth_inverse in the same order (the +1 of row j is carried in the pending sum of
+// its lane from the start, which adds only exact zeros to it), so the result is bit for bit the
+// same.  The factor table (rows from the block's first column to the last) is staged in shared
+// memory for each pass; the 32 band entries a lane needs in a run of 32 rows are read into
+// registers before the run, off the shuffle-and-FMA chain.
+template <typename V, int BW, int NWI>
+__global__ void __launch_bounds__(32 * NWI) k_gth_inverse_warp(const V* __restrict__ gcol_all,
+                                                               const V* __restrict__ grow_all,
+                                                               V* __restrict__ X_all, int nc, GkState* st) {
+    constexpr int BWP = (BW + 1 + 3) & ~3;
+    extern __shared__ __align__(128) unsigned char tabraw[];
+    V* tab = reinterpret_cast<V*>(tabraw);
+    __shared__ __align__(8) uint64_t bar[2];
+    const int inst = blockIdx.y;
+    if (parked(st[inst])) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (blockIdx.x * NWI) & ~31;  // first staged row
+    const int j = blockIdx.x * NWI + warp;
+    const bool live = j < nc;
+    const V* gc = gcol_all + (int64_t)inst * nc * BWP;
+    const V* gr = grow_all + (int64_t)inst * nc * BWP;
+    V* X = X_all + (int64_t)inst * nc * nc;
+    const uint32_t bytes = (uint32_t)((nc - r0) * BWP * sizeof(V));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_expect_tx(&bar[0], bytes);
+        bulk_load(tab, gc + (int64_t)r0 * BWP, bytes, &bar[0]);
+    }
+    __syncthreads();
+    tma_wait_tile(&bar[0], st, inst);
+    // ---- forward over rows j, j+1, ... (runs of 32 rows aligned to multiples of 32) ----
+    if (live) {
+        V pend = lane == (j & 31) ? (V)1 : (V)0;
+        for (int base = j & ~31; base < nc; base += 32) {
+            V lt[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {  // lane's row at step k = base + u is k + t
+                const int k = base + u, d = (lane - u) & 31, t = d ? d : 32;
+                lt[u] = (k < nc && t <= BW) ? tab[(int64_t)(k - r0) * BWP + t] : (V)0;
+            }
+            const V rdv = base + lane < nc ? tab[(int64_t)(base + lane - r0) * BWP] : (V)0;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int k = base + u;
+                const V z = __shfl_sync(0xffffffffu, pend, u);
+                if (lane == u) {
+                    if (k >= j && k < nc) X[(int64_t)k * nc + j] = z * rdv;
+                    pend = (V)0;
+                }
+                pend = fma(lt[u], z, pend);
+            }
+        }
+    }
+    __syncthreads();  // every warp is done with the forward table
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar[1], bytes);
+        bulk_load(tab, gr + (int64_t)r0 * BWP, bytes, &bar[1]);
+    }
+    tma_wait_tile(&bar[1], st, inst);
+    if (!live) return;
+    // ---- backward over rows nc-1, nc-2, ..., j ----
+    const int top = nc - 1;
+    V pend = (V)0;
+    int cb = top & ~31;
+    V yv = (cb + lane <= top && cb + lane >= j) ? X[(int64_t)(cb + lane) * nc + j] : (V)0;  // y of row cb + lane
+    for (; cb >= (j & ~31); cb -= 32) {
+        const int nb = cb - 32;  // y of the next run down, loaded one run ahead (this thread wrote them)
+        const V ynx = (nb >= 0 && nb + lane >= j) ? X[(int64_t)(nb + lane) * nc + j] : (V)0;
+        V lt[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {  // step i = cb + 31 - u; lane's row is i - t
+            const int i = cb + 31 - u, d = (i - lane) & 31, t = d ? d : 32;
+            lt[u] = (i <= top && t <= BW) ? tab[(int64_t)(i - r0) * BWP + t] : (V)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            const int i = cb + 31 - u, own = 31 - u;
+            if (i <= top) {
+                const V x = __shfl_sync(0xffffffffu, yv + pend, own);
+                if (lane == own) {
+                    if (i >= j) {
+                        X[(int64_t)i * nc + j] = x;
+                        if (i != j) X[(int64_t)j * nc + i] = x;
+                    }
+                    pend = (V)0;
+                }
+                pend = fma(lt[u], x, pend);
+            }
+        }
+        yv = ynx;
     }
 }
 
@@ -708,6 +825,15 @@ static void gth_launch(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* s
         if (sp > 48 * 1024) cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
         kq<<<B, 32 * (1 + GTH_BULK), sp, s>>>(gcol, grow, nc, bw, st);
         klaunched("k_ldl_gth_split");
+    }
+    if (gth_inverse_by_warp(B, sizeof(V))) {
+        constexpr int NWI = sizeof(V) == 8 ? 8 : 16;  // double: the registers of 32 band entries
+        auto kw = k_gth_inverse_warp<V, BW, NWI>;
+        if (stage > 48 * 1024) cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage);
+        dim3 wgrid((unsigned)((nc + NWI - 1) / NWI), B);
+        kw<<<wgrid, 32 * NWI, stage, s>>>(gcol, grow, X, nc, st);
+        klaunched("k_gth_inverse_warp");
+        return;
     }
     auto ki = k_gth_inverse<V, BW>;
     const size_t ism = stage + sizeof(V) * 4 * BW * 33;

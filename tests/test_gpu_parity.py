@@ -220,6 +220,27 @@ def test_four_warp_float_factor_matches_one_warp(shape, levels, monkeypatch):
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape,levels", [((256, 256), 4), ((136, 200), 4), ((64, 64), 3), ((16, 24), 1),
+                                          ((37, 8), 1), ((21, 13), 1), ((5, 7), 1)])
+def test_coarse_inverse_by_warp_matches_by_thread(prec, shape, levels, monkeypatch):
+    """The coarse inverse by one warp per column against one thread per column (PLSQR_GTH_INV): each
+    performs the same operations on every entry in the same order, so the V-cycles agree bit for
+    bit.  The shapes cover coarse grids 32, 25, 16, 8, 13 and 7 cells wide, with 35 to 1024 cells
+    (not multiples of 32 too)."""
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(16).standard_normal(shape)
+    outs = []
+    for inv in ("warp", "thread"):
+        monkeypatch.setenv("PLSQR_GTH_INV", inv)
+        S = _P().Solver(shape, prec, levels=levels)
+        S.prec_setup(dev(kappa, prec))
+        outs.append(host(S.prec_apply(dev(b, prec))))
+    assert np.all(np.isfinite(outs[0]))
+    assert np.array_equal(outs[1], outs[0])
+    assert rel(outs[0], O.Multigrid(kappa, levels, 2, 1).apply(b)) < (1e-11 if prec == "fp64" else 1e-4)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nu", [1, 2, 3])
 def test_fused_vcycle_matches_one_launch_per_half_sweep(prec, nu, monkeypatch):
