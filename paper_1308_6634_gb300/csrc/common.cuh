@@ -98,10 +98,32 @@ struct Red {
     int32_t max_blocks;
 };
 
-// Grid extents of one level (nz = 1 for 2D).
+// Division of 0 <= n < 2^31 by a divisor d >= 1 fixed at launch, by one multiply-high, an add and
+// a shift (the method of Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1 (< 2^32),
+// floor(n / d) = (mulhi(m, n) + n) >> l, and mulhi(m, n) < n keeps the sum below 2^32.  The index
+// arithmetic of the 3D kernels otherwise divides 64-bit integers, which the GPU does in software.
+struct FDiv {
+    uint32_t d, m;
+    int32_t l;
+};
+
+inline FDiv make_fdiv(int64_t d) {
+    FDiv f{};
+    f.d = (uint32_t)(d < 1 ? 1 : d);
+    while ((1ull << f.l) < f.d) ++f.l;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << f.l) - f.d)) / f.d) + 1);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
+
+// Grid extents of one level (nz = 1 for 2D), with the divisors of the index arithmetic (nx, ny and
+// nx / 2), set by make_dims.
 struct Dims {
     int32_t nx, ny, nz, ndim;
     int64_t N;  // nx*ny*nz
+    FDiv fx, fy, fh;
 };
 
 // Per-level buffers of the coarse end of a 2D V-cycle (conductances, right-hand side, pre-smoothed

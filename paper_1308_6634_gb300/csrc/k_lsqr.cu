@@ -238,6 +238,7 @@ void gk_init_norm(const T* g, int64_t m, int B, GkState* st, Red red, cudaStream
 template <typename T, bool INIT>
 __global__ void __launch_bounds__(256) k_dot_rotate(const T* __restrict__ v, const T* __restrict__ p, int64_t N,
                                                     GkState* st, Hist hist, Red red) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     if (inner_off(st[inst])) return;
     const T* vi = v + (int64_t)inst * N;
@@ -255,8 +256,8 @@ void gk_dot_rotate(const T* v, const T* p, int64_t N, int B, bool init, GkState*
                    cudaStream_t s) {
     kbegin(KC_GK, s);
     int nblk = std::min(red_blocks(N), red.max_blocks);
-    if (init) k_dot_rotate<T, true><<<dim3(nblk, B), 256, 0, s>>>(v, p, N, st, hist, red);
-    else k_dot_rotate<T, false><<<dim3(nblk, B), 256, 0, s>>>(v, p, N, st, hist, red);
+    if (init) launch_k(k_dot_rotate<T, true>, dim3(nblk, B), dim3(256), 0, s, v, p, N, st, hist, red);
+    else launch_k(k_dot_rotate<T, false>, dim3(nblk, B), dim3(256), 0, s, v, p, N, st, hist, red);
     klaunched("k_dot_rotate");
     kfinish(s);
 }
@@ -266,6 +267,7 @@ void gk_dot_rotate(const T* v, const T* p, int64_t N, int B, bool init, GkState*
 template <typename T, bool INIT>
 __global__ void __launch_bounds__(256) k_update(T* __restrict__ f, T* __restrict__ w, const T* __restrict__ v,
                                                 int64_t N, const GkState* st) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const GkState& s = st[inst];
     if (parked(s) || (!INIT && inner_off(s))) return;
@@ -287,8 +289,8 @@ template <typename T>
 void gk_update(T* f, T* w, const T* v, int64_t N, int B, bool init, const GkState* st, cudaStream_t s) {
     kbegin(KC_GK, s);
     int nblk = (int)std::min<int64_t>((N + 1023) / 1024, 2048);
-    if (init) k_update<T, true><<<dim3(nblk, B), 256, 0, s>>>(f, w, v, N, st);
-    else k_update<T, false><<<dim3(nblk, B), 256, 0, s>>>(f, w, v, N, st);
+    if (init) launch_k(k_update<T, true>, dim3(nblk, B), dim3(256), 0, s, f, w, v, N, st);
+    else launch_k(k_update<T, false>, dim3(nblk, B), dim3(256), 0, s, f, w, v, N, st);
     klaunched("k_update");
     kfinish(s);
 }

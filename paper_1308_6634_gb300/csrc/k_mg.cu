@@ -13,6 +13,7 @@
 // and the exact coarse solve keep P a fixed SPD operator.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <stdexcept>
 #include <string>
 
@@ -59,9 +60,10 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ f, T*
     double part = 0.0;
     const int64_t plane = (int64_t)d.nx * d.ny;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * 256) {
-        const int x = (int)(i % d.nx);
-        const int y = (int)((i / d.nx) % d.ny);
-        const int z = (int)(i / plane);
+        const uint32_t ri = fdiv((uint32_t)i, d.fx), zu = fdiv(ri, d.fy);
+        const int x = (int)((uint32_t)i - ri * (uint32_t)d.nx);
+        const int y = (int)(ri - zu * (uint32_t)d.ny);
+        const int z = (int)zu;
         const T c = fi[i];
         T gx = (x + 1 < d.nx ? fi[i + 1] : (T)0) - c;
         T t2 = gx * gx;
@@ -141,15 +143,16 @@ __device__ __forceinline__ void stencil(const T* __restrict__ c, const T* x, con
 template <typename T, bool KAPPA, bool ZERO>
 __global__ void __launch_bounds__(256) k_gs_half(const T* __restrict__ cond, const T* __restrict__ b, T* x, Dims d,
                                                  int colour) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const int hx = d.nx >> 1;
     const int64_t Nh = d.N >> 1;
     const int64_t h = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (h >= Nh) return;
-    const int64_t rest = h / hx;
-    const int y = (int)(rest % d.ny), z = (int)(rest / d.ny);
-    const int par = (y + z + colour) & 1;
-    const int xx = 2 * (int)(h - rest * hx) + par;
+    const uint32_t rest = fdiv((uint32_t)h, d.fh), z = fdiv(rest, d.fy);
+    const int y = (int)(rest - z * (uint32_t)d.ny);
+    const int par = (y + (int)z + colour) & 1;
+    const int xx = 2 * (int)((uint32_t)h - rest * (uint32_t)hx) + par;
     const int64_t i = xx + (int64_t)d.nx * (y + (int64_t)d.ny * z);
     const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
     const T* bi = b + (int64_t)inst * d.N;
@@ -166,11 +169,11 @@ void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colo
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
     dim3 grid((unsigned)((d.N / 2 + 255) / 256), B);
     if (is_kappa) {
-        if (zero_init) k_gs_half<T, true, true><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
-        else k_gs_half<T, true, false><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+        if (zero_init) launch_k(k_gs_half<T, true, true>, grid, dim3(256), 0, s, cond, b, x, d, colour);
+        else launch_k(k_gs_half<T, true, false>, grid, dim3(256), 0, s, cond, b, x, d, colour);
     } else {
-        if (zero_init) k_gs_half<T, false, true><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
-        else k_gs_half<T, false, false><<<grid, 256, 0, s>>>(cond, b, x, d, colour);
+        if (zero_init) launch_k(k_gs_half<T, false, true>, grid, dim3(256), 0, s, cond, b, x, d, colour);
+        else launch_k(k_gs_half<T, false, false>, grid, dim3(256), 0, s, cond, b, x, d, colour);
     }
     klaunched("k_gs_half");
     kfinish(s);
@@ -181,10 +184,12 @@ template <typename T, bool KAPPA>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ cond, const T* __restrict__ b,
                                                         const T* __restrict__ x, T* __restrict__ bc, Dims df,
                                                         Dims dc) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (I >= dc.N) return;
-    const int X = (int)(I % dc.nx), Y = (int)((I / dc.nx) % dc.ny), Z = (int)(I / ((int64_t)dc.nx * dc.ny));
+    const uint32_t rI = fdiv((uint32_t)I, dc.fx), Zu = fdiv(rI, dc.fy);
+    const int X = (int)((uint32_t)I - rI * (uint32_t)dc.nx), Y = (int)(rI - Zu * (uint32_t)dc.ny), Z = (int)Zu;
     const T* c = cond + (KAPPA ? (int64_t)inst * df.N : (int64_t)inst * df.ndim * df.N);
     const T* bi = b + (int64_t)inst * df.N;
     const T* xi = x + (int64_t)inst * df.N;
@@ -207,8 +212,8 @@ void mg_resid_restrict(const T* cond, bool is_kappa, const T* b, const T* x, T* 
                        cudaStream_t s) {
     kbegin(KC_MG_OTHER, s);
     dim3 grid((unsigned)((dc.N + 255) / 256), B);
-    if (is_kappa) k_resid_restrict<T, true><<<grid, 256, 0, s>>>(cond, b, x, bc, df, dc);
-    else k_resid_restrict<T, false><<<grid, 256, 0, s>>>(cond, b, x, bc, df, dc);
+    if (is_kappa) launch_k(k_resid_restrict<T, true>, grid, dim3(256), 0, s, cond, b, x, bc, df, dc);
+    else launch_k(k_resid_restrict<T, false>, grid, dim3(256), 0, s, cond, b, x, bc, df, dc);
     klaunched("k_resid_restrict");
     kfinish(s);
 }
@@ -216,10 +221,12 @@ void mg_resid_restrict(const T* cond, bool is_kappa, const T* b, const T* x, T* 
 // x_i += xc_parent(i)
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ xc, T* __restrict__ x, Dims df, Dims dc) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= df.N) return;
-    const int fx = (int)(i % df.nx), fy = (int)((i / df.nx) % df.ny), fz = (int)(i / ((int64_t)df.nx * df.ny));
+    const uint32_t ri = fdiv((uint32_t)i, df.fx), fzu = fdiv(ri, df.fy);
+    const int fx = (int)((uint32_t)i - ri * (uint32_t)df.nx), fy = (int)(ri - fzu * (uint32_t)df.ny), fz = (int)fzu;
     const int64_t I = (fx >> 1) + (int64_t)dc.nx * ((fy >> 1) + (int64_t)dc.ny * (fz >> 1));
     x[(int64_t)inst * df.N + i] += xc[(int64_t)inst * dc.N + I];
 }
@@ -227,8 +234,242 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ xc, T
 template <typename T>
 void mg_prolong_add(const T* xc, T* x, Dims df, Dims dc, int B, cudaStream_t s) {
     kbegin(KC_MG_OTHER, s);
-    k_prolong_add<T><<<dim3((unsigned)((df.N + 255) / 256), B), 256, 0, s>>>(xc, x, df, dc);
+    launch_k(k_prolong_add<T>, dim3((unsigned)((df.N + 255) / 256), B), dim3(256), 0, s, xc, x, df, dc);
     klaunched("k_prolong_add");
+    kfinish(s);
+}
+
+// ---- red-black split storage of a 3D level ---------------------------------------------------
+//
+// With x stored in natural order, a red-black half sweep reads the other colour's neighbours and
+// its own right-hand side from sectors of which it uses half, and writes half of each sector of x.
+// The split layout keeps the cells of colour c = (x + y + z) & 1 of row (y, z) contiguous:
+// xs[c][z][y][h] holds cell x = 2h + p, p = (y + z + c) & 1 (nx even), [inst][2][N/2].  In it the
+// other colour's neighbours of a cell (h, y, z) of colour c sit at h - 1 + p and h + p of its own
+// row, and at h of the rows y +- 1 and z +- 1; the conductances stay in natural order (a half
+// sweep reads all of them anyway).  The arithmetic of every cell is that of the natural-order
+// kernels above, in the same order, so the V-cycle is bit for bit the same.
+
+// stencil() for a cell of the split layout: xo = the other colour's array, hs = the cell's index in
+// its own colour's array, p its parity in the row.
+template <typename T, bool KAPPA, bool WITH_X>
+__device__ __forceinline__ void stencil_split(const T* __restrict__ c, const T* xo, const Dims& d, int64_t i,
+                                              int64_t hs, int nh, int p, int cx, int cy, int cz, T& diag, T& off) {
+    diag = (T)0;
+    off = (T)0;
+    const int co[3] = {cx, cy, cz};
+    const int n[3] = {d.nx, d.ny, d.nz};
+    const int64_t strd[3] = {1, (int64_t)d.nx, (int64_t)d.nx * d.ny};
+    const int64_t hi[3] = {hs + p, hs + nh, hs + (int64_t)nh * d.ny};
+    const int64_t lo[3] = {hs - 1 + p, hs - nh, hs - (int64_t)nh * d.ny};
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        const T chi = cond_at<T, KAPPA>(c, dd, d.N, i);
+        if (co[dd] > 0) {
+            const T clo = cond_at<T, KAPPA>(c, dd, d.N, i - strd[dd]);
+            diag += chi + clo;
+            if (WITH_X) {
+                if (co[dd] + 1 < n[dd]) off += chi * xo[hi[dd]];
+                off += clo * xo[lo[dd]];
+            }
+        } else {
+            diag += chi;
+            if (WITH_X && co[dd] + 1 < n[dd]) off += chi * xo[hi[dd]];
+        }
+    }
+}
+
+// One half sweep in the split layout.  MODE 0: first half sweep of the finest level (x = 0 before
+// it): b is in natural order and is also written out split (bs) for the later sweeps; the other
+// colour of x is written 0.  MODE 1: first half sweep of a coarser level (b split, x = 0 before).
+// MODE 2: any other half sweep.  MODE 3: the last half sweep of the finest level, which also
+// writes both colours of x in natural order to `out`.  Each thread takes the cells (h, y) of ZC
+// consecutive planes, so that the loads of several planes are in flight together (xc and xo, this
+// colour's and the other colour's halves of the split array, do not overlap).
+template <typename T, bool KAPPA, int MODE, int ZC>
+__global__ void __launch_bounds__(256) k_gs_half_split(const T* __restrict__ cond, const T* __restrict__ b,
+                                                       T* __restrict__ bs, T* __restrict__ xc_all,
+                                                       T* __restrict__ xo_all, T* __restrict__ out, Dims d,
+                                                       int colour) {
+    pdl_grid_sync();
+    const int inst = blockIdx.y;
+    const int nh = d.nx >> 1;
+    const int64_t Nh = d.N >> 1;
+    const int nzc = (d.nz + ZC - 1) / ZC;
+    const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (t >= (int64_t)nh * d.ny * nzc) return;
+    const uint32_t rest = fdiv((uint32_t)t, d.fh);
+    const int zc = (int)fdiv(rest, d.fy), y = (int)(rest - (uint32_t)zc * (uint32_t)d.ny);
+    const int h = (int)((uint32_t)t - rest * (uint32_t)nh);
+    const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
+    T* xc = xc_all + (int64_t)inst * d.N;  // colour-c half of instance inst (stride d.N between instances)
+    T* xo = xo_all + (int64_t)inst * d.N;
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int z = zc * ZC + k;
+        if (z < d.nz) {
+            const int p = (y + z + colour) & 1;
+            const int xx = 2 * h + p;
+            const int64_t hs = h + (int64_t)nh * (y + (int64_t)d.ny * z);
+            const int64_t i = xx + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+            T diag, off;
+            stencil_split<T, KAPPA, (MODE >= 2)>(c, xo, d, i, hs, nh, p, xx, y, z, diag, off);
+            T bv;
+            if (MODE == 0) {
+                const T* bn = b + (int64_t)inst * d.N;
+                bv = bn[i];
+                const T bo = bn[i + (p ? -1 : 1)];  // the other colour's cell at the same h
+                bs[(int64_t)inst * d.N + (int64_t)colour * Nh + hs] = bv;
+                bs[(int64_t)inst * d.N + (int64_t)(1 - colour) * Nh + hs] = bo;
+            } else {
+                bv = b[(int64_t)inst * d.N + (int64_t)colour * Nh + hs];
+            }
+            const T xn = (bv + off) * ((T)1 / diag);
+            xc[hs] = xn;
+            if (MODE <= 1) xo[hs] = (T)0;
+            if (MODE == 3) {
+                T* o = out + (int64_t)inst * d.N;
+                o[i] = xn;
+                o[i + (p ? -1 : 1)] = xo[hs];
+            }
+        }
+    }
+}
+
+// planes per thread of the split half sweep (PLSQR_MG3_ZC = 1, 2, 4 or 8; 2 measured best)
+int split_planes() {
+    static int zc = [] {
+        const char* e = std::getenv("PLSQR_MG3_ZC");
+        const int v = e ? std::atoi(e) : 2;
+        return v == 1 || v == 4 || v == 8 ? v : 2;
+    }();
+    return zc;
+}
+
+template <typename T>
+void mg_gs_half_split(const T* cond, bool is_kappa, const T* b, T* bs, T* xs, T* out, Dims d, int colour, int mode,
+                      int B, cudaStream_t s) {
+    kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
+    const int zcn = split_planes();
+    const int64_t Nh = d.N / 2;
+    T* xc = xs + (int64_t)colour * Nh;
+    T* xo = xs + (int64_t)(1 - colour) * Nh;
+    const int64_t threads = (int64_t)(d.nx / 2) * d.ny * ((d.nz + zcn - 1) / zcn);
+    dim3 grid((unsigned)((threads + 255) / 256), B);
+#define GS_SPLIT(K, M, Z) launch_k(k_gs_half_split<T, K, M, Z>, grid, dim3(256), 0, s, cond, b, bs, xc, xo, out, d, colour)
+#define GS_SPLIT_Z(K, M)                 \
+    switch (zcn) {                       \
+        case 1: GS_SPLIT(K, M, 1); break; \
+        default: GS_SPLIT(K, M, 2); break; \
+        case 8: GS_SPLIT(K, M, 8); break; \
+        case 4: GS_SPLIT(K, M, 4); break; \
+    }
+    if (is_kappa) {
+        switch (mode) {
+            case 0: GS_SPLIT_Z(true, 0); break;
+            case 1: GS_SPLIT_Z(true, 1); break;
+            case 2: GS_SPLIT_Z(true, 2); break;
+            default: GS_SPLIT_Z(true, 3); break;
+        }
+    } else {
+        switch (mode) {
+            case 0: GS_SPLIT_Z(false, 0); break;
+            case 1: GS_SPLIT_Z(false, 1); break;
+            case 2: GS_SPLIT_Z(false, 2); break;
+            default: GS_SPLIT_Z(false, 3); break;
+        }
+    }
+#undef GS_SPLIT_Z
+#undef GS_SPLIT
+    klaunched("k_gs_half_split");
+    kfinish(s);
+}
+
+// k_resid_restrict with b and x split; the coarse right-hand side is written split (OUT_SPLIT,
+// for a coarse level that is smoothed) or in natural order (the coarsest level).
+template <typename T, bool KAPPA, bool OUT_SPLIT>
+__global__ void __launch_bounds__(256) k_resid_restrict_split(const T* __restrict__ cond, const T* __restrict__ bs,
+                                                              const T* __restrict__ xs, T* __restrict__ bc, Dims df,
+                                                              Dims dc) {
+    pdl_grid_sync();
+    const int inst = blockIdx.y;
+    const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (I >= dc.N) return;
+    const uint32_t rI = fdiv((uint32_t)I, dc.fx), Zu = fdiv(rI, dc.fy);
+    const int X = (int)((uint32_t)I - rI * (uint32_t)dc.nx), Y = (int)(rI - Zu * (uint32_t)dc.ny), Z = (int)Zu;
+    const T* c = cond + (KAPPA ? (int64_t)inst * df.N : (int64_t)inst * df.ndim * df.N);
+    const int nh = df.nx >> 1;
+    const int64_t Nh = df.N >> 1;
+    const T* bi = bs + (int64_t)inst * df.N;
+    const T* xi = xs + (int64_t)inst * df.N;
+    T sum = (T)0;
+    for (int oz = 0; oz < 2; ++oz)
+        for (int oy = 0; oy < 2; ++oy)
+            for (int ox = 0; ox < 2; ++ox) {
+                const int fx = 2 * X + ox, fy = 2 * Y + oy, fz = 2 * Z + oz;
+                const int64_t i = fx + (int64_t)df.nx * (fy + (int64_t)df.ny * fz);
+                const int cc = (fx + fy + fz) & 1;
+                const int64_t hs = (fx >> 1) + (int64_t)nh * (fy + (int64_t)df.ny * fz);
+                T diag, off;
+                stencil_split<T, KAPPA, true>(c, xi + (int64_t)(1 - cc) * Nh, df, i, hs, nh, fx & 1, fx, fy, fz, diag,
+                                              off);
+                sum += bi[(int64_t)cc * Nh + hs] - (diag * xi[(int64_t)cc * Nh + hs] - off);
+            }
+    if (OUT_SPLIT) {
+        const int64_t Hs = (X >> 1) + (int64_t)(dc.nx >> 1) * (Y + (int64_t)dc.ny * Z);
+        bc[(int64_t)inst * dc.N + (int64_t)((X + Y + Z) & 1) * (dc.N >> 1) + Hs] = sum;
+    } else {
+        bc[(int64_t)inst * dc.N + I] = sum;
+    }
+}
+
+template <typename T>
+void mg_resid_restrict_split(const T* cond, bool is_kappa, const T* bs, const T* xs, T* bc, bool out_split, Dims df,
+                             Dims dc, int B, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    dim3 grid((unsigned)((dc.N + 255) / 256), B);
+#define RR_SPLIT(K, O) launch_k(k_resid_restrict_split<T, K, O>, grid, dim3(256), 0, s, cond, bs, xs, bc, df, dc)
+    if (is_kappa) {
+        if (out_split) RR_SPLIT(true, true);
+        else RR_SPLIT(true, false);
+    } else {
+        if (out_split) RR_SPLIT(false, true);
+        else RR_SPLIT(false, false);
+    }
+#undef RR_SPLIT
+    klaunched("k_resid_restrict_split");
+    kfinish(s);
+}
+
+// x_i += xc_parent(i) with x split; the coarse correction split (IN_SPLIT) or in natural order.
+template <typename T, bool IN_SPLIT>
+__global__ void __launch_bounds__(256) k_prolong_add_split(const T* __restrict__ xc, T* __restrict__ xs, Dims df,
+                                                           Dims dc) {
+    pdl_grid_sync();
+    const int inst = blockIdx.y;
+    const int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x;  // colour-major index of the split layout
+    if (q >= df.N) return;
+    const int nh = df.nx >> 1;
+    const int64_t Nh = df.N >> 1;
+    const int colour = q >= Nh ? 1 : 0;
+    const int64_t hs = q - colour * Nh;
+    const uint32_t rest = fdiv((uint32_t)hs, df.fh);
+    const int fz = (int)fdiv(rest, df.fy), fy = (int)(rest - (uint32_t)fz * (uint32_t)df.ny);
+    const int fx = 2 * (int)((uint32_t)hs - rest * (uint32_t)nh) + ((fy + fz + colour) & 1);
+    const int X = fx >> 1, Y = fy >> 1, Z = fz >> 1;
+    const int64_t I = IN_SPLIT ? (int64_t)((X + Y + Z) & 1) * (dc.N >> 1) + (X >> 1) +
+                                     (int64_t)(dc.nx >> 1) * (Y + (int64_t)dc.ny * Z)
+                               : X + (int64_t)dc.nx * (Y + (int64_t)dc.ny * Z);
+    xs[(int64_t)inst * df.N + q] += xc[(int64_t)inst * dc.N + I];
+}
+
+template <typename T>
+void mg_prolong_add_split(const T* xc, bool in_split, T* xs, Dims df, Dims dc, int B, cudaStream_t s) {
+    kbegin(KC_MG_OTHER, s);
+    dim3 grid((unsigned)((df.N + 255) / 256), B);
+    if (in_split) launch_k(k_prolong_add_split<T, true>, grid, dim3(256), 0, s, xc, xs, df, dc);
+    else launch_k(k_prolong_add_split<T, false>, grid, dim3(256), 0, s, xc, xs, df, dc);
+    klaunched("k_prolong_add_split");
     kfinish(s);
 }
 
@@ -236,10 +477,12 @@ void mg_prolong_add(const T* xc, T* x, Dims df, Dims dc, int B, cudaStream_t s) 
 template <typename T, bool KAPPA>
 __global__ void __launch_bounds__(256) k_apply_level(const T* __restrict__ cond, const T* __restrict__ x,
                                                      const T* __restrict__ b, T* __restrict__ y, Dims d) {
+    pdl_grid_sync();
     const int inst = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= d.N) return;
-    const int cx = (int)(i % d.nx), cy = (int)((i / d.nx) % d.ny), cz = (int)(i / ((int64_t)d.nx * d.ny));
+    const uint32_t ri = fdiv((uint32_t)i, d.fx), czu = fdiv(ri, d.fy);
+    const int cx = (int)((uint32_t)i - ri * (uint32_t)d.nx), cy = (int)(ri - czu * (uint32_t)d.ny), cz = (int)czu;
     const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
     const T* xi = x + (int64_t)inst * d.N;
     T diag, off;
@@ -252,8 +495,8 @@ template <typename T>
 void mg_apply_level(const T* cond, bool is_kappa, const T* x, const T* b, T* y, Dims d, int B, cudaStream_t s) {
     kbegin(KC_MG_OTHER, s);
     dim3 grid((unsigned)((d.N + 255) / 256), B);
-    if (is_kappa) k_apply_level<T, true><<<grid, 256, 0, s>>>(cond, x, b, y, d);
-    else k_apply_level<T, false><<<grid, 256, 0, s>>>(cond, x, b, y, d);
+    if (is_kappa) launch_k(k_apply_level<T, true>, grid, dim3(256), 0, s, cond, x, b, y, d);
+    else launch_k(k_apply_level<T, false>, grid, dim3(256), 0, s, cond, x, b, y, d);
     klaunched("k_apply_level");
     kfinish(s);
 }
@@ -280,7 +523,8 @@ __global__ void __launch_bounds__(256) k_coarsen(const T* __restrict__ cf, T* __
     const int inst = blockIdx.y;
     const int64_t I = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (I >= dc.N) return;
-    const int X = (int)(I % dc.nx), Y = (int)((I / dc.nx) % dc.ny), Z = (int)(I / ((int64_t)dc.nx * dc.ny));
+    const uint32_t rI = fdiv((uint32_t)I, dc.fx), Zu = fdiv(rI, dc.fy);
+    const int X = (int)((uint32_t)I - rI * (uint32_t)dc.nx), Y = (int)(rI - Zu * (uint32_t)dc.ny), Z = (int)Zu;
     const T* c = cf + (KAPPA ? (int64_t)inst * df.N : (int64_t)inst * df.ndim * df.N);
     T* o = cc + (int64_t)inst * dc.ndim * dc.N;
     for (int dd = 0; dd < df.ndim; ++dd) {
@@ -354,7 +598,8 @@ __global__ void __launch_bounds__(256) k_coarse_assemble(const T* __restrict__ c
     const int W = bw + 1;
     double* row = band + ((int64_t)inst * d.N + i) * W;
     for (int k = 0; k < W; ++k) row[k] = 0.0;
-    const int cx = (int)(i % d.nx), cy = (int)((i / d.nx) % d.ny), cz = (int)(i / ((int64_t)d.nx * d.ny));
+    const uint32_t ri = fdiv((uint32_t)i, d.fx), czu = fdiv(ri, d.fy);
+    const int cx = (int)((uint32_t)i - ri * (uint32_t)d.nx), cy = (int)(ri - czu * (uint32_t)d.ny), cz = (int)czu;
     const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
     T diag, off;
     stencil<T, KAPPA, false>(c, (const T*)nullptr, d, i, cx, cy, cz, diag, off);
@@ -699,7 +944,11 @@ void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
     template void mg_apply_level<T>(const T*, bool, const T*, const T*, T*, Dims, int, cudaStream_t);      \
     template void mg_axpy<T>(T*, const T*, int64_t, cudaStream_t);                                         \
     template void coarse_assemble<T>(const T*, bool, double*, Dims, int, int, cudaStream_t);               \
-    template void coarse_symv<T>(const T*, const T*, T*, int, int, const GkState*, cudaStream_t);
+    template void coarse_symv<T>(const T*, const T*, T*, int, int, const GkState*, cudaStream_t);           \
+    template void mg_gs_half_split<T>(const T*, bool, const T*, T*, T*, T*, Dims, int, int, int, cudaStream_t); \
+    template void mg_resid_restrict_split<T>(const T*, bool, const T*, const T*, T*, bool, Dims, Dims, int,     \
+                                             cudaStream_t);                                                    \
+    template void mg_prolong_add_split<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t);
 
 PLSQR_INST_MG(float)
 PLSQR_INST_MG(double)

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(BNT) k_blur2d(const T* __restrict__ in, T* out
                                                 const uint8_t* __restrict__ mask, Dims d,
                                                 const T* __restrict__ wx, int Rx, const T* __restrict__ wy,
                                                 int Ry, GkState* st, Red red) {
+    pdl_grid_sync();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int plane = blockIdx.z;  // z + nz * inst
     const int inst = plane / d.nz;
@@ -301,6 +302,7 @@ template <typename T, int EPI, bool MASK_OUT>
 __global__ void __launch_bounds__(256) k_blur_z(const T* __restrict__ in, T* out, const T* prev,
                                                 const uint8_t* __restrict__ mask, Dims d,
                                                 const T* __restrict__ wz, int Rz, GkState* st, Red red) {
+    pdl_grid_sync();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nzt = (d.nz + ZTZ - 1) / ZTZ;
     const int inst = blockIdx.z / nzt, zt = blockIdx.z - inst * nzt;
@@ -864,8 +866,8 @@ static void launch_blur2d(const OpDev& op, const T* in, T* out, const T* prev, i
     dim3 grid((d.nx + BTX - 1) / BTX, (d.ny + BTY - 1) / BTY, d.nz * B);
     if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * d.nz > red.max_blocks)
         throw std::runtime_error("blur2d: too many blocks for the reduction scratch");
-    kfn<<<grid, BNT, smem, s>>>(in, out, prev, op.mask, d, (const T*)op.taps[0], Rx, (const T*)op.taps[1], Ry, st,
-                                red);
+    launch_k(kfn, grid, dim3(BNT), smem, s, in, out, prev, (const uint8_t*)op.mask, d, (const T*)op.taps[0], Rx,
+             (const T*)op.taps[1], Ry, st, red);
     klaunched("k_blur2d");
 }
 
@@ -906,7 +908,8 @@ static void launch_blur_z(const OpDev& op, const T* in, T* out, const T* prev, i
     dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, nzt * B);
     if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * nzt > red.max_blocks)
         throw std::runtime_error("blur_z: too many blocks for the reduction scratch");
-    kfn<<<grid, 256, smem, s>>>(in, out, prev, op.mask, d, (const T*)op.taps[2], Rz, st, red);
+    launch_k(kfn, grid, dim3(256), smem, s, in, out, prev, (const uint8_t*)op.mask, d, (const T*)op.taps[2], Rz, st,
+             red);
     klaunched("k_blur_z");
 }
 

@@ -108,6 +108,18 @@ void mg_prolong_add(const T* xc, T* x, Dims df, Dims dc, int B, cudaStream_t s);
 // r = b - M x (b may be null: r = -M x is not needed; y = M x when b == null and negate=false)
 template <typename T>
 void mg_apply_level(const T* cond, bool is_kappa, const T* x, const T* b, T* y, Dims d, int B, cudaStream_t s);
+// The same half sweep, restriction and prolongation with x (and b) in the red-black split layout of
+// a 3D level (nx even): [inst][colour][nz][ny][nx/2].  mode: 0 first half sweep of the finest level
+// (b natural, copied split to bs), 1 first of a coarser level, 2 any other, 3 the last of the finest
+// level (x also written in natural order to out).
+template <typename T>
+void mg_gs_half_split(const T* cond, bool is_kappa, const T* b, T* bs, T* xs, T* out, Dims d, int colour, int mode,
+                      int B, cudaStream_t s);
+template <typename T>
+void mg_resid_restrict_split(const T* cond, bool is_kappa, const T* bs, const T* xs, T* bc, bool out_split, Dims df,
+                             Dims dc, int B, cudaStream_t s);
+template <typename T>
+void mg_prolong_add_split(const T* xc, bool in_split, T* xs, Dims df, Dims dc, int B, cudaStream_t s);
 template <typename T>
 void mg_axpy(T* y, const T* x, int64_t n, cudaStream_t s);  // y += x
 template <typename T>

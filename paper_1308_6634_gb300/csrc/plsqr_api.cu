@@ -149,6 +149,12 @@ struct plsqr_ctx {
     bool kbf16 = false;
     __nv_bfloat16* kappa16 = nullptr;
     bool generic_mg = false;  // PLSQR_GENERIC_MG=1: one launch per half sweep (comparisons)
+    // 3D V-cycle in the red-black split layout (opt-in, PLSQR_MG_SPLIT=1; every smoothed level has
+    // an even nx): the finest level's split x and b in xs0, bs0, the coarser levels' in their own b
+    // and x.  Measured slower than natural order on the 192^3 workload (the half sweeps are bound by
+    // the latency of their scattered loads, not by the DRAM sectors the split layout saves).
+    bool split3 = false;
+    char *xs0 = nullptr, *bs0 = nullptr;
     int tail_lc = 16;         // first level of the one-launch coarse end of the 2D V-cycle (>= L: none)
     // the whole 2D V-cycle in one cooperative launch: -1 undecided (the autotuner times both
     // schedules), 0 per-level launches, 1 cooperative; PLSQR_MG_COOP=0/1 fixes it
@@ -227,6 +233,9 @@ Dims make_dims(int ndim, int64_t nx, int64_t ny, int64_t nz) {
     d.ny = (int32_t)ny;
     d.nz = ndim == 3 ? (int32_t)nz : 1;
     d.N = (int64_t)d.nx * d.ny * d.nz;
+    d.fx = make_fdiv(d.nx);
+    d.fy = make_fdiv(d.ny);
+    d.fh = make_fdiv(d.nx / 2);
     return d;
 }
 
@@ -238,6 +247,7 @@ struct Plan {
     size_t bytes;
     bool gth;   // float factor and inverse (bandwidth <= 32)
     bool gthw;  // float factor and inverse of a wide band
+    bool split3;  // 3D V-cycle in the red-black split layout
 };
 
 Plan make_plan(const plsqr_config* c, int64_t m) {
@@ -281,6 +291,12 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += esz * B * (2 * m + 5 * N);  // g, u, f, p, v, w, kappa
     b += esz * B * (N + m);          // tmp (N), tmpm (m)
     if (c->mg_cycles > 1) b += esz * B * 2 * N;
+    {  // PLSQR_MG_SPLIT=1 (3D, every smoothed level with an even nx): split x and b of level 0
+        const char* es = std::getenv("PLSQR_MG_SPLIT");
+        pl.split3 = c->ndim == 3 && pl.L >= 2 && c->mg_sweeps >= 1 && es && es[0] == '1';
+        for (int l = 0, nx = c->n[0]; l + 1 < pl.L; ++l, nx /= 2) pl.split3 = pl.split3 && nx % 2 == 0;
+        if (pl.split3) b += esz * B * 2 * N;
+    }
     for (int l = 1; l < pl.L; ++l) b += esz * B * pl.level_N[l] * (c->ndim + 3);
     if (c->ndim == 2)
         for (int l = 0; l + 1 < pl.L; ++l) b += esz * B * pl.level_N[l];  // reciprocal diagonals
@@ -332,8 +348,38 @@ Hist hist_of(plsqr_ctx* h) {
 }
 
 
+// The 3D V-cycle in the split layout: level 0 takes b and gives x in natural order; the smoothed
+// levels below it keep b and x split; the coarsest is in natural order.  The same half sweeps in
+// the same order as vcycle below.
+template <typename T>
+void vcycle_split(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
+    const Level& Lv = h->lv[l];
+    const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
+    const bool isk = l == 0;
+    T* xs = l == 0 ? P<T>(h->xs0) : x;
+    T* bs = l == 0 ? P<T>(h->bs0) : const_cast<T*>(b);
+    const Level& C = h->lv[l + 1];
+    const bool c_split = l + 1 < h->L - 1;
+    for (int k = 0; k < h->nu; ++k) {
+        mg_gs_half_split<T>(cond, isk, k == 0 ? b : bs, bs, xs, nullptr, Lv.d, 0, k > 0 ? 2 : (l == 0 ? 0 : 1), B, s);
+        mg_gs_half_split<T>(cond, isk, bs, bs, xs, nullptr, Lv.d, 1, 2, B, s);
+    }
+    mg_resid_restrict_split<T>(cond, isk, bs, xs, P<T>(C.b), c_split, Lv.d, C.d, B, s);
+    if (c_split) vcycle_split<T>(h, l + 1, P<T>(C.b), P<T>(C.x), B, s);
+    else coarse_symv<T>(coarse_inverse_of<T>(h), P<T>(C.b), P<T>(C.x), h->nc, B, h->st, s);
+    mg_prolong_add_split<T>(P<T>(C.x), c_split, xs, Lv.d, C.d, B, s);
+    for (int k = 0; k < h->nu; ++k) {
+        mg_gs_half_split<T>(cond, isk, bs, bs, xs, nullptr, Lv.d, 1, 2, B, s);
+        mg_gs_half_split<T>(cond, isk, bs, bs, xs, x, Lv.d, 0, (l == 0 && k == h->nu - 1) ? 3 : 2, B, s);
+    }
+}
+
 template <typename T>
 void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
+    if (l == 0 && h->split3) {
+        vcycle_split<T>(h, 0, b, x, B, s);
+        return;
+    }
     const Level& Lv = h->lv[l];
     const T* cond = l == 0 ? P<T>(h->kappa) : P<T>(Lv.cond);
     const bool isk = l == 0;
@@ -1066,6 +1112,11 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         }
         if (h->d.ndim == 2)
             for (int l = 0; l + 1 < h->L; ++l) h->lv[l].rd = dalloc(h, e * B * h->lv[l].d.N);
+        h->split3 = pl.split3;
+        if (h->split3) {
+            h->xs0 = dalloc(h, e * B * N);
+            h->bs0 = dalloc(h, e * B * N);
+        }
         h->coop_sync = (unsigned*)dalloc(h, 4 * sizeof(unsigned));
         {
             const char* ec = std::getenv("PLSQR_MG_COOP");
