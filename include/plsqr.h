@@ -336,6 +336,27 @@ int plsqr_query(plsqr_handle h);
 int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32_t* active);
 int plsqr_slot_finish(plsqr_handle h, int32_t slot, void* f_out, plsqr_stats* stats);
 
+/* ---- checkpoint and resume of a slot ---------------------------------------------------------
+ * The paper has no checkpointing.  Algorithm 3 restarts MLSQR from zero in every outer step (Sec.
+ * 4.1), so between two outer steps a request is fully described by f^k, its data g, R(f^k), the
+ * outer counter, status, r, T, tau and stopping rule, the histories so far and its blur taps:
+ * saving these lets a request be moved to another handle or process, or resumed after a restart,
+ * and continue bit for bit as if it had never stopped.
+ * plsqr_slot_state_bytes: bytes of one checkpoint of this handle (its grid, data length, history
+ *   sizes and taps), or -1 when the handle is not in slot mode.
+ * plsqr_slot_save: waits for the handle's stream, then writes the running `slot`'s checkpoint to
+ *   the host buffer buf (cap >= plsqr_slot_state_bytes).  The slot keeps running.
+ * plsqr_slot_restore: starts `slot` (0 <= slot < max_batch, not busy) from a checkpoint made by
+ *   plsqr_slot_save of the same library build on a handle with the same precision, grid, operator
+ *   kind, data length and kappa storage (any max_batch, slot index or tile shapes); the request
+ *   continues with its remaining outer steps under plsqr_step and ends with plsqr_slot_finish.
+ *   n_inner must equal, and the request's n_outer not exceed, those of the slots already running.
+ *   A buffer that is not a checkpoint, is too short or does not fit the handle: PLSQR_E_INVALID.
+ *   Ordered after the work already on the caller's stream; returns once the copies are done. */
+int64_t plsqr_slot_state_bytes(plsqr_handle h);
+int plsqr_slot_save(plsqr_handle h, int32_t slot, void* buf, int64_t cap);
+int plsqr_slot_restore(plsqr_handle h, int32_t slot, const void* buf, int64_t len);
+
 /* ---- blur without device allocation ---------------------------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that cannot allocate
  * device memory: a serving process that hands all device memory to its own pool and admits work

@@ -1587,6 +1587,169 @@ int plsqr_slot_progress(plsqr_handle h, int32_t slot, int32_t* outer_done, int32
     return PLSQR_OK;
 }
 
+// ---- checkpoint of a slot at an outer-step boundary ----------------------------------------------
+// Between two outer steps of Algorithm 3 a request is f^k, its data g and its scalars (R(f^k) for
+// the outer stop, the outer counter, the status, r, T, tau and the stopping rule), with the
+// histories so far and, where set, its blur taps; every other vector is rebuilt by the next step.
+// The blob: a header, then f (N values), g (m values), the histories (n_outer x n_inner, n_outer + 1
+// and n_outer doubles of the handle that saved it) and the taps row.
+namespace {
+constexpr uint64_t kCkptMagic = 0x31544b43524c5350ull;  // "PLSRCKT1"
+struct CkptHeader {
+    uint64_t magic;
+    int32_t esz, ndim, n[3], kind;
+    int64_t m;
+    int32_t h_outer, h_inner, outer_done, target, taps_w, kbf16;
+    GkState st;
+    SolveParams prm;
+};
+
+int64_t ckpt_bytes(const plsqr_ctx* h) {
+    const int64_t no = h->h_outer, ni = h->h_inner;
+    const int64_t W = h->taps_inst ? 2 * (2 * h->od.R[0] + 1) : 0;
+    return (int64_t)sizeof(CkptHeader) + (int64_t)h->esz * (h->d.N + h->m) +
+           (int64_t)sizeof(double) * (no * ni + (no + 1) + no) + (int64_t)sizeof(float) * W;
+}
+}  // namespace
+
+int64_t plsqr_slot_state_bytes(plsqr_handle h) {
+    if (!h || !h->serving || !h->h_rbar) return -1;
+    return ckpt_bytes(h);
+}
+
+int plsqr_slot_save(plsqr_handle h, int32_t slot, void* buf, int64_t cap) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (slot < 0 || slot >= h->B) throw InvalidArg("slot out of range");
+        if (!h->serving || !h->slot_active[slot]) throw std::logic_error("slot is not running");
+        if (!buf) throw InvalidArg("buf is NULL");
+        const int64_t need = ckpt_bytes(h);
+        if (cap < need) throw InvalidArg("buffer smaller than plsqr_slot_state_bytes");
+        cudaStream_t s = h->stream;
+        ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");  // the slot is between two outer steps
+        CkptHeader hd{};
+        hd.magic = kCkptMagic;
+        hd.esz = (int32_t)h->esz;
+        hd.ndim = h->d.ndim;
+        hd.n[0] = h->d.nx;
+        hd.n[1] = h->d.ny;
+        hd.n[2] = h->d.nz;
+        hd.kind = h->op.kind;
+        hd.m = h->m;
+        hd.h_outer = h->h_outer;
+        hd.h_inner = h->h_inner;
+        hd.outer_done = h->slot_outer[slot];
+        hd.target = h->slot_target[slot];
+        hd.taps_w = h->taps_inst ? 2 * (2 * h->od.R[0] + 1) : 0;
+        hd.kbf16 = h->kbf16 ? 1 : 0;
+        hd.prm = h->prm_host[slot];
+        char* out = static_cast<char*>(buf);
+        ck(cudaMemcpy(&hd.st, h->st + slot, sizeof(GkState), cudaMemcpyDeviceToHost), "state");
+        std::memcpy(out, &hd, sizeof(hd));
+        char* q = out + sizeof(hd);
+        const size_t nb = h->esz * h->d.N, mb = h->esz * h->m;
+        ck(cudaMemcpy(q, h->f + slot * nb, nb, cudaMemcpyDeviceToHost), "f");
+        q += nb;
+        ck(cudaMemcpy(q, h->g + slot * mb, mb, cudaMemcpyDeviceToHost), "g");
+        q += mb;
+        const int64_t nr = (int64_t)h->h_outer * h->h_inner, nR = h->h_outer + 1, ne = h->h_outer;
+        ck(cudaMemcpy(q, h->h_rbar + slot * nr, sizeof(double) * nr, cudaMemcpyDeviceToHost), "hist");
+        q += sizeof(double) * nr;
+        ck(cudaMemcpy(q, h->h_R + slot * nR, sizeof(double) * nR, cudaMemcpyDeviceToHost), "hist");
+        q += sizeof(double) * nR;
+        ck(cudaMemcpy(q, h->h_resid + slot * ne, sizeof(double) * ne, cudaMemcpyDeviceToHost), "hist");
+        q += sizeof(double) * ne;
+        if (hd.taps_w) std::memcpy(q, h->taps_inst_host + (size_t)slot * hd.taps_w, sizeof(float) * hd.taps_w);
+        return PLSQR_OK;
+    });
+}
+
+int plsqr_slot_restore(plsqr_handle h, int32_t slot, const void* buf, int64_t len) {
+    if (!h) return PLSQR_E_INVALID;
+    return guarded(h, [&]() -> int {
+        if (!h->op_set) throw std::logic_error("set_operator must be called before plsqr_slot_restore");
+        if (slot < 0 || slot >= h->B) throw InvalidArg("slot out of range");
+        if (!buf || len < (int64_t)sizeof(CkptHeader)) throw InvalidArg("checkpoint too short");
+        CkptHeader hd;
+        std::memcpy(&hd, buf, sizeof(hd));
+        if (hd.magic != kCkptMagic) throw InvalidArg("not a slot checkpoint");
+        if (hd.esz != (int32_t)h->esz || hd.ndim != h->d.ndim || hd.n[0] != h->d.nx || hd.n[1] != h->d.ny ||
+            hd.n[2] != h->d.nz || hd.kind != h->op.kind || hd.m != h->m)
+            throw InvalidArg("checkpoint of another precision, grid or operator");
+        if (hd.kbf16 != (h->kbf16 ? 1 : 0)) throw InvalidArg("checkpoint taken with another kappa storage");
+        if (hd.h_outer < 1 || hd.h_inner < 1 || hd.outer_done < 0 || hd.outer_done > hd.target ||
+            hd.target > hd.h_outer || hd.taps_w < 0 || hd.taps_w > 2 * (2 * 64 + 1))
+            throw InvalidArg("corrupt checkpoint header");
+        const int64_t nr = (int64_t)hd.h_outer * hd.h_inner, nR = hd.h_outer + 1, ne = hd.h_outer;
+        const int64_t need = (int64_t)sizeof(CkptHeader) + (int64_t)h->esz * (h->d.N + h->m) +
+                             (int64_t)sizeof(double) * (nr + nR + ne) + (int64_t)sizeof(float) * hd.taps_w;
+        if (len < need) throw InvalidArg("checkpoint too short");
+        const int W = 2 * (2 * h->od.R[0] + 1);
+        if (hd.taps_w && hd.taps_w != W) throw InvalidArg("checkpoint taps of another blur radius");
+        enter_slot_mode(h);
+        if (h->slot_active[slot]) throw std::logic_error("slot is busy");
+        bool any = false;
+        for (int b = 0; b < h->B; ++b) any = any || h->slot_active[b];
+        if (!any) ensure_hist(h, hd.h_outer, hd.h_inner);
+        else if (hd.h_inner != h->h_inner || hd.target > h->h_outer)
+            throw InvalidArg("n_inner must equal, and n_outer not exceed, those of the running slots");
+        cudaStream_t s = h->stream;
+        ck(cudaEventRecord(h->ev_in, h->user_stream), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(s, h->ev_in, 0), "cudaStreamWaitEvent");
+        ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");  // no step or copy of the states in flight
+        const char* q = static_cast<const char*>(buf) + sizeof(hd);
+        const size_t nb = h->esz * h->d.N, mb = h->esz * h->m;
+        ck(cudaMemcpy(h->f + slot * nb, q, nb, cudaMemcpyHostToDevice), "f");
+        q += nb;
+        ck(cudaMemcpy(h->g + slot * mb, q, mb, cudaMemcpyHostToDevice), "g");
+        q += mb;
+        // histories: rows of the checkpoint's n_outer x n_inner layout into the handle's (NaN beyond)
+        const int64_t hr = (int64_t)h->h_outer * h->h_inner, hR = h->h_outer + 1, he = h->h_outer;
+        std::vector<double> tmp((size_t)std::max<int64_t>(hr, 1), std::nan(""));
+        std::memcpy(tmp.data(), q, sizeof(double) * std::min(nr, hr));
+        ck(cudaMemcpy(h->h_rbar + slot * hr, tmp.data(), sizeof(double) * hr, cudaMemcpyHostToDevice), "hist");
+        q += sizeof(double) * nr;
+        std::vector<double> tR((size_t)hR, std::nan(""));
+        std::memcpy(tR.data(), q, sizeof(double) * std::min(nR, hR));
+        ck(cudaMemcpy(h->h_R + slot * hR, tR.data(), sizeof(double) * hR, cudaMemcpyHostToDevice), "hist");
+        q += sizeof(double) * nR;
+        std::vector<double> te((size_t)std::max<int64_t>(he, 1), std::nan(""));
+        std::memcpy(te.data(), q, sizeof(double) * std::min(ne, he));
+        ck(cudaMemcpy(h->h_resid + slot * he, te.data(), sizeof(double) * he, cudaMemcpyHostToDevice), "hist");
+        q += sizeof(double) * ne;
+        if (hd.taps_w || h->taps_inst) {
+            if (!h->taps_inst) {  // from now on every slot reads its own taps
+                h->taps_inst = (float*)dalloc(h, sizeof(float) * W * h->B);
+                ck(cudaMallocHost((void**)&h->taps_inst_host, sizeof(float) * W * h->B), "cudaMallocHost");
+                for (int b = 0; b < h->B; ++b)
+                    for (int k = 0; k < W; ++k)
+                        h->taps_inst_host[b * W + k] = (float)h->od.taps_host[k < W / 2 ? 0 : 1][k % (W / 2)];
+                ck(cudaMemcpy(h->taps_inst, h->taps_inst_host, sizeof(float) * W * h->B, cudaMemcpyHostToDevice),
+                   "taps");
+                h->od.tapt = h->taps_inst;
+                clear_graphs(h);
+            }
+            float* row = h->taps_inst_host + (size_t)slot * W;
+            if (hd.taps_w) std::memcpy(row, q, sizeof(float) * W);
+            else
+                for (int k = 0; k < W; ++k) row[k] = (float)h->od.taps_host[k < W / 2 ? 0 : 1][k % (W / 2)];
+            ck(cudaMemcpy(h->taps_inst + (size_t)slot * W, row, sizeof(float) * W, cudaMemcpyHostToDevice), "taps");
+        }
+        h->prm_host[slot] = hd.prm;
+        ck(cudaMemcpy(h->prm_dev + slot, &hd.prm, sizeof(SolveParams), cudaMemcpyHostToDevice), "params");
+        GkState st = hd.st;
+        st.frozen = 0;
+        ck(cudaMemcpy(h->st + slot, &st, sizeof(GkState), cudaMemcpyHostToDevice), "state");
+        h->st_host[slot] = st;
+        h->slot_active[slot] = 1;
+        h->slot_outer[slot] = hd.outer_done;
+        h->slot_target[slot] = hd.target;
+        ck(cudaEventRecord(h->ev_out, s), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0), "cudaStreamWaitEvent");
+        return PLSQR_OK;
+    });
+}
+
 int plsqr_slot_finish(plsqr_handle h, int32_t slot, void* f_out, plsqr_stats* stats) {
     if (!h) return PLSQR_E_INVALID;
     return guarded(h, [&]() -> int {

@@ -84,6 +84,9 @@ def lib():
         "plsqr_query": ([vp], C.c_int),
         "plsqr_slot_progress": ([vp, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "plsqr_slot_finish": ([vp, i32, vp, C.POINTER(Stats)], C.c_int),
+        "plsqr_slot_state_bytes": ([vp], i64),
+        "plsqr_slot_save": ([vp, i32, vp, i64], C.c_int),
+        "plsqr_slot_restore": ([vp, i32, vp, i64], C.c_int),
         "plsqr_autotune": ([vp, i32], C.c_int),
         "plsqr_mlsqr_multi_tau": ([vp, vp, i32, i32, C.POINTER(d), C.POINTER(vp), C.POINTER(d), C.POINTER(i32)],
                                   C.c_int),
@@ -108,6 +111,7 @@ EXPORTED = ["plsqr_create", "plsqr_set_operator", "plsqr_solve", "plsqr_solve_ho
             "plsqr_diffusivity", "plsqr_prec_setup", "plsqr_prec_apply", "plsqr_apply_M", "plsqr_mlsqr",
             "plsqr_profile", "plsqr_profile_read", "plsqr_last_launches", "plsqr_check_guards", "plsqr_blur_noalloc",
             "plsqr_set_stopping", "plsqr_set_kappa_bf16", "plsqr_slot_start", "plsqr_step", "plsqr_query", "plsqr_slot_progress", "plsqr_slot_finish",
+            "plsqr_slot_state_bytes", "plsqr_slot_save", "plsqr_slot_restore",
             "plsqr_autotune", "plsqr_set_tile_shape", "plsqr_tile_shape", "plsqr_tune_cache_export",
             "plsqr_tune_cache_import", "plsqr_mg_schedule", "plsqr_mlsqr_multi_tau",
             "plsqr_projected_solve", "plsqr_selftest_wait"]
@@ -482,6 +486,23 @@ class Solver:
         self._slot_shape.pop(int(slot), None)
         info["status"] = rc
         return f_out, info
+
+    def slot_save(self, slot):
+        """The checkpoint of running `slot` at its current outer-step boundary (bytes; see
+        plsqr_slot_save).  The slot keeps running."""
+        n = int(lib().plsqr_slot_state_bytes(self.h))
+        if n < 0:
+            raise PlsqrError(E_STATE, "the handle is not in slot mode")
+        buf = (C.c_char * n)()
+        _check(self.h, lib().plsqr_slot_save(self.h, int(slot), buf, n))
+        return bytes(buf)
+
+    def slot_restore(self, slot, data, n_outer, n_inner):
+        """Starts `slot` from a checkpoint of slot_save (of a request started for n_outer steps of
+        n_inner iterations); it continues under step() and ends with slot_finish."""
+        buf = (C.c_char * len(data)).from_buffer_copy(data)
+        _check(self.h, lib().plsqr_slot_restore(self.h, int(slot), buf, len(data)))
+        self._slot_shape[int(slot)] = (int(n_outer), int(n_inner))
 
     # ---- single steps ----
     def apply_A(self, x, y=None):

@@ -90,3 +90,13 @@ def test_noalloc_binding_refuses_other_dtypes_before_the_library():
     with pytest.raises(TypeError):
         plsqr.plsqr_blur_noalloc(torch.zeros((8, 8), dtype=torch.float32), (1.0, 1.0), (2, 2),
                                  y=torch.zeros((8, 8), dtype=torch.float16))
+
+
+def test_checkpoint_entry_points_refuse_a_null_handle_without_gpu():
+    """The checkpoint entry points check their handle before touching the device."""
+    from paper_1308_6634_gb300 import plsqr
+    L = plsqr.lib()
+    assert L.plsqr_slot_state_bytes(None) == -1
+    buf = (plsqr.C.c_char * 64)()
+    assert L.plsqr_slot_save(None, 0, buf, 64) == plsqr.E_INVALID
+    assert L.plsqr_slot_restore(None, 0, buf, 64) == plsqr.E_INVALID

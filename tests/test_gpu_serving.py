@@ -225,3 +225,82 @@ def test_slot_history_regrowth_keeps_per_slot_taps():
     assert torch.equal(f1, f2)
     assert np.array_equal(info1["rbar_hist"], info2["rbar_hist"])
     S.close()
+
+
+@pytest.mark.parametrize("per_slot_sigma,stop", [(False, False), (True, False), (False, True)])
+def test_checkpoint_resume_equals_uninterrupted_solve(per_slot_sigma, stop):
+    """A request saved after k outer steps (plsqr_slot_save) and restored into another slot of
+    another handle (plsqr_slot_restore: other max_batch, other slot index, a running neighbour)
+    finishes with f and histories bit for bit those of the uninterrupted run: between outer steps
+    of Algorithm 3 the state is f^k with its scalars and histories.  With the outer stopping rule
+    on, the rule compares R(f^k) with the saved R(f^{k-1})."""
+    from paper_1308_6634_gb300 import plsqr
+    n, sigma, R, n_outer, n_inner, k = 96, 4.0, 12, 4, 6, 2
+    g = _deblur_data(n, sigma, R, 7)
+    sg = (3.5, 3.5) if per_slot_sigma else None
+
+    def handle(B):
+        S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=B)
+        S.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+        if stop:
+            S.set_stopping(0.0, 0.0, 0.05)
+        return S
+
+    S1 = handle(2)
+    S1.slot_start(0, g, "pm_log", 5e-2, 1e-3, n_outer, n_inner, sigma=sg)
+    for _ in range(n_outer):
+        S1.step()
+    f1, info1 = S1.slot_finish(0, n_outer, n_inner)
+    S2 = handle(2)
+    S2.slot_start(1, g, "pm_log", 5e-2, 1e-3, n_outer, n_inner, sigma=sg)
+    for _ in range(k):
+        S2.step()
+    ck = S2.slot_save(1)
+    assert len(ck) == plsqr.lib().plsqr_slot_state_bytes(S2.h)
+    S3 = handle(3)
+    other = _deblur_data(n, sigma, R, 9)
+    S3.slot_start(0, other, "tv", 1e-2, 1e-3, n_outer, n_inner)
+    S3.step()
+    S3.slot_restore(2, ck, n_outer, n_inner)
+    assert S3.slot_progress(2)[0] == k
+    for _ in range(n_outer - k):
+        S3.step()
+    f3, info3 = S3.slot_finish(2, n_outer, n_inner)
+    S3.slot_finish(0, n_outer, n_inner)
+    torch.cuda.synchronize()
+    assert info3["status"] == info1["status"]
+    assert torch.equal(f1, f3)
+    for key in ("rbar_hist", "R_hist", "resid_hist"):
+        assert np.array_equal(info1[key], info3[key], equal_nan=True), key
+
+
+def test_checkpoint_restore_refusals():
+    """plsqr_slot_restore refuses a buffer that is not a checkpoint, one that is truncated, one of
+    another grid, and a busy slot, and leaves the handle usable."""
+    from paper_1308_6634_gb300 import plsqr
+    n, sigma, R = 64, 3.0, 9
+    g = _deblur_data(n, sigma, R, 11)
+    S = plsqr.Solver((n, n), "fp32", levels=3, max_batch=2)
+    S.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    S.slot_start(0, g, "tv", 1e-2, 1e-3, 2, 4)
+    S.step()
+    ck = S.slot_save(0)
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_restore(1, b"\0" * len(ck), 2, 4)
+    assert e.value.code == plsqr.E_INVALID
+    with pytest.raises(plsqr.PlsqrError) as e:
+        S.slot_restore(1, ck[: len(ck) // 2], 2, 4)
+    assert e.value.code == plsqr.E_INVALID
+    with pytest.raises(plsqr.PlsqrError):
+        S.slot_restore(0, ck, 2, 4)  # busy
+    T = plsqr.Solver((2 * n, n), "fp32", levels=3, max_batch=1)
+    T.set_operator("blur", sigma=(sigma, sigma), radius=(R, R))
+    with pytest.raises(plsqr.PlsqrError) as e:
+        T.slot_restore(0, ck, 2, 4)
+    assert e.value.code == plsqr.E_INVALID
+    S.slot_restore(1, ck, 2, 4)
+    S.step()
+    fa, ia = S.slot_finish(0, 2, 4)
+    fb, ib = S.slot_finish(1, 2, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(fa, fb)
