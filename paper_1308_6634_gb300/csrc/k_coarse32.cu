@@ -646,6 +646,145 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_window(float* __restrict__ gco
     }
 }
 
+// The same elimination with look-ahead: in step k, warps 0 .. GP-1 (GP = ceil(bw / 32)) apply
+// pivot k to column k+1 only, sum it and form 1/d_{k+1} and l_{.,k+1}, while the other warps apply
+// pivot k to columns k+2 .. k+bw (thread t of group q: row offset t of the columns k + tau, tau =
+// q + 2, q + 2 + NQ, ..; each thread takes the row offsets t and bw - t, so that every thread has
+// about the same number of columns) and copy column k+bw+1 into the window.  One block barrier
+// ends a step.
+// The window holds bw + 2 slots (column c in slot c mod (bw + 2)), so the entering column never
+// shares a slot with a column read in the same step.  The pivot sums use the warps, lanes and
+// order of k_ldl_gth_window (thread i holds entry i + 1, thread 0 also the excess; shuffle-down
+// within a warp, the warp totals in warp order), and every entry receives the same multiply-adds
+// in the same order: bit for bit its factor.  In k_ldl_gth_window the pivot chain (sum, reciprocal,
+// l) runs after each step's bulk update and both sit between block barriers: ~4400 cycles per
+// pivot on the 192^3 workload's 12^3 coarse grid (band 144).
+__global__ void __launch_bounds__(1024) k_ldl_gth_ahead(float* __restrict__ gcol_all, float* __restrict__ grow_all,
+                                                        int nc, int bw, int BWP, GkState* st) {
+    extern __shared__ __align__(16) float win[];
+    __shared__ float sl[2][2 * 256 + 4];  // l of pivots k (k & 1) and k + 1, zero beyond bw
+    __shared__ float pw[8];
+    const int S = bw + 1, S2 = bw + 2, SW = S | 1;
+    const int GP = (bw + 31) / 32;
+    const int H = bw / 2 + 1;  // row pairs (r, bw - r) of the update group, r < H
+    const int NU = blockDim.x - 32 * GP, NQ = NU / H;
+    const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (parked(st[inst])) return;
+    float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    for (int e = tid; e < nc * BWP; e += blockDim.x)  // row layout: entries no pivot writes
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
+    for (int e = tid; e < min(S, nc) * S; e += blockDim.x) {
+        const int c = e / S, r = e - c * S;
+        win[c * SW + r] = gc[(int64_t)c * BWP + r];  // columns 0 .. bw in slots 0 .. bw
+    }
+    for (int e = tid; e < 2 * (2 * 256 + 4); e += blockDim.x) (&sl[0][0])[e] = 0.f;
+    const bool pgrp = warp < GP;
+    const int u = tid - 32 * GP;  // index in the update group
+    const int q = pgrp ? 0 : u / H, tr = pgrp ? 0 : u - q * H;
+    float pre = (!pgrp && u < S && S < nc) ? gc[(int64_t)S * BWP + u] : 0.f;  // column S, copied in step 0
+    __syncthreads();
+    // the pivot group's part of a step: column c (all previous pivots applied) -> 1/d_c and l_{.,c}
+    auto pivot = [&](int c, float e, float e0) {
+        const int t = tid + 1;
+        float part = (t <= bw ? e : 0.f) + (tid == 0 ? e0 : 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if (lane == 0) pw[warp] = part;
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * GP) : "memory");
+        float dk = 0.f;
+        for (int w = 0; w < GP; ++w) dk += pw[w];
+        const float rd = 1.0f / dk;
+        if (t <= bw) {
+            const float l = e * rd;
+            sl[c & 1][t] = l;
+            gc[(int64_t)c * BWP + t] = l;
+            if (c + t < nc) gr[(int64_t)(c + t) * BWP + t] = l;
+        }
+        if (tid == 0) gc[(int64_t)c * BWP] = rd;
+    };
+    if (pgrp) {  // pivot 0
+        const int t = tid + 1;
+        pivot(0, t <= bw ? win[t] : 0.f, win[0]);
+    }
+    __syncthreads();
+    for (int k = 0; k < nc; ++k) {
+        const float* ck = win + (k % S2) * SW;  // column k, the pivot
+        const float* lk = sl[k & 1];
+        if (pgrp) {
+            if (k + 1 < nc) {
+                float* c1 = win + ((k + 1) % S2) * SW;
+                const int t = tid + 1;
+                float e = t <= bw ? c1[t] : 0.f;
+                if (t <= bw) {
+                    e = fmaf(lk[1 + t], ck[1], e);
+                    c1[t] = e;
+                }
+                float e0 = 0.f;
+                if (tid == 0) {
+                    e0 = fmaf(lk[1], ck[0], c1[0]);
+                    c1[0] = e0;
+                }
+                pivot(k + 1, e, e0);
+            }
+        } else {
+            if (q < NQ) {
+                // row offsets tr and bw - tr (about bw / NQ columns together, whatever tr), columns
+                // k + tau, tau = q + 2, q + 2 + NQ, ..; row 0 is the excess (l_{k+tau,k} s_k)
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int r = pass == 0 ? tr : bw - tr;
+                    if (pass == 1 && r == tr) break;
+                    const int last = min(bw - r, nc - 1 - k);
+                    int tau = q + 2;
+                    if (tau > last) continue;
+                    int slot = (k + tau) % S2;
+                    const float* lp = lk + tau + r;
+                    const float* ap = r == 0 ? ck : ck + tau;
+                    const int as = r == 0 ? 0 : NQ;
+                    for (; tau + 3 * NQ <= last; tau += 4 * NQ) {  // four columns: loads first
+                        float* ep[4];
+                        float ev[4], lv[4], av[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            ep[c] = win + slot * SW + r;
+                            ev[c] = *ep[c];
+                            lv[c] = lp[c * NQ];
+                            av[c] = ap[c * as];
+                            slot += NQ;
+                            if (slot >= S2) slot -= S2;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) *ep[c] = fmaf(lv[c], av[c], ev[c]);
+                        lp += 4 * NQ;
+                        ap += 4 * as;
+                    }
+                    for (; tau <= last; tau += NQ) {
+                        float* e = win + slot * SW + r;
+                        *e = fmaf(*lp, *ap, *e);
+                        slot += NQ;
+                        if (slot >= S2) slot -= S2;
+                        lp += NQ;
+                        ap += as;
+                    }
+                }
+            }
+            if (u < S && k + S < nc) {  // column k + S enters its slot (read from step k + 1 on)
+                win[((k + S) % S2) * SW + u] = pre;
+                pre = k + S + 1 < nc ? gc[(int64_t)(k + S + 1) * BWP + u] : 0.f;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// PLSQR_GTH_AHEAD=0 keeps k_ldl_gth_window (comparisons)
+bool gth_ahead_supported(int bw, int nc) {
+    const int S = bw + 1, SW = S | 1, GP = (bw + 31) / 32;
+    const char* e = std::getenv("PLSQR_GTH_AHEAD");
+    return !(e && e[0] == '0') && bw > 32 && bw <= 256 && GP <= 8 && (1024 - 32 * GP) / (bw / 2 + 1) >= 1 &&
+           (size_t)(S + 1) * SW * sizeof(float) <= 200 * 1024 && nc > 0;
+}
+
 // X = L^{-T} D^{-1} L^{-1} for wide bands, one warp per column j: forward z_i = delta_ij +
 // sum_t l_{i,i-t} z_{i-t} over the rows i >= j (row layout, consecutive lanes on consecutive t),
 // y_i = z_i / d_i kept in X[i][j]; backward x_i = y_i + sum_t l_{i+t,i} x_{i+t} from the last row
@@ -771,9 +910,18 @@ void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw,
     const size_t smem = sizeof(float) * (size_t)S * SW;
     const int nt0 = std::max(32, ((bw + 31) / 32) * 32);
     const int nt = nt0 * std::max(1, std::min(GTH_WQ, 1024 / nt0));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ldl_gth_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ldl_gth_window<<<B, nt, smem, s>>>(gcol, grow, nc, bw, BWP, st);
-    klaunched("k_ldl_gth_window");
+    if (gth_ahead_supported(bw, nc)) {
+        const size_t smem2 = sizeof(float) * (size_t)(S + 1) * SW;
+        if (smem2 > 48 * 1024)
+            cudaFuncSetAttribute(k_ldl_gth_ahead, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        k_ldl_gth_ahead<<<B, 1024, smem2, s>>>(gcol, grow, nc, bw, BWP, st);
+        klaunched("k_ldl_gth_ahead");
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_ldl_gth_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ldl_gth_window<<<B, nt, smem, s>>>(gcol, grow, nc, bw, BWP, st);
+        klaunched("k_ldl_gth_window");
+    }
     constexpr int NW = 4;
     dim3 grid((unsigned)((nc + NW - 1) / NW), B);
     k_gth_inverse_wide<NW><<<grid, 32 * NW, sizeof(float) * NW * (bw + 1), s>>>(gcol, grow, X, nc, bw, BWP, st);
