@@ -548,6 +548,215 @@ __global__ void __launch_bounds__(32 * NWI) k_gth_inverse_warp(const V* __restri
     }
 }
 
+// ---- the inverse in 32 x 32 blocks (bandwidth <= 32) --------------------------------------------
+// With L = I - N (N >= 0: the l of the factor) cut into 32 x 32 blocks, L is block lower
+// bidiagonal: N_ii strictly lower, N_{i,i-1} upper triangular (bandwidth <= 32).  Then
+//   W = L^{-1}:  W_jj = G_j = (I - N_jj)^{-1},  W_ij = P_i W_{i-1,j} with P_i = G_i N_{i,i-1} (i > j),
+//   X = W^T D^{-1} W:  X_ab = sum_{i >= max(a,b)} W_ia^T D_i^{-1} W_ib.
+// Every quantity is a sum of products of non-negative numbers, as in the row-by-row kernels, so the
+// result keeps their componentwise accuracy; but the chains of dependent steps are 32 (G), nb (W)
+// and nb (X) block steps spread over many blocks instead of 2 nc row steps on one thread.  Only X_ab
+// with a <= b is formed (and the diagonal blocks' upper halves), and mirrored: X is exactly
+// symmetric.  Rows beyond nc are padding (N = 0, 1/d = 0).  Scratch per instance: G and P (2 nb
+// blocks) and W (nb (nb + 1) / 2 blocks, packed by block rows).
+constexpr int XB = 32;
+
+template <typename V>
+__device__ __forceinline__ V tab_l(const V* gc, int BWP, int bw, int nc, int r, int c) {  // l_{r,c}, r > c
+    return (r < nc && c >= 0 && r > c && r - c <= bw) ? gc[(int64_t)c * BWP + (r - c)] : (V)0;
+}
+
+// G_i and P_i of block row i (one block of 32 x 32 threads per block row and instance)
+template <typename V>
+__global__ void __launch_bounds__(1024) k_xblk_diag(const V* __restrict__ gcol_all, V* __restrict__ gp_all, int nc,
+                                                    int bw, int BWP, int nb, GkState* st) {
+    __shared__ V nd[XB][XB + 1], ns[XB][XB + 1], gs[XB][XB + 1];
+    const int inst = blockIdx.y, i = blockIdx.x;
+    if (parked(st[inst])) return;
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+    const V* gc = gcol_all + (int64_t)inst * nc * BWP;
+    nd[r][c] = tab_l(gc, BWP, bw, nc, XB * i + r, XB * i + c);
+    ns[r][c] = i > 0 ? tab_l(gc, BWP, bw, nc, XB * i + r, XB * (i - 1) + c) : (V)0;
+    __syncthreads();
+    // column c of G by warp c (= r here): lane l holds g_l; when g_s is final the rows below it
+    // receive N_ls g_s
+    {
+        const int col = r, l = c;
+        V g = l == col ? (V)1 : (V)0;
+        for (int s2 = 0; s2 < XB; ++s2) {
+            const V gsv = __shfl_sync(0xffffffffu, g, s2);
+            if (l > s2) g = fma(nd[l][s2], gsv, g);
+        }
+        gs[l][col] = g;
+    }
+    __syncthreads();
+    V* gp = gp_all + ((int64_t)inst * nb + i) * 2 * XB * XB;
+    gp[r * XB + c] = gs[r][c];
+    V acc = (V)0;
+#pragma unroll 8
+    for (int m = 0; m < XB; ++m) acc = fma(gs[r][m], ns[m][c], acc);
+    gp[XB * XB + r * XB + c] = acc;
+}
+
+// 32 x 32 blocks in shared memory with a row stride of XS elements (pairs of a row 8- or 16-byte
+// aligned for the vector loads of the 2 x 2 register tiles below)
+constexpr int XS = XB + 2;
+
+template <typename V> struct V2of;
+template <> struct V2of<float> { using type = float2; };
+template <> struct V2of<double> { using type = double2; };
+
+// acc (2 x 2, rows r0, r0+1, columns c0, c0+1) += A^T B over m, A = sa[m][r], B = sb[m][c]
+template <typename V>
+__device__ __forceinline__ void tile_atb(const V (*sa)[XS], const V (*sb)[XS], int r0, int c0, V (&acc)[2][2]) {
+    using V2 = typename V2of<V>::type;
+#pragma unroll 8
+    for (int m = 0; m < XB; ++m) {
+        const V2 ar = *reinterpret_cast<const V2*>(&sa[m][r0]);
+        const V2 bc = *reinterpret_cast<const V2*>(&sb[m][c0]);
+        acc[0][0] = fma(ar.x, bc.x, acc[0][0]);
+        acc[0][1] = fma(ar.x, bc.y, acc[0][1]);
+        acc[1][0] = fma(ar.y, bc.x, acc[1][0]);
+        acc[1][1] = fma(ar.y, bc.y, acc[1][1]);
+    }
+}
+
+// W_jj .. W_{nb-1,j} of block column j: W_ij = P_i W_{i-1,j}.  256 threads, each a 2 x 2 tile;
+// P_i is staged transposed (pt[m][r] = P_i[r][m]) so that the product reads rows of both operands.
+template <typename V>
+__global__ void __launch_bounds__(256) k_xblk_wchain(const V* __restrict__ gp_all, V* __restrict__ w_all, int nb,
+                                                     GkState* st) {
+    using V2 = typename V2of<V>::type;
+    __shared__ __align__(16) V ws[2][XB][XS], pt[2][XB][XS];
+    const int inst = blockIdx.y, j = blockIdx.x;
+    if (parked(st[inst])) return;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const int r0 = 2 * ty, c0 = 2 * tx;
+    const V* gp = gp_all + (int64_t)inst * nb * 2 * XB * XB;
+    V* w = w_all + (int64_t)inst * (nb * (nb + 1) / 2) * XB * XB;
+    // this thread's four elements of a staged block: rows r0, r0+1, columns c0, c0+1
+    auto ld2 = [&](const V* blk, int row) { return *reinterpret_cast<const V2*>(blk + row * XB + c0); };
+    {
+        const V* g = gp + (int64_t)j * 2 * XB * XB;
+        const V2 g0 = ld2(g, r0), g1 = ld2(g, r0 + 1);
+        *reinterpret_cast<V2*>(&ws[0][r0][c0]) = g0;
+        *reinterpret_cast<V2*>(&ws[0][r0 + 1][c0]) = g1;
+        V* wj = w + ((int64_t)j * (j + 1) / 2 + j) * XB * XB;
+        *reinterpret_cast<V2*>(wj + r0 * XB + c0) = g0;
+        *reinterpret_cast<V2*>(wj + (r0 + 1) * XB + c0) = g1;
+    }
+    V2 p0{}, p1{};
+    if (j + 1 < nb) {
+        const V* pn = gp + (int64_t)(j + 1) * 2 * XB * XB + XB * XB;
+        p0 = ld2(pn, r0);
+        p1 = ld2(pn, r0 + 1);
+    }
+    for (int i = j + 1; i < nb; ++i) {
+        const int cur = (i - j - 1) & 1;
+        pt[cur][c0][r0] = p0.x;  // transposed: pt[m][r] = P[r][m]
+        pt[cur][c0 + 1][r0] = p0.y;
+        pt[cur][c0][r0 + 1] = p1.x;
+        pt[cur][c0 + 1][r0 + 1] = p1.y;
+        if (i + 1 < nb) {
+            const V* pn = gp + (int64_t)(i + 1) * 2 * XB * XB + XB * XB;
+            p0 = ld2(pn, r0);
+            p1 = ld2(pn, r0 + 1);
+        }
+        __syncthreads();
+        V acc[2][2] = {{(V)0, (V)0}, {(V)0, (V)0}};
+        tile_atb<V>(pt[cur], ws[cur], r0, c0, acc);
+        const V2 o0 = {acc[0][0], acc[0][1]}, o1 = {acc[1][0], acc[1][1]};
+        *reinterpret_cast<V2*>(&ws[cur ^ 1][r0][c0]) = o0;
+        *reinterpret_cast<V2*>(&ws[cur ^ 1][r0 + 1][c0]) = o1;
+        V* wi = w + ((int64_t)i * (i + 1) / 2 + j) * XB * XB;
+        *reinterpret_cast<V2*>(wi + r0 * XB + c0) = o0;
+        *reinterpret_cast<V2*>(wi + (r0 + 1) * XB + c0) = o1;
+        __syncthreads();
+    }
+}
+
+// X_ab (a <= b) = sum_{i >= b} W_ia^T D_i^{-1} W_ib, written with its mirror.  256 threads, each a
+// 2 x 2 tile; the next block row's two blocks are loaded into registers while this one is summed.
+template <typename V>
+__global__ void __launch_bounds__(256) k_xblk_syrk(const V* __restrict__ w_all, const V* __restrict__ gcol_all,
+                                                   V* __restrict__ X_all, int nc, int BWP, int nb, GkState* st) {
+    using V2 = typename V2of<V>::type;
+    __shared__ __align__(16) V wa[2][XB][XS], wb[2][XB][XS];
+    const int inst = blockIdx.y;
+    if (parked(st[inst])) return;
+    const int p = blockIdx.x;
+    int b = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+    while ((b + 1) * (b + 2) / 2 <= p) ++b;
+    while (b * (b + 1) / 2 > p) --b;
+    const int a = p - b * (b + 1) / 2;  // a <= b
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const int r0 = 2 * ty, c0 = 2 * tx;
+    const V* w = w_all + (int64_t)inst * (nb * (nb + 1) / 2) * XB * XB;
+    const V* gc = gcol_all + (int64_t)inst * nc * BWP;
+    // staging: this thread moves rows r0, r0+1, columns c0, c0+1 of W_ia and (scaled by 1/d) W_ib
+    auto fetch = [&](int i, V2 (&fa)[2], V2 (&fb)[2]) {
+        const V* A = w + ((int64_t)i * (i + 1) / 2 + a) * XB * XB;
+        const V* Bm = w + ((int64_t)i * (i + 1) / 2 + b) * XB * XB;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int row = XB * i + r0 + q;
+            const V dinv = row < nc ? gc[(int64_t)row * BWP] : (V)0;
+            fa[q] = *reinterpret_cast<const V2*>(A + (r0 + q) * XB + c0);
+            const V2 t = *reinterpret_cast<const V2*>(Bm + (r0 + q) * XB + c0);
+            fb[q] = {dinv * t.x, dinv * t.y};
+        }
+    };
+    V2 fa[2], fb[2];
+    fetch(b, fa, fb);
+    V acc[2][2] = {{(V)0, (V)0}, {(V)0, (V)0}};
+    for (int i = b; i < nb; ++i) {
+        const int cur = (i - b) & 1;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            *reinterpret_cast<V2*>(&wa[cur][r0 + q][c0]) = fa[q];
+            *reinterpret_cast<V2*>(&wb[cur][r0 + q][c0]) = fb[q];
+        }
+        if (i + 1 < nb) fetch(i + 1, fa, fb);
+        __syncthreads();
+        tile_atb<V>(wa[cur], wb[cur], r0, c0, acc);  // sum over m of W_ia[m][r] (W_ib[m][c] / d_m)
+        // the other buffer is written next; a barrier per block row keeps the reads of this one
+        // ahead of that (two buffers, so one barrier suffices)
+    }
+    V* X = X_all + (int64_t)inst * nc * nc;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int r = r0 + q, c = c0 + e;
+            const int gi = XB * a + r, gj = XB * b + c;
+            if (gi < nc && gj < nc) {
+                if (a < b || r <= c) X[(int64_t)gi * nc + gj] = acc[q][e];
+                if (a < b || r < c) X[(int64_t)gj * nc + gi] = acc[q][e];
+            }
+        }
+}
+
+int xblk_blocks(int nc) { return (nc + XB - 1) / XB; }
+
+// scratch elements per instance of the blocked inverse
+int64_t xblk_scratch(int nc) {
+    const int64_t nb = xblk_blocks(nc);
+    return (2 * nb + nb * (nb + 1) / 2) * XB * XB;
+}
+
+template <typename V>
+static void xblk_inverse(const V* gcol, V* X, V* scratch, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+    const int BWP = gth_stride(bw), nb = xblk_blocks(nc);
+    V* gp = scratch;
+    V* w = scratch + (int64_t)B * 2 * nb * XB * XB;
+    k_xblk_diag<V><<<dim3(nb, B), 1024, 0, s>>>(gcol, gp, nc, bw, BWP, nb, st);
+    klaunched("k_xblk_diag");
+    k_xblk_wchain<V><<<dim3(nb, B), 256, 0, s>>>(gp, w, nb, st);
+    klaunched("k_xblk_wchain");
+    k_xblk_syrk<V><<<dim3(nb * (nb + 1) / 2, B), 256, 0, s>>>(w, gcol, X, nc, BWP, nb, st);
+    klaunched("k_xblk_syrk");
+}
+
 // Wide bands (3D coarsest grids): the same elimination with a circular window of the bw + 1
 // columns pivot k touches, in shared memory (column j in slot j mod (bw + 1), an odd slot stride
 // so that consecutive rows of different slots fall in different banks).  The block has NQ groups
@@ -954,7 +1163,7 @@ void gth_assemble(const T* cond, bool is_kappa, V* gcol, Dims d, int bw, int B, 
 }
 
 template <typename V, int BW>
-static void gth_launch(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+static void gth_launch(V* gcol, V* grow, V* X, V* xscr, int nc, int bw, int B, GkState* st, cudaStream_t s) {
     const int BWP = gth_stride(bw);
     const size_t stage = sizeof(V) * (size_t)nc * BWP;
     const size_t sp = stage + sizeof(V) * BWP;
@@ -974,6 +1183,10 @@ static void gth_launch(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* s
         kq<<<B, 32 * (1 + GTH_BULK), sp, s>>>(gcol, grow, nc, bw, st);
         klaunched("k_ldl_gth_split");
     }
+    if (xscr) {  // the blocked inverse
+        xblk_inverse<V>(gcol, X, xscr, nc, bw, B, st, s);
+        return;
+    }
     if (gth_inverse_by_warp(B, sizeof(V))) {
         constexpr int NWI = sizeof(V) == 8 ? 8 : 16;  // double: the registers of 32 band entries
         auto kw = k_gth_inverse_warp<V, BW, NWI>;
@@ -992,15 +1205,15 @@ static void gth_launch(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* s
 }
 
 template <typename V>
-void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+void gth_factor_inverse(V* gcol, V* grow, V* X, V* xscr, int nc, int bw, int B, GkState* st, cudaStream_t s) {
     if (!gth_supported(bw, nc, sizeof(V)))
         throw std::runtime_error("gth_factor_inverse: bandwidth or size not supported");
     kbegin(KC_SETUP, s);
     switch (gth_window(bw)) {
-        case 8: gth_launch<V, 8>(gcol, grow, X, nc, bw, B, st, s); break;
-        case 16: gth_launch<V, 16>(gcol, grow, X, nc, bw, B, st, s); break;
+        case 8: gth_launch<V, 8>(gcol, grow, X, xscr, nc, bw, B, st, s); break;
+        case 16: gth_launch<V, 16>(gcol, grow, X, xscr, nc, bw, B, st, s); break;
         case 32:
-            if constexpr (sizeof(V) == 4) gth_launch<V, 32>(gcol, grow, X, nc, bw, B, st, s);
+            if constexpr (sizeof(V) == 4) gth_launch<V, 32>(gcol, grow, X, xscr, nc, bw, B, st, s);
             break;
     }
     kfinish(s);
@@ -1009,7 +1222,7 @@ void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* 
 template void gth_assemble<float, float>(const float*, bool, float*, Dims, int, int, cudaStream_t);
 template void gth_assemble<double, float>(const double*, bool, float*, Dims, int, int, cudaStream_t);
 template void gth_assemble<double, double>(const double*, bool, double*, Dims, int, int, cudaStream_t);
-template void gth_factor_inverse<float>(float*, float*, float*, int, int, int, GkState*, cudaStream_t);
-template void gth_factor_inverse<double>(double*, double*, double*, int, int, int, GkState*, cudaStream_t);
+template void gth_factor_inverse<float>(float*, float*, float*, float*, int, int, int, GkState*, cudaStream_t);
+template void gth_factor_inverse<double>(double*, double*, double*, double*, int, int, int, GkState*, cudaStream_t);
 
 }  // namespace plsqr

@@ -136,8 +136,11 @@ int gth_stride(int bw);
 bool gth_supported(int bw, int nc, size_t esz);
 template <typename T, typename V>
 void gth_assemble(const T* cond, bool is_kappa, V* gcol, Dims d, int bw, int B, cudaStream_t s);
+// xscr: scratch of the blocked inverse (B * xblk_scratch(nc) elements), or null for the row-by-row
+// kernels.
 template <typename V>
-void gth_factor_inverse(V* gcol, V* grow, V* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
+void gth_factor_inverse(V* gcol, V* grow, V* X, V* xscr, int nc, int bw, int B, GkState* st, cudaStream_t s);
+int64_t xblk_scratch(int nc);
 // Wide bands: the float L D L^T with a window of bw + 1 columns, and the float inverse with a warp
 // per column.
 bool gth_wide_supported(int bw, int nc);

@@ -127,6 +127,7 @@ struct plsqr_ctx {
     char* gcol = nullptr;  // [B][nc][stride] (float, or double for FP64 handles): column layout
                            // (input conductances, then l and 1/d)
     char* grow = nullptr;  // [B][nc][stride]: row layout of l
+    char* xblk = nullptr;  // scratch of the blocked inverse, or null (row-by-row kernels)
     GkState* st = nullptr;
     SolveParams* prm_dev = nullptr;
     SolveParams* prm_host = nullptr;  // pinned
@@ -239,6 +240,15 @@ Dims make_dims(int ndim, int64_t nx, int64_t ny, int64_t nz) {
     return d;
 }
 
+// The coarse inverse in 32 x 32 blocks (k_xblk_*) whatever the batch, so that an instance's
+// result does not depend on how many share its handle; PLSQR_GTH_BLOCKED=0 keeps the row-by-row
+// kernels (comparisons).
+bool xblk_enabled(int B) {
+    (void)B;
+    const char* e = std::getenv("PLSQR_GTH_BLOCKED");
+    return !(e && e[0] == '0');
+}
+
 // Sizes of everything create() allocates (used by plsqr_workspace_bytes too).
 struct Plan {
     Dims d;
@@ -302,6 +312,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
         for (int l = 0; l + 1 < pl.L; ++l) b += esz * B * pl.level_N[l];  // reciprocal diagonals
     if (pl.gth || pl.gthw) {
         b += (pl.gth ? vsz : sizeof(float)) * B * (size_t)pl.nc * (2 * gth_stride(pl.bw) + pl.nc);
+        if (pl.gth && xblk_enabled((int)B)) b += vsz * B * (size_t)xblk_scratch(pl.nc);
     } else {
         b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
         b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
@@ -491,8 +502,8 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     const T* cc = lc == 0 ? P<T>(h->kappa) : P<T>(h->lv[lc].cond);
     if (h->gth) {  // tables and inverse in the handle's type
         gth_assemble<T, T>(cc, lc == 0, P<T>(h->gcol), h->lv[lc].d, h->bw, B, s);
-        gth_factor_inverse<T>(P<T>(h->gcol), P<T>(h->grow), const_cast<T*>(coarse_inverse_of<T>(h)), h->nc, h->bw,
-                              B, h->st, s);
+        gth_factor_inverse<T>(P<T>(h->gcol), P<T>(h->grow), const_cast<T*>(coarse_inverse_of<T>(h)), P<T>(h->xblk),
+                              h->nc, h->bw, B, h->st, s);
         return;
     }
     if (h->gthw) {
@@ -1157,6 +1168,7 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         if (h->gth || h->gthw) {  // tables in the handle's type (the wide route: float only)
             const size_t vsz = h->gth ? h->esz : sizeof(float);
             h->gcol = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
+            if (h->gth && xblk_enabled(B)) h->xblk = dalloc(h, vsz * B * (size_t)xblk_scratch(h->nc));
             h->grow = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
             if (h->fp64) h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
         } else {
