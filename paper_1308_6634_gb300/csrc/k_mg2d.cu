@@ -218,6 +218,8 @@ bool mg2d_shape(bool fine, int id, int* tx, int* ty, int* nth) {
             case 1: v[0] = F1::TX, v[1] = F1::TY, v[2] = F1::NTH; break;
             case 2: v[0] = F2::TX, v[1] = F2::TY, v[2] = F2::NTH; break;
             case 3: v[0] = F3::TX, v[1] = F3::TY, v[2] = F3::NTH; break;
+            case 4: v[0] = F4::TX, v[1] = F4::TY, v[2] = F4::NTH; break;
+            case 5: v[0] = F5::TX, v[1] = F5::TY, v[2] = F5::NTH; break;
             default: return false;
         }
     } else {
@@ -244,6 +246,8 @@ void mg2d_pre(const T* cond, bool is_kappa, const T* b, const T* rd, T* x, T* bc
         if (shape == 1) done = pre_shape<T, true, F1, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (shape == 2) done = pre_shape<T, true, F2, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (shape == 3) done = pre_shape<T, true, F3, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
+        if (shape == 4) done = pre_shape<T, true, F4, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
+        if (shape == 5) done = pre_shape<T, true, F5, false>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
         if (!done) pre_shape<T, true, F0, true>(cond, b, rd, x, bc, d, dc, nu, B, st, s, k16);
     } else {
         switch (shape) {
@@ -273,6 +277,10 @@ void mg2d_post(const T* cond, bool is_kappa, const T* b, const T* rd, const T* x
             done = post_shape<T, true, F2, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
         if (shape == 3)
             done = post_shape<T, true, F3, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
+        if (shape == 4)
+            done = post_shape<T, true, F4, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
+        if (shape == 5)
+            done = post_shape<T, true, F5, false>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
         if (!done) post_shape<T, true, F0, true>(cond, b, rd, xi, x, xc, d, dc, nu, B, dot, st, hist, red, s, k16);
     } else {
         switch (shape) {

@@ -47,6 +47,8 @@ using F0 = Shape<64, 32, 256>;
 using F1 = Shape<32, 32, 256, 7>;
 using F2 = Shape<32, 16, 256>;
 using F3 = Shape<64, 32, 512>;
+using F4 = Shape<16, 16, 256>;  // small tiles: more SMs on small grids (the fused alpha needs 32 x 16 segments)
+using F5 = Shape<16, 8, 128>;
 using C0 = Shape<64, 32, 1024>;
 using C1 = Shape<32, 16, 512>;
 using C2 = Shape<32, 16, 256>;
@@ -495,6 +497,10 @@ bool post_nu(const T* cond, const T* b, const T* rd, const T* xi, T* x, const T*
     if constexpr (!L0) {
         return post_launch<T, false, NU, false, false, S, PLAIN>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s,
                                                                  k16);
+    } else if constexpr (S::TX % 32 != 0 || S::TY % 16 != 0) {  // no whole alpha segments: no fused alpha
+        if (dot != 0) return false;
+        return post_launch<T, true, NU, false, false, S, PLAIN>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red, s,
+                                                                k16);
     } else {
         if (dot == 0)
             return post_launch<T, true, NU, false, false, S, PLAIN>(cond, b, rd, xi, x, xc, d, dc, B, st, hist, red,
@@ -532,7 +538,11 @@ bool post_shape(const T* cond, const T* b, const T* rd, const T* xi, T* x, const
     PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F2, false)      \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F2, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F3, false)      \
-    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F3, false)
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F3, false)     \
+    PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F4, false)      \
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F4, false)     \
+    PLSQR_MG2D_SHAPE_DECL(EXT, float, true, F5, false)      \
+    PLSQR_MG2D_SHAPE_DECL(EXT, double, true, F5, false)
 #define PLSQR_MG2D_ALT_COARSE(EXT)                          \
     PLSQR_MG2D_SHAPE_DECL(EXT, float, false, C1, false)     \
     PLSQR_MG2D_SHAPE_DECL(EXT, double, false, C1, false)    \

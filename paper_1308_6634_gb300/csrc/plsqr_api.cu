@@ -742,6 +742,9 @@ void autotune(plsqr_ctx* h, bool fresh = false) {
             for (int id = 0;; ++id) {
                 int tx, ty, nth;
                 if (!mg2d_shape(isk, id, &tx, &ty, &nth)) break;
+                // finest-level tiles narrower than 32 x 16 cannot carry the fused alpha (it would
+                // fall back to the default shape): candidates only when alpha is a separate kernel
+                if (isk && (tx % 32 != 0 || ty % 16 != 0) && h->cycles == 1) continue;
                 cudaGraph_t graph = nullptr;
                 cudaGraphExec_t exec = nullptr;
                 ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");

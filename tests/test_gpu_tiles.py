@@ -39,7 +39,7 @@ def _kappa_field(shape, seed=5):
     return O.diffusivity(f, "pm_log", 0.05)[0]
 
 N_COARSE = 6  # shapes 0..5 of the coarser levels
-N_FINE = 4    # shapes 0..3 of the finest level
+N_FINE = 6    # shapes 0..5 of the finest level
 
 
 @pytest.mark.parametrize("shape,levels,prec", [((1024, 1024), 6, "fp32"), ((136, 200), 4, "fp32"),

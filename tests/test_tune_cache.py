@@ -39,7 +39,7 @@ def test_json_round_trip():
     assert _entries(P) == before
 
 
-@pytest.mark.parametrize("bad", ["779 64 1 4 2 1 0 4",       # level 0 has shapes 0..3
+@pytest.mark.parametrize("bad", ["779 64 1 4 2 1 0 6",       # level 0 has shapes 0..5
                                  "779 64 1 4 2 0 0 6",       # coarser levels 0..5
                                  "779 64 1 2 2 0 0 1",       # element size 4 or 8
                                  "779 64 1 4 4 0 0 1",       # 1..3 sweeps
