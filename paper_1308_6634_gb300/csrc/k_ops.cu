@@ -73,7 +73,10 @@ __device__ __forceinline__ void finalize_beta(GkState& s, double tot) {
 
 constexpr int BTX = 64, BTY = 32, BNT = 256;
 
-template <typename T, int EPI, bool MASK_IN, bool MASK_OUT>
+// TX x TY output tiles with NT threads; launch_blur2d picks smaller tiles when the grid would
+// otherwise give few blocks (small double-precision images, where the blur is bound by the double
+// pipe of the SMs it occupies).
+template <typename T, int EPI, bool MASK_IN, bool MASK_OUT, int BTX = 64, int BTY = 32, int BNT = 256>
 __global__ void __launch_bounds__(BNT) k_blur2d(const T* __restrict__ in, T* out, const T* prev,
                                                 const uint8_t* __restrict__ mask, Dims d,
                                                 const T* __restrict__ wx, int Rx, const T* __restrict__ wy,
@@ -859,15 +862,33 @@ static void launch_blur2d(const OpDev& op, const T* in, T* out, const T* prev, i
             }
         }
     }
-    size_t smem = sizeof(T) * ((2 * Rx + 1) + (2 * Ry + 1) + (size_t)(BTX + 2 * Rx) * (BTY + 2 * Ry) +
-                               (size_t)(BTY + 2 * Ry) * BTX);
-    auto kfn = k_blur2d<T, EPI, MI, MO>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((d.nx + BTX - 1) / BTX, (d.ny + BTY - 1) / BTY, d.nz * B);
-    if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * d.nz > red.max_blocks)
-        throw std::runtime_error("blur2d: too many blocks for the reduction scratch");
-    launch_k(kfn, grid, dim3(BNT), smem, s, in, out, prev, (const uint8_t*)op.mask, d, (const T*)op.taps[0], Rx,
-             (const T*)op.taps[1], Ry, st, red);
+    // the largest of 64x32, 32x16, 16x16, 16x8 and 8x8 tiles that gives at least 152 blocks per
+    // instance (else 8x8); the choice depends on the grid only, not on the batch
+    auto blocks = [&](int tx, int ty) { return (int64_t)((d.nx + tx - 1) / tx) * ((d.ny + ty - 1) / ty) * d.nz; };
+    int pick = 4;
+    const int tiles[4][2] = {{64, 32}, {32, 16}, {16, 16}, {16, 8}};
+    for (int q = 0; q < 4; ++q)
+        if (blocks(tiles[q][0], tiles[q][1]) >= 152) {
+            pick = q;
+            break;
+        }
+    auto go = [&](auto kfn, int tx, int ty, int nt) {
+        size_t smem = sizeof(T) * ((2 * Rx + 1) + (2 * Ry + 1) + (size_t)(tx + 2 * Rx) * (ty + 2 * Ry) +
+                                   (size_t)(ty + 2 * Ry) * tx);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid((d.nx + tx - 1) / tx, (d.ny + ty - 1) / ty, d.nz * B);
+        if (EPI == EPI_FWD && (int64_t)grid.x * grid.y * d.nz > red.max_blocks)
+            throw std::runtime_error("blur2d: too many blocks for the reduction scratch");
+        launch_k(kfn, grid, dim3(nt), smem, s, in, out, prev, (const uint8_t*)op.mask, d, (const T*)op.taps[0], Rx,
+                 (const T*)op.taps[1], Ry, st, red);
+    };
+    switch (pick) {
+        case 0: go(k_blur2d<T, EPI, MI, MO, 64, 32, 256>, 64, 32, 256); break;
+        case 1: go(k_blur2d<T, EPI, MI, MO, 32, 16, 256>, 32, 16, 256); break;
+        case 2: go(k_blur2d<T, EPI, MI, MO, 16, 16, 256>, 16, 16, 256); break;
+        case 3: go(k_blur2d<T, EPI, MI, MO, 16, 8, 128>, 16, 8, 128); break;
+        default: go(k_blur2d<T, EPI, MI, MO, 8, 8, 64>, 8, 8, 64); break;
+    }
     klaunched("k_blur2d");
 }
 
