@@ -548,17 +548,18 @@ __global__ void __launch_bounds__(32 * NWI) k_gth_inverse_warp(const V* __restri
     }
 }
 
-// ---- the inverse in 32 x 32 blocks (bandwidth <= 32) --------------------------------------------
-// With L = I - N (N >= 0: the l of the factor) cut into 32 x 32 blocks, L is block lower
-// bidiagonal: N_ii strictly lower, N_{i,i-1} upper triangular (bandwidth <= 32).  Then
-//   W = L^{-1}:  W_jj = G_j = (I - N_jj)^{-1},  W_ij = P_i W_{i-1,j} with P_i = G_i N_{i,i-1} (i > j),
+// ---- the inverse in 32 x 32 blocks ---------------------------------------------------------------
+// With L = I - N (N >= 0: the l of the factor) cut into 32 x 32 blocks, L is block lower banded with
+// K = ceil(bw / 32) blocks below the diagonal: N_ii strictly lower, N_{i,i-k} (k = 1..K).  Then
+//   W = L^{-1}:  W_jj = G_j = (I - N_jj)^{-1},
+//                W_ij = sum_{k=1..min(K, i-j)} P_{i,k} W_{i-k,j} with P_{i,k} = G_i N_{i,i-k} (i > j),
 //   X = W^T D^{-1} W:  X_ab = sum_{i >= max(a,b)} W_ia^T D_i^{-1} W_ib.
 // Every quantity is a sum of products of non-negative numbers, as in the row-by-row kernels, so the
 // result keeps their componentwise accuracy; but the chains of dependent steps are 32 (G), nb (W)
 // and nb (X) block steps spread over many blocks instead of 2 nc row steps on one thread.  Only X_ab
 // with a <= b is formed (and the diagonal blocks' upper halves), and mirrored: X is exactly
-// symmetric.  Rows beyond nc are padding (N = 0, 1/d = 0).  Scratch per instance: G and P (2 nb
-// blocks) and W (nb (nb + 1) / 2 blocks, packed by block rows).
+// symmetric.  Rows beyond nc are padding (N = 0, 1/d = 0).  Scratch per instance: G and the P
+// ((1 + K) nb blocks) and W (nb (nb + 1) / 2 blocks, packed by block rows).
 constexpr int XB = 32;
 
 template <typename V>
@@ -566,17 +567,16 @@ __device__ __forceinline__ V tab_l(const V* gc, int BWP, int bw, int nc, int r, 
     return (r < nc && c >= 0 && r > c && r - c <= bw) ? gc[(int64_t)c * BWP + (r - c)] : (V)0;
 }
 
-// G_i and P_i of block row i (one block of 32 x 32 threads per block row and instance)
+// G_i and P_{i,1..K} of block row i (one block of 32 x 32 threads per block row and instance)
 template <typename V>
 __global__ void __launch_bounds__(1024) k_xblk_diag(const V* __restrict__ gcol_all, V* __restrict__ gp_all, int nc,
-                                                    int bw, int BWP, int nb, GkState* st) {
+                                                    int bw, int BWP, int nb, int K, GkState* st) {
     __shared__ V nd[XB][XB + 1], ns[XB][XB + 1], gs[XB][XB + 1];
     const int inst = blockIdx.y, i = blockIdx.x;
     if (parked(st[inst])) return;
     const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
     const V* gc = gcol_all + (int64_t)inst * nc * BWP;
     nd[r][c] = tab_l(gc, BWP, bw, nc, XB * i + r, XB * i + c);
-    ns[r][c] = i > 0 ? tab_l(gc, BWP, bw, nc, XB * i + r, XB * (i - 1) + c) : (V)0;
     __syncthreads();
     // column c of G by warp c (= r here): lane l holds g_l; when g_s is final the rows below it
     // receive N_ls g_s
@@ -590,12 +590,17 @@ __global__ void __launch_bounds__(1024) k_xblk_diag(const V* __restrict__ gcol_a
         gs[l][col] = g;
     }
     __syncthreads();
-    V* gp = gp_all + ((int64_t)inst * nb + i) * 2 * XB * XB;
+    V* gp = gp_all + ((int64_t)inst * nb + i) * (1 + K) * XB * XB;
     gp[r * XB + c] = gs[r][c];
-    V acc = (V)0;
+    for (int k = 1; k <= K; ++k) {
+        ns[r][c] = i - k >= 0 ? tab_l(gc, BWP, bw, nc, XB * i + r, XB * (i - k) + c) : (V)0;
+        __syncthreads();
+        V acc = (V)0;
 #pragma unroll 8
-    for (int m = 0; m < XB; ++m) acc = fma(gs[r][m], ns[m][c], acc);
-    gp[XB * XB + r * XB + c] = acc;
+        for (int m = 0; m < XB; ++m) acc = fma(gs[r][m], ns[m][c], acc);
+        gp[k * XB * XB + r * XB + c] = acc;
+        __syncthreads();
+    }
 }
 
 // 32 x 32 blocks in shared memory with a row stride of XS elements (pairs of a row 8- or 16-byte
@@ -621,23 +626,26 @@ __device__ __forceinline__ void tile_atb(const V (*sa)[XS], const V (*sb)[XS], i
     }
 }
 
-// W_jj .. W_{nb-1,j} of block column j: W_ij = P_i W_{i-1,j}.  256 threads, each a 2 x 2 tile;
-// P_i is staged transposed (pt[m][r] = P_i[r][m]) so that the product reads rows of both operands.
+// W_jj .. W_{nb-1,j} of block column j: W_ij = sum_k P_{i,k} W_{i-k,j}.  256 threads, each a 2 x 2
+// tile; the last K blocks of the column stay in a ring in shared memory (dynamic, K + 1 slots), and
+// each P_{i,k} is staged transposed (pt[m][r] = P[r][m]) so that the product reads rows of both.
 template <typename V>
 __global__ void __launch_bounds__(256) k_xblk_wchain(const V* __restrict__ gp_all, V* __restrict__ w_all, int nb,
-                                                     GkState* st) {
+                                                     int K, GkState* st) {
     using V2 = typename V2of<V>::type;
-    __shared__ __align__(16) V ws[2][XB][XS], pt[2][XB][XS];
+    extern __shared__ __align__(16) unsigned char wraw[];
+    V(*ws)[XB][XS] = reinterpret_cast<V(*)[XB][XS]>(wraw);  // K + 1 slots: W_{i,j} in slot (i - j) % (K + 1)
+    __shared__ __align__(16) V pt[2][XB][XS];
     const int inst = blockIdx.y, j = blockIdx.x;
     if (parked(st[inst])) return;
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
     const int r0 = 2 * ty, c0 = 2 * tx;
-    const V* gp = gp_all + (int64_t)inst * nb * 2 * XB * XB;
+    const int64_t PS = (int64_t)(1 + K) * XB * XB;  // G and P blocks of one block row
+    const V* gp = gp_all + (int64_t)inst * nb * PS;
     V* w = w_all + (int64_t)inst * (nb * (nb + 1) / 2) * XB * XB;
-    // this thread's four elements of a staged block: rows r0, r0+1, columns c0, c0+1
     auto ld2 = [&](const V* blk, int row) { return *reinterpret_cast<const V2*>(blk + row * XB + c0); };
     {
-        const V* g = gp + (int64_t)j * 2 * XB * XB;
+        const V* g = gp + (int64_t)j * PS;
         const V2 g0 = ld2(g, r0), g1 = ld2(g, r0 + 1);
         *reinterpret_cast<V2*>(&ws[0][r0][c0]) = g0;
         *reinterpret_cast<V2*>(&ws[0][r0 + 1][c0]) = g1;
@@ -645,29 +653,37 @@ __global__ void __launch_bounds__(256) k_xblk_wchain(const V* __restrict__ gp_al
         *reinterpret_cast<V2*>(wj + r0 * XB + c0) = g0;
         *reinterpret_cast<V2*>(wj + (r0 + 1) * XB + c0) = g1;
     }
-    V2 p0{}, p1{};
+    int use = 0;  // P blocks staged so far (alternating buffers)
+    V2 p0{}, p1{};  // the next P block to stage, loaded one product ahead
     if (j + 1 < nb) {
-        const V* pn = gp + (int64_t)(j + 1) * 2 * XB * XB + XB * XB;
-        p0 = ld2(pn, r0);
-        p1 = ld2(pn, r0 + 1);
+        p0 = ld2(gp + (int64_t)(j + 1) * PS + XB * XB, r0);
+        p1 = ld2(gp + (int64_t)(j + 1) * PS + XB * XB, r0 + 1);
     }
     for (int i = j + 1; i < nb; ++i) {
-        const int cur = (i - j - 1) & 1;
-        pt[cur][c0][r0] = p0.x;  // transposed: pt[m][r] = P[r][m]
-        pt[cur][c0 + 1][r0] = p0.y;
-        pt[cur][c0][r0 + 1] = p1.x;
-        pt[cur][c0 + 1][r0 + 1] = p1.y;
-        if (i + 1 < nb) {
-            const V* pn = gp + (int64_t)(i + 1) * 2 * XB * XB + XB * XB;
-            p0 = ld2(pn, r0);
-            p1 = ld2(pn, r0 + 1);
-        }
-        __syncthreads();
+        const int kmax = min(K, i - j);
         V acc[2][2] = {{(V)0, (V)0}, {(V)0, (V)0}};
-        tile_atb<V>(pt[cur], ws[cur], r0, c0, acc);
+        for (int k = 1; k <= kmax; ++k) {
+            const int cur = use++ & 1;
+            pt[cur][c0][r0] = p0.x;  // transposed: pt[m][r] = P[r][m]
+            pt[cur][c0 + 1][r0] = p0.y;
+            pt[cur][c0][r0 + 1] = p1.x;
+            pt[cur][c0 + 1][r0 + 1] = p1.y;
+            if (k < kmax) {
+                const V* pn = gp + (int64_t)i * PS + (int64_t)(k + 1) * XB * XB;
+                p0 = ld2(pn, r0);
+                p1 = ld2(pn, r0 + 1);
+            } else if (i + 1 < nb) {  // P_{i+1,1}
+                const V* pn = gp + (int64_t)(i + 1) * PS + XB * XB;
+                p0 = ld2(pn, r0);
+                p1 = ld2(pn, r0 + 1);
+            }
+            __syncthreads();
+            tile_atb<V>(pt[cur], ws[(i - k - j) % (K + 1)], r0, c0, acc);
+        }
         const V2 o0 = {acc[0][0], acc[0][1]}, o1 = {acc[1][0], acc[1][1]};
-        *reinterpret_cast<V2*>(&ws[cur ^ 1][r0][c0]) = o0;
-        *reinterpret_cast<V2*>(&ws[cur ^ 1][r0 + 1][c0]) = o1;
+        __syncthreads();  // every thread is done with the slot W_{i-K-1,j} held
+        *reinterpret_cast<V2*>(&ws[(i - j) % (K + 1)][r0][c0]) = o0;
+        *reinterpret_cast<V2*>(&ws[(i - j) % (K + 1)][r0 + 1][c0]) = o1;
         V* wi = w + ((int64_t)i * (i + 1) / 2 + j) * XB * XB;
         *reinterpret_cast<V2*>(wi + r0 * XB + c0) = o0;
         *reinterpret_cast<V2*>(wi + (r0 + 1) * XB + c0) = o1;
@@ -737,21 +753,24 @@ __global__ void __launch_bounds__(256) k_xblk_syrk(const V* __restrict__ w_all, 
 }
 
 int xblk_blocks(int nc) { return (nc + XB - 1) / XB; }
+int xblk_sub(int bw) { return std::max(1, (bw + XB - 1) / XB); }
 
 // scratch elements per instance of the blocked inverse
-int64_t xblk_scratch(int nc) {
-    const int64_t nb = xblk_blocks(nc);
-    return (2 * nb + nb * (nb + 1) / 2) * XB * XB;
+int64_t xblk_scratch(int nc, int bw) {
+    const int64_t nb = xblk_blocks(nc), K = xblk_sub(bw);
+    return ((1 + K) * nb + nb * (nb + 1) / 2) * XB * XB;
 }
 
 template <typename V>
 static void xblk_inverse(const V* gcol, V* X, V* scratch, int nc, int bw, int B, GkState* st, cudaStream_t s) {
-    const int BWP = gth_stride(bw), nb = xblk_blocks(nc);
+    const int BWP = gth_stride(bw), nb = xblk_blocks(nc), K = xblk_sub(bw);
     V* gp = scratch;
-    V* w = scratch + (int64_t)B * 2 * nb * XB * XB;
-    k_xblk_diag<V><<<dim3(nb, B), 1024, 0, s>>>(gcol, gp, nc, bw, BWP, nb, st);
+    V* w = scratch + (int64_t)B * (1 + K) * nb * XB * XB;
+    k_xblk_diag<V><<<dim3(nb, B), 1024, 0, s>>>(gcol, gp, nc, bw, BWP, nb, K, st);
     klaunched("k_xblk_diag");
-    k_xblk_wchain<V><<<dim3(nb, B), 256, 0, s>>>(gp, w, nb, st);
+    const size_t wsm = sizeof(V) * (size_t)(K + 1) * XB * XS;
+    if (wsm > 48 * 1024) cudaFuncSetAttribute(k_xblk_wchain<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+    k_xblk_wchain<V><<<dim3(nb, B), 256, wsm, s>>>(gp, w, nb, K, st);
     klaunched("k_xblk_wchain");
     k_xblk_syrk<V><<<dim3(nb * (nb + 1) / 2, B), 256, 0, s>>>(w, gcol, X, nc, BWP, nb, st);
     klaunched("k_xblk_syrk");
@@ -1111,7 +1130,8 @@ bool gth_wide_supported(int bw, int nc) {
     return bw > 0 && bw <= 32 * JT && (size_t)S * SW * sizeof(float) <= 200 * 1024 && nc > 0;
 }
 
-void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s) {
+void gth_wide_factor_inverse(float* gcol, float* grow, float* X, float* xscr, int nc, int bw, int B, GkState* st,
+                             cudaStream_t s) {
     if (!gth_wide_supported(bw, nc)) throw std::runtime_error("gth_wide_factor_inverse: bandwidth not supported");
     kbegin(KC_SETUP, s);
     const int BWP = gth_stride(bw);
@@ -1131,10 +1151,14 @@ void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw,
         k_ldl_gth_window<<<B, nt, smem, s>>>(gcol, grow, nc, bw, BWP, st);
         klaunched("k_ldl_gth_window");
     }
-    constexpr int NW = 4;
-    dim3 grid((unsigned)((nc + NW - 1) / NW), B);
-    k_gth_inverse_wide<NW><<<grid, 32 * NW, sizeof(float) * NW * (bw + 1), s>>>(gcol, grow, X, nc, bw, BWP, st);
-    klaunched("k_gth_inverse_wide");
+    if (xscr) {
+        xblk_inverse<float>(gcol, X, xscr, nc, bw, B, st, s);
+    } else {
+        constexpr int NW = 4;
+        dim3 grid((unsigned)((nc + NW - 1) / NW), B);
+        k_gth_inverse_wide<NW><<<grid, 32 * NW, sizeof(float) * NW * (bw + 1), s>>>(gcol, grow, X, nc, bw, BWP, st);
+        klaunched("k_gth_inverse_wide");
+    }
     kfinish(s);
 }
 

@@ -140,11 +140,12 @@ void gth_assemble(const T* cond, bool is_kappa, V* gcol, Dims d, int bw, int B, 
 // kernels.
 template <typename V>
 void gth_factor_inverse(V* gcol, V* grow, V* X, V* xscr, int nc, int bw, int B, GkState* st, cudaStream_t s);
-int64_t xblk_scratch(int nc);
+int64_t xblk_scratch(int nc, int bw);
 // Wide bands: the float L D L^T with a window of bw + 1 columns, and the float inverse with a warp
 // per column.
 bool gth_wide_supported(int bw, int nc);
-void gth_wide_factor_inverse(float* gcol, float* grow, float* X, int nc, int bw, int B, GkState* st, cudaStream_t s);
+void gth_wide_factor_inverse(float* gcol, float* grow, float* X, float* xscr, int nc, int bw, int B, GkState* st,
+                             cudaStream_t s);
 
 // ---- the whole 2D V-cycle in one cooperative launch ----
 constexpr int COOP_LEVELS = 8;

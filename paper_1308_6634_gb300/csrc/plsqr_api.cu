@@ -312,7 +312,7 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
         for (int l = 0; l + 1 < pl.L; ++l) b += esz * B * pl.level_N[l];  // reciprocal diagonals
     if (pl.gth || pl.gthw) {
         b += (pl.gth ? vsz : sizeof(float)) * B * (size_t)pl.nc * (2 * gth_stride(pl.bw) + pl.nc);
-        if (pl.gth && xblk_enabled((int)B)) b += vsz * B * (size_t)xblk_scratch(pl.nc);
+        if (xblk_enabled((int)B)) b += (pl.gth ? vsz : sizeof(float)) * B * (size_t)xblk_scratch(pl.nc, pl.bw);
     } else {
         b += sizeof(double) * B * (size_t)pl.nc * (pl.bw + 2);
         b += (sizeof(double) + (c->precision == PLSQR_FP64 ? 0 : sizeof(float))) * B * (size_t)pl.nc * pl.nc;
@@ -508,7 +508,8 @@ void prec_setup(plsqr_ctx* h, int B, cudaStream_t s) {
     }
     if (h->gthw) {
         gth_assemble<T, float>(cc, lc == 0, P<float>(h->gcol), h->lv[lc].d, h->bw, B, s);
-        gth_wide_factor_inverse(P<float>(h->gcol), P<float>(h->grow), h->Xf, h->nc, h->bw, B, h->st, s);
+        gth_wide_factor_inverse(P<float>(h->gcol), P<float>(h->grow), h->Xf, P<float>(h->xblk), h->nc, h->bw, B,
+                                h->st, s);
         return;
     }
     coarse_assemble<T>(cc, lc == 0, h->band, h->lv[lc].d, h->bw, B, s);
@@ -1171,7 +1172,7 @@ int plsqr_create(const plsqr_config* cfg, void* stream, plsqr_handle* out) {
         if (h->gth || h->gthw) {  // tables in the handle's type (the wide route: float only)
             const size_t vsz = h->gth ? h->esz : sizeof(float);
             h->gcol = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
-            if (h->gth && xblk_enabled(B)) h->xblk = dalloc(h, vsz * B * (size_t)xblk_scratch(h->nc));
+            if (xblk_enabled(B)) h->xblk = dalloc(h, vsz * B * (size_t)xblk_scratch(h->nc, h->bw));
             h->grow = dalloc(h, vsz * B * (size_t)h->nc * gth_stride(h->bw));
             if (h->fp64) h->X = (double*)dalloc(h, sizeof(double) * B * (size_t)h->nc * h->nc);
         } else {

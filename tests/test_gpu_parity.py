@@ -302,6 +302,25 @@ def test_blocked_coarse_inverse_matches_row_by_row(prec, shape, levels, monkeypa
     assert rel(outs[0], O.Multigrid(kappa, levels, 2, 1).apply(b)) < (1e-11 if prec == "fp64" else 1e-4)
 
 
+@pytest.mark.parametrize("shape,levels", [((8, 8, 8), 1), ((12, 12, 12), 1), ((6, 10, 14), 1), ((48, 48, 48), 3),
+                                          ((20, 12, 36), 2)])
+def test_blocked_wide_coarse_inverse_matches_row_by_row(shape, levels, monkeypatch):
+    """3D coarse grids (bands 64 to 144, two to five 32 x 32 blocks below the diagonal of L): the
+    blocked inverse against the warp-per-column kernel of the wide route, and both against the
+    oracle."""
+    kappa = _kappa_field(shape)
+    b = np.random.default_rng(20).standard_normal(shape)
+    outs = []
+    for blocked in ("1", "0"):
+        monkeypatch.setenv("PLSQR_GTH_BLOCKED", blocked)
+        S = _P().Solver(shape, "fp32", levels=levels)
+        S.prec_setup(dev(kappa, "fp32"))
+        outs.append(host(S.prec_apply(dev(b, "fp32"))))
+    assert np.all(np.isfinite(outs[0]))
+    assert rel(outs[0], outs[1]) < 2e-6
+    assert rel(outs[0], O.Multigrid(kappa, levels, 2, 1).apply(b)) < 1e-4
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nu", [1, 2, 3])
 def test_fused_vcycle_matches_one_launch_per_half_sweep(prec, nu, monkeypatch):
