@@ -238,13 +238,18 @@ int plsqr_selftest_wait(int32_t complete, int32_t* status_out);
  *
  * plsqr_autotune: tune now (fresh != 0: measure again instead of using the cache).  Uses the
  *   handle's scratch buffers: not while slots are in use (PLSQR_E_STATE).
- * plsqr_set_tile_shape: level 0 .. mg_levels-2 takes shape `shape` (0 is the default; level 0 has
- *   its own list); marks the handle as tuned, and keeps the shapes when plsqr_set_kappa_bf16 later
- *   changes the kappa storage (which otherwise makes the next solve tune again).  PLSQR_E_INVALID
- *   for an unknown level or shape.
- * plsqr_tile_shape: the shape of a level (-1 and zero extents where the level is not run by the
- *   tiled 2D kernels: 3D handles, the coarsest level), its tile extents and threads per block.
- *   Any output pointer may be NULL. */
+ * 3D handles run each red-black half sweep as its own launch, one thread per cell row position;
+ * there the tuned "shape" is the number of planes each thread takes (1, 2 or 4: the loads of
+ * several planes in flight together), timed and cached the same way (per level extents, batch and
+ * element size); the result does not depend on it.
+ *
+ * plsqr_set_tile_shape: level 0 .. mg_levels-2 takes shape `shape` (2D: 0 is the default, level 0
+ *   has its own list; 3D: 1, 2 or 4 planes per thread); marks the handle as tuned, and keeps the
+ *   shapes when plsqr_set_kappa_bf16 later changes the kappa storage (which otherwise makes the next
+ *   solve tune again).  PLSQR_E_INVALID for an unknown level or shape.
+ * plsqr_tile_shape: the shape of a level, its tile extents and threads per block (3D: the planes
+ *   per thread as the shape, extents 1 x planes, 256 threads); -1 and zero extents for the coarsest
+ *   level and for the one-launch-per-half-sweep 2D comparison path.  Any output pointer may be NULL. */
 /* The autotuner's choices are kept per process; these two calls move them between processes
  * (no GPU needed).  Text format, one entry per line, eight decimal integers:
  *     nx ny batch element_size sweeps finest kappa_bf16 shape

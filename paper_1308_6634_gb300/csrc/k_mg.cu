@@ -140,41 +140,59 @@ __device__ __forceinline__ void stencil(const T* __restrict__ c, const T* x, con
 // One red-black Gauss-Seidel half sweep: cells of `colour` get x = (b + off) * (1 / diag) (the
 // form of the temporally blocked kernels, which keep 1 / diag per cell).
 // zero_init: x is implicitly 0 (first half sweep of a level); the other colour is written 0.
-template <typename T, bool KAPPA, bool ZERO>
+// ZC: each thread takes the cell (h, y) of ZC consecutive planes (3D; the loads of several planes in
+// flight together); the arithmetic of a cell does not depend on ZC.
+template <typename T, bool KAPPA, bool ZERO, int ZC>
 __global__ void __launch_bounds__(256) k_gs_half(const T* __restrict__ cond, const T* __restrict__ b, T* x, Dims d,
                                                  int colour) {
     pdl_grid_sync();
     const int inst = blockIdx.y;
     const int hx = d.nx >> 1;
-    const int64_t Nh = d.N >> 1;
-    const int64_t h = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (h >= Nh) return;
-    const uint32_t rest = fdiv((uint32_t)h, d.fh), z = fdiv(rest, d.fy);
-    const int y = (int)(rest - z * (uint32_t)d.ny);
-    const int par = (y + (int)z + colour) & 1;
-    const int xx = 2 * (int)((uint32_t)h - rest * (uint32_t)hx) + par;
-    const int64_t i = xx + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+    const int nzc = (d.nz + ZC - 1) / ZC;
+    const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (t >= (int64_t)hx * d.ny * nzc) return;
+    const uint32_t rest = fdiv((uint32_t)t, d.fh), zc = fdiv(rest, d.fy);
+    const int y = (int)(rest - zc * (uint32_t)d.ny);
+    const int hh = (int)((uint32_t)t - rest * (uint32_t)hx);
     const T* c = cond + (KAPPA ? (int64_t)inst * d.N : (int64_t)inst * d.ndim * d.N);
     const T* bi = b + (int64_t)inst * d.N;
     T* xi = x + (int64_t)inst * d.N;
-    T diag, off;
-    stencil<T, KAPPA, !ZERO>(c, xi, d, i, xx, y, z, diag, off);
-    xi[i] = (bi[i] + off) * ((T)1 / diag);
-    if (ZERO) xi[i + (par ? -1 : 1)] = (T)0;
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int z = (int)zc * ZC + k;
+        if (z < d.nz) {
+            const int par = (y + z + colour) & 1;
+            const int xx = 2 * hh + par;
+            const int64_t i = xx + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+            T diag, off;
+            stencil<T, KAPPA, !ZERO>(c, xi, d, i, xx, y, z, diag, off);
+            xi[i] = (bi[i] + off) * ((T)1 / diag);
+            if (ZERO) xi[i + (par ? -1 : 1)] = (T)0;
+        }
+    }
 }
 
 template <typename T>
 void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colour, bool zero_init, int B,
-                cudaStream_t s) {
+                cudaStream_t s, int zc) {
     kbegin(is_kappa ? KC_GS_FINE : KC_MG_OTHER, s);
-    dim3 grid((unsigned)((d.N / 2 + 255) / 256), B);
-    if (is_kappa) {
-        if (zero_init) launch_k(k_gs_half<T, true, true>, grid, dim3(256), 0, s, cond, b, x, d, colour);
-        else launch_k(k_gs_half<T, true, false>, grid, dim3(256), 0, s, cond, b, x, d, colour);
-    } else {
-        if (zero_init) launch_k(k_gs_half<T, false, true>, grid, dim3(256), 0, s, cond, b, x, d, colour);
-        else launch_k(k_gs_half<T, false, false>, grid, dim3(256), 0, s, cond, b, x, d, colour);
+    if (zc != 2 && zc != 4) zc = 1;
+    const int64_t threads = (int64_t)(d.nx / 2) * d.ny * ((d.nz + zc - 1) / zc);
+    dim3 grid((unsigned)((threads + 255) / 256), B);
+#define GS_HALF(K, Z, C) launch_k(k_gs_half<T, K, Z, C>, grid, dim3(256), 0, s, cond, b, x, d, colour)
+#define GS_HALF_ZC(K, Z)                \
+    switch (zc) {                       \
+        case 2: GS_HALF(K, Z, 2); break; \
+        case 4: GS_HALF(K, Z, 4); break; \
+        default: GS_HALF(K, Z, 1); break; \
     }
+    if (is_kappa) {
+        if (zero_init) GS_HALF_ZC(true, true) else GS_HALF_ZC(true, false)
+    } else {
+        if (zero_init) GS_HALF_ZC(false, true) else GS_HALF_ZC(false, false)
+    }
+#undef GS_HALF_ZC
+#undef GS_HALF
     klaunched("k_gs_half");
     kfinish(s);
 }
@@ -937,7 +955,7 @@ void round_to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
                                  __nv_bfloat16*);                                                         \
     template void mg_coarsen<T>(const T*, bool, T*, Dims, Dims, int, cudaStream_t, const __nv_bfloat16*);  \
     template void mg_rdiag2d<T>(const T*, bool, T*, Dims, int, cudaStream_t, const __nv_bfloat16*);        \
-    template void mg_gs_half<T>(const T*, bool, const T*, T*, Dims, int, bool, int, cudaStream_t);         \
+    template void mg_gs_half<T>(const T*, bool, const T*, T*, Dims, int, bool, int, cudaStream_t, int);    \
     template void mg_resid_restrict<T>(const T*, bool, const T*, const T*, T*, Dims, Dims, int,            \
                                        cudaStream_t);                                                     \
     template void mg_prolong_add<T>(const T*, T*, Dims, Dims, int, cudaStream_t);                          \

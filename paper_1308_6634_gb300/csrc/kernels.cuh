@@ -99,7 +99,7 @@ void mg_rdiag2d(const T* cond, bool is_kappa, T* rd, Dims d, int B, cudaStream_t
 void to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
 template <typename T>
 void mg_gs_half(const T* cond, bool is_kappa, const T* b, T* x, Dims d, int colour, bool zero_init, int B,
-                cudaStream_t s);
+                cudaStream_t s, int zc = 1);  // zc: planes per thread (1, 2 or 4; 3D)
 template <typename T>
 void mg_resid_restrict(const T* cond, bool is_kappa, const T* b, const T* x, T* bc, Dims df, Dims dc, int B,
                        cudaStream_t s);

@@ -165,6 +165,7 @@ struct plsqr_ctx {
     bool coop_ok = false;           // supported for this handle (2D, nu = 2, TMA, levels, coarse size)
     unsigned* coop_sync = nullptr;  // grid barrier counters and abort flag (zero between launches)
     int tile[16] = {};        // tile shape of each 2D V-cycle level (mg2d_shape ids; 0 the default)
+    int zc3[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 3D: planes per thread of each level's half sweeps
     bool tuned = false;       // tile shapes chosen (autotuned or set)
     bool tiles_set = false;   // chosen by plsqr_set_tile_shape: kept when the kappa storage changes
     // stored Lanczos vectors of the running inner solve (plsqr_mlsqr_multi_tau): V_j, (alpha, beta)
@@ -399,16 +400,16 @@ void vcycle(plsqr_ctx* h, int l, const T* b, T* x, int B, cudaStream_t s) {
         return;
     }
     for (int k = 0; k < h->nu; ++k) {
-        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, k == 0, B, s);
-        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, k == 0, B, s, h->zc3[l]);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s, h->zc3[l]);
     }
     const Level& C = h->lv[l + 1];
     mg_resid_restrict<T>(cond, isk, b, x, P<T>(C.b), Lv.d, C.d, B, s);
     vcycle<T>(h, l + 1, P<T>(C.b), P<T>(C.x), B, s);
     mg_prolong_add<T>(P<T>(C.x), x, Lv.d, C.d, B, s);
     for (int k = 0; k < h->nu; ++k) {
-        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s);
-        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, false, B, s);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s, h->zc3[l]);
+        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, false, B, s, h->zc3[l]);
     }
 }
 
@@ -692,9 +693,107 @@ void choose_schedule(plsqr_ctx* h, GkState* st0, cudaEvent_t e0, cudaEvent_t e1,
     schedule_cache()[key] = cand[best];
 }
 
+// 3D levels: the planes per thread of the half sweeps (1, 2 or 4), timed like the 2D tile shapes
+// (a CUDA graph of 8 red-black sweeps per candidate on the level's own hierarchy, writing only its
+// V-cycle scratch) and cached per process by level extents, batch and element size.
+std::map<std::tuple<int, int, int, int, int>, int>& tune3_cache() {
+    static std::map<std::tuple<int, int, int, int, int>, int> m;
+    return m;
+}
+
+template <typename T>
+void autotune3(plsqr_ctx* h, bool fresh) {
+    const int B = h->B;
+    cudaStream_t s = h->stream;
+    Profiler* prev = current_profiler();
+    current_profiler() = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        current_profiler() = prev;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    try {
+        ck(cudaStreamSynchronize(h->user_stream), "autotune");
+        ck(cudaEventCreate(&e0), "cudaEventCreate");
+        ck(cudaEventCreate(&e1), "cudaEventCreate");
+        for (int l = 0; l + 1 < h->L; ++l) {
+            const Level& Lv = h->lv[l];
+            const bool isk = l == 0;
+            const auto key = std::make_tuple(Lv.d.nx, Lv.d.ny, Lv.d.nz, B, (int)h->esz);
+            if (!fresh) {
+                std::lock_guard<std::mutex> lk(tune_mutex());
+                auto it = tune3_cache().find(key);
+                if (it != tune3_cache().end()) {
+                    h->zc3[l] = it->second;
+                    continue;
+                }
+            }
+            const T* cond = isk ? P<T>(h->kappa) : P<T>(Lv.cond);
+            T* b = isk ? P<T>(h->p) : P<T>(Lv.b);
+            T* x = isk ? P<T>(h->tmp) : P<T>(Lv.x);
+            const int64_t n = (int64_t)B * Lv.d.N;
+            ck(cudaMemsetAsync(b, 0, sizeof(T) * n, s), "memset");
+            ck(cudaMemsetAsync(x, 0, sizeof(T) * n, s), "memset");
+            int best = 1;
+            float best_ms = 0.f;
+            const int cand[3] = {1, 2, 4};
+            for (int q = 0; q < 3; ++q) {
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+                try {
+                    for (int r = 0; r < 8; ++r) {
+                        mg_gs_half<T>(cond, isk, b, x, Lv.d, 0, false, B, s, cand[q]);
+                        mg_gs_half<T>(cond, isk, b, x, Lv.d, 1, false, B, s, cand[q]);
+                    }
+                } catch (...) {
+                    cudaStreamEndCapture(s, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                ck(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+                const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                ck(ie, "cudaGraphInstantiate");
+                float ms = 0.f;
+                cudaError_t e = cudaGraphLaunch(exec, s);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                cudaGraphExecDestroy(exec);
+                ck(e, "autotune");
+                const char* lg = std::getenv("PLSQR_TUNE_LOG");
+                if (lg && lg[0] == '1')
+                    std::fprintf(stderr, "plsqr planes level %d (%dx%dx%d) batch %d: %d per thread: %.2f us per sweep\n",
+                                 l, Lv.d.nx, Lv.d.ny, Lv.d.nz, B, cand[q], 1e3f * ms / 24.f);
+                if (q == 0 || ms < best_ms) {
+                    best = cand[q];
+                    best_ms = ms;
+                }
+            }
+            h->zc3[l] = best;
+            std::lock_guard<std::mutex> lk(tune_mutex());
+            tune3_cache()[key] = best;
+        }
+        ck(cudaStreamSynchronize(s), "autotune");
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
 template <typename T>
 void autotune(plsqr_ctx* h, bool fresh = false) {
     h->tuned = true;
+    if (h->d.ndim == 3 && !h->generic_mg && !h->split3 && h->L > 1) {
+        Range range("plsqr_autotune");
+        autotune3<T>(h, fresh);
+        return;
+    }
     if (!use_fused_mg(h) || !tma_enabled()) return;
     Range range("plsqr_autotune");
     const int B = h->B;
@@ -1401,6 +1500,14 @@ int plsqr_set_tile_shape(plsqr_handle h, int32_t level, int32_t shape) {
     return guarded(h, [&]() -> int {
         if (h->serving) throw std::logic_error("tile shapes cannot change while slots are in use");
         if (level < 0 || level >= h->L - 1) throw InvalidArg("level must be in 0..mg_levels-2");
+        if (h->d.ndim == 3) {  // planes per thread of the 3D half sweeps
+            if (shape != 1 && shape != 2 && shape != 4) throw InvalidArg("3D levels take 1, 2 or 4 planes per thread");
+            h->zc3[level] = shape;
+            h->tuned = true;
+            h->tiles_set = true;
+            clear_graphs(h);
+            return PLSQR_OK;
+        }
         int tx, ty, nth;
         if (shape < 0 || !mg2d_shape(level == 0, shape, &tx, &ty, &nth)) throw InvalidArg("no such tile shape");
         h->tile[level] = shape;
@@ -1416,9 +1523,16 @@ int plsqr_tile_shape(plsqr_handle h, int32_t level, int32_t* shape, int32_t* tx,
     return guarded(h, [&]() -> int {
         if (level < 0 || level >= 16) throw InvalidArg("bad level");
         const bool fused = use_fused_mg(h) && level < h->L - 1;
-        const int id = fused ? h->tile[level] : -1;
+        const bool planes = h->d.ndim == 3 && !h->generic_mg && !h->split3 && level < h->L - 1;
+        int id = fused ? h->tile[level] : -1;
         int v[3] = {0, 0, 0};
         if (fused) mg2d_shape(level == 0, id, &v[0], &v[1], &v[2]);
+        if (planes) {  // 3D: "shape" = planes per thread of the half sweeps (256 threads, one cell row each)
+            id = h->zc3[level];
+            v[0] = 1;
+            v[1] = h->zc3[level];
+            v[2] = 256;
+        }
         if (shape) *shape = id;
         if (tx) *tx = v[0];
         if (ty) *ty = v[1];

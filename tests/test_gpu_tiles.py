@@ -72,7 +72,36 @@ def test_tile_shape_queries_and_invalid_shapes():
         with pytest.raises(RuntimeError):
             S.set_tile_shape(lv, sh)
     S3 = _P().Solver((16, 16, 16), "fp32", levels=2)
-    assert S3.tile_shape(0)[0] == -1               # 3D levels are not tiled by the 2D kernels
+    assert S3.tile_shape(0) == (1, 1, 1, 256)      # 3D: one plane per thread before any tuning
+    S3.set_tile_shape(0, 4)
+    assert S3.tile_shape(0) == (4, 1, 4, 256)
+    for sh in (0, 3, 8):
+        with pytest.raises(RuntimeError):
+            S3.set_tile_shape(0, sh)
+    assert S3.tile_shape(1)[0] == -1               # the coarsest level is the exact solve
+
+
+@pytest.mark.parametrize("shape,levels,prec", [((40, 24, 56), 3, "fp32"), ((24, 24, 24), 4, "fp64"),
+                                               ((12, 20, 8), 2, "fp32")])
+def test_every_plane_count_gives_the_same_3d_vcycle(shape, levels, prec):
+    """The 3D half sweeps with 1, 2 or 4 planes per thread on every level (ragged last chunk of
+    planes included): the V-cycle is bit for bit the same."""
+    import oracle as O
+    from paper_1308_6634_gb300 import synth
+    rng = np.random.default_rng(23)
+    f = synth.phantom_ellipsoids(shape, 6, 5) + 0.01 * rng.standard_normal(shape)
+    kappa = O.diffusivity(f, "tv", 1e-2)[0]
+    b = rng.standard_normal(shape)
+    S = _P().Solver(shape, prec, levels=levels, cycles=2)
+    S.prec_setup(dev(kappa, prec))
+    for l in range(levels - 1):
+        S.set_tile_shape(l, 1)
+    ref = host(S.prec_apply(dev(b, prec)))
+    assert np.all(np.isfinite(ref))
+    for zc in (2, 4):
+        for l in range(levels - 1):
+            S.set_tile_shape(l, zc)
+        assert np.array_equal(host(S.prec_apply(dev(b, prec))), ref), zc
 
 
 def test_autotuned_solve_equals_default_shapes(monkeypatch):
