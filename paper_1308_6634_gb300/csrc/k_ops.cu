@@ -674,9 +674,9 @@ __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, 
 
 // Gather adjoint when every half-width is at most one bin (ds >= max(|cos|, |sin|)): the rays that
 // reach a pixel are the two bins around s_ij, floor(t) and floor(t) + 1, with weights
-// max(0, 1 - |k - t| / h).  Tiles of 16 (x) x 32 (y) pixels, two pixels per thread (rows y and
-// y + 16); per angle the tile's bin band (KB bins from k0) is staged in shared memory together
-// with (c1, c2, cdet - k0, 1/h) and the weight 1/h.
+// max(0, 1 - |k - t| / h).  Tiles of 16 (x) x JY (y) pixels, two pixels per thread (rows y and
+// y + JY/2); per angle the tile's bin band (KB bins from k0) is staged in shared memory, and
+// (c1, c2, cdet - k0, 1/h) and the weight 1/h are kept for every angle.
 constexpr int JAX = 16, JAY = 32;
 
 template <typename T>
@@ -684,10 +684,17 @@ struct __align__(4 * sizeof(T)) JosephAdjAngle {
     T c1, c2, off, ih;  // t - k0 = x c1 + y c2 + off; 1 / h
 };
 
-template <typename T, int EPI>
-__global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino, T* out,
-                                                     const JosephAngle<T>* __restrict__ tab, int n, int na, int nb,
-                                                     int KB, GkState* st) {
+// JY: tile height (JAX x JY pixels, JAX * JY / 2 threads, two pixels each).  The angles are taken
+// in chunks of JA_CH (their bin bands staged one chunk at a time), so that the shared memory of a
+// block stays small and every block of a launch is resident at once.  The per-pixel sums run over
+// the angles in order, whatever the chunking.
+constexpr int JA_CH = 128;
+
+template <typename T, int EPI, int JY>
+__global__ void __launch_bounds__(JAX * JY / 2) k_joseph_adj2(const T* __restrict__ sino, T* out,
+                                                              const JosephAngle<T>* __restrict__ tab, int n, int na,
+                                                              int nb, int KB, GkState* st) {
+    constexpr int NT = JAX * JY / 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     using T4 = JosephAdjAngle<T>;
     T4* sp = reinterpret_cast<T4*>(smraw);                 // (c1, c2, cdet - k0, 1/h)
@@ -697,10 +704,10 @@ __global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino,
     const int inst = blockIdx.z;
     if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
-    const int tj = blockIdx.x * JAX, ti = blockIdx.y * JAY;
+    const int tj = blockIdx.x * JAX, ti = blockIdx.y * JY;
     const T xa = (T)tj - cimg, xb = (T)min(tj + JAX - 1, n - 1) - cimg;
-    const T ya = (T)ti - cimg, yb = (T)min(ti + JAY - 1, n - 1) - cimg;
-    for (int a = threadIdx.x; a < na; a += 256) {
+    const T ya = (T)ti - cimg, yb = (T)min(ti + JY - 1, n - 1) - cimg;
+    for (int a = threadIdx.x; a < na; a += NT) {
         const JosephAngle<T> J = tab[a];
         const T tmin = fmin(xa * J.c1, xb * J.c1) + fmin(ya * J.c2, yb * J.c2) + cdet;
         const int k0 = (int)floor(tmin - J.hw) - 1;
@@ -713,39 +720,42 @@ __global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino,
         sp[a] = pv;
         sw[a] = J.wgt;
     }
-    __syncthreads();
     const T* sg = sino + (int64_t)inst * na * nb;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < na * KB; e += 256) {
-        const int a = e / KB, kk = e - a * KB;
-        const int k = sk0[a] + kk;
-        sbin[e] = (k >= 0 && k < nb) ? sg[(int64_t)a * nb + k] : (T)0;
-    }
-    __syncthreads();
-    const int j = tj + (threadIdx.x & (JAX - 1)), i0 = ti + (threadIdx.x / JAX), i1 = i0 + JAY / 2;
+    const int j = tj + (threadIdx.x & (JAX - 1)), i0 = ti + (threadIdx.x / JAX), i1 = i0 + JY / 2;
     // pixels beyond a ragged edge are evaluated at the edge (inside the staged band), not stored
     const T x = (T)min(j, n - 1) - cimg, y0 = (T)min(i0, n - 1) - cimg, y1 = (T)min(i1, n - 1) - cimg;
     T acc0 = (T)0, acc1 = (T)0;
-    for (int a = 0; a < na; ++a) {
-        const T4 pv = sp[a];
-        const T wa = sw[a];
-        const T* row = sbin + a * KB;
-        const T ux = fma(x, pv.c1, pv.off);
-        {
-            const T u = fma(y0, pv.c2, ux);  // t - k0
-            const T fu = floor(u);
-            const int q = (int)fu;
-            const T fr = u - fu;
-            const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
-            acc0 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+    for (int a0 = 0; a0 < na; a0 += JA_CH) {
+        const int a1 = min(na, a0 + JA_CH);
+        __syncthreads();  // the table is written (first chunk) / the previous chunk's bins are read
+#pragma unroll 4
+        for (int e = threadIdx.x; e < (a1 - a0) * KB; e += NT) {
+            const int a = a0 + e / KB, kk = e - (a - a0) * KB;
+            const int k = sk0[a] + kk;
+            sbin[e] = (k >= 0 && k < nb) ? sg[(int64_t)a * nb + k] : (T)0;
         }
-        {
-            const T u = fma(y1, pv.c2, ux);
-            const T fu = floor(u);
-            const int q = (int)fu;
-            const T fr = u - fu;
-            const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
-            acc1 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+        __syncthreads();
+        for (int a = a0; a < a1; ++a) {
+            const T4 pv = sp[a];
+            const T wa = sw[a];
+            const T* row = sbin + (a - a0) * KB;
+            const T ux = fma(x, pv.c1, pv.off);
+            {
+                const T u = fma(y0, pv.c2, ux);  // t - k0
+                const T fu = floor(u);
+                const int q = (int)fu;
+                const T fr = u - fu;
+                const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
+                acc0 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+            }
+            {
+                const T u = fma(y1, pv.c2, ux);
+                const T fu = floor(u);
+                const int q = (int)fu;
+                const T fr = u - fu;
+                const T w0 = fmax((T)0, (T)1 - fr * pv.ih), w1 = fmax((T)0, (T)1 - ((T)1 - fr) * pv.ih);
+                acc1 += (w0 * row[q] + w1 * row[q + 1]) * wa;
+            }
         }
     }
     T ca, cp;
@@ -754,9 +764,21 @@ __global__ void __launch_bounds__(256) k_joseph_adj2(const T* __restrict__ sino,
     if (j < n && i1 < n) epi_store<T, EPI>(acc1, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i1 * n + j);
 }
 
-// Bins a JAX x JAY tile can touch for one angle (two-tap kernel), and whether every half-width
+// Tile height of the two-tap adjoint: 16 rows (128 threads) when 32-row tiles would give fewer
+// than four blocks per SM, else 32 (measured on the 512^2 tomography apply: 87 -> 83 us at batch 1,
+// 1.88 -> 1.97 ms at batch 32 with 16 rows); PLSQR_JOSEPH_ROWS=16 or 32 forces one.
+static int joseph_adj_rows(int n, int B) {
+    if (const char* e = getenv("PLSQR_JOSEPH_ROWS")) {
+        const int r = atoi(e);
+        if (r == 16 || r == 32) return r;
+    }
+    const int64_t blocks32 = (int64_t)((n + JAX - 1) / JAX) * ((n + 31) / 32) * B;
+    return blocks32 < 4 * 152 ? 16 : 32;
+}
+
+// Bins a JAX x JY tile can touch for one angle (two-tap kernel), and whether every half-width
 // is at most one bin.
-static int joseph_tile_bins2(const OpDev& op, bool* two_tap) {
+static int joseph_tile_bins2(const OpDev& op, bool* two_tap, int JY = JAY) {
     const double ds = op.ds;
     double w = 0.0, hmax = 0.0;
     for (int a = 0; a < op.na; ++a) {
@@ -765,7 +787,7 @@ static int joseph_tile_bins2(const OpDev& op, bool* two_tap) {
         const bool rows = (4 * a < op.na) || (4 * a > 3 * op.na);
         const double hw = (rows ? c : sn) / ds;
         hmax = std::max(hmax, hw);
-        w = std::max(w, ((JAX - 1) * c + (JAY - 1) * sn) / ds + 2.0 * hw);
+        w = std::max(w, ((JAX - 1) * c + (JY - 1) * sn) / ds + 2.0 * hw);
     }
     *two_tap = hmax <= 1.0;
     return (int)std::ceil(w) + 4;
@@ -988,16 +1010,17 @@ static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const 
                 klaunched("k_joseph_fwd");
             } else {
                 bool two = false;
-                const int KB2 = joseph_tile_bins2(op, &two);
+                const int jy = joseph_adj_rows(n, B);
+                const int KB2 = joseph_tile_bins2(op, &two, jy);
                 const size_t head2 =
                     (sizeof(T) * 4 * op.na + sizeof(T) * op.na + sizeof(int) * op.na + 15) & ~(size_t)15;
-                const size_t smem2 = head2 + sizeof(T) * (size_t)op.na * KB2;
+                const size_t smem2 = head2 + sizeof(T) * (size_t)std::min(op.na, JA_CH) * KB2;
                 if (two && smem2 <= 227 * 1024) {
-                    auto kfn = k_joseph_adj2<T, EPI>;
+                    auto kfn = jy == 16 ? k_joseph_adj2<T, EPI, 16> : k_joseph_adj2<T, EPI, 32>;
                     if (smem2 > 48 * 1024)
                         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-                    dim3 grid((n + JAX - 1) / JAX, (n + JAY - 1) / JAY, B);
-                    kfn<<<grid, 256, smem2, s>>>(in, out, tab, n, op.na, op.nb, KB2, st);
+                    dim3 grid((n + JAX - 1) / JAX, (n + jy - 1) / jy, B);
+                    kfn<<<grid, JAX * jy / 2, smem2, s>>>(in, out, tab, n, op.na, op.nb, KB2, st);
                     klaunched("k_joseph_adj2");
                     return;
                 }

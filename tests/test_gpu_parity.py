@@ -110,6 +110,22 @@ def test_joseph(prec, n, na, nb, ds):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("rows", ["32", "16"])
+@pytest.mark.parametrize("n,na", [(96, 300), (40, 257), (70, 128)])
+def test_joseph_adjoint_angle_chunks(monkeypatch, prec, rows, n, na):
+    """The two-tap adjoint stages the bin bands of 128 angles at a time: angle counts of several
+    chunks with a ragged last one, tiles of 32 or 16 rows (PLSQR_JOSEPH_ROWS), ragged image edges."""
+    monkeypatch.setenv("PLSQR_JOSEPH_ROWS", rows)
+    rng = np.random.default_rng(31)
+    nb = int(np.ceil(n * 2 ** 0.5)) + 3
+    y = rng.standard_normal((na, nb))
+    S = _P().Solver((n, n), prec, levels=1)
+    S.set_operator("joseph", n_angles=na, n_bins=nb)
+    op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb)
+    assert rel(host(S.apply_At(dev(y, prec))), op.At(y)) < (1e-11 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("reg", ["tikhonov", "tv", "pm_log", "pm_exp"])
 @pytest.mark.parametrize("shape", [(48, 80), (12, 20, 28)])
 def test_diffusivity(prec, reg, shape):
