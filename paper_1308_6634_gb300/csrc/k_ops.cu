@@ -481,8 +481,12 @@ __global__ void __launch_bounds__(128) k_joseph_fwd(const T* __restrict__ img, c
 // Joseph forward projection, band-staged: one block per (angle, instance), a thread per ray
 // (bins tid, tid + 256, ...).  The image (img for rows-stepped angles, imgT for columns-stepped
 // ones) is streamed through shared memory in bands of QB rows with cp.async double buffering, and
-// every ray takes its samples of the band from shared memory, rows in increasing order, with the
-// interpolation written x0 + fr (x1 - x0).
+// every ray takes its samples of the band from shared memory, with the interpolation written
+// x0 + fr (x1 - x0).  A ray's samples are summed in two parts, the rows below n/2 and the rest,
+// each in increasing row order, and the parts are added.  One block takes both parts (H = 1), or,
+// when the (angle, instance) pairs are too few to fill the GPU, two blocks take one part each
+// (H = 2): the second to finish adds the two parts from the scratch `part` (its arrival counted in
+// `cnt`, which it resets).  The sums do not depend on H or QB, so neither does the result.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -493,18 +497,37 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 constexpr int JF_RAYS = 4;  // rays per thread (nb <= 1024)
 constexpr int JF_PAD = 4;   // zero elements on each side of a staged row
 
+// acc += the samples of rows lo..hi (in order) of a ray; rowp = the staged row lo
+template <typename T>
+__device__ __forceinline__ void joseph_march(T& acc, int lo, int hi, T u0, T a2, T cimg, const T* rowp, int pitch) {
+    T qc = (T)lo - cimg;  // q - cimg, exact
+#pragma unroll 4
+    for (int q = lo; q <= hi; ++q) {
+        const T u = u0 - qc * a2;
+        const T fl = floor(u);
+        const int j0 = (int)fl;
+        const T fr = u - fl;
+        const T x0 = rowp[j0], x1 = rowp[j0 + 1];
+        acc += x0 + fr * (x1 - x0);
+        qc += (T)1;
+        rowp += pitch;
+    }
+}
+
 template <typename T, int EPI>
-__global__ void __launch_bounds__(256) k_joseph_fwd_band(const T* __restrict__ img, const T* __restrict__ imgT,
+__global__ void __launch_bounds__(256, 5) k_joseph_fwd_band(const T* __restrict__ img, const T* __restrict__ imgT,
                                                          T* out, const T* prev,
                                                          const JosephAngle<T>* __restrict__ tab, int n, int na,
-                                                         int nb, T ds, int QB, GkState* st, Red red) {
+                                                         int nb, T ds, int QB, FDiv fvec, GkState* st, Red red,
+                                                         T* part, unsigned* cnt) {
     // band rows are stored with JF_PAD zero elements on each side (pitch n + 2 JF_PAD), so that the
     // samples just outside the image (u in (-4, n + 3) for the conservative row ranges below, as
     // |a2| <= 1) read zeros without a bounds test
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ unsigned s_last;
     T* sbuf = reinterpret_cast<T*>(smraw);  // two bands of QB x pitch
     const int pitch = n + 2 * JF_PAD;
-    const int inst = blockIdx.y, a = blockIdx.x;
+    const int inst = blockIdx.y, a = blockIdx.x, h = blockIdx.z, H = gridDim.z;
     if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const JosephAngle<T> J = tab[a];
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
@@ -513,12 +536,13 @@ __global__ void __launch_bounds__(256) k_joseph_fwd_band(const T* __restrict__ i
         const int r = i / (2 * JF_PAD), c = i - r * (2 * JF_PAD);
         sbuf[(size_t)r * pitch + (c < JF_PAD ? c : n + c)] = (T)0;
     }
-    T u0[JF_RAYS], acc[JF_RAYS];
+    T u0[JF_RAYS], acc[JF_RAYS], accA[JF_RAYS];
     int qlo[JF_RAYS], qhi[JF_RAYS];
 #pragma unroll
     for (int r = 0; r < JF_RAYS; ++r) {
         const int k = threadIdx.x + 256 * r;
         acc[r] = (T)0;
+        accA[r] = (T)0;
         qlo[r] = 0;
         qhi[r] = -1;
         u0[r] = (T)0;
@@ -536,64 +560,94 @@ __global__ void __launch_bounds__(256) k_joseph_fwd_band(const T* __restrict__ i
             }
         }
     }
-    const int nband = (n + QB - 1) / QB;
+    // bands: the rows [0, qs) of the first part in bands of QB from row 0, then the rows [qs, n)
+    // of the second part in bands of QB from row qs
+    const int qs = n / 2;
+    const int nbA = (qs + QB - 1) / QB, nbB = (n - qs + QB - 1) / QB;
+    const int b_lo = (H == 2 && h == 1) ? nbA : 0, b_hi = (H == 2 && h == 0) ? nbA : nbA + nbB;
+    auto row0 = [&](int b) { return b < nbA ? b * QB : qs + (b - nbA) * QB; };
+    auto row_end = [&](int b) { return b < nbA ? min(qs, (b + 1) * QB) : min(n, qs + (b - nbA + 1) * QB); };
     const int vec = n * (int)sizeof(T) / 16;  // 16-byte chunks per row
     auto stage = [&](int b) {
         T* dst = sbuf + (size_t)(b & 1) * QB * pitch + JF_PAD;
-        const int rows = min(QB, n - b * QB);
-        const T* src = im + (int64_t)b * QB * n;
+        const int q0 = row0(b), rows = row_end(b) - q0;
+        const T* src = im + (int64_t)q0 * n;
         for (int c = threadIdx.x; c < rows * vec; c += 256) {
-            const int r = c / vec, v = c - r * vec;
+            const int r = (int)fdiv((uint32_t)c, fvec), v = c - r * vec;
             cp_async16(reinterpret_cast<char*>(dst + (size_t)r * pitch) + 16 * v,
                        reinterpret_cast<const char*>(src + (int64_t)r * n) + 16 * v);
         }
         cp_async_commit();
     };
-    stage(0);
+    if (b_lo < b_hi) stage(b_lo);
     const T a2 = J.a2;
-    for (int b = 0; b < nband; ++b) {
-        if (b + 1 < nband) {
+    for (int b = b_lo; b < b_hi; ++b) {
+        if (b + 1 < b_hi) {
             stage(b + 1);
             cp_async_wait1();
         } else {
             cp_async_wait0();
         }
+        if (b == nbA && b_lo == 0) {  // the first part is complete (one block takes both)
+#pragma unroll
+            for (int r = 0; r < JF_RAYS; ++r) {
+                accA[r] = acc[r];
+                acc[r] = (T)0;
+            }
+        }
         __syncthreads();
         const T* band = sbuf + (size_t)(b & 1) * QB * pitch + JF_PAD;
-        const int q0 = b * QB, q1 = min(n, q0 + QB) - 1;
+        const int q0 = row0(b), q1 = row_end(b) - 1;
 #pragma unroll
         for (int r = 0; r < JF_RAYS; ++r) {
             const int lo = max(qlo[r], q0), hi = min(qhi[r], q1);
-            T qc = (T)lo - cimg;  // q - cimg, exact
-            const T* rowp = band + (size_t)(lo - q0) * pitch;
-#pragma unroll 4
-            for (int q = lo; q <= hi; ++q) {
-                const T u = u0[r] - qc * a2;
-                const T fl = floor(u);
-                const int j0 = (int)fl;
-                const T fr = u - fl;
-                const T x0 = rowp[j0], x1 = rowp[j0 + 1];
-                acc[r] += x0 + fr * (x1 - x0);
-                qc += (T)1;
-                rowp += pitch;
-            }
+            joseph_march<T>(acc[r], lo, hi, u0[r], a2, cimg, band + (ptrdiff_t)(lo - q0) * pitch, pitch);
         }
         __syncthreads();  // the buffer of band b is refilled with band b + 2
     }
+    if (H == 1) {
+#pragma unroll
+        for (int r = 0; r < JF_RAYS; ++r) acc[r] = accA[r] + acc[r];  // the loop passed band nbA (nbB >= 1)
+    } else {
+        T* pp = part + ((int64_t)h * gridDim.y + inst) * na * nb + (int64_t)a * nb;
+#pragma unroll
+        for (int r = 0; r < JF_RAYS; ++r) {
+            const int k = threadIdx.x + 256 * r;
+            if (k < nb) pp[k] = acc[r];
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned* c = cnt + (int64_t)inst * na + a;
+            const unsigned old = atomicAdd(c, 1u);
+            s_last = old == 1u;
+            if (old == 1u) *c = 0u;  // for the next launch
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const T* p0 = part + (int64_t)inst * na * nb + (int64_t)a * nb;
+        const T* p1 = p0 + (int64_t)gridDim.y * na * nb;
+#pragma unroll
+        for (int r = 0; r < JF_RAYS; ++r) {
+            const int k = threadIdx.x + 256 * r;
+            acc[r] = k < nb ? __ldcg(p0 + k) + __ldcg(p1 + k) : (T)0;
+        }
+    }
     T ca, cp;
     if (EPI != EPI_PLAIN) epi_coefs<T, EPI>(st[inst], ca, cp);
-    T part = (T)0;
+    T psum = (T)0;
 #pragma unroll
     for (int r = 0; r < JF_RAYS; ++r) {
         const int k = threadIdx.x + 256 * r;
         if (k < nb) {
             const T v = epi_store<T, EPI>(acc[r] * J.wgt, ca, cp, out, prev, (int64_t)inst * na * nb + (int64_t)a * nb + k);
-            if (EPI == EPI_FWD) part = fma(v, v, part);
+            if (EPI == EPI_FWD) psum = fma(v, v, psum);
         }
     }
     if (EPI == EPI_FWD) {
         double tot;
-        if (reduce_last<256>((double)part, red, inst, a, na, &tot)) finalize_beta(st[inst], tot);
+        if (reduce_last<256>((double)psum, red, inst, a, na, &tot)) finalize_beta(st[inst], tot);
     }
 }
 
@@ -674,8 +728,8 @@ __global__ void __launch_bounds__(256) k_joseph_adj(const T* __restrict__ sino, 
 
 // Gather adjoint when every half-width is at most one bin (ds >= max(|cos|, |sin|)): the rays that
 // reach a pixel are the two bins around s_ij, floor(t) and floor(t) + 1, with weights
-// max(0, 1 - |k - t| / h).  Tiles of 16 (x) x JY (y) pixels, two pixels per thread (rows y and
-// y + JY/2); per angle the tile's bin band (KB bins from k0) is staged in shared memory, and
+// max(0, 1 - |k - t| / h).  Tiles of 16 (x) x 32 (y) pixels, two pixels per thread (rows y and
+// y + 16); per angle the tile's bin band (KB bins from k0) is staged in shared memory, and
 // (c1, c2, cdet - k0, 1/h) and the weight 1/h are kept for every angle.
 constexpr int JAX = 16, JAY = 32;
 
@@ -684,17 +738,16 @@ struct __align__(4 * sizeof(T)) JosephAdjAngle {
     T c1, c2, off, ih;  // t - k0 = x c1 + y c2 + off; 1 / h
 };
 
-// JY: tile height (JAX x JY pixels, JAX * JY / 2 threads, two pixels each).  The angles are taken
-// in chunks of JA_CH (their bin bands staged one chunk at a time), so that the shared memory of a
-// block stays small and every block of a launch is resident at once.  The per-pixel sums run over
-// the angles in order, whatever the chunking.
+// The angles are taken in chunks of JA_CH (their bin bands staged one chunk at a time), so that
+// the shared memory of a block stays small and every block of a launch is resident at once.  The
+// per-pixel sums run over the angles in order, whatever the chunking.
 constexpr int JA_CH = 128;
 
-template <typename T, int EPI, int JY>
-__global__ void __launch_bounds__(JAX * JY / 2) k_joseph_adj2(const T* __restrict__ sino, T* out,
-                                                              const JosephAngle<T>* __restrict__ tab, int n, int na,
-                                                              int nb, int KB, GkState* st) {
-    constexpr int NT = JAX * JY / 2;
+template <typename T, int EPI>
+__global__ void __launch_bounds__(JAX * JAY / 2) k_joseph_adj2(const T* __restrict__ sino, T* out,
+                                                               const JosephAngle<T>* __restrict__ tab, int n, int na,
+                                                               int nb, int KB, GkState* st) {
+    constexpr int NT = JAX * JAY / 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     using T4 = JosephAdjAngle<T>;
     T4* sp = reinterpret_cast<T4*>(smraw);                 // (c1, c2, cdet - k0, 1/h)
@@ -704,9 +757,9 @@ __global__ void __launch_bounds__(JAX * JY / 2) k_joseph_adj2(const T* __restric
     const int inst = blockIdx.z;
     if (EPI != EPI_PLAIN && inner_off(st[inst])) return;
     const T cimg = (T)0.5 * (T)(n - 1), cdet = (T)0.5 * (T)(nb - 1);
-    const int tj = blockIdx.x * JAX, ti = blockIdx.y * JY;
+    const int tj = blockIdx.x * JAX, ti = blockIdx.y * JAY;
     const T xa = (T)tj - cimg, xb = (T)min(tj + JAX - 1, n - 1) - cimg;
-    const T ya = (T)ti - cimg, yb = (T)min(ti + JY - 1, n - 1) - cimg;
+    const T ya = (T)ti - cimg, yb = (T)min(ti + JAY - 1, n - 1) - cimg;
     for (int a = threadIdx.x; a < na; a += NT) {
         const JosephAngle<T> J = tab[a];
         const T tmin = fmin(xa * J.c1, xb * J.c1) + fmin(ya * J.c2, yb * J.c2) + cdet;
@@ -721,7 +774,7 @@ __global__ void __launch_bounds__(JAX * JY / 2) k_joseph_adj2(const T* __restric
         sw[a] = J.wgt;
     }
     const T* sg = sino + (int64_t)inst * na * nb;
-    const int j = tj + (threadIdx.x & (JAX - 1)), i0 = ti + (threadIdx.x / JAX), i1 = i0 + JY / 2;
+    const int j = tj + (threadIdx.x & (JAX - 1)), i0 = ti + (threadIdx.x / JAX), i1 = i0 + JAY / 2;
     // pixels beyond a ragged edge are evaluated at the edge (inside the staged band), not stored
     const T x = (T)min(j, n - 1) - cimg, y0 = (T)min(i0, n - 1) - cimg, y1 = (T)min(i1, n - 1) - cimg;
     T acc0 = (T)0, acc1 = (T)0;
@@ -764,21 +817,22 @@ __global__ void __launch_bounds__(JAX * JY / 2) k_joseph_adj2(const T* __restric
     if (j < n && i1 < n) epi_store<T, EPI>(acc1, ca, cp, out, out, (int64_t)inst * n * n + (int64_t)i1 * n + j);
 }
 
-// Tile height of the two-tap adjoint: 16 rows (128 threads) when 32-row tiles would give fewer
-// than four blocks per SM, else 32 (measured on the 512^2 tomography apply: 87 -> 83 us at batch 1,
-// 1.88 -> 1.97 ms at batch 32 with 16 rows); PLSQR_JOSEPH_ROWS=16 or 32 forces one.
-static int joseph_adj_rows(int n, int B) {
-    if (const char* e = getenv("PLSQR_JOSEPH_ROWS")) {
-        const int r = atoi(e);
-        if (r == 16 || r == 32) return r;
+// Blocks per (angle, instance) of the band-staged forward projection: 2 when the launch has fewer
+// than three (angle, instance) pairs per SM and the operator holds the scratch for B instances;
+// PLSQR_JOSEPH_PARTS=1 or 2 forces one (2 only within the scratch).
+static int joseph_fwd_parts(const OpDev& op, int B) {
+    const bool room = op.jpart && op.jcnt && B <= op.jcap;
+    if (const char* e = getenv("PLSQR_JOSEPH_PARTS")) {
+        const int p = atoi(e);
+        if (p == 1) return 1;
+        if (p == 2) return room ? 2 : 1;
     }
-    const int64_t blocks32 = (int64_t)((n + JAX - 1) / JAX) * ((n + 31) / 32) * B;
-    return blocks32 < 4 * 152 ? 16 : 32;
+    return room && (int64_t)op.na * B < 3 * 152 ? 2 : 1;
 }
 
-// Bins a JAX x JY tile can touch for one angle (two-tap kernel), and whether every half-width
+// Bins a JAX x JAY tile can touch for one angle (two-tap kernel), and whether every half-width
 // is at most one bin.
-static int joseph_tile_bins2(const OpDev& op, bool* two_tap, int JY = JAY) {
+static int joseph_tile_bins2(const OpDev& op, bool* two_tap) {
     const double ds = op.ds;
     double w = 0.0, hmax = 0.0;
     for (int a = 0; a < op.na; ++a) {
@@ -787,7 +841,7 @@ static int joseph_tile_bins2(const OpDev& op, bool* two_tap, int JY = JAY) {
         const bool rows = (4 * a < op.na) || (4 * a > 3 * op.na);
         const double hw = (rows ? c : sn) / ds;
         hmax = std::max(hmax, hw);
-        w = std::max(w, ((JAX - 1) * c + (JY - 1) * sn) / ds + 2.0 * hw);
+        w = std::max(w, ((JAX - 1) * c + (JAY - 1) * sn) / ds + 2.0 * hw);
     }
     *two_tap = hmax <= 1.0;
     return (int)std::ceil(w) + 4;
@@ -991,15 +1045,23 @@ static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const 
                 k_transpose<T><<<tg, 256, 0, s>>>(in, tmp, n);
                 klaunched("k_transpose");
                 // band-staged form: rows of 16-byte multiples, at most JF_RAYS * 256 bins
-                const int QB = std::max(1, std::min(64, (int)(32768 / ((size_t)n * sizeof(T)))));
+                int QB = std::max(1, std::min(64, (int)(32768 / ((size_t)n * sizeof(T)))));
                 if ((n * sizeof(T)) % 16 == 0 && op.nb <= JF_RAYS * 256 && !op_generic_joseph()) {
+                    const int H = joseph_fwd_parts(op, B);
+                    if (H == 2) {  // bands small enough that all 2 na B blocks are resident at once
+                        const int64_t per_sm = ((int64_t)2 * op.na * B + 151) / 152;
+                        const int64_t budget = 228 * 1024 / per_sm - 1024 - 128;
+                        const int64_t qb = budget / (2 * (int64_t)sizeof(T) * (n + 2 * JF_PAD));
+                        QB = (int)std::max<int64_t>(1, std::min<int64_t>(QB, qb));
+                    }
                     const size_t smem = 2 * sizeof(T) * (size_t)QB * (n + 2 * JF_PAD);
                     auto kfn = k_joseph_fwd_band<T, EPI>;
                     if (smem > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     if (EPI == EPI_FWD && op.na > red.max_blocks)
                         throw std::runtime_error("joseph_fwd: too many blocks for the reduction scratch");
-                    kfn<<<dim3(op.na, B), 256, smem, s>>>(in, tmp, out, prev, tab, n, op.na, op.nb, (T)op.ds, QB, st,
-                                                          red);
+                    const FDiv fvec = make_fdiv((int64_t)n * sizeof(T) / 16);
+                    kfn<<<dim3(op.na, B, H), 256, smem, s>>>(in, tmp, out, prev, tab, n, op.na, op.nb, (T)op.ds, QB,
+                                                             fvec, st, red, (T*)op.jpart, op.jcnt);
                     klaunched("k_joseph_fwd_band");
                     return;
                 }
@@ -1010,17 +1072,16 @@ static void apply_epi(const OpDev& op, bool adjoint, const T* in, T* out, const 
                 klaunched("k_joseph_fwd");
             } else {
                 bool two = false;
-                const int jy = joseph_adj_rows(n, B);
-                const int KB2 = joseph_tile_bins2(op, &two, jy);
+                const int KB2 = joseph_tile_bins2(op, &two);
                 const size_t head2 =
                     (sizeof(T) * 4 * op.na + sizeof(T) * op.na + sizeof(int) * op.na + 15) & ~(size_t)15;
                 const size_t smem2 = head2 + sizeof(T) * (size_t)std::min(op.na, JA_CH) * KB2;
                 if (two && smem2 <= 227 * 1024) {
-                    auto kfn = jy == 16 ? k_joseph_adj2<T, EPI, 16> : k_joseph_adj2<T, EPI, 32>;
+                    auto kfn = k_joseph_adj2<T, EPI>;
                     if (smem2 > 48 * 1024)
                         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-                    dim3 grid((n + JAX - 1) / JAX, (n + jy - 1) / jy, B);
-                    kfn<<<grid, JAX * jy / 2, smem2, s>>>(in, out, tab, n, op.na, op.nb, KB2, st);
+                    dim3 grid((n + JAX - 1) / JAX, (n + JAY - 1) / JAY, B);
+                    kfn<<<grid, JAX * JAY / 2, smem2, s>>>(in, out, tab, n, op.na, op.nb, KB2, st);
                     klaunched("k_joseph_adj2");
                     return;
                 }

@@ -67,6 +67,11 @@ struct OpDev {
     const void* jtab;    // JosephAngle<T>[n_angles]
     int na, nb;
     double ds;
+    // Joseph forward in two row parts per (angle, instance): scratch T[2][jcap][na][nb] for the
+    // parts and unsigned[jcap][na] arrival counters (zero between launches); null: one part
+    void* jpart;
+    unsigned* jcnt;
+    int jcap;
     // per-instance blur taps (2D single precision, no mask): [B][2][2R+1] (x then y), or null when
     // every instance uses taps[] (slots of a serving handle may each have their own width)
     const float* tapt;

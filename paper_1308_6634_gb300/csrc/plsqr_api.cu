@@ -111,6 +111,9 @@ struct plsqr_ctx {
     int64_t m = 0;
     void* taps[3] = {nullptr, nullptr, nullptr};
     void* jtab = nullptr;
+    void* jpart = nullptr;  // Joseph forward: the two row parts and their arrival counters
+    void* jcnt = nullptr;
+    int jcap = 0;
     uint8_t* mask = nullptr;
     // workspace
     char *g = nullptr, *f = nullptr, *u = nullptr, *p = nullptr, *v = nullptr, *w = nullptr;
@@ -322,6 +325,12 @@ Plan make_plan(const plsqr_config* c, int64_t m) {
     b += sizeof(double) * B * std::max<int64_t>(8192, (int64_t)((pl.d.ny + 15) / 16) * ((pl.d.nx + 31) / 32));
     pl.bytes = b;
     return pl;
+}
+
+// Instances (at most B) for which the Joseph forward may run in two row parts per (angle,
+// instance): those with n_angles x instances below 3 x 152.
+int joseph_parts_cap(int64_t B, int na) {
+    return na < 1 ? 0 : (int)std::min<int64_t>(B, (3 * 152 - 1) / na);
 }
 
 int64_t op_data_len(const plsqr_operator* op, const Dims& d) {
@@ -1359,6 +1368,18 @@ int plsqr_set_operator(plsqr_handle h, const plsqr_operator* op) {
             od.na = op->n_angles;
             od.nb = op->n_bins;
             od.ds = op->bin_spacing;
+            // the forward's two-part launches: instances with n_angles x B below 3 x 152
+            dfree(h, h->jpart);
+            dfree(h, h->jcnt);
+            h->jpart = h->jcnt = nullptr;
+            h->jcap = joseph_parts_cap(h->B, op->n_angles);
+            if (h->jcap > 0) {
+                h->jpart = dalloc(h, h->esz * 2 * h->jcap * (size_t)op->n_angles * op->n_bins);
+                h->jcnt = dalloc(h, sizeof(unsigned) * h->jcap * (size_t)op->n_angles);
+            }
+            od.jpart = h->jpart;
+            od.jcnt = static_cast<unsigned*>(h->jcnt);
+            od.jcap = h->jcap;
         }
         h->od = od;
         h->op = *op;
@@ -1942,7 +1963,13 @@ int64_t plsqr_workspace_bytes(const plsqr_config* cfg, const plsqr_operator* op)
     try {
         Plan pl = make_plan(cfg, 0);
         int64_t m = op_data_len(op, pl.d);
-        return (int64_t)make_plan(cfg, m).bytes;
+        int64_t bytes = (int64_t)make_plan(cfg, m).bytes;
+        if (op && op->kind == PLSQR_OP_JOSEPH) {
+            const int64_t cap = joseph_parts_cap(cfg->max_batch, op->n_angles);
+            const int64_t esz = cfg->precision == PLSQR_FP64 ? 8 : 4;
+            bytes += cap * (2 * esz * m + (int64_t)sizeof(unsigned) * op->n_angles);
+        }
+        return bytes;
     } catch (...) {
         return -1;
     }

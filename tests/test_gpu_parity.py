@@ -110,12 +110,10 @@ def test_joseph(prec, n, na, nb, ds):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("rows", ["32", "16"])
 @pytest.mark.parametrize("n,na", [(96, 300), (40, 257), (70, 128)])
-def test_joseph_adjoint_angle_chunks(monkeypatch, prec, rows, n, na):
+def test_joseph_adjoint_angle_chunks(prec, n, na):
     """The two-tap adjoint stages the bin bands of 128 angles at a time: angle counts of several
-    chunks with a ragged last one, tiles of 32 or 16 rows (PLSQR_JOSEPH_ROWS), ragged image edges."""
-    monkeypatch.setenv("PLSQR_JOSEPH_ROWS", rows)
+    chunks with a ragged last one, ragged image edges."""
     rng = np.random.default_rng(31)
     nb = int(np.ceil(n * 2 ** 0.5)) + 3
     y = rng.standard_normal((na, nb))
@@ -123,6 +121,51 @@ def test_joseph_adjoint_angle_chunks(monkeypatch, prec, rows, n, na):
     S.set_operator("joseph", n_angles=na, n_bins=nb)
     op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb)
     assert rel(host(S.apply_At(dev(y, prec))), op.At(y)) < (1e-11 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,na,nb", [(96, 300, 139), (64, 90, 93), (40, 45, 61), (36, 20, 1000)])
+def test_joseph_forward_in_two_parts(monkeypatch, prec, n, na, nb):
+    """The band-staged forward sums each ray over the rows below n/2 and the rest, then adds the
+    two: one block per (angle, instance) or two (PLSQR_JOSEPH_PARTS), the same result bit for bit
+    (bands of 64 rows that straddle n/2 or cover the image, up to 1000 bins), and both the
+    oracle's."""
+    rng = np.random.default_rng(32)
+    x = rng.uniform(0, 1, (n, n))
+    S = _P().Solver((n, n), prec, levels=1)
+    S.set_operator("joseph", n_angles=na, n_bins=nb)
+    op = O.Operator("joseph", (n, n), n_angles=na, n_bins=nb)
+    out = {}
+    for parts in ("1", "2", "2"):  # twice in two parts: the arrival counters are reset
+        monkeypatch.setenv("PLSQR_JOSEPH_PARTS", parts)
+        y = host(S.apply_A(dev(x, prec)))
+        assert rel(y, op.A(x)) < (1e-11 if prec == "fp64" else 2e-5)
+        if parts in out:
+            assert np.array_equal(y, out[parts])
+        out[parts] = y
+    assert np.array_equal(out["1"], out["2"])
+
+
+def test_tomography_batched_equals_single():
+    """Tomography instances solved together give the results they give alone, although the batch
+    changes the launch shape of the forward projection (two blocks per angle alone, one in the
+    batch of three)."""
+    W = synth.Workload("tb", "joseph", (64, 64), "fp32", "pm_exp", 2e-2, 0.0, 2, 8, levels=3, nu=2, cycles=1,
+                       n_angles=180, n_bins=93, phantom=dict(type="ellipses", count=6))
+    gs, singles = [], []
+    op = None
+    for seed in range(3):
+        op, g, _ = _problem(W, seed)
+        gs.append(g)
+    S = _solver_for(W, op, None, max_batch=3)
+    regs, Ts = ["pm_exp", "tv", "pm_log"], [2e-2, 3e-2, 5e-2]
+    for k in range(3):
+        f, info = S.solve(dev(gs[k], "fp32"), regs[k], Ts[k], 0.0, W.n_outer, W.n_inner)
+        singles.append((host(f), info))
+    fs, infos = S.solve_batch([dev(g, "fp32") for g in gs], regs, Ts, [0.0] * 3, W.n_outer, W.n_inner)
+    for k in range(3):
+        assert np.array_equal(host(fs[k]), singles[k][0])
+        assert np.array_equal(infos[k]["rbar_hist"], singles[k][1]["rbar_hist"])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
