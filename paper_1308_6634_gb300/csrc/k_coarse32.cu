@@ -1005,6 +1005,150 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_ahead(float* __restrict__ gcol
     }
 }
 
+// The same elimination with the window in registers (bandwidths 33 .. 158, M = ceil(bw / 32)).
+// Column c lives in slot c mod (bw + 2); slot sigma belongs to warp sigma mod 32 (its J =
+// ceil((bw + 2) / 32) slots per warp as registers j = sigma / 32), lane i holding the row offsets r = 32 m + i + 1
+// (m < M) and lane 0 also the excess (r = 0).  Step k: the warp holding column k + 1 applies
+// pivot k to it, sums it (the lanes, shuffle-down trees and group order of the pivot group of
+// k_ldl_gth_ahead, one group of 32 rows per warp there), forms 1/d_{k+1} and l_{.,k+1}, publishes
+// l and the column (the multipliers of the next step) in shared memory and loads column
+// k + 1 + bw + 2 into the freed registers (first updated two steps later); every warp applies
+// pivot k to its other columns k + tau (2 <= tau <= bw), each entry with the multiply-add of the
+// window kernels (those outside the band with l = 0: the entry is unchanged).  One block barrier
+// per step and no shared-memory window.  Bit for bit k_ldl_gth_ahead.
+template <int M>
+__device__ __forceinline__ void gth_reg_pivot(const float (&e)[M], float e0, int c, int nc, int bw, int BWP,
+                                              int lane, float* Ld, float* Ad, float* Sd, float* gc, float* gr) {
+    float part[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int r = 32 * m + lane + 1;
+        part[m] = (r <= bw ? e[m] : 0.f) + (m == 0 && lane == 0 ? e0 : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) part[m] += __shfl_down_sync(0xffffffffu, part[m], o);
+    }
+    float dk = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) dk += part[m];  // the group totals, in group order (lane 0)
+    dk = __shfl_sync(0xffffffffu, dk, 0);
+    const float rd = 1.0f / dk;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int r = 32 * m + lane + 1;
+        if (r <= bw) {
+            const float l = e[m] * rd;
+            Ld[r] = l;
+            Ad[r] = e[m];
+            gc[(int64_t)c * BWP + r] = l;
+            if (c + r < nc) gr[(int64_t)(c + r) * BWP + r] = l;
+        }
+    }
+    if (lane == 0) {
+        *Sd = e0;
+        gc[(int64_t)c * BWP] = rd;
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void gth_reg_load(float (&e)[M], float& e0, const float* gc, int c, int nc, int bw,
+                                             int BWP, int lane) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int r = 32 * m + lane + 1;
+        e[m] = (c < nc && r <= bw) ? gc[(int64_t)c * BWP + r] : 0.f;
+    }
+    e0 = (c < nc && lane == 0) ? gc[(int64_t)c * BWP] : 0.f;
+}
+
+template <int M, int J>
+__global__ void __launch_bounds__(1024, 1) k_ldl_gth_reg(float* __restrict__ gcol_all, float* __restrict__ grow_all,
+                                                         int nc, int bw, int BWP, GkState* st) {
+    // M = ceil(bw / 32) row groups, J = ceil((bw + 2) / 32) slots per warp
+    constexpr int LW = 64 * M + 2;
+    // l and the column of a pivot at t = 1 .. bw, zero beyond: a multiply-add of an entry outside
+    // pivot k's band (tau + r > bw) reads l = 0 and leaves the entry as it is, exactly
+    __shared__ float sL[2][LW], sA[2][LW];
+    __shared__ float sS[2];
+    const int S2 = bw + 2;
+    const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (parked(st[inst])) return;
+    float* gc = gcol_all + (int64_t)inst * nc * BWP;
+    float* gr = grow_all + (int64_t)inst * nc * BWP;
+    for (int e = tid; e < nc * BWP; e += blockDim.x)  // row layout: entries no pivot writes
+        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
+    for (int e = tid; e < 2 * LW; e += blockDim.x) {
+        (&sL[0][0])[e] = 0.f;
+        (&sA[0][0])[e] = 0.f;
+    }
+    float ent[J][M], ex[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {  // columns 0 .. bw + 1 in slots 0 .. bw + 1
+        const int sig = warp + 32 * j;
+        gth_reg_load<M>(ent[j], ex[j], gc, sig < S2 ? sig : nc, nc, bw, BWP, lane);
+    }
+    __syncthreads();
+    if (warp == 0) {  // pivot 0 (slot 0), then column bw + 2 enters the slot
+        gth_reg_pivot<M>(ent[0], ex[0], 0, nc, bw, BWP, lane, sL[0], sA[0], &sS[0], gc, gr);
+        gth_reg_load<M>(ent[0], ex[0], gc, S2, nc, bw, BWP, lane);
+    }
+    __syncthreads();
+    int kmod = 0;  // k mod S2
+    for (int k = 0; k < nc; ++k) {
+        const int b = k & 1;
+        const float* Lk = sL[b];
+        const float* Ak = sA[b];
+        const float sk = sS[b];
+        const int sn = kmod + 1 == S2 ? 0 : kmod + 1;  // slot of column k + 1
+        if (k + 1 < nc && (sn & 31) == warp) {
+            const int jp = sn >> 5;
+            float pe[M], pe0 = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) pe[m] = 0.f;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (j == jp) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        ent[j][m] = fmaf(Lk[32 * m + lane + 2], Ak[1], ent[j][m]);
+                        pe[m] = ent[j][m];
+                    }
+                    if (lane == 0) ex[j] = fmaf(Lk[1], sk, ex[j]);
+                    pe0 = ex[j];
+                }
+            }
+            gth_reg_pivot<M>(pe, pe0, k + 1, nc, bw, BWP, lane, sL[b ^ 1], sA[b ^ 1], &sS[b ^ 1], gc, gr);
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                if (j == jp) gth_reg_load<M>(ent[j], ex[j], gc, k + 1 + S2, nc, bw, BWP, lane);
+        }
+        const int tmax = min(bw, nc - 1 - k);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int sig = warp + 32 * j;
+            int tau = sig - kmod;
+            if (tau < 0) tau += S2;
+            if (sig < S2 && tau >= 2 && tau <= tmax) {  // the same in every lane
+                const float a = Ak[tau];
+                const float* lt = Lk + tau + lane + 1;  // row offset r = 32 m + lane + 1: l at tau + r
+#pragma unroll
+                for (int m = 0; m < M; ++m) ent[j][m] = fmaf(lt[32 * m], a, ent[j][m]);
+                if (lane == 0) ex[j] = fmaf(Lk[tau], sk, ex[j]);
+            }
+        }
+        kmod = sn;
+        __syncthreads();
+    }
+}
+
+// PLSQR_GTH_REG=0 keeps k_ldl_gth_ahead (comparisons)
+bool gth_reg_supported(int bw, int nc) {
+    const char* e = std::getenv("PLSQR_GTH_REG");
+    return !(e && e[0] == '0') && bw > 32 && bw <= 158 && nc > 0;  // M <= 5, J <= 5 (64 registers)
+}
+
 // PLSQR_GTH_AHEAD=0 keeps k_ldl_gth_window (comparisons)
 bool gth_ahead_supported(int bw, int nc) {
     const int S = bw + 1, SW = S | 1, GP = (bw + 31) / 32;
@@ -1139,7 +1283,15 @@ void gth_wide_factor_inverse(float* gcol, float* grow, float* X, float* xscr, in
     const size_t smem = sizeof(float) * (size_t)S * SW;
     const int nt0 = std::max(32, ((bw + 31) / 32) * 32);
     const int nt = nt0 * std::max(1, std::min(GTH_WQ, 1024 / nt0));
-    if (gth_ahead_supported(bw, nc)) {
+    if (gth_reg_supported(bw, nc)) {
+        const int M = (bw + 31) / 32, J = (bw + 2 + 31) / 32;
+        auto kfn = M == 2 ? (J == 2 ? k_ldl_gth_reg<2, 2> : k_ldl_gth_reg<2, 3>)
+                 : M == 3 ? (J == 3 ? k_ldl_gth_reg<3, 3> : k_ldl_gth_reg<3, 4>)
+                 : M == 4 ? (J == 4 ? k_ldl_gth_reg<4, 4> : k_ldl_gth_reg<4, 5>)
+                          : k_ldl_gth_reg<5, 5>;
+        kfn<<<B, 1024, 0, s>>>(gcol, grow, nc, bw, BWP, st);
+        klaunched("k_ldl_gth_reg");
+    } else if (gth_ahead_supported(bw, nc)) {
         const size_t smem2 = sizeof(float) * (size_t)(S + 1) * SW;
         if (smem2 > 48 * 1024)
             cudaFuncSetAttribute(k_ldl_gth_ahead, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);

@@ -231,21 +231,24 @@ def test_single_precision_coarse_solve(shape):
 
 
 @pytest.mark.parametrize("shape,levels", [((8, 8, 8), 1), ((12, 12, 12), 1), ((6, 10, 14), 1), ((48, 48, 48), 3),
-                                          ((20, 12, 36), 2)])
-def test_wide_factor_with_look_ahead_matches_windowed_factor(shape, levels, monkeypatch):
-    """The wide-band float factorisation with look-ahead (one group of warps runs the pivot chain
-    while the others apply the previous pivot) performs the sums and multiply-adds of the windowed
-    kernel (PLSQR_GTH_AHEAD=0) in the same order: the V-cycles agree bit for bit (bands 64 to 144)."""
+                                          ((20, 12, 36), 2), ((4, 5, 9), 1), ((5, 3, 11), 1), ((3, 12, 13), 1)])
+def test_wide_factor_routes_match_windowed_factor(shape, levels, monkeypatch):
+    """The wide-band float factorisations -- the window in registers (default), with look-ahead in
+    shared memory (PLSQR_GTH_REG=0) and the windowed kernel (and PLSQR_GTH_AHEAD=0) -- perform the
+    same sums and multiply-adds in the same order: the V-cycles agree bit for bit (bands 33 to
+    156, one to five row groups of 32)."""
     kappa = _kappa_field(shape)
     b = np.random.default_rng(18).standard_normal(shape)
     outs = []
-    for ahead in ("1", "0"):
+    for reg, ahead in (("1", "1"), ("0", "1"), ("0", "0")):
+        monkeypatch.setenv("PLSQR_GTH_REG", reg)
         monkeypatch.setenv("PLSQR_GTH_AHEAD", ahead)
         S = _P().Solver(shape, "fp32", levels=levels)
         S.prec_setup(dev(kappa, "fp32"))
         outs.append(host(S.prec_apply(dev(b, "fp32"))))
     assert np.all(np.isfinite(outs[0]))
     assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
 
 
 @pytest.mark.parametrize("shape,levels", [((256, 256), 4), ((48, 48, 48), 3)])
