@@ -315,123 +315,6 @@ __global__ void __launch_bounds__(32 * (1 + GTH_BULK)) k_ldl_gth_split(V* __rest
     }
 }
 
-// The narrow float factorisation (bandwidth <= 32) with the window in registers: NW warps, column c
-// in slot c mod S (S = bw + 2 + GTH_LEAD), slot sigma in warp sigma mod NW, lane i holding row
-// offset i + 1 of its columns and lane 0 also the excess.  Step k: the warp holding column k + 1
-// applies pivot k to it, stages it in shared memory and forms 1/d_{k+1} = rcp_rn(pivot_sum(.)) and
-// l as k_ldl_gth_split's pivot warp does, publishes l and the column (double-buffered by step
-// parity) and loads column k + 1 + S into the freed registers, GTH_LEAD + 2 steps before its first
-// update; every warp applies pivot k to its other columns, with l = 0 (the entry unchanged, exactly)
-// outside the pivot's band.  Each entry receives the multiply-adds of the split kernel in the same
-// order, so the factor is bit for bit its factor; the window in registers replaces the staged
-// instance and each step's loads of the pivot column by every bulk warp.
-constexpr int GTH_LEAD = 6;
-
-template <int NW, int BWP>
-__global__ void __launch_bounds__(32 * NW) k_ldl_gth_reg1(float* __restrict__ gcol_all, float* __restrict__ grow_all,
-                                                          int nc, int bw, GkState* st) {
-    constexpr int SMAX = 32 + 2 + GTH_LEAD;
-    constexpr int J = (SMAX + NW - 1) / NW;  // slots per warp
-    constexpr int LW = 2 * 32 + 2;           // l at t = 1 .. bw, zero up to t = 65
-    __shared__ float sL[2][LW], sA[2][LW];
-    __shared__ float sS[2];
-    __shared__ __align__(16) float colbuf[BWP];  // the next pivot's column: excess, rows 1 .. bw, zeros
-    const int S = bw + 2 + GTH_LEAD;
-    const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t = lane + 1;
-    if (parked(st[inst])) return;
-    float* gc = gcol_all + (int64_t)inst * nc * BWP;
-    float* gr = grow_all + (int64_t)inst * nc * BWP;
-    for (int e = tid; e < nc * BWP; e += 32 * NW)  // row layout: entries no pivot writes
-        if (e % BWP == 0 || e % BWP > bw || e / BWP < e % BWP) gr[e] = 0.f;
-    for (int e = tid; e < 2 * LW; e += 32 * NW) {
-        (&sL[0][0])[e] = 0.f;
-        (&sA[0][0])[e] = 0.f;
-    }
-    for (int e = tid; e < BWP; e += 32 * NW) colbuf[e] = 0.f;
-    auto load = [&](float& e, float& e0, int c) {
-        e = (c < nc && t <= bw) ? gc[(int64_t)c * BWP + t] : 0.f;
-        e0 = (c < nc && lane == 0) ? gc[(int64_t)c * BWP] : 0.f;
-    };
-    // column c (all earlier pivots applied) -> 1/d_c and l_{.,c}, published in buffer b
-    auto pivot = [&](float e, float e0, int c, int b) {
-        if (lane == 0) colbuf[0] = e0;
-        if (t < BWP) colbuf[t] = e;  // zero beyond bw
-        __syncwarp();
-        float cw[BWP];
-        load_row<BWP>(cw, colbuf);
-        const float rd = rcp_rn(pivot_sum<float, BWP>(cw));
-        if (t <= bw) {
-            const float l = e * rd;
-            sL[b][t] = l;
-            sA[b][t] = e;
-            gc[(int64_t)c * BWP + t] = l;
-            if (c + t < nc) gr[(int64_t)(c + t) * BWP + t] = l;
-        }
-        if (lane == 0) {
-            sS[b] = e0;
-            gc[(int64_t)c * BWP] = rd;
-        }
-        __syncwarp();
-    };
-    float ent[J], ex[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {  // columns 0 .. S - 1 in slots 0 .. S - 1
-        const int sig = warp + NW * j;
-        load(ent[j], ex[j], sig < S ? sig : nc);
-    }
-    __syncthreads();
-    if (warp == 0) {  // pivot 0 (slot 0), then column S enters the slot
-        pivot(ent[0], ex[0], 0, 0);
-        load(ent[0], ex[0], S);
-    }
-    __syncthreads();
-    int kmod = 0;  // k mod S
-    for (int k = 0; k < nc; ++k) {
-        const int b = k & 1;
-        const float* Lk = sL[b];
-        const float* Ak = sA[b];
-        const float sk = sS[b];
-        const int sn = kmod + 1 == S ? 0 : kmod + 1;  // slot of column k + 1
-        if (k + 1 < nc && sn % NW == warp) {
-            const int jp = sn / NW;
-            float pe = 0.f, pe0 = 0.f;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                if (j == jp) {
-                    ent[j] = fmaf(Lk[t + 1], Ak[1], ent[j]);
-                    if (lane == 0) ex[j] = fmaf(Lk[1], sk, ex[j]);
-                    pe = ent[j];
-                    pe0 = ex[j];
-                }
-            }
-            pivot(pe, pe0, k + 1, b ^ 1);
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                if (j == jp) load(ent[j], ex[j], k + 1 + S);
-        }
-        const int tmax = min(bw, nc - 1 - k);
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int sig = warp + NW * j;
-            int tau = sig - kmod;
-            if (tau < 0) tau += S;
-            if (sig < S && tau >= 2 && tau <= tmax) {  // the same in every lane
-                ent[j] = fmaf(Lk[tau + t], Ak[tau], ent[j]);
-                if (lane == 0) ex[j] = fmaf(Lk[tau], sk, ex[j]);
-            }
-        }
-        kmod = sn;
-        __syncthreads();
-    }
-}
-
-// PLSQR_GTH_REG=0 keeps k_ldl_gth_split (comparisons)
-bool gth_reg1_enabled() {
-    const char* e = std::getenv("PLSQR_GTH_REG");
-    return !(e && e[0] == '0');
-}
-
 // The inverse by one warp per column for double tables and batches up to 16; PLSQR_GTH_INV=thread
 // or =warp forces one (comparisons).  Measured at batch 1 on the GB300: with double tables (16-wide
 // band, 256 cells) the thread-per-column kernel runs its band of multiply-adds on the narrow
@@ -1462,13 +1345,7 @@ static void gth_launch(V* gcol, V* grow, V* X, V* xscr, int nc, int bw, int B, G
     const size_t sp = stage + sizeof(V) * BWP;
     bool done = false;
     if constexpr (sizeof(V) == 4) {
-        if (gth_reg1_enabled() && gth_split_enabled()) {
-            constexpr int BWPC = (BW + 1 + 3) & ~3;
-            if (BWP != BWPC) throw std::runtime_error("gth_launch: table stride");
-            k_ldl_gth_reg1<16, BWPC><<<B, 32 * 16, 0, s>>>((float*)gcol, (float*)grow, nc, bw, st);
-            klaunched("k_ldl_gth_reg1");
-            done = true;
-        } else if (!gth_split_enabled()) {
+        if (!gth_split_enabled()) {
             auto kp = k_ldl_gth_pipe<BW>;
             if (sp > 48 * 1024) cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
             kp<<<B, 32, sp, s>>>(gcol, grow, nc, bw, st);
