@@ -133,7 +133,10 @@ int plsqr_solve_batch(plsqr_handle h, int32_t count, const void* const* g, const
 
 void plsqr_destroy(plsqr_handle h);
 const char* plsqr_last_error(plsqr_handle h);
-/* Device bytes a handle with this config would allocate (for admission by memory). */
+/* Device bytes a handle with this config would allocate (for admission by memory).  op may be
+ * NULL (data length = image size).  With a Joseph operator this includes the forward projection's
+ * two-part scratch: for the first min(max_batch, floor(455 / n_angles)) instances, 2 x data length
+ * elements and one 4-byte arrival counter per angle.  Host only; -1 for an invalid config. */
 int64_t plsqr_workspace_bytes(const plsqr_config* cfg, const plsqr_operator* op);
 
 /* ---- single steps of the path (for parity tests and custom loops) ---------------------- */

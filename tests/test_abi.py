@@ -46,6 +46,28 @@ def test_workspace_bytes_and_invalid_configs_without_gpu():
     assert plsqr.plsqr_workspace_bytes(too_coarse) == -1
 
 
+@pytest.mark.parametrize("prec,esz", [("fp32", 4), ("fp64", 8)])
+def test_workspace_counts_the_joseph_forward_parts(prec, esz):
+    """A Joseph operator whose launches can split each angle over two blocks (n_angles x instances
+    below 3 x 152) adds the scratch of the two row parts (2 x data length per instance) and an
+    arrival counter per angle and instance; at 456 angles no instance qualifies.  The two operators
+    compared have the same data length, so the workspaces differ by exactly that scratch: 455
+    angles, one instance at max_batch 1 and still one at 4; 60 angles at max_batch 8, seven."""
+    from paper_1308_6634_gb300 import plsqr
+
+    def extra(max_batch, na_split, nb_split, na_whole, nb_whole):
+        assert na_split * nb_split == na_whole * nb_whole
+        c = plsqr.make_config((256, 256), prec, levels=4, max_batch=max_batch)
+        split = plsqr.plsqr_workspace_bytes(c, plsqr.make_operator("joseph", n_angles=na_split, n_bins=nb_split))
+        whole = plsqr.plsqr_workspace_bytes(c, plsqr.make_operator("joseph", n_angles=na_whole, n_bins=nb_whole))
+        assert split > 0 and whole > 0
+        return split - whole
+
+    assert extra(1, 455, 456, 456, 455) == 1 * (2 * esz * 455 * 456 + 4 * 455)
+    assert extra(4, 455, 456, 456, 455) == 1 * (2 * esz * 455 * 456 + 4 * 455)
+    assert extra(8, 60, 2280, 600, 228) == 7 * (2 * esz * 60 * 2280 + 4 * 60)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     """Without the built library every entry of the binding raises; nothing falls back to the
     oracle or to any other CPU path."""
