@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(1024) k_ldl_gth_ahead(float* __restrict__ gcol
 // pivot k to it, sums it (the lanes, shuffle-down trees and group order of the pivot group of
 // k_ldl_gth_ahead, one group of 32 rows per warp there), forms 1/d_{k+1} and l_{.,k+1}, publishes
 // l and the column (the multipliers of the next step) in shared memory and loads column
-// k + 1 + bw + 2 into the freed registers (first updated two steps later); every warp applies
+// k + 1 + bw + 2 for the freed slot (first updated two steps later); every warp applies
 // pivot k to its other columns k + tau (2 <= tau <= bw), each entry with the multiply-add of the
 // window kernels (those outside the band with l = 0: the entry is unchanged).  One block barrier
 // per step and no shared-memory window.  Bit for bit k_ldl_gth_ahead.
@@ -1095,6 +1095,13 @@ __global__ void __launch_bounds__(1024, 1) k_ldl_gth_reg(float* __restrict__ gco
         gth_reg_load<M>(ent[0], ex[0], gc, S2, nc, bw, BWP, lane);
     }
     __syncthreads();
+    // a column entering slot jpend: loaded into pf by the step that freed the slot and moved into
+    // the slot's registers at the start of the next step (the load has landed by then, and no
+    // instruction of the step that issued it waits for it)
+    float pf[M], pf0 = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) pf[m] = 0.f;
+    int jpend = -1;
     int kmod = 0;  // k mod S2
     for (int k = 0; k < nc; ++k) {
         const int b = k & 1;
@@ -1102,6 +1109,17 @@ __global__ void __launch_bounds__(1024, 1) k_ldl_gth_reg(float* __restrict__ gco
         const float* Ak = sA[b];
         const float sk = sS[b];
         const int sn = kmod + 1 == S2 ? 0 : kmod + 1;  // slot of column k + 1
+        if (jpend >= 0) {  // the same in every lane
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (j == jpend) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) ent[j][m] = pf[m];
+                    ex[j] = pf0;
+                }
+            }
+            jpend = -1;
+        }
         if (k + 1 < nc && (sn & 31) == warp) {
             const int jp = sn >> 5;
             float pe[M], pe0 = 0.f;
@@ -1120,9 +1138,8 @@ __global__ void __launch_bounds__(1024, 1) k_ldl_gth_reg(float* __restrict__ gco
                 }
             }
             gth_reg_pivot<M>(pe, pe0, k + 1, nc, bw, BWP, lane, sL[b ^ 1], sA[b ^ 1], &sS[b ^ 1], gc, gr);
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                if (j == jp) gth_reg_load<M>(ent[j], ex[j], gc, k + 1 + S2, nc, bw, BWP, lane);
+            gth_reg_load<M>(pf, pf0, gc, k + 1 + S2, nc, bw, BWP, lane);  // slot jp, first read at step k + 3
+            jpend = jp;
         }
         const int tmax = min(bw, nc - 1 - k);
 #pragma unroll
